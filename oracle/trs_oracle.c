@@ -1,0 +1,856 @@
+/*
+ * CPU oracle for dynamic tile / rectangular-slice (TRS) frame partitioning,
+ * "Quality-driven Dynamic VVC Frame Partitioning for efficient Parallel
+ * Processing" (Amestoy, Hamidouche, Bergeron, Menard, ICIP 2020).
+ *
+ * TEST INFRASTRUCTURE.  This file is the plain, slow reference that the CUDA
+ * library is checked against.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load it; the library never does.  It shares
+ * no code, header, table or constant with the CUDA path.
+ *
+ * Contents, each following the passage cited beside it:
+ *   oracle_texture      per-CTU luma sums S1 = sum p, S2 = sum p^2, N     (Sec. 2.2, Eq. 2)
+ *   oracle_time_q       Q16 fixed-point CTU times                          (Sec. 2.1, Eq. 1 input)
+ *   oracle_sat          summed-area table by its definition (direct sums)
+ *   oracle_search_enum  O1: every TRS configuration enumerated in canonical
+ *                       code order, evaluated by direct sums:
+ *                       step 1 T_min (Eq. 3), step 2 arg-min of Eq. 2 under
+ *                       Eq. 4, both under k*A_min > A_max (Sec. 2.3)
+ *   oracle_search_dp    O2: exact dynamic programme over the same space;
+ *                       equal to O1 by construction (checked by the tests)
+ *
+ * Readings of the paper used here (the paper is silent on these points):
+ *   - CTUs are 128x128 luma samples; edge CTUs are clipped to the frame.
+ *   - A partition has exactly n rectangular slices (one per thread, Sec. 2.1).
+ *     A slice is a run of complete CTU rows inside one tile (Sec. 1); tiles
+ *     form a grid on CTU lines; every tile holds >= 1 slice.
+ *   - "Area" in k*A_min > A_max counts luma samples; k = 3; strict '>'.
+ *     The rule applies to both search steps.
+ *   - Times are quantised to Q16: Tq = rint(t * 65536), t finite, 0 <= t < 65536.
+ *   - lambda_q = rint(lambda * 65536); Eq. 4 is tested as
+ *     T(P) * 65536 <= T_min * (65536 + lambda_q), inclusive.
+ *   - The quality term of a slice is the floor of its exact luma SSE,
+ *     S2 - ceil(S1^2 / N); Q(P) is the sum over slices.
+ *   - Ties on Q are broken by the smallest canonical code: the tile-row cut
+ *     bits top to bottom, then per tile column left to right its right edge
+ *     followed by the in-tile slice cut bits of its tiles top to bottom
+ *     ('0' < '1').
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef unsigned __int128 u128;
+
+#define OR_CTU 128
+#define OR_MAX_C 64
+#define OR_MAX_R 64
+#define OR_MAX_N 64
+#define OR_INF UINT64_MAX
+
+enum { OR_OK = 0, OR_EINVAL = 1, OR_ERANGE = 2, OR_EINFEASIBLE = 3, OR_ENOMEM = 4 };
+
+typedef struct {
+    int status;
+    int n;              /* number of rectangular slices */
+    int c;              /* tile columns */
+    int r;              /* tile rows */
+    uint64_t row_mask;  /* tile-row cuts: bit (y-1) set => tile boundary at CTU line y */
+    int x_edges[OR_MAX_C + 1];      /* tile column edges, x_edges[0]=0 .. x_edges[c]=C */
+    uint64_t band_cuts[OR_MAX_C];   /* per tile column: every horizontal slice boundary */
+    uint64_t t_min;     /* Eq. 3, Q16 */
+    uint64_t thr;       /* largest T(P) allowed by Eq. 4 */
+    uint64_t t;         /* T(P*) */
+    uint64_t q;         /* Q(P*) */
+    uint64_t n_candidates;   /* configurations enumerated (O1) */
+    uint64_t n_valid;        /* of those, passing the area rule (O1) */
+    uint64_t n_windows;      /* area windows examined (O2) */
+    double t_real, t_min_real, sse_real;
+} oracle_result;
+
+/* ------------------------------------------------------------------ */
+/* Frame geometry                                                      */
+
+typedef struct {
+    int W, H, C, R;
+    const uint64_t *S1, *S2, *N;   /* per CTU, row-major R x C */
+    const uint32_t *Tq;            /* per CTU, Q16 */
+} frame_t;
+
+static int ctu_w(const frame_t *f, int x) {
+    int e = (x + 1) * OR_CTU;
+    return (e <= f->W ? e : f->W) - x * OR_CTU;
+}
+static int ctu_h(const frame_t *f, int y) {
+    int e = (y + 1) * OR_CTU;
+    return (e <= f->H ? e : f->H) - y * OR_CTU;
+}
+
+/* Sums over the CTUs of rectangle [x0,x1) x [y0,y1), by direct loops. */
+typedef struct { uint64_t T, S1, S2, N; } rsum_t;
+
+static rsum_t rect_direct(const frame_t *f, int x0, int x1, int y0, int y1) {
+    rsum_t s = {0, 0, 0, 0};
+    for (int y = y0; y < y1; ++y)
+        for (int x = x0; x < x1; ++x) {
+            int i = y * f->C + x;
+            s.T += f->Tq[i];
+            s.S1 += f->S1[i];
+            s.S2 += f->S2[i];
+            s.N += f->N[i];
+        }
+    return s;
+}
+
+/* Floor of the exact SSE of a region: S2 - ceil(S1^2 / N)  (Eq. 2 summand). */
+static uint64_t sse_floor(uint64_t S1, uint64_t S2, uint64_t N) {
+    u128 sq = (u128)S1 * (u128)S1;
+    u128 c = (sq + (u128)(N - 1)) / (u128)N;
+    return S2 - (uint64_t)c;
+}
+
+static long double sse_exact(uint64_t S1, uint64_t S2, uint64_t N) {
+    return (long double)S2 - ((long double)S1 * (long double)S1) / (long double)N;
+}
+
+/* Memo of rectangle sums keyed by (x0,x1,y0,y1); each entry filled by rect_direct. */
+typedef struct {
+    const frame_t *f;
+    rsum_t *tab;
+    uint8_t *have;
+} memo_t;
+
+static size_t memo_idx(const frame_t *f, int x0, int x1, int y0, int y1) {
+    return (((size_t)x0 * (f->C + 1) + x1) * (f->R + 1) + y0) * (f->R + 1) + y1;
+}
+
+static int memo_init(memo_t *m, const frame_t *f) {
+    size_t n = (size_t)(f->C + 1) * (f->C + 1) * (f->R + 1) * (f->R + 1);
+    m->f = f;
+    m->tab = (rsum_t *)malloc(n * sizeof(rsum_t));
+    m->have = (uint8_t *)calloc(n, 1);
+    return (m->tab && m->have) ? 0 : -1;
+}
+static void memo_free(memo_t *m) {
+    free(m->tab);
+    free(m->have);
+}
+static rsum_t memo_get(memo_t *m, int x0, int x1, int y0, int y1) {
+    size_t i = memo_idx(m->f, x0, x1, y0, y1);
+    if (!m->have[i]) {
+        m->tab[i] = rect_direct(m->f, x0, x1, y0, y1);
+        m->have[i] = 1;
+    }
+    return m->tab[i];
+}
+
+/* ------------------------------------------------------------------ */
+/* a1: per-CTU texture statistics (Eq. 2 needs sum p and sum p^2 per RS) */
+
+int oracle_texture(const void *luma, int W, int H, size_t pitch, int bd,
+                   uint64_t *S1, uint64_t *S2, uint64_t *N, uint32_t *vmax) {
+    if (!luma || W <= 0 || H <= 0 || bd < 8 || bd > 12) return OR_EINVAL;
+    int bps = (bd == 8) ? 1 : 2;
+    if (pitch < (size_t)W * bps) return OR_EINVAL;
+    int C = (W + OR_CTU - 1) / OR_CTU, R = (H + OR_CTU - 1) / OR_CTU;
+    for (int i = 0; i < C * R; ++i) {
+        S1[i] = 0;
+        S2[i] = 0;
+        N[i] = 0;
+        vmax[i] = 0;
+    }
+    int bad = 0;
+    const uint8_t *base = (const uint8_t *)luma;
+    for (int y = 0; y < H; ++y) {
+        const uint8_t *row = base + (size_t)y * pitch;
+        for (int x = 0; x < W; ++x) {
+            uint32_t p;
+            if (bps == 1) {
+                p = row[x];
+            } else {
+                p = (uint32_t)row[2 * x] | ((uint32_t)row[2 * x + 1] << 8); /* little endian */
+            }
+            int i = (y / OR_CTU) * C + (x / OR_CTU);
+            S1[i] += p;
+            S2[i] += (uint64_t)p * p;
+            N[i] += 1;
+            if (p > vmax[i]) vmax[i] = p;
+            if (p >> bd) bad = 1;
+        }
+    }
+    return bad ? OR_ERANGE : OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* a2 inputs: Q16 CTU times (estimator values of Sec. 2.1)             */
+
+int oracle_time_q(const float *t, int count, uint32_t *Tq) {
+    int bad = 0;
+    for (int i = 0; i < count; ++i) {
+        double v = (double)t[i];
+        if (!(v >= 0.0) || !(v < 65536.0)) {
+            Tq[i] = 0;
+            bad = 1;
+            continue;
+        }
+        Tq[i] = (uint32_t)rint(v * 65536.0);
+    }
+    return bad ? OR_ERANGE : OR_OK;
+}
+
+uint32_t oracle_lambda_q(float lambda) { return (uint32_t)rint((double)lambda * 65536.0); }
+
+/* Summed-area table by definition: sat[y][x] = sum of v over [0,x) x [0,y). */
+void oracle_sat(const uint64_t *v, int C, int R, uint64_t *sat) {
+    for (int y = 0; y <= R; ++y)
+        for (int x = 0; x <= C; ++x) {
+            uint64_t s = 0;
+            for (int yy = 0; yy < y; ++yy)
+                for (int xx = 0; xx < x; ++xx) s += v[yy * C + xx];
+            sat[y * (C + 1) + x] = s;
+        }
+}
+
+/* ------------------------------------------------------------------ */
+/* Shared pieces of both searches                                       */
+
+static int check_inputs(int W, int H, int n, int k_area) {
+    if (W <= 0 || H <= 0 || n < 1 || n > OR_MAX_N || k_area < 1) return OR_EINVAL;
+    int C = (W + OR_CTU - 1) / OR_CTU, R = (H + OR_CTU - 1) / OR_CTU;
+    if (C > OR_MAX_C || R > OR_MAX_R) return OR_EINVAL;
+    return OR_OK;
+}
+
+/* Eq. 4 bound as the largest integer T with T*65536 <= T_min*(65536+lambda_q). */
+static uint64_t eq4_thr(uint64_t t_min, uint32_t lambda_q) {
+    u128 v = (u128)t_min * (u128)(65536u + (u128)lambda_q);
+    u128 q = v / 65536u;
+    return q > (u128)UINT64_MAX ? UINT64_MAX : (uint64_t)q;
+}
+
+static void fill_reporting(const frame_t *f, memo_t *m, oracle_result *res) {
+    long double sse = 0.0L;
+    for (int b = 0; b < res->c; ++b) {
+        int y0 = 0;
+        for (int y = 1; y <= f->R; ++y) {
+            if (y == f->R || ((res->band_cuts[b] >> (y - 1)) & 1u)) {
+                rsum_t s = memo_get(m, res->x_edges[b], res->x_edges[b + 1], y0, y);
+                sse += sse_exact(s.S1, s.S2, s.N);
+                y0 = y;
+            }
+        }
+    }
+    res->sse_real = (double)sse;
+    res->t_real = (double)res->t / 65536.0;
+    res->t_min_real = (double)res->t_min / 65536.0;
+}
+
+/* ------------------------------------------------------------------ */
+/* O1: plain enumeration of every TRS configuration in code order       */
+
+typedef struct {
+    const frame_t *f;
+    memo_t *memo;
+    int n, k_area, area_rule, pass;
+    uint64_t row_mask;           /* current tile-row cut lines */
+    int r;                       /* tile rows */
+    int free_lines[OR_MAX_R];    /* CTU lines (1..R-1) that are not tile-row cuts, top to bottom */
+    int n_free;
+    int nb;                      /* bands chosen so far */
+    int x_edges[OR_MAX_C + 1];
+    uint64_t band_cuts[OR_MAX_C];
+    /* results */
+    uint64_t t_min, thr;
+    uint32_t lambda_q;
+    uint64_t best_q;
+    int have_best;
+    oracle_result *res;
+    uint64_t n_candidates, n_valid;
+} enum_t;
+
+static void enum_evaluate(enum_t *e) {
+    const frame_t *f = e->f;
+    e->n_candidates++;
+    uint64_t amin = OR_INF, amax = 0, tmax = 0, q = 0;
+    for (int b = 0; b < e->nb; ++b) {
+        int y0 = 0;
+        for (int y = 1; y <= f->R; ++y) {
+            if (y == f->R || ((e->band_cuts[b] >> (y - 1)) & 1u)) {
+                rsum_t s = memo_get(e->memo, e->x_edges[b], e->x_edges[b + 1], y0, y);
+                if (s.N < amin) amin = s.N;
+                if (s.N > amax) amax = s.N;
+                if (s.T > tmax) tmax = s.T;
+                q += sse_floor(s.S1, s.S2, s.N);
+                y0 = y;
+            }
+        }
+    }
+    if (e->area_rule && !((u128)e->k_area * amin > (u128)amax)) return;
+    e->n_valid++;
+    if (e->pass == 1) {
+        if (tmax < e->t_min) e->t_min = tmax;
+        return;
+    }
+    /* pass 2: Eq. 4 as printed, T(P) <= T_min * (1 + lambda), in Q16 integers;
+       then the first (= lex-smallest code) minimum of Q */
+    if ((u128)tmax * 65536u > (u128)e->t_min * (65536u + (u128)e->lambda_q)) return;
+    if (!e->have_best || q < e->best_q) {
+        e->have_best = 1;
+        e->best_q = q;
+        oracle_result *r = e->res;
+        r->c = e->nb;
+        r->r = e->r;
+        r->row_mask = e->row_mask;
+        for (int b = 0; b <= e->nb; ++b) r->x_edges[b] = e->x_edges[b];
+        for (int b = 0; b < e->nb; ++b) r->band_cuts[b] = e->band_cuts[b];
+        r->t = tmax;
+        r->q = q;
+    }
+}
+
+static void enum_bands(enum_t *e, int x, int used) {
+    const frame_t *f = e->f;
+    if (x == f->C) {
+        if (used == e->n) enum_evaluate(e);
+        return;
+    }
+    if (used + e->r > e->n) return; /* every further tile column holds >= r slices */
+    for (int x1 = x + 1; x1 <= f->C; ++x1) {
+        /* in-tile slice cut bits over the free lines, topmost free line first */
+        uint64_t lim = 1ull << e->n_free;
+        for (uint64_t u = 0; u < lim; ++u) {
+            int k = e->r;
+            uint64_t cuts = e->row_mask;
+            for (int j = 0; j < e->n_free; ++j) {
+                if ((u >> (e->n_free - 1 - j)) & 1u) {
+                    cuts |= 1ull << (e->free_lines[j] - 1);
+                    k++;
+                }
+            }
+            if (used + k > e->n) continue;
+            e->x_edges[e->nb + 1] = x1;
+            e->band_cuts[e->nb] = cuts;
+            e->nb++;
+            enum_bands(e, x1, used + k);
+            e->nb--;
+        }
+    }
+}
+
+static void enum_all(enum_t *e) {
+    const frame_t *f = e->f;
+    int L = f->R - 1;
+    uint64_t lim = 1ull << L;
+    for (uint64_t v = 0; v < lim; ++v) {
+        /* tile-row cut bits, line 1 most significant */
+        e->row_mask = 0;
+        e->r = 1;
+        e->n_free = 0;
+        for (int y = 1; y <= L; ++y) {
+            if ((v >> (L - y)) & 1u) {
+                e->row_mask |= 1ull << (y - 1);
+                e->r++;
+            } else {
+                e->free_lines[e->n_free++] = y;
+            }
+        }
+        if (e->r > e->n) continue;
+        e->nb = 0;
+        e->x_edges[0] = 0;
+        enum_bands(e, 0, 0);
+    }
+}
+
+/*
+ * O1.  Enumerates S(n) literally: tile rows, tile columns, in-tile slice cuts,
+ * exactly n slices, the k*A_min > A_max rule (Sec. 2.3) when area_rule != 0.
+ * Step 1 (Eq. 3) and step 2 (Eq. 2 under Eq. 4) are two passes over the same
+ * enumeration.  Exponential: for small grids only.
+ */
+int oracle_search_enum(int W, int H, const uint64_t *S1, const uint64_t *S2, const uint64_t *N,
+                       const uint32_t *Tq, int n, int k_area, uint32_t lambda_q, int area_rule,
+                       oracle_result *res) {
+    memset(res, 0, sizeof(*res));
+    int st = check_inputs(W, H, n, k_area);
+    if (st) {
+        res->status = st;
+        return st;
+    }
+    frame_t f = {W, H, (W + OR_CTU - 1) / OR_CTU, (H + OR_CTU - 1) / OR_CTU, S1, S2, N, Tq};
+    memo_t m;
+    if (memo_init(&m, &f)) {
+        memo_free(&m);
+        res->status = OR_ENOMEM;
+        return OR_ENOMEM;
+    }
+    enum_t e;
+    memset(&e, 0, sizeof(e));
+    e.f = &f;
+    e.memo = &m;
+    e.n = n;
+    e.k_area = k_area;
+    e.area_rule = area_rule;
+    e.res = res;
+    e.t_min = OR_INF;
+    e.pass = 1;
+    enum_all(&e);
+    res->n_candidates = e.n_candidates;
+    res->n_valid = e.n_valid;
+    res->n = n;
+    if (e.t_min == OR_INF) {
+        res->status = OR_EINFEASIBLE;
+        memo_free(&m);
+        return OR_EINFEASIBLE;
+    }
+    e.thr = eq4_thr(e.t_min, lambda_q);
+    e.lambda_q = lambda_q;
+    e.pass = 2;
+    e.n_candidates = 0;
+    e.n_valid = 0;
+    enum_all(&e);
+    res->t_min = e.t_min;
+    res->thr = e.thr;
+    fill_reporting(&f, &m, res);
+    memo_free(&m);
+    res->status = OR_OK;
+    return OR_OK;
+}
+
+/* Counts the configurations of S(n) (no objective); a test of the enumerator. */
+int oracle_count_enum(int W, int H, int n, int k_area, int area_rule, uint64_t *count) {
+    int st = check_inputs(W, H, n, k_area);
+    if (st) return st;
+    int C = (W + OR_CTU - 1) / OR_CTU, R = (H + OR_CTU - 1) / OR_CTU;
+    size_t cells = (size_t)C * R;
+    uint64_t *S = (uint64_t *)calloc(cells, sizeof(uint64_t));
+    uint64_t *Nn = (uint64_t *)calloc(cells, sizeof(uint64_t));
+    uint32_t *T = (uint32_t *)calloc(cells, sizeof(uint32_t));
+    if (!S || !Nn || !T) {
+        free(S);
+        free(Nn);
+        free(T);
+        return OR_ENOMEM;
+    }
+    frame_t f = {W, H, C, R, S, S, Nn, T};
+    for (int y = 0; y < R; ++y)
+        for (int x = 0; x < C; ++x) Nn[y * C + x] = (uint64_t)ctu_w(&f, x) * ctu_h(&f, y);
+    memo_t m;
+    if (memo_init(&m, &f)) {
+        memo_free(&m);
+        free(S);
+        free(Nn);
+        free(T);
+        return OR_ENOMEM;
+    }
+    oracle_result res;
+    enum_t e;
+    memset(&e, 0, sizeof(e));
+    e.f = &f;
+    e.memo = &m;
+    e.n = n;
+    e.k_area = k_area;
+    e.area_rule = area_rule;
+    e.res = &res;
+    e.t_min = OR_INF;
+    e.pass = 1;
+    enum_all(&e);
+    *count = area_rule ? e.n_valid : e.n_candidates;
+    memo_free(&m);
+    free(S);
+    free(Nn);
+    free(T);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* O2: exact dynamic programme                                          */
+/*
+ * Two facts make the search decomposable.
+ *
+ * (i) Tile rows add no geometry.  A tile-row cut at line y forces a slice
+ *     boundary at y in every tile column; the same slices are reached with no
+ *     tile-row cut by cutting at y inside each tile.  So every partition of
+ *     S(n) is also a partition with a single tile row, and since that
+ *     configuration's code starts with all-zero tile-row bits it is the
+ *     smallest code of its geometry.  The search therefore runs over tile
+ *     columns, each split into horizontal slices.
+ *
+ * (ii) The area rule becomes local through windows.  If 3*A_min > A_max then
+ *     every slice area lies in [a, 3a-1] with a = A_min; conversely if every
+ *     area lies in [a, 3a-1] the rule holds.  So S(n) is the union over the
+ *     distinct slice areas a of the partitions whose slices all lie in the
+ *     window [a, k*a-1].  Within a window, max (Eq. 1) and sum (Eq. 2) are
+ *     separable over tile columns and, inside a column, over slices.
+ *
+ * Per window: step 1 is a min-max DP, step 2 a min-sum DP over slices that
+ * also satisfy T(s) <= thr (max over slices <= thr iff each slice <= thr).
+ * The lex-smallest code among the minimisers is rebuilt from suffix tables.
+ */
+
+typedef struct {
+    const frame_t *f;
+    memo_t *memo;
+    int n, k_area;
+    uint64_t a_lo, a_hi;  /* window */
+    uint64_t thr;         /* step 2 only */
+} dpctx_t;
+
+static int strip_ok(const dpctx_t *d, rsum_t s, int step) {
+    if (s.N < d->a_lo || s.N > d->a_hi) return 0;
+    if (step == 2 && s.T > d->thr) return 0;
+    return 1;
+}
+
+/* Step 1, one band [x0,x1): V[k] = min over k-slice splits of the max slice time. */
+static void band_minmax(const dpctx_t *d, int x0, int x1, uint64_t *V /* [n+1] */) {
+    const frame_t *f = d->f;
+    int R = f->R, n = d->n;
+    /* G[y][k]: rows [0,y) split into k slices */
+    uint64_t G[OR_MAX_R + 1][OR_MAX_N + 1];
+    for (int y = 0; y <= R; ++y)
+        for (int k = 0; k <= n; ++k) G[y][k] = OR_INF;
+    G[0][0] = 0;
+    for (int y = 1; y <= R; ++y)
+        for (int yp = 0; yp < y; ++yp) {
+            rsum_t s = memo_get(d->memo, x0, x1, yp, y);
+            if (!strip_ok(d, s, 1)) continue;
+            for (int k = 1; k <= n; ++k) {
+                if (G[yp][k - 1] == OR_INF) continue;
+                uint64_t v = G[yp][k - 1] > s.T ? G[yp][k - 1] : s.T;
+                if (v < G[y][k]) G[y][k] = v;
+            }
+        }
+    for (int k = 0; k <= n; ++k) V[k] = G[R][k];
+}
+
+static uint64_t window_tmin(const dpctx_t *d) {
+    const frame_t *f = d->f;
+    int C = f->C, n = d->n;
+    uint64_t *V = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(C + 1) * (C + 1) * (n + 1));
+    if (!V) return OR_INF;
+    for (int x0 = 0; x0 < C; ++x0)
+        for (int x1 = x0 + 1; x1 <= C; ++x1)
+            band_minmax(d, x0, x1, V + ((size_t)x0 * (C + 1) + x1) * (n + 1));
+    /* F[x][m]: columns [0,x) with m slices */
+    uint64_t F[OR_MAX_C + 1][OR_MAX_N + 1];
+    for (int x = 0; x <= C; ++x)
+        for (int m = 0; m <= n; ++m) F[x][m] = OR_INF;
+    F[0][0] = 0;
+    for (int x = 1; x <= C; ++x)
+        for (int xp = 0; xp < x; ++xp) {
+            const uint64_t *Vb = V + ((size_t)xp * (C + 1) + x) * (n + 1);
+            for (int m = 1; m <= n; ++m)
+                for (int k = 1; k <= m; ++k) {
+                    if (F[xp][m - k] == OR_INF || Vb[k] == OR_INF) continue;
+                    uint64_t v = F[xp][m - k] > Vb[k] ? F[xp][m - k] : Vb[k];
+                    if (v < F[x][m]) F[x][m] = v;
+                }
+        }
+    uint64_t r = F[C][n];
+    free(V);
+    return r;
+}
+
+/* Step 2 tables for one band: Gs[y][k] = min Q for rows [y,R) in k slices. */
+static void band_minsum(const dpctx_t *d, int x0, int x1, uint64_t Gs[OR_MAX_R + 1][OR_MAX_N + 1]) {
+    const frame_t *f = d->f;
+    int R = f->R, n = d->n;
+    for (int y = 0; y <= R; ++y)
+        for (int k = 0; k <= n; ++k) Gs[y][k] = OR_INF;
+    Gs[R][0] = 0;
+    for (int y = R - 1; y >= 0; --y)
+        for (int y1 = y + 1; y1 <= R; ++y1) {
+            rsum_t s = memo_get(d->memo, x0, x1, y, y1);
+            if (!strip_ok(d, s, 2)) continue;
+            uint64_t qs = sse_floor(s.S1, s.S2, s.N);
+            for (int k = 1; k <= n; ++k) {
+                if (Gs[y1][k - 1] == OR_INF) continue;
+                uint64_t v = Gs[y1][k - 1] + qs;
+                if (v < Gs[y][k]) Gs[y][k] = v;
+            }
+        }
+}
+
+/* Lex-smallest cut bits of a k-slice split of band [x0,x1) reaching Gs[0][k]. */
+static uint64_t band_lexmin_bits(const dpctx_t *d, int x0, int x1,
+                                 uint64_t Gs[OR_MAX_R + 1][OR_MAX_N + 1], int k) {
+    const frame_t *f = d->f;
+    int R = f->R;
+    uint64_t bits = 0;
+    int y = 0, kk = k;
+    while (kk > 1) {
+        /* the largest next cut keeps the bit string smallest */
+        int chosen = -1;
+        for (int y1 = R - 1; y1 > y; --y1) {
+            rsum_t s = memo_get(d->memo, x0, x1, y, y1);
+            if (!strip_ok(d, s, 2) || Gs[y1][kk - 1] == OR_INF) continue;
+            if (Gs[y1][kk - 1] + sse_floor(s.S1, s.S2, s.N) == Gs[y][kk]) {
+                chosen = y1;
+                break;
+            }
+        }
+        if (chosen < 0) return OR_INF; /* cannot happen when Gs[y][kk] is finite */
+        bits |= 1ull << (chosen - 1);
+        y = chosen;
+        kk--;
+    }
+    return bits;
+}
+
+/* bit strings top to bottom with line 1 first: compare as reversed bit order */
+static int bits_less(uint64_t a, uint64_t b, int R) {
+    for (int y = 1; y < R; ++y) {
+        int ba = (int)((a >> (y - 1)) & 1u), bb = (int)((b >> (y - 1)) & 1u);
+        if (ba != bb) return ba < bb;
+    }
+    return 0;
+}
+
+typedef struct {
+    int c;
+    int x_edges[OR_MAX_C + 1];
+    uint64_t band_cuts[OR_MAX_C];
+    uint64_t q, t;
+} code_t;
+
+static int code_less(const code_t *a, const code_t *b, int R) {
+    int c = a->c < b->c ? a->c : b->c;
+    for (int i = 0; i < c; ++i) {
+        if (a->x_edges[i + 1] != b->x_edges[i + 1]) return a->x_edges[i + 1] < b->x_edges[i + 1];
+        if (a->band_cuts[i] != b->band_cuts[i]) return bits_less(a->band_cuts[i], b->band_cuts[i], R);
+    }
+    return 0;
+}
+
+/* Step 2 within one window: Q_w and its lex-smallest minimiser. */
+static uint64_t window_step2(const dpctx_t *d, code_t *best) {
+    const frame_t *f = d->f;
+    int C = f->C, R = f->R, n = d->n;
+    size_t nbands = (size_t)(C + 1) * (C + 1);
+    uint64_t *V = (uint64_t *)malloc(sizeof(uint64_t) * nbands * (n + 1));
+    uint64_t(*Gs)[OR_MAX_N + 1] = malloc(sizeof(uint64_t) * (OR_MAX_R + 1) * (OR_MAX_N + 1));
+    if (!V || !Gs) {
+        free(V);
+        free(Gs);
+        return OR_INF;
+    }
+    for (int x0 = 0; x0 < C; ++x0)
+        for (int x1 = x0 + 1; x1 <= C; ++x1) {
+            band_minsum(d, x0, x1, Gs);
+            for (int k = 0; k <= n; ++k) V[((size_t)x0 * (C + 1) + x1) * (n + 1) + k] = Gs[0][k];
+        }
+    /* H[x][m]: columns [x,C) with m slices */
+    uint64_t H[OR_MAX_C + 1][OR_MAX_N + 1];
+    for (int x = 0; x <= C; ++x)
+        for (int m = 0; m <= n; ++m) H[x][m] = OR_INF;
+    H[C][0] = 0;
+    for (int x = C - 1; x >= 0; --x)
+        for (int x1 = x + 1; x1 <= C; ++x1) {
+            const uint64_t *Vb = V + ((size_t)x * (C + 1) + x1) * (n + 1);
+            for (int m = 1; m <= n; ++m)
+                for (int k = 1; k <= m; ++k) {
+                    if (Vb[k] == OR_INF || H[x1][m - k] == OR_INF) continue;
+                    uint64_t v = Vb[k] + H[x1][m - k];
+                    if (v < H[x][m]) H[x][m] = v;
+                }
+        }
+    uint64_t qw = H[0][n];
+    if (qw != OR_INF) {
+        /* rebuild the lex-smallest code: smallest next edge, then smallest bits */
+        int x = 0, m = n;
+        best->c = 0;
+        best->x_edges[0] = 0;
+        best->q = qw;
+        best->t = 0;
+        while (x < C) {
+            int found = 0;
+            for (int x1 = x + 1; x1 <= C && !found; ++x1) {
+                const uint64_t *Vb = V + ((size_t)x * (C + 1) + x1) * (n + 1);
+                uint64_t bbits = 0;
+                int bk = -1;
+                int need_tables = 1;
+                for (int k = 1; k <= m; ++k) {
+                    if (Vb[k] == OR_INF || H[x1][m - k] == OR_INF) continue;
+                    if (Vb[k] + H[x1][m - k] != H[x][m]) continue;
+                    if (need_tables) {
+                        band_minsum(d, x, x1, Gs);
+                        need_tables = 0;
+                    }
+                    uint64_t bits = band_lexmin_bits(d, x, x1, Gs, k);
+                    if (bk < 0 || bits_less(bits, bbits, R)) {
+                        bbits = bits;
+                        bk = k;
+                    }
+                }
+                if (bk >= 0) {
+                    best->band_cuts[best->c] = bbits;
+                    best->c++;
+                    best->x_edges[best->c] = x1;
+                    x = x1;
+                    m -= bk;
+                    found = 1;
+                }
+            }
+            if (!found) break; /* cannot happen when H[0][n] is finite */
+        }
+        /* T of the rebuilt partition */
+        for (int b = 0; b < best->c; ++b) {
+            int y0 = 0;
+            for (int y = 1; y <= R; ++y)
+                if (y == R || ((best->band_cuts[b] >> (y - 1)) & 1u)) {
+                    rsum_t s = memo_get(d->memo, best->x_edges[b], best->x_edges[b + 1], y0, y);
+                    if (s.T > best->t) best->t = s.T;
+                    y0 = y;
+                }
+        }
+    }
+    free(V);
+    free(Gs);
+    return qw;
+}
+
+static int cmp_u64(const void *a, const void *b) {
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* Distinct slice areas a with a*n <= A and (k*a-1)*n >= A: the windows that can hold a partition. */
+static int list_windows(const frame_t *f, int n, int k_area, uint64_t **out, int *count) {
+    int C = f->C, R = f->R;
+    size_t cap = (size_t)C * (C + 1) / 2 * R * (R + 1) / 2;
+    uint64_t *a = (uint64_t *)malloc(sizeof(uint64_t) * (cap ? cap : 1));
+    if (!a) return OR_ENOMEM;
+    size_t cnt = 0;
+    uint64_t A = (uint64_t)f->W * f->H;
+    for (int x0 = 0; x0 < C; ++x0)
+        for (int x1 = x0 + 1; x1 <= C; ++x1)
+            for (int y0 = 0; y0 < R; ++y0)
+                for (int y1 = y0 + 1; y1 <= R; ++y1) {
+                    uint64_t w = 0, h = 0;
+                    for (int x = x0; x < x1; ++x) w += ctu_w(f, x);
+                    for (int y = y0; y < y1; ++y) h += ctu_h(f, y);
+                    uint64_t ar = w * h;
+                    if (ar * (uint64_t)n <= A && ((uint64_t)k_area * ar - 1) * (uint64_t)n >= A) a[cnt++] = ar;
+                }
+    qsort(a, cnt, sizeof(uint64_t), cmp_u64);
+    size_t u = 0;
+    for (size_t i = 0; i < cnt; ++i)
+        if (u == 0 || a[i] != a[u - 1]) a[u++] = a[i];
+    *out = a;
+    *count = (int)u;
+    return OR_OK;
+}
+
+/*
+ * O2.  Same result as O1 (area rule on) by facts (i) and (ii) above:
+ * step 1 min over windows of the min-max DP; step 2 min over windows of the
+ * min-sum DP under Eq. 4; ties to the lex-smallest code over all windows.
+ */
+int oracle_search_dp(int W, int H, const uint64_t *S1, const uint64_t *S2, const uint64_t *N,
+                     const uint32_t *Tq, int n, int k_area, uint32_t lambda_q, oracle_result *res) {
+    memset(res, 0, sizeof(*res));
+    int st = check_inputs(W, H, n, k_area);
+    if (st) {
+        res->status = st;
+        return st;
+    }
+    frame_t f = {W, H, (W + OR_CTU - 1) / OR_CTU, (H + OR_CTU - 1) / OR_CTU, S1, S2, N, Tq};
+    memo_t m;
+    if (memo_init(&m, &f)) {
+        memo_free(&m);
+        res->status = OR_ENOMEM;
+        return OR_ENOMEM;
+    }
+    uint64_t *win = NULL;
+    int nw = 0;
+    if (list_windows(&f, n, k_area, &win, &nw)) {
+        memo_free(&m);
+        res->status = OR_ENOMEM;
+        return OR_ENOMEM;
+    }
+    res->n = n;
+    res->n_windows = (uint64_t)nw;
+    dpctx_t d = {&f, &m, n, k_area, 0, 0, 0};
+    uint64_t t_min = OR_INF;
+    for (int i = 0; i < nw; ++i) {
+        d.a_lo = win[i];
+        d.a_hi = (uint64_t)k_area * win[i] - 1;
+        uint64_t t = window_tmin(&d);
+        if (t < t_min) t_min = t;
+    }
+    if (t_min == OR_INF) {
+        free(win);
+        memo_free(&m);
+        res->status = OR_EINFEASIBLE;
+        return OR_EINFEASIBLE;
+    }
+    d.thr = eq4_thr(t_min, lambda_q);
+    code_t best, cur;
+    memset(&best, 0, sizeof(best));
+    memset(&cur, 0, sizeof(cur));
+    int have = 0;
+    for (int i = 0; i < nw; ++i) {
+        d.a_lo = win[i];
+        d.a_hi = (uint64_t)k_area * win[i] - 1;
+        uint64_t q = window_step2(&d, &cur);
+        if (q == OR_INF) continue;
+        if (!have || q < best.q || (q == best.q && code_less(&cur, &best, f.R))) {
+            best = cur;
+            have = 1;
+        }
+    }
+    free(win);
+    if (!have) { /* cannot happen: the T_min partition satisfies Eq. 4 */
+        memo_free(&m);
+        res->status = OR_EINFEASIBLE;
+        return OR_EINFEASIBLE;
+    }
+    res->c = best.c;
+    res->r = 1;
+    res->row_mask = 0;
+    for (int b = 0; b <= best.c; ++b) res->x_edges[b] = best.x_edges[b];
+    for (int b = 0; b < best.c; ++b) res->band_cuts[b] = best.band_cuts[b];
+    res->t_min = t_min;
+    res->thr = d.thr;
+    res->t = best.t;
+    res->q = best.q;
+    fill_reporting(&f, &m, res);
+    memo_free(&m);
+    res->status = OR_OK;
+    return OR_OK;
+}
+
+/* Objective of a given partition by direct sums (used to check any result). */
+int oracle_evaluate(int W, int H, const uint64_t *S1, const uint64_t *S2, const uint64_t *N,
+                    const uint32_t *Tq, int c, const int *x_edges, const uint64_t *band_cuts,
+                    uint64_t *t_out, uint64_t *q_out, uint64_t *amin_out, uint64_t *amax_out,
+                    int *nreg_out) {
+    if (W <= 0 || H <= 0) return OR_EINVAL;
+    frame_t f = {W, H, (W + OR_CTU - 1) / OR_CTU, (H + OR_CTU - 1) / OR_CTU, S1, S2, N, Tq};
+    if (c < 1 || c > f.C || x_edges[0] != 0 || x_edges[c] != f.C) return OR_EINVAL;
+    uint64_t t = 0, q = 0, amin = OR_INF, amax = 0;
+    int nreg = 0;
+    for (int b = 0; b < c; ++b) {
+        if (x_edges[b + 1] <= x_edges[b]) return OR_EINVAL;
+        int y0 = 0;
+        for (int y = 1; y <= f.R; ++y)
+            if (y == f.R || ((band_cuts[b] >> (y - 1)) & 1u)) {
+                rsum_t s = rect_direct(&f, x_edges[b], x_edges[b + 1], y0, y);
+                if (s.T > t) t = s.T;
+                q += sse_floor(s.S1, s.S2, s.N);
+                if (s.N < amin) amin = s.N;
+                if (s.N > amax) amax = s.N;
+                nreg++;
+                y0 = y;
+            }
+    }
+    *t_out = t;
+    *q_out = q;
+    *amin_out = amin;
+    *amax_out = amax;
+    *nreg_out = nreg;
+    return OR_OK;
+}
+
+size_t oracle_result_size(void) { return sizeof(oracle_result); }
