@@ -1,0 +1,258 @@
+/*
+ * trs.h -- C ABI of the GB300 library for dynamic tile / rectangular-slice
+ * (TRS) frame partitioning, after "Quality-driven Dynamic VVC Frame
+ * Partitioning for efficient Parallel Processing" (Amestoy et al., ICIP 2020).
+ *
+ * The hot path of the method, one frame at a time or batched:
+ *   trs_texture_map    per-CTU luma statistics (the texture measure of Eq. 2,
+ *                      Sec. 2.2: sum p, sum p^2 and the sample count per CTU)
+ *   trs_region_tables  Q16 CTU times (the estimator values of Sec. 2.1),
+ *                      summed-area tables and the per-rectangle table of
+ *                      slice times (Eq. 1) and floored slice SSE (Eq. 2)
+ *   trs_search         step 1: T_min = min_P T(P) (Eq. 3); step 2: the
+ *                      partition minimising Eq. 2 subject to Eq. 4,
+ *                      T(P) <= T_min (1 + lambda); both over the partitions
+ *                      with exactly n slices and k*A_min > A_max (Sec. 2.3)
+ *
+ * Conventions shared by every call:
+ *   - All pointers named *_dev are CUDA device pointers on the context's
+ *     device; *_host are host pointers.  The caller owns every buffer it
+ *     passes.  The context owns its scratch memory.  The first call that
+ *     sees a new frame shape (width, height, n) builds that shape's search
+ *     plan and may grow the scratch, synchronously; later calls with shapes
+ *     seen before allocate nothing and only enqueue work, so warm a shape up
+ *     before capturing calls in a CUDA graph.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device-pointer calls only enqueue work and return; their
+ *     outputs are valid after the stream has been synchronised.  Calls that
+ *     take host buffers synchronise the stream before they return.
+ *   - Errors found from the arguments are returned at once (TRS_EINVAL ...).
+ *     Errors that depend on the data (a sample >= 2^bit_depth, a time that
+ *     is not finite or outside [0, 65536), no partition satisfying the area
+ *     rule) are reported in trs_partition.status, written on the device.
+ *   - A context serves one host thread at a time.
+ *
+ * Readings of the paper fixed by this library (the paper is silent on them):
+ *   CTUs are 128x128 luma samples, edge CTUs clipped.  A partition has
+ *   exactly n slices (one per thread, Sec. 2.1); a slice is a run of whole
+ *   CTU rows inside one tile (Sec. 1).  Areas count luma samples; the area
+ *   rule is 3*A_min > A_max with a strict '>'; it constrains both steps.
+ *   Times are quantised Tq = rint(t * 65536); lambda_q = rint(lambda * 65536)
+ *   and Eq. 4 holds iff T(P)*65536 <= T_min*(65536 + lambda_q).  The quality
+ *   term of a slice is floor(SSE) = S2 - ceil(S1^2 / N).  Among partitions of
+ *   equal quality the smallest canonical code wins (tile-row cut bits top to
+ *   bottom, then per tile column its right edge and its slice cut bits top to
+ *   bottom, '0' < '1'); such a winner never has tile-row cuts, since a slice
+ *   cut at the same line gives the same slices with a smaller code.
+ */
+#ifndef TRS_H
+#define TRS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TRS_ABI_VERSION 1
+
+#define TRS_CTU 128          /* CTU edge in luma samples */
+#define TRS_MAX_COLS 64      /* CTU columns: width  <= 8192 */
+#define TRS_MAX_ROWS 32      /* CTU rows:    height <= 4096 */
+#define TRS_MAX_REGIONS 32   /* n, slices (= threads) per frame */
+
+enum trs_status {
+    TRS_OK = 0,
+    TRS_EINVAL = 1,       /* bad argument (null pointer, size out of range, misaligned) */
+    TRS_ERANGE = 2,       /* a sample >= 2^bit_depth, or a CTU time not finite / outside [0, 65536) */
+    TRS_EINFEASIBLE = 3,  /* no partition with n slices satisfies the area rule */
+    TRS_ENOMEM = 4,       /* a size beyond what the context was created for, or allocation failed */
+    TRS_EBUSY = 5,        /* server: admission refused (no slot or memory budget) */
+    TRS_ETIMEOUT = 6,     /* a bounded device or host wait gave up */
+    TRS_ECUDA = 7         /* a CUDA runtime call failed; see trs_last_error() */
+};
+
+typedef struct trs_ctx trs_ctx;
+
+/* Limits fixed when a context is created; every later call must fit them. */
+typedef struct trs_opts {
+    int max_width;     /* largest luma width,  1..8192 */
+    int max_height;    /* largest luma height, 1..4096 */
+    int max_regions;   /* largest n, 1..TRS_MAX_REGIONS */
+    int max_batch;     /* frames per batched call, >= 1 */
+    int k_area;        /* area-rule factor k of Sec. 2.3 (the paper uses 3), >= 1 */
+    int device;        /* CUDA device ordinal */
+} trs_opts;
+
+/* Per-CTU statistics, structure of arrays, each R*C entries, row-major over
+ * the CTU grid (R = ceil(H/128) rows, C = ceil(W/128) columns).  Device
+ * memory owned by the caller. */
+typedef struct trs_ctu_stats {
+    uint32_t *s1;      /* sum of samples */
+    uint64_t *s2;      /* sum of squared samples */
+    uint32_t *count;   /* samples in the (clipped) CTU */
+    uint32_t *vmax;    /* largest sample */
+    uint32_t *flags;   /* one word: bit 0 set if a sample was >= 2^bit_depth */
+} trs_ctu_stats;
+
+/* Byte layout of the region tables of one frame (see trs_region_tables).
+ * Offsets are from the start of the caller's device buffer; every array
+ * starts on a 256-byte boundary. */
+typedef struct trs_tables_layout {
+    int width, height, cols, rows;  /* W, H, C, R */
+    int bands;                      /* C*(C+1)/2 tile-column candidates */
+    int reserved;
+    size_t bytes;                   /* total size of the buffer */
+    size_t off_tq;       /* uint32 [R*C]: Q16 CTU times */
+    size_t off_sat_s1;   /* uint64 [(R+1)*(C+1)]: sat[y][x] = sum over CTUs [0,x) x [0,y) */
+    size_t off_sat_s2;   /* uint64 [(R+1)*(C+1)] */
+    size_t off_sat_t;    /* uint64 [(R+1)*(C+1)], of Tq */
+    size_t off_rect_t;   /* uint64 [bands][R][R]: entry (b, d-1, y) = time of the slice spanning
+                            tile column b, CTU rows [y, y+d) (Eq. 1); band b of columns [x0,x1)
+                            has b = x0*(2C-x0+1)/2 + (x1-x0-1); entries with y+d > R are unused */
+    size_t off_rect_q;   /* uint64 [bands][R][R]: floor of the slice's luma SSE (Eq. 2), same index */
+    size_t off_status;   /* int32 [4]: [0] data status of this frame (TRS_OK / TRS_ERANGE) */
+} trs_tables_layout;
+
+/* The decision for one frame, written by the device. */
+typedef struct trs_partition {
+    int32_t status;          /* TRS_OK, TRS_ERANGE or TRS_EINFEASIBLE */
+    int32_t n_regions;       /* n */
+    int32_t cols, rows;      /* CTU grid C, R */
+    int32_t n_tile_cols;     /* tiles: n_tile_cols x n_tile_rows */
+    int32_t n_tile_rows;
+    int32_t n_windows;       /* area windows searched */
+    int32_t reserved;
+    uint64_t t_min_q;        /* Eq. 3, Q16 */
+    uint64_t thr_q;          /* largest T(P) satisfying Eq. 4 */
+    uint64_t t_q;            /* T(P*) (Eq. 1), Q16 */
+    uint64_t q;              /* Q(P*): sum over slices of floor(SSE) (Eq. 2) */
+    double t_min;            /* t_min_q / 65536 */
+    double t;                /* t_q / 65536 */
+    double sse;              /* exact sum of slice SSE, in double */
+    uint64_t tile_row_mask;                  /* bit y-1: tile-row boundary at CTU line y */
+    int16_t col_bd[TRS_MAX_COLS + 1];        /* tile-column edges, n_tile_cols + 1 entries */
+    int16_t row_bd[TRS_MAX_ROWS + 1];        /* tile-row edges, n_tile_rows + 1 entries */
+    uint32_t slice_cuts[TRS_MAX_COLS];       /* per tile column: bit y-1 set = slice boundary at CTU line y */
+    int16_t region[TRS_MAX_REGIONS][4];      /* slices x0, y0, x1, y1 (CTU units, half-open), in tile
+                                                raster order, top to bottom inside a tile */
+    uint8_t tile_slices[TRS_MAX_REGIONS];    /* slices per tile, tile raster order */
+} trs_partition;
+
+/* One frame of a batched call. */
+typedef struct trs_frame_desc {
+    const void *luma_dev;     /* W*H samples, rows pitch_bytes apart; uint8 if bit_depth == 8 else
+                                 little-endian uint16 */
+    const float *ctu_time_dev;/* R*C co-located CTU times (Sec. 2.1), row-major */
+    int width, height;
+    size_t pitch_bytes;
+    int bit_depth;            /* 8..12 */
+    int n_regions;            /* n */
+    float lambda;             /* Eq. 4, >= 0 */
+} trs_frame_desc;
+
+/* --- introspection (no GPU needed) --------------------------------------- */
+
+/* Size in bytes of the ABI structure called `name` ("trs_opts",
+ * "trs_ctu_stats", "trs_tables_layout", "trs_partition", "trs_frame_desc"),
+ * 0 for an unknown name; lets bindings check their copies of the layouts. */
+size_t trs_sizeof(const char *name);
+
+/* Search-plan figures of a frame shape: the number of area windows
+ * [a, k*a - 1] (Sec. 2.3's rule made local, one per admissible smallest
+ * slice area a) and of distinct row-DP units.  Pure host arithmetic.
+ * TRS_EINVAL for sizes beyond the limits. */
+int trs_plan_stats(int width, int height, int n_regions, int k_area, int *n_windows, int *n_items);
+
+/* Algorithmic work of one search step of a frame shape, counted from the
+ * plan: row_relax = candidate slices examined by the row DPs (for every
+ * item and slice count k <= kmax, every admissible slice [y, y+d)),
+ * col_relax = candidate (tile column, k, m) triples examined by the column
+ * DPs of all windows.  Each relaxation is one 64-bit combine (max for Eq. 1,
+ * + for Eq. 2) and one 64-bit minimum.  Pure host arithmetic. */
+int trs_plan_work(int width, int height, int n_regions, int k_area, double *row_relax, double *col_relax);
+
+/* --- context ------------------------------------------------------------ */
+
+int trs_version(void);
+const char *trs_strerror(int status);
+/* Text of the last CUDA error seen by this process (thread-local), "" if none. */
+const char *trs_last_error(void);
+
+/* Creates a context on opts->device and allocates all of its scratch memory.
+ * Returns TRS_EINVAL for limits out of range, TRS_ENOMEM / TRS_ECUDA on failure. */
+int trs_create(trs_ctx **out, const trs_opts *opts);
+/* Synchronises the context's work and frees it.  NULL is accepted. */
+int trs_destroy(trs_ctx *ctx);
+/* Bytes of device memory the context holds. */
+size_t trs_ctx_bytes(const trs_ctx *ctx);
+
+/* --- the hot path, one frame ------------------------------------------- */
+
+/* a1.  Per-CTU luma statistics of one frame (Eq. 2 needs S1, S2, N of every
+ * slice; they are sums of these).  luma_dev: W*H samples with rows
+ * pitch_bytes apart (pitch >= W * bytes per sample).  Samples >= 2^bit_depth
+ * set stats->flags bit 0 and are still summed.  Rows and the base address
+ * aligned to 16 bytes take the vector path; others a scalar path.
+ * TRS_EINVAL: null pointers, W/H beyond the context, bit_depth outside 8..12. */
+int trs_texture_map(trs_ctx *ctx, const void *luma_dev, int width, int height, size_t pitch_bytes,
+                    int bit_depth, const trs_ctu_stats *stats, void *stream);
+
+/* Fills *out with the table layout of a W x H frame.  TRS_EINVAL if the
+ * frame exceeds TRS_MAX_COLS / TRS_MAX_ROWS CTUs. */
+int trs_tables_layout_get(int width, int height, trs_tables_layout *out);
+
+/* a2.  Region tables of one frame from its CTU statistics and the CTU times
+ * of the co-located previous frame (the estimator of Sec. 2.1), into the
+ * caller's device buffer tables_dev of tables_bytes >= layout.bytes.
+ * ctu_time_dev: R*C floats.  A bad time, or stats->flags bit 0, sets the
+ * frame status TRS_ERANGE (reported by trs_search). */
+int trs_region_tables(trs_ctx *ctx, const trs_ctu_stats *stats, const float *ctu_time_dev, int width,
+                      int height, void *tables_dev, size_t tables_bytes, void *stream);
+
+/* a3-a5.  Both search steps of Sec. 2.3 over the tables of one frame, and the
+ * decoding of the winner into out_dev (device memory, one trs_partition).
+ * n_regions in 1..opts.max_regions; lambda finite, 0 <= lambda <= 1000. */
+int trs_search(trs_ctx *ctx, const void *tables_dev, int width, int height, int n_regions, float lambda,
+               trs_partition *out_dev, void *stream);
+
+/* a1-a5 in one call, with the context's own statistics and table buffers. */
+int trs_decide(trs_ctx *ctx, const void *luma_dev, int width, int height, size_t pitch_bytes, int bit_depth,
+               const float *ctu_time_dev, int n_regions, float lambda, trs_partition *out_dev,
+               void *stream);
+
+/* a1-a5 from host memory: copies the plane and the times to the device,
+ * decides, copies the partition back into *out_host and synchronises. */
+int trs_decide_host(trs_ctx *ctx, const void *luma_host, int width, int height, size_t pitch_bytes,
+                    int bit_depth, const float *ctu_time_host, int n_regions, float lambda,
+                    trs_partition *out_host, void *stream);
+
+/* --- batched form -------------------------------------------------------- */
+
+/* Decides nframes frames (1..opts.max_batch) of any sizes, depths, n and
+ * lambda with one launch of each kernel over all of them; out_dev holds
+ * nframes partitions.  The launch sequence is captured in a CUDA graph the
+ * first time a batch of a given composition is seen and replayed after. */
+int trs_batch_decide(trs_ctx *ctx, const trs_frame_desc *frames_host, int nframes, trs_partition *out_dev,
+                     void *stream);
+
+/* Like trs_batch_decide, with every plane and time map in host memory
+ * (pinned memory gives asynchronous copies): copies them into device
+ * staging owned by the context, decides, copies the nframes partitions back
+ * into out_host and synchronises.  The staging memory is allocated on the
+ * first call that needs more than any call before. */
+int trs_batch_decide_host(trs_ctx *ctx, const trs_frame_desc *frames_host, int nframes, trs_partition *out_host,
+                          void *stream);
+
+/* Device time in milliseconds of each stage of the most recent batched call
+ * (texture, tables, step-1 rows, step-1 columns, step-2 rows, step-2
+ * columns, decode), read from CUDA events recorded inside its graph.
+ * Synchronises on that call.  Returns the number of stages written. */
+int trs_batch_stage_ms(trs_ctx *ctx, float *ms, int max_stages);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRS_H */

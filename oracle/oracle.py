@@ -113,6 +113,8 @@ def lib():
         _lib.oracle_evaluate.argtypes = [ct.c_int, ct.c_int, u64p, u64p, u64p, u32p, ct.c_int,
                                          ct.POINTER(ct.c_int), u64p, u64p, u64p, u64p, u64p,
                                          ct.POINTER(ct.c_int)]
+        _lib.oracle_rect.argtypes = [ct.c_int, ct.c_int, u64p, u64p, u64p, u32p, ct.c_int, ct.c_int, ct.c_int,
+                                     ct.c_int, u64p, u64p]
         _lib.oracle_result_size.restype = ct.c_size_t
         assert _lib.oracle_result_size() == ct.sizeof(_Result)
     return _lib
@@ -241,6 +243,16 @@ def evaluate(st: Stats, Tq: np.ndarray, x_edges: list, band_cuts: list) -> dict:
     if s != OK:
         raise ValueError(f"oracle_evaluate status {s}")
     return dict(t=int(o[0][0]), q=int(o[1][0]), amin=int(o[2][0]), amax=int(o[3][0]), n=nreg.value)
+
+
+def rect(st: Stats, Tq: np.ndarray, x0: int, x1: int, y0: int, y1: int) -> tuple[int, int]:
+    """(time, floor SSE) of the CTU rectangle [x0,x1) x [y0,y1) by direct sums."""
+    S1, S2, N, T = _search_args(st, Tq)
+    t, q = np.zeros(1, np.uint64), np.zeros(1, np.uint64)
+    s = lib().oracle_rect(st.width, st.height, _p64(S1), _p64(S2), _p64(N), _p32(T), x0, x1, y0, y1, _p64(t), _p64(q))
+    if s != OK:
+        raise ValueError(f"oracle_rect status {s}")
+    return int(t[0]), int(q[0])
 
 
 def decide(plane: np.ndarray, times: np.ndarray, bit_depth: int, n: int, lam: float,

@@ -853,4 +853,15 @@ int oracle_evaluate(int W, int H, const uint64_t *S1, const uint64_t *S2, const 
     return OR_OK;
 }
 
+/* Time (Eq. 1) and floored SSE (Eq. 2) of one rectangle [x0,x1) x [y0,y1) by direct sums. */
+int oracle_rect(int W, int H, const uint64_t *S1, const uint64_t *S2, const uint64_t *N, const uint32_t *Tq,
+                int x0, int x1, int y0, int y1, uint64_t *t_out, uint64_t *q_out) {
+    frame_t f = {W, H, (W + OR_CTU - 1) / OR_CTU, (H + OR_CTU - 1) / OR_CTU, S1, S2, N, Tq};
+    if (x0 < 0 || x1 > f.C || x0 >= x1 || y0 < 0 || y1 > f.R || y0 >= y1) return OR_EINVAL;
+    rsum_t s = rect_direct(&f, x0, x1, y0, y1);
+    *t_out = s.T;
+    *q_out = sse_floor(s.S1, s.S2, s.N);
+    return OR_OK;
+}
+
 size_t oracle_result_size(void) { return sizeof(oracle_result); }

@@ -1,0 +1,638 @@
+// The C ABI of include/trs.h: contexts, argument checks, buffers, plans and
+// the launch sequences of the one-frame and batched paths.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "plan.h"
+#include "trs_internal.cuh"
+
+using namespace trs;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int cuda_fail(cudaError_t e, const char *what) {
+    std::snprintf(g_err, sizeof(g_err), "%s: %s", what, cudaGetErrorString(e));
+    return TRS_ECUDA;
+}
+
+#define TRS_CK(call)                                              \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);       \
+    } while (0)
+
+#define TRS_TRY(expr)               \
+    do {                            \
+        int s_ = (expr);            \
+        if (s_ != TRS_OK) return s_; \
+    } while (0)
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t n = 0;
+};
+
+int dev_alloc(DevBuf &b, size_t bytes, size_t *total) {
+    if (b.n >= bytes && b.p) return TRS_OK;
+    if (b.p) {
+        cudaDeviceSynchronize();
+        cudaFree(b.p);
+        *total -= b.n;
+        b.p = nullptr;
+        b.n = 0;
+    }
+    if (bytes == 0) return TRS_OK;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        cuda_fail(e, "cudaMalloc");
+        b.p = nullptr;
+        return TRS_ENOMEM;
+    }
+    b.n = bytes;
+    *total += bytes;
+    return TRS_OK;
+}
+
+void dev_free(DevBuf &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.n = 0;
+}
+
+struct PlanEntry {
+    HostPlan host;
+    DevBuf blob;
+    const DevPlan *dev = nullptr;
+    SearchScratch scr{};
+};
+
+struct BatchGraph {
+    cudaGraphExec_t exec = nullptr;
+    size_t staged_bytes = 0;
+};
+
+uint32_t lambda_to_q(float lambda) { return (uint32_t)std::rint((double)lambda * 65536.0); }
+
+int check_frame(const trs_ctx *ctx, int W, int H);
+
+}  // namespace
+
+struct trs_ctx {
+    trs_opts o{};
+    size_t total = 0;
+    int maxC = 0, maxR = 0;
+    // one-frame path
+    DevBuf s1, s2, cnt, vmax, flags, tables, scratch, scal, part, luma_stage, time_stage;
+    // plans by (W, H, n)
+    std::map<std::tuple<int, int, int>, PlanEntry *> plans;
+    // batched path
+    DevBuf arena, desc;
+    void *staging = nullptr;  // pinned host copy of the descriptor blob
+    size_t staging_n = 0;
+    cudaStream_t cap = nullptr;
+    cudaEvent_t copied = nullptr;
+    static constexpr int kStages = 7;
+    cudaEvent_t stage[kStages + 1] = {};  // timing events recorded inside batch graphs
+    bool stage_valid = false;
+    // host-buffer batches: device staging of planes, times and partitions
+    DevBuf hb_luma, hb_time, hb_out;
+    std::map<std::vector<int64_t>, BatchGraph> graphs;
+};
+
+namespace {
+
+int check_frame(const trs_ctx *ctx, int W, int H) {
+    if (W <= 0 || H <= 0 || W > ctx->o.max_width || H > ctx->o.max_height) return TRS_EINVAL;
+    return TRS_OK;
+}
+
+int get_plan(trs_ctx *ctx, int W, int H, int n, PlanEntry **out) {
+    auto key = std::make_tuple(W, H, n);
+    auto it = ctx->plans.find(key);
+    if (it != ctx->plans.end()) {
+        *out = it->second;
+        return TRS_OK;
+    }
+    PlanEntry *e = new PlanEntry();
+    int s = build_plan(W, H, n, ctx->o.k_area, &e->host);
+    if (s != TRS_OK) {
+        delete e;
+        return s;
+    }
+    std::vector<uint8_t> blob;
+    s = dev_alloc(e->blob, plan_blob_bytes(e->host), &ctx->total);
+    if (s != TRS_OK) {
+        delete e;
+        return s;
+    }
+    plan_serialize(e->host, (uint8_t *)e->blob.p, blob);
+    cudaError_t ce = cudaMemcpy(e->blob.p, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) {
+        ctx->total -= e->blob.n;
+        dev_free(e->blob);
+        delete e;
+        return cuda_fail(ce, "plan upload");
+    }
+    e->dev = (const DevPlan *)e->blob.p;
+    e->scr = scratch_layout(e->host);
+    ctx->plans[key] = e;
+    *out = e;
+    return TRS_OK;
+}
+
+size_t stats_bytes(int C, int R) {
+    return align256((size_t)R * C * 4) * 3 + align256((size_t)R * C * 8) + 256;
+}
+
+}  // namespace
+
+extern "C" {
+
+int trs_version(void) { return TRS_ABI_VERSION; }
+
+const char *trs_strerror(int status) {
+    switch (status) {
+        case TRS_OK: return "ok";
+        case TRS_EINVAL: return "invalid argument";
+        case TRS_ERANGE: return "sample or time out of range";
+        case TRS_EINFEASIBLE: return "no partition satisfies the area rule";
+        case TRS_ENOMEM: return "out of memory or beyond the context's limits";
+        case TRS_EBUSY: return "admission refused";
+        case TRS_ETIMEOUT: return "a bounded wait gave up";
+        case TRS_ECUDA: return "CUDA runtime error";
+        default: return "unknown status";
+    }
+}
+
+const char *trs_last_error(void) { return g_err; }
+
+size_t trs_sizeof(const char *name) {
+    if (!name) return 0;
+    if (!std::strcmp(name, "trs_opts")) return sizeof(trs_opts);
+    if (!std::strcmp(name, "trs_ctu_stats")) return sizeof(trs_ctu_stats);
+    if (!std::strcmp(name, "trs_tables_layout")) return sizeof(trs_tables_layout);
+    if (!std::strcmp(name, "trs_partition")) return sizeof(trs_partition);
+    if (!std::strcmp(name, "trs_frame_desc")) return sizeof(trs_frame_desc);
+    return 0;
+}
+
+int trs_plan_work(int width, int height, int n, int k, double *row_relax, double *col_relax) {
+    if (!row_relax || !col_relax) return TRS_EINVAL;
+    HostPlan p;
+    TRS_TRY(build_plan(width, height, n, k, &p));
+    double rows = 0.0, cols = 0.0;
+    for (const PlanItem &it : p.items) {
+        double per_k = 0.0;
+        for (int y = 0; y < p.R; ++y)
+            for (int y1 = y + 1; y1 <= p.R; ++y1) {
+                const uint32_t h = line_px(y1, p.H) - line_px(y, p.H);
+                if (h >= it.hlo && h <= it.hhi) per_k += 1.0;
+            }
+        rows += per_k * it.kmax;
+    }
+    for (size_t w = 0; w < p.win_a.size(); ++w)
+        for (int b = 0; b < p.nb; ++b) {
+            const int32_t slot = p.slot_of[w * p.nb + b];
+            if (slot < 0) continue;
+            const int km = p.items[slot].kmax;
+            for (int kk = 1; kk <= km; ++kk) cols += (double)(p.n - kk + 1);
+        }
+    *row_relax = rows;
+    *col_relax = cols;
+    return TRS_OK;
+}
+
+int trs_plan_stats(int width, int height, int n, int k, int *n_windows, int *n_items) {
+    if (!n_windows || !n_items) return TRS_EINVAL;
+    HostPlan p;
+    TRS_TRY(build_plan(width, height, n, k, &p));
+    *n_windows = (int)p.win_a.size();
+    *n_items = (int)p.items.size();
+    return TRS_OK;
+}
+
+int trs_create(trs_ctx **out, const trs_opts *o) {
+    if (!out || !o) return TRS_EINVAL;
+    *out = nullptr;
+    if (o->max_width < 1 || o->max_width > kCtu * kMaxC || o->max_height < 1 || o->max_height > kCtu * kMaxR ||
+        o->max_regions < 1 || o->max_regions > kMaxN || o->max_batch < 1 || o->k_area < 1)
+        return TRS_EINVAL;
+    TRS_CK(cudaSetDevice(o->device));
+    trs_ctx *c = new trs_ctx();
+    c->o = *o;
+    c->maxC = (o->max_width + kCtu - 1) / kCtu;
+    c->maxR = (o->max_height + kCtu - 1) / kCtu;
+    const size_t cells = (size_t)c->maxC * c->maxR;
+    const int bps = 2;
+    int s = TRS_OK;
+    s = s ? s : dev_alloc(c->s1, cells * 4, &c->total);
+    s = s ? s : dev_alloc(c->s2, cells * 8, &c->total);
+    s = s ? s : dev_alloc(c->cnt, cells * 4, &c->total);
+    s = s ? s : dev_alloc(c->vmax, cells * 4, &c->total);
+    s = s ? s : dev_alloc(c->flags, 256, &c->total);
+    s = s ? s : dev_alloc(c->tables, tables_offsets(c->maxC, c->maxR).bytes, &c->total);
+    s = s ? s : dev_alloc(c->scal, 256, &c->total);
+    s = s ? s : dev_alloc(c->part, sizeof(trs_partition), &c->total);
+    s = s ? s : dev_alloc(c->luma_stage, (size_t)align256((size_t)o->max_width * bps) * o->max_height, &c->total);
+    s = s ? s : dev_alloc(c->time_stage, cells * 4, &c->total);
+    if (s == TRS_OK && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) s = TRS_ECUDA;
+    if (s == TRS_OK && cudaEventCreateWithFlags(&c->copied, cudaEventDisableTiming) != cudaSuccess) s = TRS_ECUDA;
+    for (int i = 0; i <= trs_ctx::kStages && s == TRS_OK; ++i)
+        if (cudaEventCreate(&c->stage[i]) != cudaSuccess) s = TRS_ECUDA;
+    if (s != TRS_OK) {
+        trs_destroy(c);
+        return s;
+    }
+    *out = c;
+    return TRS_OK;
+}
+
+int trs_destroy(trs_ctx *c) {
+    if (!c) return TRS_OK;
+    cudaDeviceSynchronize();
+    for (auto &g : c->graphs)
+        if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
+    for (auto &p : c->plans) {
+        dev_free(p.second->blob);
+        delete p.second;
+    }
+    DevBuf *bufs[] = {&c->s1, &c->s2, &c->cnt, &c->vmax, &c->flags, &c->tables, &c->scratch, &c->scal,
+                      &c->part, &c->luma_stage, &c->time_stage, &c->arena, &c->desc,
+                      &c->hb_luma, &c->hb_time, &c->hb_out};
+    for (DevBuf *b : bufs) dev_free(*b);
+    if (c->staging) cudaFreeHost(c->staging);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->copied) cudaEventDestroy(c->copied);
+    for (int i = 0; i <= trs_ctx::kStages; ++i)
+        if (c->stage[i]) cudaEventDestroy(c->stage[i]);
+    delete c;
+    return TRS_OK;
+}
+
+size_t trs_ctx_bytes(const trs_ctx *c) { return c ? c->total : 0; }
+
+int trs_tables_layout_get(int width, int height, trs_tables_layout *out) {
+    if (!out || width <= 0 || height <= 0) return TRS_EINVAL;
+    const int C = (width + kCtu - 1) / kCtu, R = (height + kCtu - 1) / kCtu;
+    if (C > kMaxC || R > kMaxR) return TRS_EINVAL;
+    const TablesOffsets o = tables_offsets(C, R);
+    out->width = width;
+    out->height = height;
+    out->cols = C;
+    out->rows = R;
+    out->bands = num_bands(C);
+    out->reserved = 0;
+    out->bytes = o.bytes;
+    out->off_tq = o.tq;
+    out->off_sat_s1 = o.sat_s1;
+    out->off_sat_s2 = o.sat_s2;
+    out->off_sat_t = o.sat_t;
+    out->off_rect_t = o.rect_t;
+    out->off_rect_q = o.rect_q;
+    out->off_status = o.status;
+    return TRS_OK;
+}
+
+int trs_texture_map(trs_ctx *ctx, const void *luma, int W, int H, size_t pitch, int bd, const trs_ctu_stats *st,
+                    void *stream) {
+    if (!ctx || !luma || !st || !st->s1 || !st->s2 || !st->count || !st->vmax || !st->flags) return TRS_EINVAL;
+    TRS_TRY(check_frame(ctx, W, H));
+    if (bd < 8 || bd > 12) return TRS_EINVAL;
+    const int bps = bd == 8 ? 1 : 2;
+    if (pitch < (size_t)W * bps) return TRS_EINVAL;
+    LaunchArgs a{};
+    DevFrame &f = a.single;
+    f.luma = (const uint8_t *)luma;
+    f.pitch = pitch;
+    f.W = W;
+    f.H = H;
+    f.bd = bd;
+    f.vec_ok = ((uintptr_t)luma % 16 == 0) && (pitch % 16 == 0);
+    f.C = (W + kCtu - 1) / kCtu;
+    f.R = (H + kCtu - 1) / kCtu;
+    f.s1 = st->s1;
+    f.s2 = st->s2;
+    f.cnt = st->count;
+    f.vmax = st->vmax;
+    f.flags = st->flags;
+    a.nframes = 1;
+    a.single_ctus = f.C * f.R;
+    TRS_CK(cudaMemsetAsync(st->flags, 0, sizeof(uint32_t), (cudaStream_t)stream));
+    TRS_CK((cudaError_t)launch_texture(a, f.C * f.R, stream));
+    return TRS_OK;
+}
+
+int trs_region_tables(trs_ctx *ctx, const trs_ctu_stats *st, const float *times, int W, int H, void *tables,
+                      size_t tables_bytes, void *stream) {
+    if (!ctx || !st || !st->s1 || !st->s2 || !st->flags || !times || !tables) return TRS_EINVAL;
+    TRS_TRY(check_frame(ctx, W, H));
+    const int C = (W + kCtu - 1) / kCtu, R = (H + kCtu - 1) / kCtu;
+    const TablesOffsets o = tables_offsets(C, R);
+    if (tables_bytes < o.bytes || (uintptr_t)tables % 256) return TRS_EINVAL;
+    LaunchArgs a{};
+    DevFrame &f = a.single;
+    f.W = W;
+    f.H = H;
+    f.C = C;
+    f.R = R;
+    f.times = times;
+    f.s1 = st->s1;
+    f.s2 = st->s2;
+    f.flags = st->flags;
+    f.tables = (uint8_t *)tables;
+    a.nframes = 1;
+    const int groups = (num_bands(C) + kBandsPerBlock - 1) / kBandsPerBlock;
+    a.single_bandgrp = groups;
+    TRS_CK((cudaError_t)launch_tables(a, groups, C, R, stream));
+    return TRS_OK;
+}
+
+static int search_one(trs_ctx *ctx, const void *tables, int W, int H, int n, float lambda, trs_partition *out,
+                      void *stream) {
+    if (!ctx || !tables || !out || (uintptr_t)tables % 256) return TRS_EINVAL;
+    TRS_TRY(check_frame(ctx, W, H));
+    if (n < 1 || n > ctx->o.max_regions) return TRS_EINVAL;
+    if (!std::isfinite(lambda) || lambda < 0.0f || lambda > 1000.0f) return TRS_EINVAL;
+    PlanEntry *pe;
+    TRS_TRY(get_plan(ctx, W, H, n, &pe));
+    TRS_TRY(dev_alloc(ctx->scratch, pe->scr.bytes, &ctx->total));
+    LaunchArgs a{};
+    DevFrame &f = a.single;
+    uint8_t *scr = (uint8_t *)ctx->scratch.p;
+    f.W = W;
+    f.H = H;
+    f.C = pe->host.C;
+    f.R = pe->host.R;
+    f.n = n;
+    f.tables = (uint8_t *)tables;
+    f.plan = pe->dev;
+    f.lambda_q = lambda_to_q(lambda);
+    f.V1 = (uint64_t *)(scr + pe->scr.V1);
+    f.V2 = (uint64_t *)(scr + pe->scr.V2);
+    f.wres1 = (uint64_t *)(scr + pe->scr.w1);
+    f.wres2 = (uint64_t *)(scr + pe->scr.w2);
+    f.H2 = (uint64_t *)(scr + pe->scr.H2);
+    f.scal = (uint64_t *)ctx->scal.p;
+    f.out = out;
+    a.nframes = 1;
+    const int nitems = (int)pe->host.items.size(), nwin = (int)pe->host.win_a.size();
+    a.single_items = nitems;
+    a.single_windows = nwin;
+    TRS_CK((cudaError_t)launch_search(a, nitems, nwin, f.scal, 4, stream));
+    return TRS_OK;
+}
+
+int trs_search(trs_ctx *ctx, const void *tables, int W, int H, int n, float lambda, trs_partition *out,
+               void *stream) {
+    return search_one(ctx, tables, W, H, n, lambda, out, stream);
+}
+
+int trs_decide(trs_ctx *ctx, const void *luma, int W, int H, size_t pitch, int bd, const float *times, int n,
+               float lambda, trs_partition *out, void *stream) {
+    if (!ctx) return TRS_EINVAL;
+    trs_ctu_stats st{(uint32_t *)ctx->s1.p, (uint64_t *)ctx->s2.p, (uint32_t *)ctx->cnt.p, (uint32_t *)ctx->vmax.p,
+                     (uint32_t *)ctx->flags.p};
+    TRS_TRY(trs_texture_map(ctx, luma, W, H, pitch, bd, &st, stream));
+    TRS_TRY(trs_region_tables(ctx, &st, times, W, H, ctx->tables.p, ctx->tables.n, stream));
+    return search_one(ctx, ctx->tables.p, W, H, n, lambda, out, stream);
+}
+
+int trs_decide_host(trs_ctx *ctx, const void *luma_host, int W, int H, size_t pitch, int bd,
+                    const float *times_host, int n, float lambda, trs_partition *out_host, void *stream) {
+    if (!ctx || !luma_host || !times_host || !out_host) return TRS_EINVAL;
+    TRS_TRY(check_frame(ctx, W, H));
+    if (bd < 8 || bd > 12) return TRS_EINVAL;
+    const int bps = bd == 8 ? 1 : 2;
+    if (pitch < (size_t)W * bps) return TRS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t dpitch = align256((size_t)W * bps);
+    const int C = (W + kCtu - 1) / kCtu, R = (H + kCtu - 1) / kCtu;
+    TRS_CK(cudaMemcpy2DAsync(ctx->luma_stage.p, dpitch, luma_host, pitch, (size_t)W * bps, H, cudaMemcpyHostToDevice,
+                             s));
+    TRS_CK(cudaMemcpyAsync(ctx->time_stage.p, times_host, (size_t)R * C * sizeof(float), cudaMemcpyHostToDevice, s));
+    TRS_TRY(trs_decide(ctx, ctx->luma_stage.p, W, H, dpitch, bd, (const float *)ctx->time_stage.p, n, lambda,
+                       (trs_partition *)ctx->part.p, stream));
+    TRS_CK(cudaMemcpyAsync(out_host, ctx->part.p, sizeof(trs_partition), cudaMemcpyDeviceToHost, s));
+    TRS_CK(cudaStreamSynchronize(s));
+    return TRS_OK;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Batched path                                                           */
+
+int trs_batch_decide(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partition *out, void *stream) {
+    if (!ctx || !fd || !out || nf < 1 || nf > ctx->o.max_batch) return TRS_EINVAL;
+    std::vector<PlanEntry *> pe(nf);
+    std::vector<int64_t> key;
+    key.reserve((size_t)nf * 5 + 1);
+    key.push_back(nf);
+    for (int i = 0; i < nf; ++i) {
+        const trs_frame_desc &d = fd[i];
+        if (!d.luma_dev || !d.ctu_time_dev) return TRS_EINVAL;
+        TRS_TRY(check_frame(ctx, d.width, d.height));
+        if (d.bit_depth < 8 || d.bit_depth > 12) return TRS_EINVAL;
+        const int bps = d.bit_depth == 8 ? 1 : 2;
+        if (d.pitch_bytes < (size_t)d.width * bps) return TRS_EINVAL;
+        if (d.n_regions < 1 || d.n_regions > ctx->o.max_regions) return TRS_EINVAL;
+        if (!std::isfinite(d.lambda) || d.lambda < 0.0f || d.lambda > 1000.0f) return TRS_EINVAL;
+        TRS_TRY(get_plan(ctx, d.width, d.height, d.n_regions, &pe[i]));
+        const int vec = ((uintptr_t)d.luma_dev % 16 == 0) && (d.pitch_bytes % 16 == 0);
+        key.push_back(d.width);
+        key.push_back(d.height);
+        key.push_back(d.bit_depth);
+        key.push_back(d.n_regions);
+        key.push_back(vec);
+    }
+    // arena layout: flags [nf] | scal [nf][4] | per frame: stats, tables, search scratch
+    size_t off = 0;
+    const size_t flags_off = off;
+    off = align256(off + (size_t)nf * 4);
+    const size_t scal_off = off;
+    off = align256(off + (size_t)nf * 4 * 8);
+    std::vector<size_t> fo(nf);
+    for (int i = 0; i < nf; ++i) {
+        fo[i] = off;
+        const HostPlan &hp = pe[i]->host;
+        off += stats_bytes(hp.C, hp.R) + tables_offsets(hp.C, hp.R).bytes + pe[i]->scr.bytes;
+    }
+    if (ctx->arena.n < off) {
+        for (auto &g : ctx->graphs)
+            if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
+        ctx->graphs.clear();
+        TRS_TRY(dev_alloc(ctx->arena, off + off / 4, &ctx->total));
+    }
+    // descriptor blob: DevFrame[nf] | prefixes ctus, bandgrp, items, windows [nf+1]
+    const size_t fr_bytes = align256((size_t)nf * sizeof(DevFrame));
+    const size_t pre_bytes = align256((size_t)(nf + 1) * 4);
+    const size_t blob = fr_bytes + 4 * pre_bytes;
+    if (ctx->desc.n < blob) {
+        for (auto &g : ctx->graphs)
+            if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
+        ctx->graphs.clear();
+        TRS_TRY(dev_alloc(ctx->desc, blob * 2, &ctx->total));
+    }
+    if (ctx->staging_n < blob) {
+        TRS_CK(cudaEventSynchronize(ctx->copied));
+        if (ctx->staging) cudaFreeHost(ctx->staging);
+        ctx->staging = nullptr;
+        ctx->staging_n = 0;
+        for (auto &g : ctx->graphs)
+            if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
+        ctx->graphs.clear();
+        TRS_CK(cudaMallocHost(&ctx->staging, blob * 2));
+        ctx->staging_n = blob * 2;
+    }
+    // the previous replay must have read the staging blob before it is rewritten
+    TRS_CK(cudaEventSynchronize(ctx->copied));
+    uint8_t *hb = (uint8_t *)ctx->staging;
+    DevFrame *hf = (DevFrame *)hb;
+    int32_t *pc = (int32_t *)(hb + fr_bytes), *pg = (int32_t *)(hb + fr_bytes + pre_bytes);
+    int32_t *pi = (int32_t *)(hb + fr_bytes + 2 * pre_bytes), *pw = (int32_t *)(hb + fr_bytes + 3 * pre_bytes);
+    uint8_t *ab = (uint8_t *)ctx->arena.p;
+    pc[0] = pg[0] = pi[0] = pw[0] = 0;
+    int maxC = 1, maxR = 1;
+    for (int i = 0; i < nf; ++i) {
+        const trs_frame_desc &d = fd[i];
+        const HostPlan &hp = pe[i]->host;
+        DevFrame f{};
+        const int C = hp.C, R = hp.R, cells = C * R;
+        uint8_t *p = ab + fo[i];
+        f.luma = (const uint8_t *)d.luma_dev;
+        f.pitch = d.pitch_bytes;
+        f.W = d.width;
+        f.H = d.height;
+        f.bd = d.bit_depth;
+        f.vec_ok = ((uintptr_t)d.luma_dev % 16 == 0) && (d.pitch_bytes % 16 == 0);
+        f.times = d.ctu_time_dev;
+        f.s1 = (uint32_t *)p;
+        f.cnt = (uint32_t *)(p + align256((size_t)cells * 4));
+        f.vmax = (uint32_t *)(p + 2 * align256((size_t)cells * 4));
+        f.s2 = (uint64_t *)(p + 3 * align256((size_t)cells * 4));
+        p += stats_bytes(C, R);
+        f.flags = (uint32_t *)(ab + flags_off) + i;
+        f.tables = p;
+        p += tables_offsets(C, R).bytes;
+        f.plan = pe[i]->dev;
+        f.C = C;
+        f.R = R;
+        f.n = d.n_regions;
+        f.lambda_q = lambda_to_q(d.lambda);
+        f.V1 = (uint64_t *)(p + pe[i]->scr.V1);
+        f.V2 = (uint64_t *)(p + pe[i]->scr.V2);
+        f.wres1 = (uint64_t *)(p + pe[i]->scr.w1);
+        f.wres2 = (uint64_t *)(p + pe[i]->scr.w2);
+        f.H2 = (uint64_t *)(p + pe[i]->scr.H2);
+        f.scal = (uint64_t *)(ab + scal_off) + 4 * i;
+        f.out = out + i;
+        hf[i] = f;
+        pc[i + 1] = pc[i] + cells;
+        pg[i + 1] = pg[i] + (num_bands(C) + kBandsPerBlock - 1) / kBandsPerBlock;
+        pi[i + 1] = pi[i] + (int)hp.items.size();
+        pw[i + 1] = pw[i] + (int)hp.win_a.size();
+        maxC = C > maxC ? C : maxC;
+        maxR = R > maxR ? R : maxR;
+    }
+    BatchGraph &g = ctx->graphs[key];
+    if (!g.exec) {
+        uint8_t *db = (uint8_t *)ctx->desc.p;
+        LaunchArgs a{};
+        a.frames = (const DevFrame *)db;
+        a.nframes = nf;
+        a.pre.ctus = (const int32_t *)(db + fr_bytes);
+        a.pre.bandgrp = (const int32_t *)(db + fr_bytes + pre_bytes);
+        a.pre.items = (const int32_t *)(db + fr_bytes + 2 * pre_bytes);
+        a.pre.windows = (const int32_t *)(db + fr_bytes + 3 * pre_bytes);
+        cudaStream_t cs = ctx->cap;
+        TRS_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        int rc = TRS_OK;
+        cudaError_t e = cudaMemcpyAsync(db, hb, blob, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(ctx->copied, cs, cudaEventRecordExternal);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ab + flags_off, 0, (size_t)nf * 4, cs);
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(ctx->stage[0], cs, cudaEventRecordExternal);
+        if (e == cudaSuccess) e = (cudaError_t)launch_texture(a, pc[nf], cs);
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(ctx->stage[1], cs, cudaEventRecordExternal);
+        if (e == cudaSuccess) e = (cudaError_t)launch_tables(a, pg[nf], maxC, maxR, cs);
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(ctx->stage[2], cs, cudaEventRecordExternal);
+        if (e == cudaSuccess)
+            e = (cudaError_t)launch_search(a, pi[nf], pw[nf], (uint64_t *)(ab + scal_off), (size_t)nf * 4, cs,
+                                           ctx->stage + 3);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "batch graph capture");
+            ctx->graphs.erase(key);
+            return rc;
+        }
+        g.staged_bytes = blob;
+    }
+    TRS_CK(cudaGraphLaunch(g.exec, (cudaStream_t)stream));
+    ctx->stage_valid = true;
+    return TRS_OK;
+}
+
+int trs_batch_stage_ms(trs_ctx *ctx, float *ms, int max_stages) {
+    if (!ctx || !ms || max_stages < 1) return 0;
+    if (!ctx->stage_valid) return 0;
+    if (cudaEventSynchronize(ctx->stage[trs_ctx::kStages]) != cudaSuccess) return 0;
+    int k = 0;
+    for (; k < trs_ctx::kStages && k < max_stages; ++k) {
+        float v = 0.0f;
+        if (cudaEventElapsedTime(&v, ctx->stage[k], ctx->stage[k + 1]) != cudaSuccess) return k;
+        ms[k] = v;
+    }
+    return k;
+}
+
+int trs_batch_decide_host(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partition *out_host, void *stream) {
+    if (!ctx || !fd || !out_host || nf < 1 || nf > ctx->o.max_batch) return TRS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<size_t> lo(nf), to(nf), dp(nf);
+    size_t lb = 0, tb = 0;
+    for (int i = 0; i < nf; ++i) {
+        const trs_frame_desc &d = fd[i];
+        if (!d.luma_dev || !d.ctu_time_dev) return TRS_EINVAL;
+        TRS_TRY(check_frame(ctx, d.width, d.height));
+        if (d.bit_depth < 8 || d.bit_depth > 12) return TRS_EINVAL;
+        const int bps = d.bit_depth == 8 ? 1 : 2;
+        if (d.pitch_bytes < (size_t)d.width * bps) return TRS_EINVAL;
+        dp[i] = align256((size_t)d.width * bps);
+        lo[i] = lb;
+        lb += dp[i] * d.height;
+        to[i] = tb;
+        tb += align256((size_t)((d.width + kCtu - 1) / kCtu) * ((d.height + kCtu - 1) / kCtu) * 4);
+    }
+    TRS_TRY(dev_alloc(ctx->hb_luma, lb, &ctx->total));
+    TRS_TRY(dev_alloc(ctx->hb_time, tb, &ctx->total));
+    TRS_TRY(dev_alloc(ctx->hb_out, (size_t)ctx->o.max_batch * sizeof(trs_partition), &ctx->total));
+    std::vector<trs_frame_desc> dd(fd, fd + nf);
+    for (int i = 0; i < nf; ++i) {
+        const trs_frame_desc &d = fd[i];
+        const int bps = d.bit_depth == 8 ? 1 : 2;
+        uint8_t *dl = (uint8_t *)ctx->hb_luma.p + lo[i];
+        uint8_t *dt = (uint8_t *)ctx->hb_time.p + to[i];
+        const size_t cells = (size_t)((d.width + kCtu - 1) / kCtu) * ((d.height + kCtu - 1) / kCtu);
+        TRS_CK(cudaMemcpy2DAsync(dl, dp[i], d.luma_dev, d.pitch_bytes, (size_t)d.width * bps, d.height,
+                                 cudaMemcpyHostToDevice, s));
+        TRS_CK(cudaMemcpyAsync(dt, d.ctu_time_dev, cells * 4, cudaMemcpyHostToDevice, s));
+        dd[i].luma_dev = dl;
+        dd[i].pitch_bytes = dp[i];
+        dd[i].ctu_time_dev = (const float *)dt;
+    }
+    TRS_TRY(trs_batch_decide(ctx, dd.data(), nf, (trs_partition *)ctx->hb_out.p, stream));
+    TRS_CK(cudaMemcpyAsync(out_host, ctx->hb_out.p, (size_t)nf * sizeof(trs_partition), cudaMemcpyDeviceToHost, s));
+    TRS_CK(cudaStreamSynchronize(s));
+    return TRS_OK;
+}
+
+}  // extern "C"

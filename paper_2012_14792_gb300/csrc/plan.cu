@@ -1,0 +1,145 @@
+// Search plan of a frame shape: which area windows exist and which row-DP
+// units ("items") the windows of every tile column reduce to.  It depends on
+// (W, H, n, k) only -- never on frame content -- and is built once per shape,
+// like the launch geometry of the kernels.
+//
+// Windows (Sec. 2.3's rule k*A_min > A_max made local): every slice area a
+// with a*n <= W*H and (k*a - 1)*n >= W*H gives the window [a, k*a - 1]; a
+// partition meets the rule iff all its slice areas fit one such window.
+//
+// Items: for tile column b of pixel width w and window [a, k*a-1], a slice of
+// pixel height h is admissible iff a <= w*h <= k*a-1.  Slice heights come
+// from a short sorted list, so the admissible heights are a range [hlo, hhi]
+// of that list.  Consecutive windows often give a column the same range;
+// each distinct (column, range) becomes one item, shared by those windows.
+#include <algorithm>
+#include <cstdint>
+#include <set>
+#include <vector>
+
+#include "plan.h"
+
+namespace trs {
+
+static std::vector<uint32_t> extents(int cells, int total) {
+    // distinct pixel lengths of runs of whole CTUs [i, j) with the last CTU clipped
+    std::set<uint32_t> s;
+    for (int i = 0; i < cells; ++i)
+        for (int j = i + 1; j <= cells; ++j) s.insert(line_px(j, total) - line_px(i, total));
+    return std::vector<uint32_t>(s.begin(), s.end());
+}
+
+int build_plan(int W, int H, int n, int k, HostPlan *p) {
+    if (W <= 0 || H <= 0 || n < 1 || n > kMaxN || k < 1) return TRS_EINVAL;
+    const int C = (W + kCtu - 1) / kCtu, R = (H + kCtu - 1) / kCtu;
+    if (C > kMaxC || R > kMaxR) return TRS_EINVAL;
+    p->W = W;
+    p->H = H;
+    p->C = C;
+    p->R = R;
+    p->n = n;
+    p->k = k;
+    p->nb = num_bands(C);
+    p->A = (uint64_t)W * (uint64_t)H;
+    const std::vector<uint32_t> ws = extents(C, W), hs = extents(R, H);
+    std::set<uint64_t> wins;
+    for (uint32_t w : ws)
+        for (uint32_t h : hs) {
+            const uint64_t a = (uint64_t)w * h;
+            if (a * (uint64_t)n <= p->A && ((uint64_t)k * a - 1) * (uint64_t)n >= p->A) wins.insert(a);
+        }
+    p->win_a.assign(wins.begin(), wins.end());
+    const int nwin = (int)p->win_a.size();
+    p->band_x0.resize(p->nb);
+    p->band_x1.resize(p->nb);
+    for (int x0 = 0; x0 < C; ++x0)
+        for (int x1 = x0 + 1; x1 <= C; ++x1) {
+            const int b = band_index(C, x0, x1);
+            p->band_x0[b] = (int16_t)x0;
+            p->band_x1[b] = (int16_t)x1;
+        }
+    p->items.clear();
+    p->slot_of.assign((size_t)nwin * p->nb, -1);
+    for (int b = 0; b < p->nb; ++b) {
+        const uint64_t wb = line_px(p->band_x1[b], W) - line_px(p->band_x0[b], W);
+        int prev_lo = -1, prev_hi = -1, prev_slot = -1;
+        for (int wi = 0; wi < nwin; ++wi) {
+            const uint64_t lo = p->win_a[wi], hi = (uint64_t)k * lo - 1;
+            // admissible heights: lo <= wb*h <= hi
+            int ilo = 0;
+            while (ilo < (int)hs.size() && wb * hs[ilo] < lo) ++ilo;
+            int ihi = (int)hs.size() - 1;
+            while (ihi >= 0 && wb * hs[ihi] > hi) --ihi;
+            if (ilo > ihi) continue;
+            if (ilo == prev_lo && ihi == prev_hi) {
+                p->slot_of[(size_t)wi * p->nb + b] = prev_slot;
+                continue;
+            }
+            PlanItem it;
+            it.b = b;
+            it.hlo = hs[ilo];
+            it.hhi = hs[ihi];
+            it.kmax = std::min(std::min(n, R), (int)(H / it.hlo));
+            prev_lo = ilo;
+            prev_hi = ihi;
+            prev_slot = (int)p->items.size();
+            p->items.push_back(it);
+            p->slot_of[(size_t)wi * p->nb + b] = prev_slot;
+        }
+    }
+    return TRS_OK;
+}
+
+size_t plan_blob_bytes(const HostPlan &p) {
+    size_t s = align256(sizeof(DevPlan));
+    s += align256(p.win_a.size() * sizeof(uint64_t) + 8);
+    s += align256(p.items.size() * sizeof(PlanItem) + 16);
+    s += align256(p.slot_of.size() * sizeof(int32_t) + 4);
+    s += 2 * align256(p.band_x0.size() * sizeof(int16_t) + 2);
+    return s;
+}
+
+void plan_serialize(const HostPlan &p, uint8_t *dev_base, std::vector<uint8_t> &blob) {
+    blob.assign(plan_blob_bytes(p), 0);
+    size_t off = align256(sizeof(DevPlan));
+    DevPlan d;
+    d.W = p.W;
+    d.H = p.H;
+    d.C = p.C;
+    d.R = p.R;
+    d.n = p.n;
+    d.k = p.k;
+    d.nb = p.nb;
+    d.nwin = (int)p.win_a.size();
+    d.nitems = (int)p.items.size();
+    d.A = p.A;
+    auto put = [&](const void *src, size_t bytes, size_t pad) -> const void * {
+        std::copy((const uint8_t *)src, (const uint8_t *)src + bytes, blob.begin() + off);
+        const void *dp = dev_base + off;
+        off += align256(bytes + pad);
+        return dp;
+    };
+    d.win_a = (const uint64_t *)put(p.win_a.data(), p.win_a.size() * sizeof(uint64_t), 8);
+    d.items = (const PlanItem *)put(p.items.data(), p.items.size() * sizeof(PlanItem), 16);
+    d.slot_of = (const int32_t *)put(p.slot_of.data(), p.slot_of.size() * sizeof(int32_t), 4);
+    d.band_x0 = (const int16_t *)put(p.band_x0.data(), p.band_x0.size() * sizeof(int16_t), 2);
+    d.band_x1 = (const int16_t *)put(p.band_x1.data(), p.band_x1.size() * sizeof(int16_t), 2);
+    std::copy((const uint8_t *)&d, (const uint8_t *)&d + sizeof(d), blob.begin());
+}
+
+// Per-frame search scratch of a plan, in bytes (256-aligned pieces).
+SearchScratch scratch_layout(const HostPlan &p) {
+    SearchScratch s;
+    const size_t v = (size_t)p.items.size() * (p.n + 1) * 8;
+    const size_t nw = p.win_a.size();
+    size_t o = 0;
+    s.V1 = o;    o += align256(v + 8);
+    s.V2 = o;    o += align256(v + 8);
+    s.w1 = o;    o += align256(nw * 8 + 8);
+    s.w2 = o;    o += align256(nw * 8 + 8);
+    s.H2 = o;    o += align256(nw * (size_t)(p.C + 1) * (p.n + 1) * 8 + 8);
+    s.bytes = o;
+    return s;
+}
+
+}  // namespace trs

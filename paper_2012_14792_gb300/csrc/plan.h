@@ -1,0 +1,30 @@
+// Host-side search plans (see plan.cpp).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "trs_internal.cuh"
+
+namespace trs {
+
+struct HostPlan {
+    int W = 0, H = 0, C = 0, R = 0, n = 0, k = 0, nb = 0;
+    uint64_t A = 0;
+    std::vector<uint64_t> win_a;
+    std::vector<PlanItem> items;
+    std::vector<int32_t> slot_of;
+    std::vector<int16_t> band_x0, band_x1;
+};
+
+struct SearchScratch {
+    size_t V1, V2, w1, w2, H2, bytes;
+};
+
+int build_plan(int W, int H, int n, int k, HostPlan *p);
+size_t plan_blob_bytes(const HostPlan &p);
+// Lays the plan out as a device blob whose pointers assume it will be copied to dev_base.
+void plan_serialize(const HostPlan &p, uint8_t *dev_base, std::vector<uint8_t> &blob);
+SearchScratch scratch_layout(const HostPlan &p);
+
+}  // namespace trs

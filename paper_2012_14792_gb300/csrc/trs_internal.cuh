@@ -1,0 +1,178 @@
+// Internal declarations shared by the CUDA translation units of libtrs.
+//
+// Frame geometry: CTUs of 128x128 luma samples, C = ceil(W/128) columns,
+// R = ceil(H/128) rows, the last column/row clipped to the frame.  A tile
+// column ("band") spans CTU columns [x0, x1); its compact index is
+// b = x0*(2C - x0 + 1)/2 + (x1 - x0 - 1).  A slice of a band spans CTU rows
+// [y, y + d).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/trs.h"
+
+namespace trs {
+
+constexpr uint64_t kInf = ~0ull;
+constexpr int kCtu = TRS_CTU;
+constexpr int kMaxC = TRS_MAX_COLS;
+constexpr int kMaxR = TRS_MAX_ROWS;
+constexpr int kMaxN = TRS_MAX_REGIONS;
+
+__host__ __device__ inline int band_index(int C, int x0, int x1) {
+    return x0 * (2 * C - x0 + 1) / 2 + (x1 - x0 - 1);
+}
+__host__ __device__ inline int num_bands(int C) { return C * (C + 1) / 2; }
+// Pixel extent of CTU lines: position of line x (clipped to the frame edge).
+__host__ __device__ inline uint32_t line_px(int x, int extent) {
+    uint32_t p = (uint32_t)x * kCtu;
+    return p < (uint32_t)extent ? p : (uint32_t)extent;
+}
+
+// Offsets of one frame's region tables inside its buffer (all 256-aligned).
+struct TablesOffsets {
+    size_t tq, sat_s1, sat_s2, sat_t, rect_t, rect_q, status, bytes;
+};
+__host__ __device__ inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+__host__ __device__ inline TablesOffsets tables_offsets(int C, int R) {
+    TablesOffsets o;
+    size_t p = 0;
+    const size_t sat = (size_t)(R + 1) * (C + 1) * 8;
+    const size_t rect = (size_t)num_bands(C) * R * R * 8;
+    o.tq = p;      p = align256(p + (size_t)R * C * 4);
+    o.sat_s1 = p;  p = align256(p + sat);
+    o.sat_s2 = p;  p = align256(p + sat);
+    o.sat_t = p;   p = align256(p + sat);
+    o.rect_t = p;  p = align256(p + rect);
+    o.rect_q = p;  p = align256(p + rect);
+    o.status = p;  p = align256(p + 16);
+    o.bytes = p;
+    return o;
+}
+
+#ifdef __CUDACC__
+// ceil(s1^2 / n) for n < 2^32 when the quotient fits 64 bits (it is at most
+// S2 by Cauchy-Schwarz); *rem = s1^2 mod n.  128-bit square, long division
+// by 32-bit digits.
+__device__ inline uint64_t ceil_square_div(uint64_t s1, uint32_t n, uint32_t *rem) {
+    const uint64_t lo = s1 * s1;
+    const uint64_t hi = __umul64hi(s1, s1);
+    uint64_t r = hi % n;
+    const uint64_t t1 = (r << 32) | (lo >> 32);
+    const uint64_t q1 = t1 / n;
+    r = t1 - q1 * n;
+    const uint64_t t2 = (r << 32) | (lo & 0xffffffffull);
+    const uint64_t q0 = t2 / n;
+    r = t2 - q0 * n;
+    *rem = (uint32_t)r;
+    return (q1 << 32) + q0 + (r != 0 ? 1u : 0u);
+}
+
+// Largest T with T * 65536 <= t_min * (65536 + lambda_q)  (Eq. 4).
+__device__ inline uint64_t eq4_threshold(uint64_t t_min, uint32_t lambda_q) {
+    if (t_min == kInf) return kInf;
+    const uint64_t m = 65536ull + lambda_q;
+    const uint64_t lo = t_min * m, hi = __umul64hi(t_min, m);
+    if (hi >> 16) return kInf;
+    return (lo >> 16) | (hi << 48);
+}
+#endif
+
+// One unit of row-DP work of the search: tile column b whose slices must
+// have a pixel height in [hlo, hhi] (the slice heights that land in the area
+// window of every window mapped to this unit).  kmax bounds the slice count.
+struct PlanItem {
+    int32_t b;
+    int32_t kmax;
+    uint32_t hlo, hhi;
+};
+
+// Search plan of one frame shape (W, H, n, k), built on the host once per
+// shape and kept in device memory.  Depends on geometry only.
+struct DevPlan {
+    int W, H, C, R, n, k, nb, nwin, nitems;
+    uint64_t A;                 // W*H
+    const uint64_t *win_a;      // [nwin] window lower bounds a (window = [a, k*a-1]), ascending
+    const PlanItem *items;      // [nitems]
+    const int32_t *slot_of;     // [nwin * nb]: item of (window, band), -1 if the band has no slice there
+    const int16_t *band_x0;     // [nb]
+    const int16_t *band_x1;     // [nb]
+};
+
+// Everything a kernel needs about one frame.  Lives in device memory for
+// batched launches, or travels by value inside LaunchArgs for one frame.
+struct DevFrame {
+    // a1 input
+    const uint8_t *luma;
+    size_t pitch;
+    int W, H, bd, vec_ok;  // vec_ok: base and pitch 16-byte aligned
+    // a2 input
+    const float *times;
+    // a1 output / a2 input
+    uint32_t *s1;
+    uint64_t *s2;
+    uint32_t *cnt;
+    uint32_t *vmax;
+    uint32_t *flags;
+    // a2 output / search input
+    uint8_t *tables;
+    // search
+    const DevPlan *plan;  // device pointer
+    int C, R, n;
+    uint32_t lambda_q;
+    uint64_t *V1, *V2;      // [nitems][n+1]
+    uint64_t *wres1, *wres2;  // [nwin]
+    uint64_t *H2;           // [nwin][(C+1)*(n+1)]
+    uint64_t *scal;         // [0] T_min, [1] Q*, [2] thr, [3] spare
+    trs_partition *out;
+};
+
+// Work prefix sums over the frames of a launch (exclusive, nframes+1 entries).
+struct WorkPrefix {
+    const int32_t *ctus;     // texture: CTUs
+    const int32_t *bandgrp;  // tables: groups of kBandsPerBlock bands
+    const int32_t *items;    // search rows: plan items
+    const int32_t *windows;  // search columns: plan windows
+};
+
+constexpr int kBandsPerBlock = 8;
+
+struct LaunchArgs {
+    DevFrame single;            // used when frames == nullptr
+    const DevFrame *frames;     // device array of nframes, or nullptr
+    int nframes;
+    WorkPrefix pre;             // device arrays (unused when nframes == 1 and frames == nullptr)
+    int single_ctus, single_bandgrp, single_items, single_windows;
+};
+
+__device__ inline const DevFrame &frame_at(const LaunchArgs &a, int f) {
+    return a.frames ? a.frames[f] : a.single;
+}
+
+// Maps a global work index to (frame, local index) through a prefix array.
+__device__ inline int locate(const LaunchArgs &a, const int32_t *pre, int single_count, int g, int *local) {
+    if (!a.frames) {
+        *local = g;
+        return 0;
+    }
+    int lo = 0, hi = a.nframes - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    *local = g - pre[lo];
+    return lo;
+}
+
+// Launchers (return cudaError_t as int).
+int launch_texture(const LaunchArgs &a, int total_ctus, void *stream);
+int launch_tables(const LaunchArgs &a, int total_groups, int maxC, int maxR, void *stream);
+// scal: the T_min / Q* words of every frame of the launch (reset to +inf first).
+// ev (optional, 5 events): recorded after each of the five search kernels.
+int launch_search(const LaunchArgs &a, int total_items, int total_windows, uint64_t *scal, size_t nscal,
+                  void *stream, cudaEvent_t *ev = nullptr);
+
+}  // namespace trs

@@ -18,6 +18,7 @@ from .frames import (  # noqa: F401
     mixed_batch,
     poisson_arrivals,
     sequence_2160p_blob,
+    sequence_2160p_frame,
     serving_streams,
     small_frame,
     time_map,

@@ -149,30 +149,48 @@ def make_frame(spec: FrameSpec, seed: int, stream: int = 0, frame: int = 0,
     return plane, times
 
 
-def sequence_2160p_blob(nframes: int = 64, seed: int = 2160):
-    """The moving-blob UHD sequence: yields (plane, times) per frame.
+def _blob_at(f: int) -> tuple[float, float, float, float]:
+    # the disk moves 32 px per frame to the right with a slow vertical swing
+    # (a triangle wave, integer arithmetic only)
+    phase = f % 32
+    swing = (phase if phase < 16 else 32 - phase) * 24 - 192
+    return (512.0 + 32.0 * f, 1080.0 + float(swing), 384.0, 40.0)
 
-    The patch background is drawn once; noise is redrawn per frame; the disk
-    centre moves 32 px per frame to the right with a slow vertical swing.
-    Frame f's time map comes from frame f-1's latent complexity.
-    """
+
+def _latent_map(p: dict, spec: FrameSpec, blob) -> np.ndarray:
+    ph, pw = p["kind"].shape
+    lat = np.broadcast_to(_patch_latent(p)[:, None, :, None], (ph, PATCH, pw, PATCH))
+    lat = lat.reshape(ph * PATCH, pw * PATCH)[: spec.height, : spec.width].astype(np.float32)
+    if blob is not None:
+        cx, cy, radius, sigma = blob
+        yy = np.arange(spec.height, dtype=np.float32)[:, None]
+        xx = np.arange(spec.width, dtype=np.float32)[None, :]
+        inside = (xx - cx) ** 2 + (yy - cy) ** 2 <= radius * radius
+        lat = np.where(inside, np.float32(sigma * sigma), lat)
+    return lat
+
+
+def sequence_2160p_frame(f: int, seed: int = 2160) -> tuple[np.ndarray, np.ndarray]:
+    """Frame f of the moving-blob UHD sequence and its time map.
+
+    The patch background is drawn once per sequence; noise is redrawn per
+    frame; frame f's time map comes from frame f-1's latent complexity
+    (frame 0 uses its own).  Frames can be drawn independently."""
     spec = SPEC_2160P10
     ph = (spec.height + PATCH - 1) // PATCH
     pw = (spec.width + PATCH - 1) // PATCH
     wid = _WORKLOAD_IDS["seq2160"]
     p = _patch_params(_rng(wid, seed, 0, 0, 0), ph, pw)
-    prev_lat = None
+    plane, _ = _render(p, spec, _rng(wid, seed, 0, f, 1), _blob_at(f))
+    src = _latent_map(p, spec, _blob_at(max(f - 1, 0)))
+    times = time_map(_ctu_mean(src, spec), _rng(wid, seed, 0, f, 2))
+    return plane, times
+
+
+def sequence_2160p_blob(nframes: int = 64, seed: int = 2160):
+    """The moving-blob UHD sequence: yields (plane, times) per frame."""
     for f in range(nframes):
-        # vertical swing: a triangle wave (integer arithmetic only)
-        phase = f % 32
-        swing = (phase if phase < 16 else 32 - phase) * 24 - 192
-        blob = (512.0 + 32.0 * f, 1080.0 + float(swing), 384.0, 40.0)
-        plane, lat = _render(p, spec, _rng(wid, seed, 0, f, 1), blob)
-        lat_ctu = _ctu_mean(lat, spec)
-        src = lat_ctu if prev_lat is None else prev_lat
-        times = time_map(src, _rng(wid, seed, 0, f, 2))
-        prev_lat = lat_ctu
-        yield plane, times
+        yield sequence_2160p_frame(f, seed)
 
 
 @dataclass

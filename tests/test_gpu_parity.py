@@ -1,0 +1,272 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle: bit-exact
+texture statistics, Q16 times, SATs, rectangle tables and partitions; the
+reported floating-point SSE within 1e-6 relative."""
+
+import numpy as np
+import pytest
+
+import golden_cases
+import synth
+from gpu_helpers import assert_partition_equal, assert_valid_partition
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def dec():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2012_14792_gb300 import runtime
+    d = runtime.Decider(max_width=8192, max_height=4096, max_regions=32, max_batch=64)
+    yield d
+    d.close()
+
+
+def _dev(plane, pad_to=None, offset=0):
+    """Device copy of a plane with an optional row pitch and byte offset."""
+    raw = np.ascontiguousarray(plane).view(np.uint8)
+    H, rb = raw.shape
+    pitch = rb if pad_to is None else pad_to
+    buf = np.zeros(offset + pitch * H + 64, np.uint8)
+    for y in range(H):
+        buf[offset + y * pitch: offset + y * pitch + rb] = raw[y]
+    t = torch.from_numpy(buf).cuda()
+    return t, t.data_ptr() + offset, pitch
+
+
+def _texture(dec, plane, bd, pad_to=None, offset=0):
+    H, W = plane.shape
+    t, ptr, pitch = _dev(plane, pad_to, offset)
+    st = dec.stats_buffers(W, H)
+    dec.texture_map(ptr, W, H, pitch, bd, st)
+    torch.cuda.synchronize()
+    u32 = lambda x: x.cpu().numpy().view(np.uint32)
+    return dict(s1=u32(st["s1"]), s2=st["s2"].cpu().numpy().view(np.uint64), count=u32(st["count"]),
+                vmax=u32(st["vmax"]), flags=int(u32(st["flags"])[0])), st, t
+
+
+@pytest.mark.parametrize("W,H,bd,pad,offset", [
+    (832, 480, 8, None, 0), (1920, 1080, 10, None, 0), (3840, 2160, 10, None, 0),
+    (1000, 700, 10, None, 0), (129, 257, 8, None, 0), (1, 1, 8, None, 0), (130, 3, 12, None, 0),
+    (1920, 1080, 10, 4096, 0), (833, 481, 8, 848, 0),        # padded, aligned pitch
+    (300, 200, 10, 602, 0), (300, 200, 10, None, 2),          # unaligned pitch / base: scalar path
+    (8192, 4096, 10, None, 0),                                # largest frame
+])
+def test_texture_bit_exact(dec, oracle, W, H, bd, pad, offset):
+    rng = np.random.default_rng(W * 7 + H + bd)
+    dt = np.uint8 if bd == 8 else np.uint16
+    plane = rng.integers(0, 2 ** bd, size=(H, W)).astype(dt)
+    got, _, _ = _texture(dec, plane, bd, pad, offset)
+    ref = oracle.texture(plane, bd)
+    assert (got["s1"] == ref.S1.ravel()).all()
+    assert (got["s2"] == ref.S2.ravel()).all()
+    assert (got["count"] == ref.N.ravel()).all()
+    assert (got["vmax"] == ref.vmax.ravel()).all()
+    assert got["flags"] == 0
+
+
+def test_texture_flags_out_of_range_sample(dec, oracle):
+    plane = np.zeros((300, 300), np.uint16)
+    plane[299, 299] = 1024
+    got, _, _ = _texture(dec, plane, 10)
+    assert got["flags"] == 1
+    assert oracle.texture(plane, 10).status == oracle.ERANGE
+
+
+@pytest.mark.parametrize("W,H,seed", [(832, 480, 1), (1920, 1080, 2), (3840, 2160, 3), (200, 520, 4)])
+def test_tables_bit_exact(dec, oracle, W, H, seed):
+    plane, times = synth.small_frame(W, H, 10, seed)
+    _, st, _keep = _texture(dec, plane, 10)
+    tt = torch.from_numpy(times).cuda()
+    tab = dec.tables_buffer(W, H)
+    dec.region_tables(st, tt, W, H, tab)
+    torch.cuda.synchronize()
+    got = dec.read_tables(tab, W, H)
+    ref = oracle.texture(plane, 10)
+    Tq, s = oracle.time_q(times)
+    assert got["status"][0] == 0 and s == 0
+    assert (got["tq"] == Tq).all()
+    assert (got["sat_s1"] == oracle.sat(ref.S1)).all()
+    assert (got["sat_s2"] == oracle.sat(ref.S2)).all()
+    assert (got["sat_t"] == oracle.sat(Tq.astype(np.uint64))).all()
+    R, C = Tq.shape
+    rng = np.random.default_rng(seed)
+    bands = [(x0, x1) for x0 in range(C) for x1 in range(x0 + 1, C + 1)]
+    sample = bands if len(bands) <= 120 else [bands[i] for i in rng.choice(len(bands), 120, replace=False)]
+    for (x0, x1) in sample:
+        b = x0 * (2 * C - x0 + 1) // 2 + (x1 - x0 - 1)
+        for y in range(R):
+            for d in range(1, R - y + 1):
+                t, q = oracle.rect(ref, Tq, x0, x1, y, y + d)
+                assert int(got["rect_t"][b, d - 1, y]) == t
+                assert int(got["rect_q"][b, d - 1, y]) == q
+
+
+@pytest.mark.parametrize("bad", [np.nan, -0.5, 65536.0, np.inf])
+def test_tables_bad_time_sets_erange(dec, bad):
+    plane, times = synth.small_frame(512, 256, 8, 9)
+    times[1, 2] = bad
+    _, st, _keep = _texture(dec, plane, 8)
+    tab = dec.tables_buffer(512, 256)
+    dec.region_tables(st, torch.from_numpy(times).cuda(), 512, 256, tab)
+    out = dec.search(tab, 512, 256, 2, 0.0)
+    p = dec.partitions(out)[0]
+    assert dec.read_tables(tab, 512, 256)["status"][0] == 2
+    assert p.status == 2
+
+
+def _decide(dec, plane, times, bd, n, lam):
+    H, W = plane.shape
+    luma, ptr, pitch = _dev(plane)
+    out = dec.decide(luma, pitch, W, H, bd, torch.from_numpy(np.ascontiguousarray(times, np.float32)).cuda(), n, lam)
+    return dec.partitions(out)[0]
+
+
+@pytest.mark.parametrize("case", golden_cases.cases(), ids=lambda c: c["name"])
+def test_hand_worked_cases(dec, case):
+    lam = case["lambda_q"] / 65536.0
+    p = _decide(dec, golden_cases.plane(case), golden_cases.times(case), case["bit_depth"], case["n"], lam)
+    e = case["expect"]
+    if e.get("infeasible"):
+        assert p.status == 3
+        return
+    assert p.status == 0
+    assert (p.t_min_q, p.t_q, p.q) == (e["t_min"], e["t"], e["q"])
+    assert p.x_edges() == e["x_edges"]
+    assert p.band_cuts() == golden_cases.band_masks(case)
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_random_frames_match_oracle(dec, oracle, seed):
+    rng = np.random.default_rng(500 + seed)
+    W = int(rng.integers(1, 1100))
+    H = int(rng.integers(1, 900))
+    bd = int(rng.choice([8, 10]))
+    n = int(rng.integers(1, 13))
+    lam = float(rng.choice([0.0, 0.05, 0.1, 0.3, 1.0]))
+    plane, times = synth.small_frame(W, H, bd, seed)
+    if seed % 5 == 0:
+        times[:] = 1.0  # uniform times: ties on T
+    if seed % 7 == 0:
+        plane[:] = plane.flat[0]  # flat frame: Q ties, the code decides
+    p = _decide(dec, plane, times, bd, n, lam)
+    d, st, Tq = oracle.decide(plane, times, bd, n, lam)
+    R = st.S1.shape[0]
+    assert_partition_equal(p, d, R)
+    if W * H < 300 * 300 and n <= 5:
+        d1 = oracle.search_enum(st, Tq, n, lam)
+        assert_partition_equal(p, d1, R)
+
+
+@pytest.mark.parametrize("lam", [0.0, 0.1, 0.3])
+@pytest.mark.parametrize("n", [4, 8, 16])
+def test_480p_matches_oracle(dec, oracle, n, lam):
+    for seed in range(3):
+        plane, times = synth.make_frame(synth.SPEC_480P8, seed)
+        p = _decide(dec, plane, times, 8, n, lam)
+        d, st, Tq = oracle.decide(plane, times, 8, n, lam)
+        assert_partition_equal(p, d, 4)
+        if n <= 8:
+            assert_partition_equal(p, oracle.search_enum(st, Tq, n, lam), 4)
+
+
+@pytest.mark.parametrize("n", [4, 8, 12])
+def test_1080p_matches_oracle(dec, oracle, n):
+    for seed in range(3):
+        plane, times = synth.make_frame(synth.SPEC_1080P10, seed)
+        p = _decide(dec, plane, times, 10, n, 0.1)
+        d, _, _ = oracle.decide(plane, times, 10, n, 0.1)
+        assert_partition_equal(p, d, 9)
+
+
+def test_2160p_sequence_matches_oracle(dec, oracle):
+    """Every 8th frame of the moving-blob UHD sequence, n = 16 and 8."""
+    for f, (plane, times) in enumerate(synth.sequence_2160p_blob(64)):
+        if f % 8:
+            continue
+        for n in (16, 8):
+            p = _decide(dec, plane, times, 10, n, 0.1)
+            d, st, Tq = oracle.decide(plane, times, 10, n, 0.1)
+            assert_partition_equal(p, d, 17)
+            assert_valid_partition(oracle, p, st, Tq, n)
+
+
+def test_single_slice_and_infeasible(dec, oracle):
+    plane, times = synth.small_frame(700, 300, 10, 3)
+    p = _decide(dec, plane, times, 10, 1, 0.0)
+    d, _, _ = oracle.decide(plane, times, 10, 1, 0.0)
+    assert_partition_equal(p, d, 3)
+    plane, times = synth.small_frame(256, 128, 8, 3)
+    assert _decide(dec, plane, times, 8, 3, 0.0).status == 3
+
+
+def test_largest_frame_and_n(dec, oracle):
+    plane, times = synth.small_frame(8192, 4096, 10, 11)
+    p = _decide(dec, plane, times, 10, 32, 0.1)
+    d, st, Tq = oracle.decide(plane, times, 10, 32, 0.1)
+    assert_partition_equal(p, d, 32)
+
+
+def test_decide_host_matches_device(dec, oracle):
+    plane, times = synth.make_frame(synth.SPEC_1080P10, 5)
+    p = dec.decide_host(plane, times, 10, 8, 0.1)
+    d, _, _ = oracle.decide(plane, times, 10, 8, 0.1)
+    assert_partition_equal(p, d, 9)
+
+
+def test_invalid_arguments(dec):
+    from paper_2012_14792_gb300 import trs
+    plane, times = synth.small_frame(256, 256, 8, 1)
+    luma, ptr, pitch = _dev(plane)
+    tt = torch.from_numpy(times).cuda()
+    out = torch.zeros(trs.PARTITION_BYTES, dtype=torch.uint8, device="cuda")
+    for args in [(ptr, 256, 256, pitch, 7, tt, 2, 0.0), (ptr, 256, 256, pitch, 8, tt, 0, 0.0),
+                 (ptr, 256, 256, pitch, 8, tt, 33, 0.0), (ptr, 256, 256, pitch, 8, tt, 2, -1.0),
+                 (ptr, 256, 256, 100, 8, tt, 2, 0.0), (ptr, 9000, 256, 9000, 8, tt, 2, 0.0),
+                 (0, 256, 256, pitch, 8, tt, 2, 0.0), (ptr, 256, 256, pitch, 8, tt, 2, float("nan"))]:
+        with pytest.raises(trs.TrsError) as e:
+            trs.trs_decide(dec.ctx, args[0], args[1], args[2], args[3], args[4], args[5], args[6], args[7], out)
+        assert e.value.status == trs.EINVAL
+
+
+def _batch_inputs(items):
+    ins, keep = [], []
+    for it in items:
+        H, W = it.plane.shape
+        luma, ptr, pitch = _dev(it.plane)
+        tt = torch.from_numpy(it.times).cuda()
+        keep += [luma, tt]
+        ins.append((ptr, pitch, W, H, it.spec.bit_depth, tt, it.n_regions, it.lam))
+    return ins, keep
+
+
+def test_batch_matches_plain_and_oracle(dec, oracle):
+    items = synth.mixed_batch(256, seed=4)[:40]
+    ins, keep = _batch_inputs(items)
+    out = dec.batch_decide(ins)
+    ps = dec.partitions(out, len(items))
+    for it, p, (ptr, pitch, W, H, bd, tt, n, lam) in zip(items, ps, ins):
+        q = dec.partitions(dec.decide(ptr, pitch, W, H, bd, tt, n, lam))[0]
+        assert bytes(p) == bytes(q)  # identical alone and in the batch
+        d, _, _ = oracle.decide(it.plane, it.times, bd, n, lam)
+        assert_partition_equal(p, d, it.spec.ctu_rows)
+
+
+def test_batch_graph_replay_with_new_frames(dec, oracle):
+    # same composition twice: the second call replays the captured graph on new inputs
+    a = synth.mixed_batch(256, seed=4)[:12]
+    b = synth.mixed_batch(256, seed=4)[:12]
+    for it, jt in zip(a, b):
+        assert it.spec == jt.spec
+    for i, jt in enumerate(b):
+        jt.plane, jt.times = synth.make_frame(jt.spec, seed=99, frame=i)
+    for items in (a, b, a):
+        ins, keep = _batch_inputs(items)
+        ps = dec.partitions(dec.batch_decide(ins), len(items))
+        for it, p in zip(items, ps):
+            d, _, _ = oracle.decide(it.plane, it.times, it.spec.bit_depth, it.n_regions, it.lam)
+            assert_partition_equal(p, d, it.spec.ctu_rows)
