@@ -97,6 +97,7 @@ def _load():
         "trs_tables_layout_get": ([i, i, ct.POINTER(trs_tables_layout)], i),
         "trs_region_tables": ([vp, ct.POINTER(trs_ctu_stats), vp, i, i, vp, sz, vp], i),
         "trs_search": ([vp, vp, i, i, i, f, vp, vp], i),
+        "trs_search_noalloc": ([vp, i, i, i, i, f, vp, vp], i),
         "trs_decide": ([vp, vp, i, i, sz, i, vp, i, f, vp, vp], i),
         "trs_decide_host": ([vp, vp, i, i, sz, i, vp, i, f, ct.POINTER(trs_partition), vp], i),
         "trs_batch_decide": ([vp, ct.POINTER(trs_frame_desc), i, vp, vp], i),
@@ -205,6 +206,11 @@ def trs_region_tables(ctx, stats: trs_ctu_stats, ctu_time, width, height, tables
 def trs_search(ctx, tables, width, height, n_regions, lam, out, stream=None) -> None:
     _check(_lib.trs_search(ctx, _ptr(tables), width, height, n_regions, lam, _ptr(out), _stream(stream)),
            "trs_search")
+
+
+def trs_search_noalloc(tables, width, height, n_regions, k_area, lam, out, stream=None) -> None:
+    _check(_lib.trs_search_noalloc(_ptr(tables), width, height, n_regions, k_area, lam, _ptr(out),
+                                   _stream(stream)), "trs_search_noalloc")
 
 
 def trs_decide(ctx, luma, width, height, pitch_bytes, bit_depth, ctu_time, n_regions, lam, out,
