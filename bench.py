@@ -308,7 +308,7 @@ def main():
                            "l2": f"inputs {tex_bytes / 1e9:.2f} GB per step > L2, no flush"},
                 "plain": {"value": plain_value, "unit": UNIT, "form": "one frame per launch chain"},
                 "stage_ms": stage, "clocks": clk.summary(), "e2e": e2e,
-                "gpu_launches": 7 * args.steps, "roofline": roof, "roofline_texture": tex_roof,
+                "gpu_launches": 8 * args.steps, "roofline": roof, "roofline_texture": tex_roof,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     dec.close()

@@ -266,7 +266,8 @@ int trs_batch_decide_host(trs_ctx *ctx, const trs_frame_desc *frames_host, int n
 
 /* Device time in milliseconds of each stage of the most recent batched call
  * (texture, tables, step-1 rows, step-1 columns, step-2 rows, step-2
- * columns, decode), read from CUDA events recorded inside its graph.
+ * columns, rebuild of the smallest code, decode), read from CUDA events
+ * recorded inside its graph.
  * Synchronises on that call.  Returns the number of stages written. */
 int trs_batch_stage_ms(trs_ctx *ctx, float *ms, int max_stages);
 

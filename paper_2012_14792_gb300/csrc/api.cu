@@ -99,7 +99,7 @@ struct trs_ctx {
     size_t staging_n = 0;
     cudaStream_t cap = nullptr;
     cudaEvent_t copied = nullptr;
-    static constexpr int kStages = 7;
+    static constexpr int kStages = 8;
     cudaEvent_t stage[kStages + 1] = {};  // timing events recorded inside batch graphs
     bool stage_valid = false;
     // host-buffer batches: device staging of planes, times and partitions
@@ -226,6 +226,8 @@ int trs_create(trs_ctx **out, const trs_opts *o) {
         o->max_regions < 1 || o->max_regions > kMaxN || o->max_batch < 1 || o->k_area < 1)
         return TRS_EINVAL;
     TRS_CK(cudaSetDevice(o->device));
+    TRS_CK((cudaError_t)prepare_tables_kernel());
+    TRS_CK((cudaError_t)prepare_search_kernels());
     trs_ctx *c = new trs_ctx();
     c->o = *o;
     c->maxC = (o->max_width + kCtu - 1) / kCtu;
@@ -380,13 +382,14 @@ static int search_one(trs_ctx *ctx, const void *tables, int W, int H, int n, flo
     f.wres1 = (uint64_t *)(scr + pe->scr.w1);
     f.wres2 = (uint64_t *)(scr + pe->scr.w2);
     f.H2 = (uint64_t *)(scr + pe->scr.H2);
+    f.codes = (WinCode *)(scr + pe->scr.codes);
     f.scal = (uint64_t *)ctx->scal.p;
     f.out = out;
     a.nframes = 1;
     const int nitems = (int)pe->host.items.size(), nwin = (int)pe->host.win_a.size();
     a.single_items = nitems;
     a.single_windows = nwin;
-    TRS_CK((cudaError_t)launch_search(a, nitems, nwin, f.scal, 4, stream));
+    TRS_CK((cudaError_t)launch_search(a, nitems, nwin, f.C, f.R, n, f.scal, 4, stream));
     return TRS_OK;
 }
 
@@ -498,7 +501,7 @@ int trs_batch_decide(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partiti
     int32_t *pi = (int32_t *)(hb + fr_bytes + 2 * pre_bytes), *pw = (int32_t *)(hb + fr_bytes + 3 * pre_bytes);
     uint8_t *ab = (uint8_t *)ctx->arena.p;
     pc[0] = pg[0] = pi[0] = pw[0] = 0;
-    int maxC = 1, maxR = 1;
+    int maxC = 1, maxR = 1, maxN = 1;
     for (int i = 0; i < nf; ++i) {
         const trs_frame_desc &d = fd[i];
         const HostPlan &hp = pe[i]->host;
@@ -530,6 +533,7 @@ int trs_batch_decide(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partiti
         f.wres1 = (uint64_t *)(p + pe[i]->scr.w1);
         f.wres2 = (uint64_t *)(p + pe[i]->scr.w2);
         f.H2 = (uint64_t *)(p + pe[i]->scr.H2);
+        f.codes = (WinCode *)(p + pe[i]->scr.codes);
         f.scal = (uint64_t *)(ab + scal_off) + 4 * i;
         f.out = out + i;
         hf[i] = f;
@@ -539,6 +543,7 @@ int trs_batch_decide(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partiti
         pw[i + 1] = pw[i] + (int)hp.win_a.size();
         maxC = C > maxC ? C : maxC;
         maxR = R > maxR ? R : maxR;
+        maxN = d.n_regions > maxN ? d.n_regions : maxN;
     }
     BatchGraph &g = ctx->graphs[key];
     if (!g.exec) {
@@ -562,8 +567,8 @@ int trs_batch_decide(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partiti
         if (e == cudaSuccess) e = (cudaError_t)launch_tables(a, pg[nf], maxC, maxR, cs);
         if (e == cudaSuccess) e = cudaEventRecordWithFlags(ctx->stage[2], cs, cudaEventRecordExternal);
         if (e == cudaSuccess)
-            e = (cudaError_t)launch_search(a, pi[nf], pw[nf], (uint64_t *)(ab + scal_off), (size_t)nf * 4, cs,
-                                           ctx->stage + 3);
+            e = (cudaError_t)launch_search(a, pi[nf], pw[nf], maxC, maxR, maxN, (uint64_t *)(ab + scal_off),
+                                           (size_t)nf * 4, cs, ctx->stage + 3);
         cudaGraph_t graph = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
         if (e == cudaSuccess) e = e2;

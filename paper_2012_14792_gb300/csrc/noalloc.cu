@@ -123,6 +123,7 @@ int layout_plan(int W, int H, int n, int k, unsigned char *dev_base, DeviceSlot 
                 if ((size_t)nitems >= item_cap) return TRS_ENOMEM;
                 PlanItem &it = items[nitems];
                 it.b = b;
+                it.w_first = wi;
                 it.hlo = hs[ilo];
                 it.hhi = hs[ihi];
                 it.kmax = std::min(std::min(n, R), (int)(H / it.hlo));
@@ -131,13 +132,15 @@ int layout_plan(int W, int H, int n, int k, unsigned char *dev_base, DeviceSlot 
                 prev_slot = nitems++;
             }
             slot[(size_t)wi * nb + b] = prev_slot;
+            items[prev_slot].w_last = wi;
         }
     }
     const size_t plan_bytes = align256(off_items + (size_t)nitems * sizeof(PlanItem) + 16);
     // scratch of the search after the plan
     const size_t v = (size_t)nitems * (n + 1) * 8;
     const size_t need = plan_bytes + 2 * align256(v + 8) + 2 * align256((size_t)nwin * 8 + 8) +
-                        align256((size_t)nwin * (C + 1) * (n + 1) * 8 + 8) + align256(4 * 8);
+                        align256((size_t)nwin * (C + 1) * (n + 1) * 8 + 8) +
+                        align256((size_t)nwin * sizeof(WinCode) + 8) + align256(4 * 8);
     if (need > kNoAllocBytes) return TRS_ENOMEM;
 
     DevPlan d;
@@ -181,6 +184,7 @@ extern "C" int trs_search_noalloc(const void *tables, int W, int H, int n, int k
     if (!s.base) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return TRS_ECUDA;
+        if (prepare_search_kernels() != (int)cudaSuccess) return TRS_ECUDA;
         s.base = (unsigned char *)p;
     }
     cudaStream_t st = (cudaStream_t)stream;
@@ -214,13 +218,14 @@ extern "C" int trs_search_noalloc(const void *tables, int W, int H, int n, int k
     f.wres1 = reinterpret_cast<uint64_t *>(p + 2 * v);
     f.wres2 = reinterpret_cast<uint64_t *>(p + 2 * v + w);
     f.H2 = reinterpret_cast<uint64_t *>(p + 2 * v + 2 * w);
-    f.scal = reinterpret_cast<uint64_t *>(p + 2 * v + 2 * w +
-                                          align256((size_t)s.nwin * (s.C + 1) * (n + 1) * 8 + 8));
+    const size_t h2 = align256((size_t)s.nwin * (s.C + 1) * (n + 1) * 8 + 8);
+    f.codes = reinterpret_cast<WinCode *>(p + 2 * v + 2 * w + h2);
+    f.scal = reinterpret_cast<uint64_t *>(p + 2 * v + 2 * w + h2 + align256((size_t)s.nwin * sizeof(WinCode) + 8));
     f.out = out;
     a.nframes = 1;
     a.single_items = s.nitems;
     a.single_windows = s.nwin;
     // launch_search resets T_min and Q* to +infinity before its kernels
-    if (launch_search(a, s.nitems, s.nwin, f.scal, 4, stream) != (int)cudaSuccess) return TRS_ECUDA;
+    if (launch_search(a, s.nitems, s.nwin, s.C, s.R, n, f.scal, 4, stream) != (int)cudaSuccess) return TRS_ECUDA;
     return TRS_OK;
 }

@@ -73,10 +73,12 @@ int build_plan(int W, int H, int n, int k, HostPlan *p) {
             if (ilo > ihi) continue;
             if (ilo == prev_lo && ihi == prev_hi) {
                 p->slot_of[(size_t)wi * p->nb + b] = prev_slot;
+                p->items[prev_slot].w_last = wi;
                 continue;
             }
             PlanItem it;
             it.b = b;
+            it.w_first = it.w_last = wi;
             it.hlo = hs[ilo];
             it.hhi = hs[ihi];
             it.kmax = std::min(std::min(n, R), (int)(H / it.hlo));
@@ -138,6 +140,7 @@ SearchScratch scratch_layout(const HostPlan &p) {
     s.w1 = o;    o += align256(nw * 8 + 8);
     s.w2 = o;    o += align256(nw * 8 + 8);
     s.H2 = o;    o += align256(nw * (size_t)(p.C + 1) * (p.n + 1) * 8 + 8);
+    s.codes = o; o += align256(nw * sizeof(WinCode) + 8);
     s.bytes = o;
     return s;
 }

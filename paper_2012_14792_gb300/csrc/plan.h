@@ -18,7 +18,7 @@ struct HostPlan {
 };
 
 struct SearchScratch {
-    size_t V1, V2, w1, w2, H2, bytes;
+    size_t V1, V2, w1, w2, H2, codes, bytes;
 };
 
 int build_plan(int W, int H, int n, int k, HostPlan *p);

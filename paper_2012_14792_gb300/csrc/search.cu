@@ -25,11 +25,12 @@
 //                       warps split the candidate edges and merge with a
 //                       shared-memory atomicMin.  Step 1's window minima
 //                       reduce into T_min (Eq. 3), step 2's into Q*.
-//  finish_kernel        one warp per frame: rebuilds, in every window that
-//                       reaches Q*, the smallest canonical code (smallest
-//                       next edge first, then the smallest cut bits, chosen
-//                       with a warp ballot), keeps the smallest over windows
-//                       and decodes it into trs_partition.
+//  rebuild_kernel       one warp per (frame, window): in a window that
+//                       reaches Q*, rebuilds the smallest canonical code
+//                       (smallest next edge first, then the smallest cut
+//                       bits, chosen with warp ballots).
+//  finish_kernel        one warp per frame: the smallest code over windows,
+//                       decoded into trs_partition.
 #include <cuda_runtime.h>
 
 #include "trs_internal.cuh"
@@ -39,8 +40,15 @@ namespace trs {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kBandWarps = 4;       // warps per block of band_kernel
-constexpr int kColThreads = 1024;   // threads per block of column_kernel
+constexpr int kBandWarps = 4;   // warps per block of band_kernel
+constexpr int kColWarps = 4;    // warps per block of column_kernel
+// Saturating infinity inside the DPs: sums of a value below 2^44 and kSoft
+// stay below 2^63, so the relaxations need no infinity branches.
+constexpr uint64_t kSoft = 1ull << 62;
+
+__device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+__device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
+__device__ __forceinline__ uint64_t hard_inf(uint64_t v) { return v >= kSoft ? kInf : v; }
 
 __device__ __forceinline__ int32_t frame_status(const DevFrame &fr) {
     const TablesOffsets off = tables_offsets(fr.C, fr.R);
@@ -49,12 +57,15 @@ __device__ __forceinline__ int32_t frame_status(const DevFrame &fr) {
 
 // Suffix row DP of one item for one warp.  After iteration k, lane y holds
 // G_k[y] = best value of rows [y, R) of the band cut into k admissible
-// slices (kInf if none).  Writes V[k] = G_k[0] for k = 1..n (kInf beyond
-// kmax) when V != nullptr, and every layer into layers[k*32 + y] when
-// layers != nullptr.
+// slices.  Each lane first stages, for every slice height d in the item's
+// range, the slice's value (time for step 1, floor-SSE for step 2) in
+// shared memory and an admissibility bit; the k loop then only shuffles
+// G_{k-1}[y+d] from lane y+d and relaxes.  Writes V[k] = G_k[0] (k = 1..n,
+// kInf where no split exists) and, when asked, every layer into
+// layers[k*32 + y].
 template <int STEP>
-__device__ void item_dp(const DevFrame &fr, const DevPlan &pl, const PlanItem &it, uint64_t thr, uint64_t *V,
-                        uint64_t *layers) {
+__device__ void item_dp(const DevFrame &fr, const PlanItem &it, uint64_t thr, int n, uint64_t *V,
+                        uint64_t *layers, uint64_t *stage, uint32_t *vm_out = nullptr) {
     const int lane = threadIdx.x & 31;
     const int R = fr.R, H = fr.H;
     const TablesOffsets off = tables_offsets(fr.C, R);
@@ -64,169 +75,193 @@ __device__ void item_dp(const DevFrame &fr, const DevPlan &pl, const PlanItem &i
     // slice row counts that can reach a pixel height in [hlo, hhi]
     const int dmin = max(1, (int)((it.hlo + kCtu - 1) / kCtu));
     const int dmax = min(R, (int)(it.hhi / kCtu) + 1);
+    const int nd = dmax - dmin + 1;
     const uint32_t ytop = line_px(lane, H);
-    uint64_t G = kInf;
-    if (layers) layers[lane] = kInf;
+    uint32_t vmask = 0;
+#pragma unroll 4
+    for (int i = 0; i < nd; ++i) {
+        const int d = dmin + i, y1 = lane + d;
+        const bool in = lane < R && y1 <= R;
+        const size_t e = in ? (size_t)(d - 1) * R + lane : 0;
+        // both words are loaded unconditionally so the loads of all heights overlap
+        const uint64_t tv = __ldg(RT + e);
+        const uint64_t qv = STEP == 2 ? __ldg(RQ + e) : 0ull;
+        const uint32_t h = line_px(y1, H) - ytop;
+        const bool ok = in && h >= it.hlo && h <= it.hhi && (STEP == 1 || tv <= thr);
+        stage[i * 32 + lane] = STEP == 1 ? tv : qv;
+        vmask |= (ok ? 1u : 0u) << i;
+    }
+    if (vm_out) vm_out[lane] = vmask;
+    __syncwarp();
+    // G_0: only the empty remainder (y = R) holds zero slices
+    uint64_t G = (lane == R) ? 0ull : kSoft;
+    if (layers) layers[lane] = hard_inf(G);
     for (int k = 1; k <= it.kmax; ++k) {
-        uint64_t best = kInf;
-        for (int d = dmin; d <= dmax; ++d) {
-            const int y1 = lane + d;
-            const uint64_t nb = __shfl_sync(kFull, G, y1 & 31);
-            const uint64_t prev = (y1 == R) ? (k == 1 ? 0ull : kInf) : nb;
-            if (y1 <= R && prev != kInf) {
-                const uint32_t h = line_px(y1, H) - ytop;
-                if (h >= it.hlo && h <= it.hhi) {
-                    const uint64_t tv = __ldg(RT + (size_t)(d - 1) * R + lane);
-                    if (STEP == 1) {
-                        const uint64_t v = prev > tv ? prev : tv;
-                        best = v < best ? v : best;
-                    } else if (tv <= thr) {
-                        const uint64_t v = prev + __ldg(RQ + (size_t)(d - 1) * R + lane);
-                        best = v < best ? v : best;
-                    }
-                }
+        const uint64_t edge = (k == 1) ? 0ull : kSoft;  // G_{k-1}[R] when R == 32 (no lane 32)
+        uint64_t best = kSoft;
+        for (int i = 0; i < nd; ++i) {
+            const int src = lane + dmin + i;
+            uint64_t prev = __shfl_sync(kFull, G, src & 31);
+            if (src >= 32) prev = edge;
+            if ((vmask >> i) & 1u) {
+                const uint64_t val = stage[i * 32 + lane];
+                const uint64_t c = STEP == 1 ? umax64(prev, val) : prev + val;
+                best = umin64(best, c);
             }
         }
-        G = (lane < R) ? best : kInf;
-        if (layers) layers[k * 32 + lane] = G;
+        G = umin64(best, kSoft);
+        if (layers) layers[k * 32 + lane] = hard_inf(G);
         if (V) {
             const uint64_t g0 = __shfl_sync(kFull, G, 0);
-            if (lane == 0) V[k] = g0;
+            if (lane == 0) V[k] = hard_inf(g0);
         }
     }
     if (V && lane == 0) {
         V[0] = kInf;
-        for (int k = it.kmax + 1; k <= pl.n; ++k) V[k] = kInf;
+        for (int k = it.kmax + 1; k <= n; ++k) V[k] = kInf;
     }
+    __syncwarp();
 }
 
 template <int STEP>
-__global__ void __launch_bounds__(kBandWarps * 32) band_kernel(LaunchArgs args, int total) {
-    const int gw = blockIdx.x * kBandWarps + (threadIdx.x >> 5);
+__global__ void __launch_bounds__(kBandWarps * 32) band_kernel(LaunchArgs args, int total, int stage_words) {
+    extern __shared__ uint64_t bsm[];
+    const int wib = threadIdx.x >> 5;
+    const int gw = blockIdx.x * kBandWarps + wib;
     if (gw >= total) return;
     int local;
     const int f = locate(args, args.pre.items, args.single_items, gw, &local);
     const DevFrame &fr = frame_at(args, f);
     const DevPlan &pl = *fr.plan;
     const int lane = threadIdx.x & 31;
-    uint64_t *V = (STEP == 1 ? fr.V1 : fr.V2) + (size_t)local * (pl.n + 1);
-    if (frame_status(fr) != TRS_OK) {
-        if (lane == 0)
-            for (int k = 0; k <= pl.n; ++k) V[k] = kInf;
+    const int n = pl.n;
+    uint64_t *V = (STEP == 1 ? fr.V1 : fr.V2) + (size_t)local * (n + 1);
+    const PlanItem it = pl.items[local];
+    bool skip = frame_status(fr) != TRS_OK;
+    uint64_t thr = kInf;
+    if (STEP == 2 && !skip) {
+        // an item only matters if one of its windows still meets Eq. 4
+        thr = eq4_threshold(fr.scal[0], fr.lambda_q);
+        bool need = false;
+        for (int w = it.w_first + lane; w <= it.w_last; w += 32) need |= fr.wres1[w] <= thr;
+        skip = !__any_sync(kFull, need);
+    }
+    if (skip) {
+        for (int k = lane; k <= n; k += 32) V[k] = kInf;
         return;
     }
-    const uint64_t thr = STEP == 2 ? eq4_threshold(fr.scal[0], fr.lambda_q) : kInf;
-    item_dp<STEP>(fr, pl, pl.items[local], thr, V, nullptr);
+    item_dp<STEP>(fr, it, thr, n, V, nullptr, bsm + (size_t)wib * stage_words);
 }
 
-// Suffix DP over tile-column edges of one window:
+// Suffix DP over tile-column edges of one window, one warp:
 //   H[x][m] = min over x1 > x, k of  V[item(w, [x,x1))][k] (+|max) H[x1][m-k],
-// H[C][0] = 0.  Lane m-1 owns column m of a row; warp j takes edges x1 = x+1+j, ...
+// H[C][0] = 0.  Lane m-1 owns slice count m.  For each x the lanes fetch
+// the items of all candidate edges at once; each edge then contributes only
+// the slice counts k whose V is finite (a ballot over its V row), and the V
+// row of the next edge is loaded while the current one is relaxed.
 template <int STEP>
-__global__ void __launch_bounds__(kColThreads) column_kernel(LaunchArgs args, int total) {
-    __shared__ uint64_t Hs[(kMaxC + 1) * (kMaxN + 1)];
+__global__ void __launch_bounds__(kColWarps * 32) column_kernel(LaunchArgs args, int total, int h_words) {
+    extern __shared__ uint64_t csm[];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kColWarps + wib;
+    if (gw >= total) return;
     int w;
-    const int f = locate(args, args.pre.windows, args.single_windows, blockIdx.x, &w);
+    const int f = locate(args, args.pre.windows, args.single_windows, gw, &w);
     const DevFrame &fr = frame_at(args, f);
     const DevPlan &pl = *fr.plan;
-    const int C = fr.C, n = pl.n, nb = pl.nb;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int C = fr.C, n = pl.n, nb = pl.nb, stride = n + 1;
     uint64_t *wres = STEP == 1 ? fr.wres1 : fr.wres2;
     const uint64_t *V = STEP == 1 ? fr.V1 : fr.V2;
     if (frame_status(fr) != TRS_OK) {
-        if (threadIdx.x == 0) wres[w] = kInf;
+        if (lane == 0) wres[w] = kInf;
         return;
     }
     if (STEP == 2) {
         // a window whose best time breaks Eq. 4 holds no step-2 candidate
         const uint64_t thr = eq4_threshold(fr.scal[0], fr.lambda_q);
         if (fr.wres1[w] > thr) {
-            if (threadIdx.x == 0) wres[w] = kInf;
+            if (lane == 0) wres[w] = kInf;
             return;
         }
     }
-    const int stride = n + 1;
-    for (int i = threadIdx.x; i < (C + 1) * stride; i += blockDim.x) Hs[i] = kInf;
-    __syncthreads();
-    if (threadIdx.x == 0) Hs[C * stride] = 0;
-    __syncthreads();
+    uint64_t *Hs = csm + (size_t)wib * h_words;
+    for (int i = lane; i < (C + 1) * stride; i += 32) Hs[i] = kSoft;
+    __syncwarp();
+    if (lane == 0) Hs[C * stride] = 0;
+    __syncwarp();
     const int32_t *slot_row = pl.slot_of + (size_t)w * nb;
+    const int m = lane + 1;
     for (int x = C - 1; x >= 0; --x) {
-        for (int x1 = x + 1 + warp; x1 <= C; x1 += nwarps) {
-            const int slot = slot_row[band_index(C, x, x1)];
-            if (slot < 0) continue;
-            const int kmax = pl.items[slot].kmax;
-            const uint64_t *Vb = V + (size_t)slot * stride;
-            const uint64_t vk = lane < n ? Vb[lane + 1] : kInf;  // lane k-1 holds V[k]
-            const uint64_t *Hrow = Hs + x1 * stride;
-            const int m = lane + 1;
-            uint64_t acc = kInf;
-            for (int k = 1; k <= kmax; ++k) {
-                const uint64_t v = __shfl_sync(kFull, vk, k - 1);
-                if (v != kInf && m >= k && m <= n) {
-                    const uint64_t h = Hrow[m - k];
-                    if (h != kInf) {
-                        const uint64_t c = STEP == 1 ? (v > h ? v : h) : v + h;
-                        acc = c < acc ? c : acc;
+        uint64_t acc = kSoft;
+        for (int half = 0; half * 32 < C - x; ++half) {
+            const int x1l = x + 1 + half * 32 + lane;
+            const int sl = x1l <= C ? slot_row[band_index(C, x, x1l)] : -1;
+            unsigned mask = __ballot_sync(kFull, sl >= 0);
+            if (!mask) continue;
+            int j = __ffs(mask) - 1;
+            mask &= mask - 1;
+            int slot = __shfl_sync(kFull, sl, j);
+            uint64_t vk = lane < n ? V[(size_t)slot * stride + lane + 1] : kInf;
+            while (true) {
+                int jn = -1;
+                uint64_t vn = kInf;
+                if (mask) {
+                    jn = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    const int sn = __shfl_sync(kFull, sl, jn);
+                    vn = lane < n ? V[(size_t)sn * stride + lane + 1] : kInf;
+                }
+                const uint64_t *Hrow = Hs + (size_t)(x + 1 + half * 32 + j) * stride;
+                unsigned fin = __ballot_sync(kFull, vk != kInf);
+                while (fin) {
+                    const int k = __ffs(fin);
+                    fin &= fin - 1;
+                    const uint64_t v = __shfl_sync(kFull, vk, k - 1);
+                    if (m >= k && m <= n) {
+                        const uint64_t h = Hrow[m - k];
+                        acc = umin64(acc, STEP == 1 ? umax64(v, h) : v + h);
                     }
                 }
+                if (jn < 0) break;
+                j = jn;
+                vk = vn;
             }
-            if (acc != kInf) atomicMin(reinterpret_cast<unsigned long long *>(&Hs[x * stride + m]), acc);
         }
-        __syncthreads();
+        if (m <= n) Hs[x * stride + m] = umin64(acc, kSoft);
+        __syncwarp();
     }
-    const uint64_t res = Hs[n];
-    if (threadIdx.x == 0) {
+    const uint64_t res = hard_inf(Hs[n]);
+    if (lane == 0) {
         wres[w] = res;
         if (res != kInf) atomicMin(reinterpret_cast<unsigned long long *>(&fr.scal[STEP == 1 ? 0 : 1]), res);
     }
     if (STEP == 2) {
         uint64_t *H2 = fr.H2 + (size_t)w * (C + 1) * stride;
-        for (int i = threadIdx.x; i < (C + 1) * stride; i += blockDim.x) H2[i] = Hs[i];
+        for (int i = lane; i < (C + 1) * stride; i += 32) H2[i] = hard_inf(Hs[i]);
     }
 }
-
-struct Code {
-    int c;
-    int16_t xe[kMaxC + 1];
-    uint32_t cut[kMaxC];
-};
 
 // '0' < '1' read from CTU line 1 downwards: compare bit-reversed words.
 __device__ __forceinline__ bool bits_less(uint32_t a, uint32_t b) { return __brev(a) < __brev(b); }
 
-__device__ bool code_less(const Code &a, const Code &b) {
-    const int c = a.c < b.c ? a.c : b.c;
-    for (int i = 0; i < c; ++i) {
-        if (a.xe[i + 1] != b.xe[i + 1]) return a.xe[i + 1] < b.xe[i + 1];
-        if (a.cut[i] != b.cut[i]) return bits_less(a.cut[i], b.cut[i]);
-    }
-    return false;
-}
-
 // Smallest cut bits of a k-slice split of the item's band that reaches
 // layers[k][0], read greedily top-down: the largest next cut line first.
-__device__ uint32_t lexmin_bits(const DevFrame &fr, const PlanItem &it, uint64_t thr, const uint64_t *layers,
-                                int k) {
+// Slice values and admissibility come from the shared-memory staging of
+// item_dp (stage[i*32 + y] = floor-SSE of rows [y, y+dmin+i), bit i of
+// vm[y] = admissible).
+__device__ uint32_t lexmin_bits(const PlanItem &it, int R, const uint64_t *layers, const uint64_t *stage,
+                                const uint32_t *vm, int k) {
     const int lane = threadIdx.x & 31;
-    const int R = fr.R, H = fr.H;
-    const TablesOffsets off = tables_offsets(fr.C, R);
-    const size_t base = (size_t)it.b * R * R;
-    const uint64_t *RT = reinterpret_cast<const uint64_t *>(fr.tables + off.rect_t) + base;
-    const uint64_t *RQ = reinterpret_cast<const uint64_t *>(fr.tables + off.rect_q) + base;
+    const int dmin = max(1, (int)((it.hlo + kCtu - 1) / kCtu));
     uint32_t bits = 0;
     int y = 0;
     for (int kk = k; kk > 1; --kk) {
         const int y1 = lane;  // candidate next cut line
+        const int i = y1 - y - dmin;
         bool ok = false;
-        if (y1 > y && y1 < R) {
-            const int d = y1 - y;
-            const uint32_t h = line_px(y1, H) - line_px(y, H);
+        if (y1 > y && y1 < R && i >= 0 && i < 32 && ((vm[y] >> i) & 1u)) {
             const uint64_t nxt = layers[(kk - 1) * 32 + y1];
-            if (h >= it.hlo && h <= it.hhi && nxt != kInf) {
-                const size_t e = (size_t)(d - 1) * R + y;
-                if (RT[e] <= thr) ok = (nxt + RQ[e] == layers[kk * 32 + y]);
-            }
+            ok = nxt != kInf && nxt + stage[i * 32 + y] == layers[kk * 32 + y];
         }
         const unsigned m = __ballot_sync(kFull, ok);
         if (!m) return ~0u;  // unreachable when layers[kk][y] is finite
@@ -237,100 +272,146 @@ __device__ uint32_t lexmin_bits(const DevFrame &fr, const PlanItem &it, uint64_t
     return bits;
 }
 
-__global__ void __launch_bounds__(32) finish_kernel(LaunchArgs args) {
-    __shared__ uint64_t layers[(kMaxN + 1) * 32];
-    __shared__ Code best, cur;
-    const int f = blockIdx.x;
+__device__ bool code_less_g(const WinCode &a, const WinCode &b) {
+    const int c = a.c < b.c ? a.c : b.c;
+    for (int i = 0; i < c; ++i) {
+        if (a.xe[i + 1] != b.xe[i + 1]) return a.xe[i + 1] < b.xe[i + 1];
+        if (a.cut[i] != b.cut[i]) return bits_less(a.cut[i], b.cut[i]);
+    }
+    return false;
+}
+
+// One warp per (frame, window): if the window reaches Q*, rebuild its
+// smallest canonical code.  At each left edge x the warp walks the
+// candidate right edges x1 in increasing order (their items fetched by the
+// lanes at once) and, with lanes over the slice count k, keeps the first x1
+// for which some k completes an optimal partition:
+//   V2[item][k] + H2[x1][m-k] == H2[x][m].
+// The band's row DP is then redone with every layer kept in shared memory
+// and, among the admissible k, the smallest cut bits win.
+__global__ void __launch_bounds__(32) rebuild_kernel(LaunchArgs args, int total, int layer_words,
+                                                      int stage_words) {
+    extern __shared__ uint64_t rsm[];
+    uint64_t *layers = rsm;
+    uint64_t *stage = rsm + layer_words;
+    __shared__ uint32_t vm[32];
+    const int gw = blockIdx.x;
+    if (gw >= total) return;
+    int w;
+    const int f = locate(args, args.pre.windows, args.single_windows, gw, &w);
     const DevFrame &fr = frame_at(args, f);
     const DevPlan &pl = *fr.plan;
     const int lane = threadIdx.x;
     const int C = fr.C, R = fr.R, n = pl.n, nb = pl.nb, stride = n + 1;
+    WinCode &code = fr.codes[w];
+    const uint64_t qstar = fr.scal[1];
+    if (frame_status(fr) != TRS_OK || qstar == kInf || fr.wres2[w] != qstar) {
+        if (lane == 0) code.c = -1;
+        return;
+    }
+    const uint64_t thr = eq4_threshold(fr.scal[0], fr.lambda_q);
+    const uint64_t *H2 = fr.H2 + (size_t)w * (C + 1) * stride;
+    const int32_t *slot_row = pl.slot_of + (size_t)w * nb;
+    int x = 0, m = n, c = 0;
+    while (x < C) {
+        const uint64_t target = H2[x * stride + m];
+        int x1 = -1, slot = -1;
+        unsigned kmask = 0;
+        for (int base = 0; base < C - x && x1 < 0; base += 32) {
+            const int cx = x + 1 + base + lane;
+            const int sl = cx <= C ? slot_row[band_index(C, x, cx)] : -1;
+            unsigned cand = __ballot_sync(kFull, sl >= 0);
+            while (cand) {
+                const int j = __ffs(cand) - 1;
+                cand &= cand - 1;
+                const int sj = __shfl_sync(kFull, sl, j);
+                const int xj = x + 1 + base + j;
+                const int k = lane + 1;
+                bool ok = false;
+                if (k <= m) {
+                    const uint64_t v = fr.V2[(size_t)sj * stride + k], h = H2[xj * stride + m - k];
+                    ok = v != kInf && h != kInf && v + h == target;
+                }
+                const unsigned km = __ballot_sync(kFull, ok);
+                if (km) {
+                    x1 = xj;
+                    slot = sj;
+                    kmask = km;
+                    break;
+                }
+            }
+        }
+        if (x1 < 0) {  // cannot happen when H2[x][m] is finite
+            if (lane == 0) code.c = -1;
+            return;
+        }
+        const PlanItem it = pl.items[slot];
+        item_dp<2>(fr, it, thr, n, nullptr, layers, stage, vm);
+        uint32_t bb = 0;
+        int bk = -1;
+        for (unsigned mm = kmask; mm; mm &= mm - 1) {
+            const int kk = __ffs(mm);  // slice count kk = bit index + 1
+            const uint32_t bits = lexmin_bits(it, R, layers, stage, vm, kk);
+            if (bk < 0 || bits_less(bits, bb)) {
+                bb = bits;
+                bk = kk;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            code.xe[c + 1] = (int16_t)x1;
+            code.cut[c] = bb;
+        }
+        c++;
+        m -= bk;
+        x = x1;
+    }
+    if (lane == 0) {
+        code.xe[0] = 0;
+        code.c = c;
+    }
+}
+
+// One warp per frame: the smallest code over the windows reaching Q*, then
+// its decoding into trs_partition (one tile row, tile columns = bands,
+// slices top to bottom).
+__global__ void __launch_bounds__(32) finish_kernel(LaunchArgs args) {
+    const int f = blockIdx.x;
+    const DevFrame &fr = frame_at(args, f);
+    const DevPlan &pl = *fr.plan;
+    const int lane = threadIdx.x;
+    const int C = fr.C, R = fr.R, n = pl.n;
     trs_partition *out = fr.out;
     int32_t status = frame_status(fr);
     const uint64_t t_min = fr.scal[0];
     if (status == TRS_OK && t_min == kInf) status = TRS_EINFEASIBLE;
     const uint64_t qstar = fr.scal[1];
     if (status == TRS_OK && qstar == kInf) status = TRS_EINFEASIBLE;  // cannot happen: P(T_min) meets Eq. 4
-    if (lane == 0) {
-        out->status = status;
-        out->n_regions = n;
-        out->cols = C;
-        out->rows = R;
-        out->n_windows = pl.nwin;
-        out->reserved = 0;
-    }
-    if (status != TRS_OK) {
-        if (lane == 0) {
-            out->n_tile_cols = out->n_tile_rows = 0;
-            out->t_min_q = out->thr_q = out->t_q = out->q = 0;
-            out->t_min = out->t = out->sse = 0.0;
-            out->tile_row_mask = 0;
-        }
-        return;
-    }
-    const uint64_t thr = eq4_threshold(t_min, fr.lambda_q);
-    bool have = false;
-    for (int w = 0; w < pl.nwin; ++w) {
-        if (fr.wres2[w] != qstar) continue;
-        const uint64_t *H2 = fr.H2 + (size_t)w * (C + 1) * stride;
-        const int32_t *slot_row = pl.slot_of + (size_t)w * nb;
-        int x = 0, m = n, c = 0;
-        bool fail = false;
-        while (x < C && !fail) {
-            bool found = false;
-            for (int x1 = x + 1; x1 <= C && !found; ++x1) {
-                const int slot = slot_row[band_index(C, x, x1)];
-                if (slot < 0) continue;
-                const PlanItem it = pl.items[slot];
-                const uint64_t *Vb = fr.V2 + (size_t)slot * stride;
-                const int k = lane + 1;
-                bool ok = false;
-                if (k <= m && k <= it.kmax) {
-                    const uint64_t v = Vb[k], h = H2[x1 * stride + m - k];
-                    ok = v != kInf && h != kInf && v + h == H2[x * stride + m];
-                }
-                const unsigned mask = __ballot_sync(kFull, ok);
-                if (!mask) continue;
-                item_dp<2>(fr, pl, it, thr, nullptr, layers);
-                __syncwarp();
-                uint32_t bb = 0;
-                int bk = -1;
-                for (unsigned mm = mask; mm; mm &= mm - 1) {
-                    const int kk = __ffs(mm);  // slice count kk = bit index + 1
-                    const uint32_t bits = lexmin_bits(fr, it, thr, layers, kk);
-                    if (bk < 0 || bits_less(bits, bb)) {
-                        bb = bits;
-                        bk = kk;
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) {
-                    cur.xe[c + 1] = (int16_t)x1;
-                    cur.cut[c] = bb;
-                }
-                c++;
-                m -= bk;
-                x = x1;
-                found = true;
-            }
-            if (!found) fail = true;
-        }
-        __syncwarp();
-        if (fail) continue;
-        if (lane == 0) {
-            cur.c = c;
-            cur.xe[0] = 0;
-            if (!have || code_less(cur, best)) best = cur;
-        }
-        have = true;
-        __syncwarp();
-    }
-    if (!have) {
-        if (lane == 0) out->status = TRS_EINFEASIBLE;
-        return;
-    }
     if (lane != 0) return;
-    // decode the winner: one tile row, tile columns = bands, slices top to bottom
+    out->status = status;
+    out->n_regions = n;
+    out->cols = C;
+    out->rows = R;
+    out->n_windows = pl.nwin;
+    out->reserved = 0;
+    if (status != TRS_OK) {
+        out->n_tile_cols = out->n_tile_rows = 0;
+        out->t_min_q = out->thr_q = out->t_q = out->q = 0;
+        out->t_min = out->t = out->sse = 0.0;
+        out->tile_row_mask = 0;
+        return;
+    }
+    int bw = -1;
+    for (int w = 0; w < pl.nwin; ++w) {
+        if (fr.codes[w].c <= 0) continue;
+        if (bw < 0 || code_less_g(fr.codes[w], fr.codes[bw])) bw = w;
+    }
+    if (bw < 0) {
+        out->status = TRS_EINFEASIBLE;
+        return;
+    }
+    const WinCode &best = fr.codes[bw];
+    const uint64_t thr = eq4_threshold(t_min, fr.lambda_q);
     const TablesOffsets off = tables_offsets(C, R);
     const uint64_t *RT = reinterpret_cast<const uint64_t *>(fr.tables + off.rect_t);
     const uint64_t *RQ = reinterpret_cast<const uint64_t *>(fr.tables + off.rect_q);
@@ -386,26 +467,54 @@ __global__ void __launch_bounds__(32) finish_kernel(LaunchArgs args) {
 
 }  // namespace
 
-int launch_search(const LaunchArgs &a, int total_items, int total_windows, uint64_t *scal, size_t nscal,
-                  void *stream, cudaEvent_t *ev) {
+// Raises the dynamic shared-memory limit of the search kernels to what the
+// largest shapes need (once per device, before any capture).
+int prepare_search_kernels() {
+    const int band_smem = kBandWarps * kMaxR * 32 * (int)sizeof(uint64_t);
+    const int col_smem = kColWarps * (kMaxC + 1) * (kMaxN + 1) * (int)sizeof(uint64_t);
+    cudaError_t e = cudaFuncSetAttribute(band_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, band_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(band_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, band_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(column_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(column_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
+    const int rb_smem = ((kMaxN + 1) * 32 + kMaxR * 32) * (int)sizeof(uint64_t);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(rebuild_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, rb_smem);
+    return (int)e;
+}
+
+int launch_search(const LaunchArgs &a, int total_items, int total_windows, int maxC, int maxR, int maxN,
+                  uint64_t *scal, size_t nscal, void *stream, cudaEvent_t *ev) {
     cudaStream_t s = (cudaStream_t)stream;
     // T_min and Q* start at +infinity; the column kernels reduce into them
     cudaError_t e = cudaMemsetAsync(scal, 0xff, nscal * sizeof(uint64_t), s);
     if (e != cudaSuccess) return (int)e;
+    const int stage_words = maxR * 32;
+    const size_t band_smem = (size_t)kBandWarps * stage_words * sizeof(uint64_t);
+    const int h_words = (maxC + 1) * (maxN + 1);
+    const size_t col_smem = (size_t)kColWarps * h_words * sizeof(uint64_t);
     const int bb = (total_items + kBandWarps - 1) / kBandWarps;
+    const int cb = (total_windows + kColWarps - 1) / kColWarps;
     auto mark = [&](int i) {
         if (ev && e == cudaSuccess) e = cudaEventRecordWithFlags(ev[i], s, cudaEventRecordExternal);
     };
-    if (total_items > 0) band_kernel<1><<<bb, kBandWarps * 32, 0, s>>>(a, total_items);
+    if (total_items > 0) band_kernel<1><<<bb, kBandWarps * 32, band_smem, s>>>(a, total_items, stage_words);
     mark(0);
-    if (total_windows > 0) column_kernel<1><<<total_windows, kColThreads, 0, s>>>(a, total_windows);
+    if (total_windows > 0) column_kernel<1><<<cb, kColWarps * 32, col_smem, s>>>(a, total_windows, h_words);
     mark(1);
-    if (total_items > 0) band_kernel<2><<<bb, kBandWarps * 32, 0, s>>>(a, total_items);
+    if (total_items > 0) band_kernel<2><<<bb, kBandWarps * 32, band_smem, s>>>(a, total_items, stage_words);
     mark(2);
-    if (total_windows > 0) column_kernel<2><<<total_windows, kColThreads, 0, s>>>(a, total_windows);
+    if (total_windows > 0) column_kernel<2><<<cb, kColWarps * 32, col_smem, s>>>(a, total_windows, h_words);
     mark(3);
-    finish_kernel<<<a.nframes, 32, 0, s>>>(a);
+    const int layer_words = (maxN + 1) * 32;
+    const size_t rb_smem = (size_t)(layer_words + stage_words) * sizeof(uint64_t);
+    if (total_windows > 0) rebuild_kernel<<<total_windows, 32, rb_smem, s>>>(a, total_windows, layer_words,
+                                                                             stage_words);
     mark(4);
+    finish_kernel<<<a.nframes, 32, 0, s>>>(a);
+    mark(5);
     if (e != cudaSuccess) return (int)e;
     return (int)cudaGetLastError();
 }

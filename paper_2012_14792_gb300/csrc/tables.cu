@@ -147,14 +147,18 @@ __global__ void __launch_bounds__(kTabThreads) tables_kernel(LaunchArgs args) {
 
 }  // namespace
 
+// Raises the dynamic shared-memory limit of tables_kernel to what the
+// largest frame needs (once per device, before any capture).
+int prepare_tables_kernel() {
+    const size_t S = (size_t)(kMaxR + 1) * (kMaxC + 1);
+    const size_t smem = S * 3 * sizeof(uint64_t) + (size_t)kMaxR * kMaxC * sizeof(uint32_t);
+    return (int)cudaFuncSetAttribute(tables_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 int launch_tables(const LaunchArgs &a, int total_groups, int maxC, int maxR, void *stream) {
     if (total_groups <= 0) return 0;
     const size_t S = (size_t)(maxR + 1) * (maxC + 1);
     const size_t smem = S * 3 * sizeof(uint64_t) + (size_t)maxR * maxC * sizeof(uint32_t);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(tables_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return (int)e;
-    }
     tables_kernel<<<total_groups, kTabThreads, smem, (cudaStream_t)stream>>>(a);
     return (int)cudaGetLastError();
 }

@@ -88,6 +88,7 @@ struct PlanItem {
     int32_t b;
     int32_t kmax;
     uint32_t hlo, hhi;
+    int32_t w_first, w_last;  // the windows mapped to this item are [w_first, w_last]
 };
 
 // Search plan of one frame shape (W, H, n, k), built on the host once per
@@ -100,6 +101,15 @@ struct DevPlan {
     const int32_t *slot_of;     // [nwin * nb]: item of (window, band), -1 if the band has no slice there
     const int16_t *band_x0;     // [nb]
     const int16_t *band_x1;     // [nb]
+};
+
+// A canonical code: c tile columns with right edges xe[1..c] (xe[0] = 0)
+// and the slice cut bits of each (bit y-1 = cut at CTU line y).  c < 0
+// marks "no code" (the window does not reach Q*).
+struct WinCode {
+    int32_t c;
+    int16_t xe[kMaxC + 1];
+    uint32_t cut[kMaxC];
 };
 
 // Everything a kernel needs about one frame.  Lives in device memory for
@@ -126,6 +136,7 @@ struct DevFrame {
     uint64_t *V1, *V2;      // [nitems][n+1]
     uint64_t *wres1, *wres2;  // [nwin]
     uint64_t *H2;           // [nwin][(C+1)*(n+1)]
+    WinCode *codes;         // [nwin]: smallest code of each window reaching Q*
     uint64_t *scal;         // [0] T_min, [1] Q*, [2] thr, [3] spare
     trs_partition *out;
 };
@@ -167,12 +178,17 @@ __device__ inline int locate(const LaunchArgs &a, const int32_t *pre, int single
     return lo;
 }
 
+// Kernel attributes for the largest shapes; call once per device before launching.
+int prepare_tables_kernel();
+int prepare_search_kernels();
+
 // Launchers (return cudaError_t as int).
 int launch_texture(const LaunchArgs &a, int total_ctus, void *stream);
 int launch_tables(const LaunchArgs &a, int total_groups, int maxC, int maxR, void *stream);
 // scal: the T_min / Q* words of every frame of the launch (reset to +inf first).
-// ev (optional, 5 events): recorded after each of the five search kernels.
-int launch_search(const LaunchArgs &a, int total_items, int total_windows, uint64_t *scal, size_t nscal,
-                  void *stream, cudaEvent_t *ev = nullptr);
+// ev (optional, 6 events): recorded after each of the six search kernels.
+// maxC / maxR / maxN: largest C, R and n over the frames of the launch (shared-memory sizing).
+int launch_search(const LaunchArgs &a, int total_items, int total_windows, int maxC, int maxR, int maxN,
+                  uint64_t *scal, size_t nscal, void *stream, cudaEvent_t *ev = nullptr);
 
 }  // namespace trs

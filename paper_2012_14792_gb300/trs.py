@@ -245,7 +245,7 @@ def trs_batch_decide_host(ctx, descs: list[trs_frame_desc], stream=None) -> list
     return list(out)
 
 
-STAGES = ("texture", "tables", "step1_rows", "step1_columns", "step2_rows", "step2_columns", "decode")
+STAGES = ("texture", "tables", "step1_rows", "step1_columns", "step2_rows", "step2_columns", "rebuild", "decode")
 
 
 def trs_batch_stage_ms(ctx) -> dict:
