@@ -389,7 +389,8 @@ static int search_one(trs_ctx *ctx, const void *tables, int W, int H, int n, flo
     const int nitems = (int)pe->host.items.size(), nwin = (int)pe->host.win_a.size();
     a.single_items = nitems;
     a.single_windows = nwin;
-    TRS_CK((cudaError_t)launch_search(a, nitems, nwin, f.C, f.R, n, f.scal, 4, stream));
+    a.single_bands = pe->host.nb;
+    TRS_CK((cudaError_t)launch_search(a, pe->host.nb, nwin, f.C, f.R, n, f.scal, 4, stream));
     return TRS_OK;
 }
 
@@ -475,7 +476,7 @@ int trs_batch_decide(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partiti
     // descriptor blob: DevFrame[nf] | prefixes ctus, bandgrp, items, windows [nf+1]
     const size_t fr_bytes = align256((size_t)nf * sizeof(DevFrame));
     const size_t pre_bytes = align256((size_t)(nf + 1) * 4);
-    const size_t blob = fr_bytes + 4 * pre_bytes;
+    const size_t blob = fr_bytes + 5 * pre_bytes;
     if (ctx->desc.n < blob) {
         for (auto &g : ctx->graphs)
             if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
@@ -499,8 +500,9 @@ int trs_batch_decide(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partiti
     DevFrame *hf = (DevFrame *)hb;
     int32_t *pc = (int32_t *)(hb + fr_bytes), *pg = (int32_t *)(hb + fr_bytes + pre_bytes);
     int32_t *pi = (int32_t *)(hb + fr_bytes + 2 * pre_bytes), *pw = (int32_t *)(hb + fr_bytes + 3 * pre_bytes);
+    int32_t *pb = (int32_t *)(hb + fr_bytes + 4 * pre_bytes);
     uint8_t *ab = (uint8_t *)ctx->arena.p;
-    pc[0] = pg[0] = pi[0] = pw[0] = 0;
+    pc[0] = pg[0] = pi[0] = pw[0] = pb[0] = 0;
     int maxC = 1, maxR = 1, maxN = 1;
     for (int i = 0; i < nf; ++i) {
         const trs_frame_desc &d = fd[i];
@@ -541,6 +543,7 @@ int trs_batch_decide(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partiti
         pg[i + 1] = pg[i] + (num_bands(C) + kBandsPerBlock - 1) / kBandsPerBlock;
         pi[i + 1] = pi[i] + (int)hp.items.size();
         pw[i + 1] = pw[i] + (int)hp.win_a.size();
+        pb[i + 1] = pb[i] + hp.nb;
         maxC = C > maxC ? C : maxC;
         maxR = R > maxR ? R : maxR;
         maxN = d.n_regions > maxN ? d.n_regions : maxN;
@@ -555,6 +558,7 @@ int trs_batch_decide(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partiti
         a.pre.bandgrp = (const int32_t *)(db + fr_bytes + pre_bytes);
         a.pre.items = (const int32_t *)(db + fr_bytes + 2 * pre_bytes);
         a.pre.windows = (const int32_t *)(db + fr_bytes + 3 * pre_bytes);
+        a.pre.bands = (const int32_t *)(db + fr_bytes + 4 * pre_bytes);
         cudaStream_t cs = ctx->cap;
         TRS_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         int rc = TRS_OK;
@@ -567,7 +571,7 @@ int trs_batch_decide(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partiti
         if (e == cudaSuccess) e = (cudaError_t)launch_tables(a, pg[nf], maxC, maxR, cs);
         if (e == cudaSuccess) e = cudaEventRecordWithFlags(ctx->stage[2], cs, cudaEventRecordExternal);
         if (e == cudaSuccess)
-            e = (cudaError_t)launch_search(a, pi[nf], pw[nf], maxC, maxR, maxN, (uint64_t *)(ab + scal_off),
+            e = (cudaError_t)launch_search(a, pb[nf], pw[nf], maxC, maxR, maxN, (uint64_t *)(ab + scal_off),
                                            (size_t)nf * 4, cs, ctx->stage + 3);
         cudaGraph_t graph = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(cs, &graph);

@@ -92,6 +92,8 @@ int layout_plan(int W, int H, int n, int k, unsigned char *dev_base, DeviceSlot 
     off = align256(off + (size_t)nb * 2 + 2);
     const size_t off_x1 = off;
     off = align256(off + (size_t)nb * 2 + 2);
+    const size_t off_bi = off;
+    off = align256(off + (size_t)(nb + 1) * 4 + 4);
     const size_t off_items = off;
     if (off_items > kNoAllocBytes) return TRS_ENOMEM;
 
@@ -99,6 +101,7 @@ int layout_plan(int W, int H, int n, int k, unsigned char *dev_base, DeviceSlot 
     int32_t *slot = reinterpret_cast<int32_t *>(g_host_plan + off_slot);
     int16_t *bx0 = reinterpret_cast<int16_t *>(g_host_plan + off_x0);
     int16_t *bx1 = reinterpret_cast<int16_t *>(g_host_plan + off_x1);
+    int32_t *bitems = reinterpret_cast<int32_t *>(g_host_plan + off_bi);
     PlanItem *items = reinterpret_cast<PlanItem *>(g_host_plan + off_items);
     const size_t item_cap = (kNoAllocBytes - off_items) / sizeof(PlanItem);
     for (size_t i = 0; i < (size_t)nwin * nb; ++i) slot[i] = -1;
@@ -110,6 +113,7 @@ int layout_plan(int W, int H, int n, int k, unsigned char *dev_base, DeviceSlot 
             bx1[b] = (int16_t)x1;
         }
     for (int b = 0; b < nb; ++b) {
+        bitems[b] = nitems;
         const uint64_t wb = line_px(bx1[b], W) - line_px(bx0[b], W);
         int prev_lo = -1, prev_hi = -1, prev_slot = -1;
         for (int wi = 0; wi < nwin; ++wi) {
@@ -135,6 +139,7 @@ int layout_plan(int W, int H, int n, int k, unsigned char *dev_base, DeviceSlot 
             items[prev_slot].w_last = wi;
         }
     }
+    bitems[nb] = nitems;
     const size_t plan_bytes = align256(off_items + (size_t)nitems * sizeof(PlanItem) + 16);
     // scratch of the search after the plan
     const size_t v = (size_t)nitems * (n + 1) * 8;
@@ -159,6 +164,7 @@ int layout_plan(int W, int H, int n, int k, unsigned char *dev_base, DeviceSlot 
     d.slot_of = reinterpret_cast<const int32_t *>(dev_base + off_slot);
     d.band_x0 = reinterpret_cast<const int16_t *>(dev_base + off_x0);
     d.band_x1 = reinterpret_cast<const int16_t *>(dev_base + off_x1);
+    d.band_items = reinterpret_cast<const int32_t *>(dev_base + off_bi);
     std::memcpy(g_host_plan, &d, sizeof(d));
     s->plan_bytes = plan_bytes;
     s->nwin = nwin;
@@ -225,7 +231,8 @@ extern "C" int trs_search_noalloc(const void *tables, int W, int H, int n, int k
     a.nframes = 1;
     a.single_items = s.nitems;
     a.single_windows = s.nwin;
+    a.single_bands = s.nb;
     // launch_search resets T_min and Q* to +infinity before its kernels
-    if (launch_search(a, s.nitems, s.nwin, s.C, s.R, n, f.scal, 4, stream) != (int)cudaSuccess) return TRS_ECUDA;
+    if (launch_search(a, s.nb, s.nwin, s.C, s.R, n, f.scal, 4, stream) != (int)cudaSuccess) return TRS_ECUDA;
     return TRS_OK;
 }

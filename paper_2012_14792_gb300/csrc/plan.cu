@@ -60,7 +60,9 @@ int build_plan(int W, int H, int n, int k, HostPlan *p) {
         }
     p->items.clear();
     p->slot_of.assign((size_t)nwin * p->nb, -1);
+    p->band_items.assign(p->nb + 1, 0);
     for (int b = 0; b < p->nb; ++b) {
+        p->band_items[b] = (int32_t)p->items.size();
         const uint64_t wb = line_px(p->band_x1[b], W) - line_px(p->band_x0[b], W);
         int prev_lo = -1, prev_hi = -1, prev_slot = -1;
         for (int wi = 0; wi < nwin; ++wi) {
@@ -89,6 +91,7 @@ int build_plan(int W, int H, int n, int k, HostPlan *p) {
             p->slot_of[(size_t)wi * p->nb + b] = prev_slot;
         }
     }
+    p->band_items[p->nb] = (int32_t)p->items.size();
     return TRS_OK;
 }
 
@@ -98,6 +101,7 @@ size_t plan_blob_bytes(const HostPlan &p) {
     s += align256(p.items.size() * sizeof(PlanItem) + 16);
     s += align256(p.slot_of.size() * sizeof(int32_t) + 4);
     s += 2 * align256(p.band_x0.size() * sizeof(int16_t) + 2);
+    s += align256(p.band_items.size() * sizeof(int32_t) + 4);
     return s;
 }
 
@@ -126,6 +130,7 @@ void plan_serialize(const HostPlan &p, uint8_t *dev_base, std::vector<uint8_t> &
     d.slot_of = (const int32_t *)put(p.slot_of.data(), p.slot_of.size() * sizeof(int32_t), 4);
     d.band_x0 = (const int16_t *)put(p.band_x0.data(), p.band_x0.size() * sizeof(int16_t), 2);
     d.band_x1 = (const int16_t *)put(p.band_x1.data(), p.band_x1.size() * sizeof(int16_t), 2);
+    d.band_items = (const int32_t *)put(p.band_items.data(), p.band_items.size() * sizeof(int32_t), 4);
     std::copy((const uint8_t *)&d, (const uint8_t *)&d + sizeof(d), blob.begin());
 }
 

@@ -15,6 +15,7 @@ struct HostPlan {
     std::vector<PlanItem> items;
     std::vector<int32_t> slot_of;
     std::vector<int16_t> band_x0, band_x1;
+    std::vector<int32_t> band_items;  // [nb+1] prefix of items per band
 };
 
 struct SearchScratch {

@@ -14,17 +14,17 @@
 // Windows that give a band the same admissible slice heights share one row
 // DP ("item" of the shape's plan).
 //
-//  band_kernel<STEP>    one warp per (frame, item): lanes are the start row
-//                       y of the remaining rows [y, R); for k = 1..kmax it
+//  band_kernel<STEP>    one warp per (frame, tile column), running all of
+//                       the column's items: lanes are the start row y of
+//                       the remaining rows [y, R); for k = 1..kmax it
 //                       relaxes every admissible slice height d, pulling
 //                       G_{k-1}[y+d] from lane y+d with a shuffle.  Step 1
 //                       combines with max (Eq. 1), step 2 with + (Eq. 2) and
 //                       drops slices whose time exceeds the Eq. 4 bound.
-//  column_kernel<STEP>  one block per (frame, window): DP over tile-column
-//                       right edges with lanes over the slice count m; the
-//                       warps split the candidate edges and merge with a
-//                       shared-memory atomicMin.  Step 1's window minima
-//                       reduce into T_min (Eq. 3), step 2's into Q*.
+//  column_kernel<STEP>  one warp per (frame, window): DP over tile-column
+//                       right edges with lanes over the slice count m.
+//                       Step 1's window minima reduce into T_min (Eq. 3),
+//                       step 2's into Q*.
 //  rebuild_kernel       one warp per (frame, window): in a window that
 //                       reaches Q*, rebuilds the smallest canonical code
 //                       (smallest next edge first, then the smallest cut
@@ -42,6 +42,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBandWarps = 4;   // warps per block of band_kernel
 constexpr int kColWarps = 4;    // warps per block of column_kernel
+constexpr int kBatch = 8;       // candidate edges whose V rows column_kernel loads together
 // Saturating infinity inside the DPs: sums of a value below 2^44 and kSoft
 // stay below 2^63, so the relaxations need no infinity branches.
 constexpr uint64_t kSoft = 1ull << 62;
@@ -123,42 +124,111 @@ __device__ void item_dp(const DevFrame &fr, const PlanItem &it, uint64_t thr, in
     __syncwarp();
 }
 
+// Row DPs, one warp per (frame, tile column): the column's slice values
+// for every height d are staged once in shared memory (stage[(d-1)*32 + y];
+// step 2 also keeps, per lane, a bit per height for the Eq. 4 bound on the
+// slice time), then every item of the column runs from there: its
+// admissible heights become a per-lane bit mask and the k loop only
+// shuffles G_{k-1}[y+d] from lane y+d and relaxes.  V[k] = G_k[0] is
+// collected in lane k and stored with one coalesced write per item.
 template <int STEP>
 __global__ void __launch_bounds__(kBandWarps * 32) band_kernel(LaunchArgs args, int total, int stage_words) {
     extern __shared__ uint64_t bsm[];
-    const int wib = threadIdx.x >> 5;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kBandWarps + wib;
     if (gw >= total) return;
-    int local;
-    const int f = locate(args, args.pre.items, args.single_items, gw, &local);
+    int b;
+    const int f = locate(args, args.pre.bands, args.single_bands, gw, &b);
     const DevFrame &fr = frame_at(args, f);
     const DevPlan &pl = *fr.plan;
-    const int lane = threadIdx.x & 31;
-    const int n = pl.n;
-    uint64_t *V = (STEP == 1 ? fr.V1 : fr.V2) + (size_t)local * (n + 1);
-    const PlanItem it = pl.items[local];
-    bool skip = frame_status(fr) != TRS_OK;
-    uint64_t thr = kInf;
-    if (STEP == 2 && !skip) {
-        // an item only matters if one of its windows still meets Eq. 4
-        thr = eq4_threshold(fr.scal[0], fr.lambda_q);
-        bool need = false;
-        for (int w = it.w_first + lane; w <= it.w_last; w += 32) need |= fr.wres1[w] <= thr;
-        skip = !__any_sync(kFull, need);
-    }
-    if (skip) {
-        for (int k = lane; k <= n; k += 32) V[k] = kInf;
+    const int n = pl.n, R = fr.R, H = fr.H;
+    const int i0 = pl.band_items[b], i1 = pl.band_items[b + 1];
+    if (i0 == i1) return;
+    uint64_t *Vall = STEP == 1 ? fr.V1 : fr.V2;
+    if (frame_status(fr) != TRS_OK) {
+        for (int ii = i0; ii < i1; ++ii)
+            for (int k = lane; k <= n; k += 32) Vall[(size_t)ii * (n + 1) + k] = kInf;
         return;
     }
-    item_dp<STEP>(fr, it, thr, n, V, nullptr, bsm + (size_t)wib * stage_words);
+    const uint64_t thr = STEP == 2 ? eq4_threshold(fr.scal[0], fr.lambda_q) : kInf;
+    const TablesOffsets off = tables_offsets(fr.C, R);
+    const size_t base = (size_t)b * R * R;
+    const uint64_t *RT = reinterpret_cast<const uint64_t *>(fr.tables + off.rect_t) + base;
+    const uint64_t *RQ = reinterpret_cast<const uint64_t *>(fr.tables + off.rect_q) + base;
+    uint64_t *stage = bsm + (size_t)wib * stage_words;
+    uint32_t tok = 0;  // step 2: bit d-1 set if the slice [lane, lane+d) meets the Eq. 4 bound
+#pragma unroll 4
+    for (int d = 1; d <= R; ++d) {
+        const bool in = lane < R && lane + d <= R;
+        const size_t e = in ? (size_t)(d - 1) * R + lane : 0;
+        const uint64_t tv = __ldg(RT + e);
+        if (STEP == 2) {
+            stage[(d - 1) * 32 + lane] = __ldg(RQ + e);
+            tok |= (in && tv <= thr ? 1u : 0u) << (d - 1);
+        } else {
+            stage[(d - 1) * 32 + lane] = tv;
+        }
+    }
+    __syncwarp();
+    const uint32_t ytop = line_px(lane, H);
+    for (int ii = i0; ii < i1; ++ii) {
+        const PlanItem it = pl.items[ii];
+        uint64_t *V = Vall + (size_t)ii * (n + 1);
+        if (STEP == 2) {
+            // an item only matters if one of its windows still meets Eq. 4
+            bool need = false;
+            for (int w = it.w_first + lane; w <= it.w_last; w += 32) need |= fr.wres1[w] <= thr;
+            if (!__any_sync(kFull, need)) {
+                for (int k = lane; k <= n; k += 32) V[k] = kInf;
+                continue;
+            }
+        }
+        const int dmin = max(1, (int)((it.hlo + kCtu - 1) / kCtu));
+        const int dmax = min(R, (int)(it.hhi / kCtu) + 1);
+        const int nd = dmax - dmin + 1;
+        uint32_t vmask = 0;
+        for (int i = 0; i < nd; ++i) {
+            const int d = dmin + i, y1 = lane + d;
+            const uint32_t h = line_px(y1, H) - ytop;
+            const bool ok = lane < R && y1 <= R && h >= it.hlo && h <= it.hhi &&
+                            (STEP == 1 || ((tok >> (d - 1)) & 1u));
+            vmask |= (ok ? 1u : 0u) << i;
+        }
+        const uint64_t *st = stage + (dmin - 1) * 32 + lane;
+        uint64_t G = (lane == R) ? 0ull : kSoft;  // G_0: only the empty remainder
+        uint64_t vreg = kInf;                      // lane k keeps V[k] (lane 0 keeps V[32])
+        for (int k = 1; k <= it.kmax; ++k) {
+            const uint64_t edge = (k == 1) ? 0ull : kSoft;  // G_{k-1}[R] when R == 32
+            uint64_t best = kSoft;
+            for (int i = 0; i < nd; ++i) {
+                const int src = lane + dmin + i;
+                uint64_t prev = __shfl_sync(kFull, G, src & 31);
+                if (src >= 32) prev = edge;
+                if ((vmask >> i) & 1u) {
+                    const uint64_t val = st[i * 32];
+                    best = umin64(best, STEP == 1 ? umax64(prev, val) : prev + val);
+                }
+            }
+            G = umin64(best, kSoft);
+            const uint64_t g0 = __shfl_sync(kFull, G, 0);
+            if (lane == (k & 31)) vreg = hard_inf(g0);
+        }
+        if (lane == 0) {
+            V[0] = kInf;
+            if (n == 32) V[32] = vreg;
+        } else if (lane <= n) {
+            V[lane] = vreg;
+        }
+    }
 }
 
 // Suffix DP over tile-column edges of one window, one warp:
 //   H[x][m] = min over x1 > x, k of  V[item(w, [x,x1))][k] (+|max) H[x1][m-k],
 // H[C][0] = 0.  Lane m-1 owns slice count m.  For each x the lanes fetch
-// the items of all candidate edges at once; each edge then contributes only
-// the slice counts k whose V is finite (a ballot over its V row), and the V
-// row of the next edge is loaded while the current one is relaxed.
+// the items of all candidate edges at once; V rows are then loaded eight
+// edges at a time (lanes over k, loads of a batch in flight together) and
+// each edge contributes only the slice counts whose V is finite (a ballot
+// per row).
 template <int STEP>
 __global__ void __launch_bounds__(kColWarps * 32) column_kernel(LaunchArgs args, int total, int h_words) {
     extern __shared__ uint64_t csm[];
@@ -193,38 +263,33 @@ __global__ void __launch_bounds__(kColWarps * 32) column_kernel(LaunchArgs args,
     const int m = lane + 1;
     for (int x = C - 1; x >= 0; --x) {
         uint64_t acc = kSoft;
-        for (int half = 0; half * 32 < C - x; ++half) {
-            const int x1l = x + 1 + half * 32 + lane;
-            const int sl = x1l <= C ? slot_row[band_index(C, x, x1l)] : -1;
-            unsigned mask = __ballot_sync(kFull, sl >= 0);
-            if (!mask) continue;
-            int j = __ffs(mask) - 1;
-            mask &= mask - 1;
-            int slot = __shfl_sync(kFull, sl, j);
-            uint64_t vk = lane < n ? V[(size_t)slot * stride + lane + 1] : kInf;
-            while (true) {
-                int jn = -1;
-                uint64_t vn = kInf;
-                if (mask) {
-                    jn = __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    const int sn = __shfl_sync(kFull, sl, jn);
-                    vn = lane < n ? V[(size_t)sn * stride + lane + 1] : kInf;
+        const int32_t *srow = slot_row + band_index(C, x, x + 1);  // edges x+1.. are consecutive bands
+        for (int base = 0; base < C - x; base += 32) {
+            const int ncand = min(32, C - x - base);
+            const int sl = lane < ncand ? srow[base + lane] : -1;
+            // edges in batches of kBatch: all V-row loads of a batch are in flight together
+            for (int j0 = 0; j0 < ncand; j0 += kBatch) {
+                uint64_t vb[kBatch];
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) {
+                    const int sj = __shfl_sync(kFull, sl, (j0 + u) & 31);
+                    vb[u] = (j0 + u < ncand && sj >= 0 && lane < n) ? __ldg(V + (size_t)sj * stride + lane + 1)
+                                                                     : kInf;
                 }
-                const uint64_t *Hrow = Hs + (size_t)(x + 1 + half * 32 + j) * stride;
-                unsigned fin = __ballot_sync(kFull, vk != kInf);
-                while (fin) {
-                    const int k = __ffs(fin);
-                    fin &= fin - 1;
-                    const uint64_t v = __shfl_sync(kFull, vk, k - 1);
-                    if (m >= k && m <= n) {
-                        const uint64_t h = Hrow[m - k];
-                        acc = umin64(acc, STEP == 1 ? umax64(v, h) : v + h);
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) {
+                    unsigned fin = __ballot_sync(kFull, vb[u] != kInf);
+                    const uint64_t *Hrow = Hs + (size_t)(x + 1 + base + j0 + u) * stride;
+                    while (fin) {
+                        const int k = __ffs(fin);
+                        fin &= fin - 1;
+                        const uint64_t v = __shfl_sync(kFull, vb[u], k - 1);
+                        if (m >= k && m <= n) {
+                            const uint64_t h = Hrow[m - k];
+                            acc = umin64(acc, STEP == 1 ? umax64(v, h) : v + h);
+                        }
                     }
                 }
-                if (jn < 0) break;
-                j = jn;
-                vk = vn;
             }
         }
         if (m <= n) Hs[x * stride + m] = umin64(acc, kSoft);
@@ -485,7 +550,7 @@ int prepare_search_kernels() {
     return (int)e;
 }
 
-int launch_search(const LaunchArgs &a, int total_items, int total_windows, int maxC, int maxR, int maxN,
+int launch_search(const LaunchArgs &a, int total_bands, int total_windows, int maxC, int maxR, int maxN,
                   uint64_t *scal, size_t nscal, void *stream, cudaEvent_t *ev) {
     cudaStream_t s = (cudaStream_t)stream;
     // T_min and Q* start at +infinity; the column kernels reduce into them
@@ -495,18 +560,20 @@ int launch_search(const LaunchArgs &a, int total_items, int total_windows, int m
     const size_t band_smem = (size_t)kBandWarps * stage_words * sizeof(uint64_t);
     const int h_words = (maxC + 1) * (maxN + 1);
     const size_t col_smem = (size_t)kColWarps * h_words * sizeof(uint64_t);
-    const int bb = (total_items + kBandWarps - 1) / kBandWarps;
+    const int bb = (total_bands + kBandWarps - 1) / kBandWarps;
     const int cb = (total_windows + kColWarps - 1) / kColWarps;
     auto mark = [&](int i) {
         if (ev && e == cudaSuccess) e = cudaEventRecordWithFlags(ev[i], s, cudaEventRecordExternal);
     };
-    if (total_items > 0) band_kernel<1><<<bb, kBandWarps * 32, band_smem, s>>>(a, total_items, stage_words);
+    if (total_bands > 0) band_kernel<1><<<bb, kBandWarps * 32, band_smem, s>>>(a, total_bands, stage_words);
     mark(0);
-    if (total_windows > 0) column_kernel<1><<<cb, kColWarps * 32, col_smem, s>>>(a, total_windows, h_words);
+    if (total_windows > 0)
+        column_kernel<1><<<cb, kColWarps * 32, col_smem, s>>>(a, total_windows, h_words);
     mark(1);
-    if (total_items > 0) band_kernel<2><<<bb, kBandWarps * 32, band_smem, s>>>(a, total_items, stage_words);
+    if (total_bands > 0) band_kernel<2><<<bb, kBandWarps * 32, band_smem, s>>>(a, total_bands, stage_words);
     mark(2);
-    if (total_windows > 0) column_kernel<2><<<cb, kColWarps * 32, col_smem, s>>>(a, total_windows, h_words);
+    if (total_windows > 0)
+        column_kernel<2><<<cb, kColWarps * 32, col_smem, s>>>(a, total_windows, h_words);
     mark(3);
     const int layer_words = (maxN + 1) * 32;
     const size_t rb_smem = (size_t)(layer_words + stage_words) * sizeof(uint64_t);

@@ -101,6 +101,7 @@ struct DevPlan {
     const int32_t *slot_of;     // [nwin * nb]: item of (window, band), -1 if the band has no slice there
     const int16_t *band_x0;     // [nb]
     const int16_t *band_x1;     // [nb]
+    const int32_t *band_items;  // [nb+1]: items of band b are [band_items[b], band_items[b+1])
 };
 
 // A canonical code: c tile columns with right edges xe[1..c] (xe[0] = 0)
@@ -147,6 +148,7 @@ struct WorkPrefix {
     const int32_t *bandgrp;  // tables: groups of kBandsPerBlock bands
     const int32_t *items;    // search rows: plan items
     const int32_t *windows;  // search columns: plan windows
+    const int32_t *bands;    // search rows: tile columns (one warp each, all of its items)
 };
 
 constexpr int kBandsPerBlock = 8;
@@ -156,7 +158,7 @@ struct LaunchArgs {
     const DevFrame *frames;     // device array of nframes, or nullptr
     int nframes;
     WorkPrefix pre;             // device arrays (unused when nframes == 1 and frames == nullptr)
-    int single_ctus, single_bandgrp, single_items, single_windows;
+    int single_ctus, single_bandgrp, single_items, single_windows, single_bands;
 };
 
 __device__ inline const DevFrame &frame_at(const LaunchArgs &a, int f) {
@@ -188,7 +190,7 @@ int launch_tables(const LaunchArgs &a, int total_groups, int maxC, int maxR, voi
 // scal: the T_min / Q* words of every frame of the launch (reset to +inf first).
 // ev (optional, 6 events): recorded after each of the six search kernels.
 // maxC / maxR / maxN: largest C, R and n over the frames of the launch (shared-memory sizing).
-int launch_search(const LaunchArgs &a, int total_items, int total_windows, int maxC, int maxR, int maxN,
+int launch_search(const LaunchArgs &a, int total_bands, int total_windows, int maxC, int maxR, int maxN,
                   uint64_t *scal, size_t nscal, void *stream, cudaEvent_t *ev = nullptr);
 
 }  // namespace trs
