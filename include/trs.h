@@ -112,7 +112,8 @@ typedef struct trs_tables_layout {
                             tile column b, CTU rows [y, y+d) (Eq. 1); band b of columns [x0,x1)
                             has b = x0*(2C-x0+1)/2 + (x1-x0-1); entries with y+d > R are unused */
     size_t off_rect_q;   /* uint64 [bands][R][R]: floor of the slice's luma SSE (Eq. 2), same index */
-    size_t off_status;   /* int32 [4]: [0] data status of this frame (TRS_OK / TRS_ERANGE) */
+    size_t off_status;   /* int32 [4]: [0] data status of this frame (TRS_OK / TRS_ERANGE), [1] W, [2] H,
+                            [3] 1 if the frame's total Q16 time is below 2^31 */
 } trs_tables_layout;
 
 /* The decision for one frame, written by the device. */

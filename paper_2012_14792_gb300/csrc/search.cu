@@ -51,6 +51,22 @@ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < 
 __device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
 __device__ __forceinline__ uint64_t hard_inf(uint64_t v) { return v >= kSoft ? kInf : v; }
 
+template <typename VT>
+struct Soft;  // saturating infinity of a value type
+template <>
+struct Soft<uint64_t> {
+    static constexpr uint64_t v = kSoft;
+};
+template <>
+struct Soft<uint32_t> {
+    static constexpr uint32_t v = 1u << 31;  // step-1 values of a frame whose total time is below 2^31
+};
+
+__device__ __forceinline__ bool frame_t32(const DevFrame &fr) {
+    const TablesOffsets off = tables_offsets(fr.C, fr.R);
+    return reinterpret_cast<const int32_t *>(fr.tables + off.status)[3] != 0;
+}
+
 __device__ __forceinline__ int32_t frame_status(const DevFrame &fr) {
     const TablesOffsets off = tables_offsets(fr.C, fr.R);
     return *reinterpret_cast<const int32_t *>(fr.tables + off.status);
@@ -124,6 +140,36 @@ __device__ void item_dp(const DevFrame &fr, const PlanItem &it, uint64_t thr, in
     __syncwarp();
 }
 
+// k loop of one item (see band_kernel).  Lane y holds G_{k-1}[y]; lane R
+// (or the edge value when R == 32) holds the empty remainder.  Returns, in
+// lane k (lane 0 for k = 32), V[k] = G_k[0] with kInf where no split exists.
+template <int STEP, typename VT>
+__device__ __forceinline__ uint64_t item_rows(const uint64_t *st, int nd, int dmin, uint32_t vmask, int kmax,
+                                              int R) {
+    const int lane = threadIdx.x & 31;
+    constexpr VT soft = Soft<VT>::v;
+    VT G = (lane == R) ? VT(0) : soft;  // G_0: only the empty remainder holds zero slices
+    uint64_t vreg = kInf;
+    for (int k = 1; k <= kmax; ++k) {
+        const VT edge = (k == 1) ? VT(0) : soft;  // G_{k-1}[R] when R == 32
+        VT best = soft;
+        for (int i = 0; i < nd; ++i) {
+            const int src = lane + dmin + i;
+            VT prev = __shfl_sync(kFull, G, src & 31);
+            if (src >= 32) prev = edge;
+            if ((vmask >> i) & 1u) {
+                const VT val = (VT)st[i * 32];
+                const VT c = STEP == 1 ? (prev > val ? prev : val) : VT(prev + val);
+                best = c < best ? c : best;
+            }
+        }
+        G = best < soft ? best : soft;
+        const VT g0 = __shfl_sync(kFull, G, 0);
+        if (lane == (k & 31)) vreg = g0 >= soft ? kInf : (uint64_t)g0;
+    }
+    return vreg;
+}
+
 // Row DPs, one warp per (frame, tile column): the column's slice values
 // for every height d are staged once in shared memory (stage[(d-1)*32 + y];
 // step 2 also keeps, per lane, a bit per height for the Eq. 4 bound on the
@@ -151,6 +197,7 @@ __global__ void __launch_bounds__(kBandWarps * 32) band_kernel(LaunchArgs args, 
         return;
     }
     const uint64_t thr = STEP == 2 ? eq4_threshold(fr.scal[0], fr.lambda_q) : kInf;
+    const bool t32 = STEP == 1 && frame_t32(fr);
     const TablesOffsets off = tables_offsets(fr.C, R);
     const size_t base = (size_t)b * R * R;
     const uint64_t *RT = reinterpret_cast<const uint64_t *>(fr.tables + off.rect_t) + base;
@@ -195,24 +242,8 @@ __global__ void __launch_bounds__(kBandWarps * 32) band_kernel(LaunchArgs args, 
             vmask |= (ok ? 1u : 0u) << i;
         }
         const uint64_t *st = stage + (dmin - 1) * 32 + lane;
-        uint64_t G = (lane == R) ? 0ull : kSoft;  // G_0: only the empty remainder
-        uint64_t vreg = kInf;                      // lane k keeps V[k] (lane 0 keeps V[32])
-        for (int k = 1; k <= it.kmax; ++k) {
-            const uint64_t edge = (k == 1) ? 0ull : kSoft;  // G_{k-1}[R] when R == 32
-            uint64_t best = kSoft;
-            for (int i = 0; i < nd; ++i) {
-                const int src = lane + dmin + i;
-                uint64_t prev = __shfl_sync(kFull, G, src & 31);
-                if (src >= 32) prev = edge;
-                if ((vmask >> i) & 1u) {
-                    const uint64_t val = st[i * 32];
-                    best = umin64(best, STEP == 1 ? umax64(prev, val) : prev + val);
-                }
-            }
-            G = umin64(best, kSoft);
-            const uint64_t g0 = __shfl_sync(kFull, G, 0);
-            if (lane == (k & 31)) vreg = hard_inf(g0);
-        }
+        const uint64_t vreg = (STEP == 1 && t32) ? item_rows<1, uint32_t>(st, nd, dmin, vmask, it.kmax, R)
+                                                 : item_rows<STEP, uint64_t>(st, nd, dmin, vmask, it.kmax, R);
         if (lane == 0) {
             V[0] = kInf;
             if (n == 32) V[32] = vreg;
@@ -220,6 +251,61 @@ __global__ void __launch_bounds__(kBandWarps * 32) band_kernel(LaunchArgs args, 
             V[lane] = vreg;
         }
     }
+}
+
+// The column DP of one window (see column_kernel) on values of type VT in
+// the warp's shared-memory table Hraw ((C+1)*(n+1) words of 8 bytes).
+// Returns H[0][n] with kInf where no partition exists; for 64-bit values
+// the table keeps every entry (kSoft for none) for the rebuild.
+template <int STEP, typename VT>
+__device__ uint64_t column_dp(uint64_t *Hraw, const uint64_t *V, const int32_t *slot_row, int C, int n) {
+    const int lane = threadIdx.x & 31;
+    const int stride = n + 1;
+    constexpr VT soft = Soft<VT>::v;
+    VT *Hs = reinterpret_cast<VT *>(Hraw);
+    for (int i = lane; i < (C + 1) * stride; i += 32) Hs[i] = soft;
+    __syncwarp();
+    if (lane == 0) Hs[C * stride] = 0;
+    __syncwarp();
+    const int m = lane + 1;
+    for (int x = C - 1; x >= 0; --x) {
+        VT acc = soft;
+        const int32_t *srow = slot_row + band_index(C, x, x + 1);  // edges x+1.. are consecutive bands
+        for (int base = 0; base < C - x; base += 32) {
+            const int ncand = min(32, C - x - base);
+            const int sl = lane < ncand ? srow[base + lane] : -1;
+            // edges in batches of kBatch: all V-row loads of a batch are in flight together
+            for (int j0 = 0; j0 < ncand; j0 += kBatch) {
+                uint64_t vb[kBatch];
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) {
+                    const int sj = __shfl_sync(kFull, sl, (j0 + u) & 31);
+                    vb[u] = (j0 + u < ncand && sj >= 0 && lane < n) ? __ldg(V + (size_t)sj * stride + lane + 1)
+                                                                     : kInf;
+                }
+#pragma unroll
+                for (int u = 0; u < kBatch; ++u) {
+                    unsigned fin = __ballot_sync(kFull, vb[u] != kInf);
+                    const VT *Hrow = Hs + (size_t)(x + 1 + base + j0 + u) * stride;
+                    const VT vv = (VT)vb[u];
+                    while (fin) {
+                        const int k = __ffs(fin);
+                        fin &= fin - 1;
+                        const VT v = __shfl_sync(kFull, vv, k - 1);
+                        if (m >= k && m <= n) {
+                            const VT h = Hrow[m - k];
+                            const VT c = STEP == 1 ? (v > h ? v : h) : VT(v + h);
+                            acc = c < acc ? c : acc;
+                        }
+                    }
+                }
+            }
+        }
+        if (m <= n) Hs[x * stride + m] = acc < soft ? acc : soft;
+        __syncwarp();
+    }
+    const VT r = Hs[n];
+    return r >= soft ? kInf : (uint64_t)r;
 }
 
 // Suffix DP over tile-column edges of one window, one warp:
@@ -254,53 +340,18 @@ __global__ void __launch_bounds__(kColWarps * 32) column_kernel(LaunchArgs args,
             return;
         }
     }
-    uint64_t *Hs = csm + (size_t)wib * h_words;
-    for (int i = lane; i < (C + 1) * stride; i += 32) Hs[i] = kSoft;
-    __syncwarp();
-    if (lane == 0) Hs[C * stride] = 0;
-    __syncwarp();
     const int32_t *slot_row = pl.slot_of + (size_t)w * nb;
-    const int m = lane + 1;
-    for (int x = C - 1; x >= 0; --x) {
-        uint64_t acc = kSoft;
-        const int32_t *srow = slot_row + band_index(C, x, x + 1);  // edges x+1.. are consecutive bands
-        for (int base = 0; base < C - x; base += 32) {
-            const int ncand = min(32, C - x - base);
-            const int sl = lane < ncand ? srow[base + lane] : -1;
-            // edges in batches of kBatch: all V-row loads of a batch are in flight together
-            for (int j0 = 0; j0 < ncand; j0 += kBatch) {
-                uint64_t vb[kBatch];
-#pragma unroll
-                for (int u = 0; u < kBatch; ++u) {
-                    const int sj = __shfl_sync(kFull, sl, (j0 + u) & 31);
-                    vb[u] = (j0 + u < ncand && sj >= 0 && lane < n) ? __ldg(V + (size_t)sj * stride + lane + 1)
-                                                                     : kInf;
-                }
-#pragma unroll
-                for (int u = 0; u < kBatch; ++u) {
-                    unsigned fin = __ballot_sync(kFull, vb[u] != kInf);
-                    const uint64_t *Hrow = Hs + (size_t)(x + 1 + base + j0 + u) * stride;
-                    while (fin) {
-                        const int k = __ffs(fin);
-                        fin &= fin - 1;
-                        const uint64_t v = __shfl_sync(kFull, vb[u], k - 1);
-                        if (m >= k && m <= n) {
-                            const uint64_t h = Hrow[m - k];
-                            acc = umin64(acc, STEP == 1 ? umax64(v, h) : v + h);
-                        }
-                    }
-                }
-            }
-        }
-        if (m <= n) Hs[x * stride + m] = umin64(acc, kSoft);
-        __syncwarp();
-    }
-    const uint64_t res = hard_inf(Hs[n]);
+    uint64_t res;
+    if (STEP == 1 && frame_t32(fr))
+        res = column_dp<1, uint32_t>(csm + (size_t)wib * h_words, V, slot_row, C, n);
+    else
+        res = column_dp<STEP, uint64_t>(csm + (size_t)wib * h_words, V, slot_row, C, n);
     if (lane == 0) {
         wres[w] = res;
         if (res != kInf) atomicMin(reinterpret_cast<unsigned long long *>(&fr.scal[STEP == 1 ? 0 : 1]), res);
     }
     if (STEP == 2) {
+        const uint64_t *Hs = csm + (size_t)wib * h_words;
         uint64_t *H2 = fr.H2 + (size_t)w * (C + 1) * stride;
         for (int i = lane; i < (C + 1) * stride; i += 32) H2[i] = hard_inf(Hs[i]);
     }

@@ -140,7 +140,9 @@ __global__ void __launch_bounds__(kTabThreads) tables_kernel(LaunchArgs args) {
             st[0] = (bad || sample_bad) ? TRS_ERANGE : TRS_OK;
             st[1] = W;
             st[2] = H;
-            st[3] = 0;
+            // 1 when every slice time (at most the frame total) fits 31 bits:
+            // the step-1 DPs may then run on 32-bit values
+            st[3] = satt[R * (C + 1) + C] < (1ull << 31) ? 1 : 0;
         }
     }
 }

@@ -270,3 +270,19 @@ def test_batch_graph_replay_with_new_frames(dec, oracle):
         for it, p in zip(items, ps):
             d, _, _ = oracle.decide(it.plane, it.times, it.spec.bit_depth, it.n_regions, it.lam)
             assert_partition_equal(p, d, it.spec.ctu_rows)
+
+
+@pytest.mark.parametrize("scale,flag", [(1.0, 1), (2000.0, 0)])
+def test_step1_value_width_paths(dec, oracle, scale, flag):
+    """Frames whose total Q16 time is below 2^31 run step 1 on 32-bit values,
+    others on 64-bit values; both must give the oracle's partition."""
+    for seed in range(3):
+        plane, times = synth.make_frame(synth.SPEC_1080P10, 40 + seed)
+        times = np.minimum(times * np.float32(scale), np.float32(65535.0)).astype(np.float32)
+        _, st, _keep = _texture(dec, plane, 10)
+        tab = dec.tables_buffer(1920, 1080)
+        dec.region_tables(st, torch.from_numpy(times).cuda(), 1920, 1080, tab)
+        p = dec.partitions(dec.search(tab, 1920, 1080, 8, 0.1))[0]
+        assert int(dec.read_tables(tab, 1920, 1080)["status"][3]) == flag
+        d, _, _ = oracle.decide(plane, times, 10, 8, 0.1)
+        assert_partition_equal(p, d, 9)
