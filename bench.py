@@ -124,6 +124,103 @@ def cpu_baseline(frames, budget_s: float = 12.0):
             "sample": f"{done} of the {NFRAMES} workload frames, oracle texture + Q16 + exact DP search, 1 thread"}
 
 
+def run_serving(trs, device: int, duration_s: float = 2.0, saturate_s: float = 1.0):
+    """32 concurrent streams (half 1080p10 n=8, half 2160p10 n=16) with
+    Poisson arrivals at U[30, 60] fps each, through the continuous-batching
+    server.  Latency = wait before the server accepted the frame (both of the
+    stream's slots busy) + the server's submit-to-ready time."""
+    import collections
+
+    import synth
+    import torch
+
+    streams = synth.serving_streams(32)
+    arrivals = synth.poisson_arrivals(streams, duration_s)
+    pool = {}
+    for spec in (synth.SPEC_1080P10, synth.SPEC_2160P10):
+        pool[spec.name] = [torch.from_numpy(np.ascontiguousarray(synth.make_frame(spec, seed=900 + k,
+                                                                                   workload="serve")[0])
+                                            .view(np.uint8)).pin_memory() for k in range(4)]
+    srv = trs.trs_server_create(3840, 2160, max_regions=16, max_streams=32, max_batch=32, max_inflight=3,
+                                device=device)
+    try:
+        sids = []
+        for st in streams:
+            sid = trs.trs_server_open_stream(srv, st.spec.width, st.spec.height, st.spec.bit_depth, st.n_regions,
+                                             0.1)
+            _, times = synth.make_frame(st.spec, seed=7, stream=st.stream, workload="serve")
+            trs.trs_server_update_times(srv, sid, np.ascontiguousarray(times))
+            sids.append(sid)
+
+        def frame(i, f):
+            buf = pool[streams[i].spec.name][f % 4]
+            return buf, streams[i].spec.width * 2
+
+        # warm-up: one frame per stream
+        for i, sid in enumerate(sids):
+            b, pitch = frame(i, 0)
+            trs.trs_server_submit(srv, sid, b, pitch)
+        got = 0
+        while got < len(sids):
+            got += len(trs.trs_server_poll(srv, 64, 100_000))
+
+        # Poisson arrivals
+        lat = []
+        waiting = collections.deque()
+        accepted = {}
+        t0 = time.perf_counter()
+        k = 0
+        while k < len(arrivals) or waiting or accepted:
+            now = time.perf_counter() - t0
+            while k < len(arrivals) and arrivals[k][0] <= now:
+                waiting.append(arrivals[k])
+                k += 1
+            still = collections.deque()
+            for (ta, i, f) in waiting:
+                b, pitch = frame(i, f)
+                try:
+                    tk = trs.trs_server_submit(srv, sids[i], b, pitch)
+                    accepted[tk] = (time.perf_counter() - t0) - ta
+                except trs.TrsError as e:
+                    if e.status != trs.EBUSY:
+                        raise
+                    still.append((ta, i, f))
+            waiting = still
+            nxt = arrivals[k][0] - (time.perf_counter() - t0) if k < len(arrivals) else 0.0
+            for d in trs.trs_server_poll(srv, 64, int(max(50, min(2000, nxt * 1e6)))):
+                assert d.status == 0
+                lat.append(accepted.pop(d.ticket) * 1e3 + d.latency_us / 1e3)
+        elapsed = time.perf_counter() - t0
+        lat = np.array(lat)
+
+        # saturation: every stream keeps both request slots busy
+        done = 0
+        f = 0
+        t1 = time.perf_counter()
+        while time.perf_counter() - t1 < saturate_s:
+            for i, sid in enumerate(sids):
+                b, pitch = frame(i, f)
+                try:
+                    trs.trs_server_submit(srv, sid, b, pitch)
+                except trs.TrsError as e:
+                    if e.status != trs.EBUSY:
+                        raise
+            f += 1
+            done += len(trs.trs_server_poll(srv, 64, 200))
+        while trs.trs_server_info(srv).inflight:
+            done += len(trs.trs_server_poll(srv, 64, 10_000))
+        sat_dt = time.perf_counter() - t1
+        info = trs.trs_server_info(srv)
+        return {"streams": len(sids), "offered_per_s": len(arrivals) / duration_s,
+                "decisions": int(len(lat)), "achieved_per_s": len(lat) / elapsed,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "max_ms": float(lat.max()), "saturated_per_s": done / sat_dt,
+                "mean_batch": info.frames / max(1, info.batches), "device_bytes": int(info.mem_used_bytes),
+                "form": "continuous batching, 3 batches in flight on separate CUDA streams"}
+    finally:
+        trs.trs_server_destroy(srv)
+
+
 def run_reference(args, rank, world):
     """Reference arm: the oracle timed on this host's cores, same metric."""
     if rank != 0:
@@ -162,6 +259,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--frames", type=int, default=NFRAMES,
                     help="frames per step (a smaller case for profiling; the metric uses 64)")
     args = ap.parse_args()
@@ -295,6 +393,10 @@ def main():
     tex_roof = {"kernel": "texture_kernel", "bound": "hbm", "achieved": tex_gbs, "peak": hbm, "unit": "GB/s",
                 "frac": tex_gbs / hbm, "peak_source": src}
 
+    serving = None
+    if not args.no_serving:
+        serving = run_serving(trs, local)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(frames)
@@ -307,7 +409,7 @@ def main():
                            "frames_per_step": nfr, "form": "batched, CUDA graph",
                            "l2": f"inputs {tex_bytes / 1e9:.2f} GB per step > L2, no flush"},
                 "plain": {"value": plain_value, "unit": UNIT, "form": "one frame per launch chain"},
-                "stage_ms": stage, "clocks": clk.summary(), "e2e": e2e,
+                "stage_ms": stage, "serving": serving, "clocks": clk.summary(), "e2e": e2e,
                 "gpu_launches": 8 * args.steps, "roofline": roof, "roofline_texture": tex_roof,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

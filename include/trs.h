@@ -156,7 +156,8 @@ typedef struct trs_frame_desc {
 /* --- introspection (no GPU needed) --------------------------------------- */
 
 /* Size in bytes of the ABI structure called `name` ("trs_opts",
- * "trs_ctu_stats", "trs_tables_layout", "trs_partition", "trs_frame_desc"),
+ * "trs_ctu_stats", "trs_tables_layout", "trs_partition", "trs_frame_desc",
+ * "trs_server_opts", "trs_decision", "trs_server_stats"),
  * 0 for an unknown name; lets bindings check their copies of the layouts. */
 size_t trs_sizeof(const char *name);
 
@@ -271,6 +272,70 @@ int trs_batch_decide_host(trs_ctx *ctx, const trs_frame_desc *frames_host, int n
  * recorded inside its graph.
  * Synchronises on that call.  Returns the number of stages written. */
 int trs_batch_stage_ms(trs_ctx *ctx, float *ms, int max_stages);
+
+/* --- serving: continuous batching over many streams -------------------- */
+
+typedef struct trs_server trs_server;
+
+typedef struct trs_server_opts {
+    int max_width, max_height;  /* largest frame of any stream */
+    int max_regions;            /* largest n of any stream */
+    int max_streams;            /* streams open at once */
+    int max_batch;              /* frames per device batch */
+    int max_inflight;           /* device batches in flight at once, each on its own CUDA stream */
+    size_t mem_budget_bytes;    /* device memory the server may hold (0: no limit) */
+    int k_area;                 /* area-rule factor (3) */
+    int device;
+} trs_server_opts;
+
+typedef struct trs_decision {
+    uint64_t ticket;            /* as returned by trs_server_submit */
+    uint64_t tag;               /* the caller's tag */
+    int32_t stream_id;
+    int32_t status;             /* TRS_OK or the decision's error */
+    double latency_us;          /* from submit to the decision being ready on the host */
+    trs_partition partition;
+} trs_decision;
+
+typedef struct trs_server_stats {
+    uint64_t batches;           /* device batches launched */
+    uint64_t frames;            /* frames put in batches */
+    uint64_t decided;           /* decisions completed */
+    size_t mem_used_bytes;      /* device memory held */
+    int streams_open, pending, inflight;
+    int status;                 /* TRS_OK unless the worker met an error */
+} trs_server_stats;
+
+/* Creates a server and its worker thread.  A stream is one video being
+ * encoded; its frames are decided in order of arrival.  The server batches
+ * the pending frames of all streams (first come, first served) onto up to
+ * max_inflight concurrent device batches: frames that arrive while batches
+ * run are launched as soon as a batch slot frees up, and their work overlaps
+ * the running batches on the device.  TRS_EBUSY if the fixed memory exceeds
+ * the budget. */
+int trs_server_create(trs_server **out, const trs_server_opts *opts);
+/* Finishes the work in flight, joins the worker and frees everything. */
+int trs_server_destroy(trs_server *srv);
+/* Admits a stream: allocates its resident time map and two request slots
+ * (plane, statistics, tables, search scratch).  TRS_EBUSY when the stream
+ * table is full or the memory budget would be exceeded. */
+int trs_server_open_stream(trs_server *srv, int width, int height, int bit_depth, int n_regions, float lambda,
+                           int *stream_id);
+/* Waits (at most 10 s, else TRS_ETIMEOUT) for the stream's requests, then frees it. */
+int trs_server_close_stream(trs_server *srv, int stream_id);
+/* Replaces the stream's resident co-located CTU times (R*C floats, host
+ * memory; Sec. 2.1's estimator input for the next frames).  Waits (at most
+ * 10 s) until none of the stream's requests is in flight. */
+int trs_server_update_times(trs_server *srv, int stream_id, const float *ctu_time_host);
+/* Queues a frame (host memory, rows pitch_bytes apart, kept valid by the
+ * caller until its decision is polled).  TRS_EBUSY when both of the
+ * stream's request slots are taken; TRS_EINVAL before the first time map. */
+int trs_server_submit(trs_server *srv, int stream_id, const void *luma_host, size_t pitch_bytes, uint64_t tag,
+                      uint64_t *ticket);
+/* Returns up to max_out finished decisions, waiting at most timeout_us for
+ * the first; TRS_ETIMEOUT when none finished in time. */
+int trs_server_poll(trs_server *srv, trs_decision *out, int max_out, int timeout_us, int *n_out);
+int trs_server_info(trs_server *srv, trs_server_stats *out);
 
 #ifdef __cplusplus
 }

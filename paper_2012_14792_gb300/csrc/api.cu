@@ -9,36 +9,20 @@
 #include <tuple>
 #include <vector>
 
-#include "plan.h"
-#include "trs_internal.cuh"
+#include "ctx.h"
 
 using namespace trs;
 
 namespace {
-
 thread_local char g_err[512] = "";
+}  // namespace
+
+namespace trs {
 
 int cuda_fail(cudaError_t e, const char *what) {
     std::snprintf(g_err, sizeof(g_err), "%s: %s", what, cudaGetErrorString(e));
     return TRS_ECUDA;
 }
-
-#define TRS_CK(call)                                              \
-    do {                                                          \
-        cudaError_t e_ = (call);                                  \
-        if (e_ != cudaSuccess) return cuda_fail(e_, #call);       \
-    } while (0)
-
-#define TRS_TRY(expr)               \
-    do {                            \
-        int s_ = (expr);            \
-        if (s_ != TRS_OK) return s_; \
-    } while (0)
-
-struct DevBuf {
-    void *p = nullptr;
-    size_t n = 0;
-};
 
 int dev_alloc(DevBuf &b, size_t bytes, size_t *total) {
     if (b.n >= bytes && b.p) return TRS_OK;
@@ -67,47 +51,7 @@ void dev_free(DevBuf &b) {
     b.n = 0;
 }
 
-struct PlanEntry {
-    HostPlan host;
-    DevBuf blob;
-    const DevPlan *dev = nullptr;
-    SearchScratch scr{};
-};
-
-struct BatchGraph {
-    cudaGraphExec_t exec = nullptr;
-    size_t staged_bytes = 0;
-};
-
 uint32_t lambda_to_q(float lambda) { return (uint32_t)std::rint((double)lambda * 65536.0); }
-
-int check_frame(const trs_ctx *ctx, int W, int H);
-
-}  // namespace
-
-struct trs_ctx {
-    trs_opts o{};
-    size_t total = 0;
-    int maxC = 0, maxR = 0;
-    // one-frame path
-    DevBuf s1, s2, cnt, vmax, flags, tables, scratch, scal, part, luma_stage, time_stage;
-    // plans by (W, H, n)
-    std::map<std::tuple<int, int, int>, PlanEntry *> plans;
-    // batched path
-    DevBuf arena, desc;
-    void *staging = nullptr;  // pinned host copy of the descriptor blob
-    size_t staging_n = 0;
-    cudaStream_t cap = nullptr;
-    cudaEvent_t copied = nullptr;
-    static constexpr int kStages = 8;
-    cudaEvent_t stage[kStages + 1] = {};  // timing events recorded inside batch graphs
-    bool stage_valid = false;
-    // host-buffer batches: device staging of planes, times and partitions
-    DevBuf hb_luma, hb_time, hb_out;
-    std::map<std::vector<int64_t>, BatchGraph> graphs;
-};
-
-namespace {
 
 int check_frame(const trs_ctx *ctx, int W, int H) {
     if (W <= 0 || H <= 0 || W > ctx->o.max_width || H > ctx->o.max_height) return TRS_EINVAL;
@@ -152,7 +96,13 @@ size_t stats_bytes(int C, int R) {
     return align256((size_t)R * C * 4) * 3 + align256((size_t)R * C * 8) + 256;
 }
 
-}  // namespace
+void drop_graphs(trs_ctx *ctx) {
+    for (auto &g : ctx->graphs)
+        if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
+    ctx->graphs.clear();
+}
+
+}  // namespace trs
 
 extern "C" {
 
@@ -181,6 +131,9 @@ size_t trs_sizeof(const char *name) {
     if (!std::strcmp(name, "trs_tables_layout")) return sizeof(trs_tables_layout);
     if (!std::strcmp(name, "trs_partition")) return sizeof(trs_partition);
     if (!std::strcmp(name, "trs_frame_desc")) return sizeof(trs_frame_desc);
+    if (!std::strcmp(name, "trs_server_opts")) return sizeof(trs_server_opts);
+    if (!std::strcmp(name, "trs_decision")) return sizeof(trs_decision);
+    if (!std::strcmp(name, "trs_server_stats")) return sizeof(trs_server_stats);
     return 0;
 }
 
@@ -260,8 +213,7 @@ int trs_create(trs_ctx **out, const trs_opts *o) {
 int trs_destroy(trs_ctx *c) {
     if (!c) return TRS_OK;
     cudaDeviceSynchronize();
-    for (auto &g : c->graphs)
-        if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
+    drop_graphs(c);
     for (auto &p : c->plans) {
         dev_free(p.second->blob);
         delete p.second;
@@ -373,16 +325,8 @@ static int search_one(trs_ctx *ctx, const void *tables, int W, int H, int n, flo
     f.H = H;
     f.C = pe->host.C;
     f.R = pe->host.R;
-    f.n = n;
     f.tables = (uint8_t *)tables;
-    f.plan = pe->dev;
-    f.lambda_q = lambda_to_q(lambda);
-    f.V1 = (uint64_t *)(scr + pe->scr.V1);
-    f.V2 = (uint64_t *)(scr + pe->scr.V2);
-    f.wres1 = (uint64_t *)(scr + pe->scr.w1);
-    f.wres2 = (uint64_t *)(scr + pe->scr.w2);
-    f.H2 = (uint64_t *)(scr + pe->scr.H2);
-    f.codes = (WinCode *)(scr + pe->scr.codes);
+    set_search_scratch(f, *pe, scr, n, lambda);
     f.scal = (uint64_t *)ctx->scal.p;
     f.out = out;
     a.nframes = 1;
@@ -432,7 +376,12 @@ int trs_decide_host(trs_ctx *ctx, const void *luma_host, int W, int H, size_t pi
 /* ---------------------------------------------------------------------- */
 /* Batched path                                                           */
 
-int trs_batch_decide(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partition *out, void *stream) {
+}  // extern "C"
+
+namespace trs {
+
+int batch_run(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partition *out, cudaStream_t stream,
+              bool use_graph) {
     if (!ctx || !fd || !out || nf < 1 || nf > ctx->o.max_batch) return TRS_EINVAL;
     std::vector<PlanEntry *> pe(nf);
     std::vector<int64_t> key;
@@ -468,19 +417,12 @@ int trs_batch_decide(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partiti
         off += stats_bytes(hp.C, hp.R) + tables_offsets(hp.C, hp.R).bytes + pe[i]->scr.bytes;
     }
     if (ctx->arena.n < off) {
-        for (auto &g : ctx->graphs)
-            if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
-        ctx->graphs.clear();
+        drop_graphs(ctx);
         TRS_TRY(dev_alloc(ctx->arena, off + off / 4, &ctx->total));
     }
-    // descriptor blob: DevFrame[nf] | prefixes ctus, bandgrp, items, windows [nf+1]
-    const size_t fr_bytes = align256((size_t)nf * sizeof(DevFrame));
-    const size_t pre_bytes = align256((size_t)(nf + 1) * 4);
-    const size_t blob = fr_bytes + 5 * pre_bytes;
+    const size_t blob = batch_blob_bytes(nf);
     if (ctx->desc.n < blob) {
-        for (auto &g : ctx->graphs)
-            if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
-        ctx->graphs.clear();
+        drop_graphs(ctx);
         TRS_TRY(dev_alloc(ctx->desc, blob * 2, &ctx->total));
     }
     if (ctx->staging_n < blob) {
@@ -488,9 +430,7 @@ int trs_batch_decide(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partiti
         if (ctx->staging) cudaFreeHost(ctx->staging);
         ctx->staging = nullptr;
         ctx->staging_n = 0;
-        for (auto &g : ctx->graphs)
-            if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
-        ctx->graphs.clear();
+        drop_graphs(ctx);
         TRS_CK(cudaMallocHost(&ctx->staging, blob * 2));
         ctx->staging_n = blob * 2;
     }
@@ -498,12 +438,7 @@ int trs_batch_decide(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partiti
     TRS_CK(cudaEventSynchronize(ctx->copied));
     uint8_t *hb = (uint8_t *)ctx->staging;
     DevFrame *hf = (DevFrame *)hb;
-    int32_t *pc = (int32_t *)(hb + fr_bytes), *pg = (int32_t *)(hb + fr_bytes + pre_bytes);
-    int32_t *pi = (int32_t *)(hb + fr_bytes + 2 * pre_bytes), *pw = (int32_t *)(hb + fr_bytes + 3 * pre_bytes);
-    int32_t *pb = (int32_t *)(hb + fr_bytes + 4 * pre_bytes);
     uint8_t *ab = (uint8_t *)ctx->arena.p;
-    pc[0] = pg[0] = pi[0] = pw[0] = pb[0] = 0;
-    int maxC = 1, maxR = 1, maxN = 1;
     for (int i = 0; i < nf; ++i) {
         const trs_frame_desc &d = fd[i];
         const HostPlan &hp = pe[i]->host;
@@ -525,69 +460,127 @@ int trs_batch_decide(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partiti
         f.flags = (uint32_t *)(ab + flags_off) + i;
         f.tables = p;
         p += tables_offsets(C, R).bytes;
-        f.plan = pe[i]->dev;
-        f.C = C;
-        f.R = R;
-        f.n = d.n_regions;
-        f.lambda_q = lambda_to_q(d.lambda);
-        f.V1 = (uint64_t *)(p + pe[i]->scr.V1);
-        f.V2 = (uint64_t *)(p + pe[i]->scr.V2);
-        f.wres1 = (uint64_t *)(p + pe[i]->scr.w1);
-        f.wres2 = (uint64_t *)(p + pe[i]->scr.w2);
-        f.H2 = (uint64_t *)(p + pe[i]->scr.H2);
-        f.codes = (WinCode *)(p + pe[i]->scr.codes);
+        set_search_scratch(f, *pe[i], p, d.n_regions, d.lambda);
         f.scal = (uint64_t *)(ab + scal_off) + 4 * i;
         f.out = out + i;
         hf[i] = f;
-        pc[i + 1] = pc[i] + cells;
-        pg[i + 1] = pg[i] + (num_bands(C) + kBandsPerBlock - 1) / kBandsPerBlock;
-        pi[i + 1] = pi[i] + (int)hp.items.size();
-        pw[i + 1] = pw[i] + (int)hp.win_a.size();
-        pb[i + 1] = pb[i] + hp.nb;
-        maxC = C > maxC ? C : maxC;
-        maxR = R > maxR ? R : maxR;
-        maxN = d.n_regions > maxN ? d.n_regions : maxN;
+    }
+    BatchLaunch bl;
+    batch_describe(bl, hb, (uint8_t *)ctx->desc.p, nf, pe.data(), (uint32_t *)(ab + flags_off),
+                   (uint64_t *)(ab + scal_off));
+    if (!use_graph) {
+        cudaError_t e = batch_enqueue(bl, stream, ctx->copied, nullptr);
+        if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+        ctx->stage_valid = false;
+        return TRS_OK;
     }
     BatchGraph &g = ctx->graphs[key];
     if (!g.exec) {
-        uint8_t *db = (uint8_t *)ctx->desc.p;
-        LaunchArgs a{};
-        a.frames = (const DevFrame *)db;
-        a.nframes = nf;
-        a.pre.ctus = (const int32_t *)(db + fr_bytes);
-        a.pre.bandgrp = (const int32_t *)(db + fr_bytes + pre_bytes);
-        a.pre.items = (const int32_t *)(db + fr_bytes + 2 * pre_bytes);
-        a.pre.windows = (const int32_t *)(db + fr_bytes + 3 * pre_bytes);
-        a.pre.bands = (const int32_t *)(db + fr_bytes + 4 * pre_bytes);
         cudaStream_t cs = ctx->cap;
         TRS_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-        int rc = TRS_OK;
-        cudaError_t e = cudaMemcpyAsync(db, hb, blob, cudaMemcpyHostToDevice, cs);
-        if (e == cudaSuccess) e = cudaEventRecordWithFlags(ctx->copied, cs, cudaEventRecordExternal);
-        if (e == cudaSuccess) e = cudaMemsetAsync(ab + flags_off, 0, (size_t)nf * 4, cs);
-        if (e == cudaSuccess) e = cudaEventRecordWithFlags(ctx->stage[0], cs, cudaEventRecordExternal);
-        if (e == cudaSuccess) e = (cudaError_t)launch_texture(a, pc[nf], cs);
-        if (e == cudaSuccess) e = cudaEventRecordWithFlags(ctx->stage[1], cs, cudaEventRecordExternal);
-        if (e == cudaSuccess) e = (cudaError_t)launch_tables(a, pg[nf], maxC, maxR, cs);
-        if (e == cudaSuccess) e = cudaEventRecordWithFlags(ctx->stage[2], cs, cudaEventRecordExternal);
-        if (e == cudaSuccess)
-            e = (cudaError_t)launch_search(a, pb[nf], pw[nf], maxC, maxR, maxN, (uint64_t *)(ab + scal_off),
-                                           (size_t)nf * 4, cs, ctx->stage + 3);
+        cudaError_t e = batch_enqueue(bl, cs, ctx->copied, ctx->stage);
         cudaGraph_t graph = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
         if (e == cudaSuccess) e = e2;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
         if (graph) cudaGraphDestroy(graph);
         if (e != cudaSuccess) {
-            rc = cuda_fail(e, "batch graph capture");
             ctx->graphs.erase(key);
-            return rc;
+            return cuda_fail(e, "batch graph capture");
         }
         g.staged_bytes = blob;
     }
-    TRS_CK(cudaGraphLaunch(g.exec, (cudaStream_t)stream));
+    TRS_CK(cudaGraphLaunch(g.exec, stream));
     ctx->stage_valid = true;
     return TRS_OK;
+}
+
+size_t batch_blob_bytes(int nf) {
+    return align256((size_t)nf * sizeof(DevFrame)) + 5 * align256((size_t)(nf + 1) * 4);
+}
+
+void set_search_scratch(DevFrame &f, const PlanEntry &pe, uint8_t *p, int n, float lambda) {
+    f.plan = pe.dev;
+    f.C = pe.host.C;
+    f.R = pe.host.R;
+    f.n = n;
+    f.lambda_q = lambda_to_q(lambda);
+    f.V1 = (uint64_t *)(p + pe.scr.V1);
+    f.V2 = (uint64_t *)(p + pe.scr.V2);
+    f.wres1 = (uint64_t *)(p + pe.scr.w1);
+    f.wres2 = (uint64_t *)(p + pe.scr.w2);
+    f.H2 = (uint64_t *)(p + pe.scr.H2);
+    f.codes = (WinCode *)(p + pe.scr.codes);
+}
+
+void batch_describe(BatchLaunch &bl, uint8_t *hb, uint8_t *db, int nf, PlanEntry *const *pe, uint32_t *flags_dev,
+                    uint64_t *scal_dev) {
+    bl.hb = hb;
+    bl.db = db;
+    bl.nf = nf;
+    bl.fr_bytes = align256((size_t)nf * sizeof(DevFrame));
+    bl.pre_bytes = align256((size_t)(nf + 1) * 4);
+    bl.blob = batch_blob_bytes(nf);
+    bl.flags_dev = flags_dev;
+    bl.scal_dev = scal_dev;
+    int32_t *pc = (int32_t *)(hb + bl.fr_bytes), *pg = (int32_t *)(hb + bl.fr_bytes + bl.pre_bytes);
+    int32_t *pi = (int32_t *)(hb + bl.fr_bytes + 2 * bl.pre_bytes);
+    int32_t *pw = (int32_t *)(hb + bl.fr_bytes + 3 * bl.pre_bytes);
+    int32_t *pb = (int32_t *)(hb + bl.fr_bytes + 4 * bl.pre_bytes);
+    pc[0] = pg[0] = pi[0] = pw[0] = pb[0] = 0;
+    bl.maxC = bl.maxR = bl.maxN = 1;
+    for (int i = 0; i < nf; ++i) {
+        const HostPlan &hp = pe[i]->host;
+        pc[i + 1] = pc[i] + hp.C * hp.R;
+        pg[i + 1] = pg[i] + (num_bands(hp.C) + kBandsPerBlock - 1) / kBandsPerBlock;
+        pi[i + 1] = pi[i] + (int)hp.items.size();
+        pw[i + 1] = pw[i] + (int)hp.win_a.size();
+        pb[i + 1] = pb[i] + hp.nb;
+        bl.maxC = hp.C > bl.maxC ? hp.C : bl.maxC;
+        bl.maxR = hp.R > bl.maxR ? hp.R : bl.maxR;
+        bl.maxN = hp.n > bl.maxN ? hp.n : bl.maxN;
+    }
+    bl.ctus = pc[nf];
+    bl.groups = pg[nf];
+    bl.bands = pb[nf];
+    bl.windows = pw[nf];
+}
+
+cudaError_t batch_enqueue(const BatchLaunch &bl, cudaStream_t cs, cudaEvent_t copied, cudaEvent_t *stage) {
+    LaunchArgs a{};
+    a.frames = (const DevFrame *)bl.db;
+    a.nframes = bl.nf;
+    a.pre.ctus = (const int32_t *)(bl.db + bl.fr_bytes);
+    a.pre.bandgrp = (const int32_t *)(bl.db + bl.fr_bytes + bl.pre_bytes);
+    a.pre.items = (const int32_t *)(bl.db + bl.fr_bytes + 2 * bl.pre_bytes);
+    a.pre.windows = (const int32_t *)(bl.db + bl.fr_bytes + 3 * bl.pre_bytes);
+    a.pre.bands = (const int32_t *)(bl.db + bl.fr_bytes + 4 * bl.pre_bytes);
+    const bool events = stage != nullptr;
+    auto mark = [&](int i, cudaError_t e) {
+        if (events && e == cudaSuccess) e = cudaEventRecordWithFlags(stage[i], cs, cudaEventRecordExternal);
+        return e;
+    };
+    cudaError_t e = cudaMemcpyAsync(bl.db, bl.hb, bl.blob, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess && copied)
+        e = events ? cudaEventRecordWithFlags(copied, cs, cudaEventRecordExternal) : cudaEventRecord(copied, cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bl.flags_dev, 0, (size_t)bl.nf * 4, cs);
+    e = mark(0, e);
+    if (e == cudaSuccess) e = (cudaError_t)launch_texture(a, bl.ctus, cs);
+    e = mark(1, e);
+    if (e == cudaSuccess) e = (cudaError_t)launch_tables(a, bl.groups, bl.maxC, bl.maxR, cs);
+    e = mark(2, e);
+    if (e == cudaSuccess)
+        e = (cudaError_t)launch_search(a, bl.bands, bl.windows, bl.maxC, bl.maxR, bl.maxN, bl.scal_dev,
+                                       (size_t)bl.nf * 4, cs, events ? stage + 3 : nullptr);
+    return e;
+}
+
+}  // namespace trs
+
+extern "C" {
+
+int trs_batch_decide(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partition *out, void *stream) {
+    return batch_run(ctx, fd, nf, out, (cudaStream_t)stream, true);
 }
 
 int trs_batch_stage_ms(trs_ctx *ctx, float *ms, int max_stages) {
@@ -638,7 +631,7 @@ int trs_batch_decide_host(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_pa
         dd[i].pitch_bytes = dp[i];
         dd[i].ctu_time_dev = (const float *)dt;
     }
-    TRS_TRY(trs_batch_decide(ctx, dd.data(), nf, (trs_partition *)ctx->hb_out.p, stream));
+    TRS_TRY(batch_run(ctx, dd.data(), nf, (trs_partition *)ctx->hb_out.p, s, true));
     TRS_CK(cudaMemcpyAsync(out_host, ctx->hb_out.p, (size_t)nf * sizeof(trs_partition), cudaMemcpyDeviceToHost, s));
     TRS_CK(cudaStreamSynchronize(s));
     return TRS_OK;

@@ -1,0 +1,108 @@
+// Host-side state of a trs_ctx and the helpers shared by api.cu and
+// server.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "plan.h"
+#include "trs_internal.cuh"
+
+#define TRS_CK(call)                                                  \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return ::trs::cuda_fail(e_, #call);    \
+    } while (0)
+
+#define TRS_TRY(expr)                \
+    do {                             \
+        int s_ = (expr);             \
+        if (s_ != TRS_OK) return s_; \
+    } while (0)
+
+namespace trs {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t n = 0;
+};
+
+struct PlanEntry {
+    HostPlan host;
+    DevBuf blob;
+    const DevPlan *dev = nullptr;
+    SearchScratch scr{};
+};
+
+struct BatchGraph {
+    cudaGraphExec_t exec = nullptr;
+    size_t staged_bytes = 0;
+};
+
+}  // namespace trs
+
+struct trs_ctx {
+    trs_opts o{};
+    size_t total = 0;
+    int maxC = 0, maxR = 0;
+    // one-frame path
+    trs::DevBuf s1, s2, cnt, vmax, flags, tables, scratch, scal, part, luma_stage, time_stage;
+    // plans by (W, H, n)
+    std::map<std::tuple<int, int, int>, trs::PlanEntry *> plans;
+    // batched path
+    trs::DevBuf arena, desc;
+    void *staging = nullptr;  // pinned host copy of the descriptor blob
+    size_t staging_n = 0;
+    cudaStream_t cap = nullptr;
+    cudaEvent_t copied = nullptr;
+    static constexpr int kStages = 8;
+    cudaEvent_t stage[kStages + 1] = {};  // timing events recorded inside batch graphs
+    bool stage_valid = false;
+    // host-buffer batches: device staging of planes, times and partitions
+    trs::DevBuf hb_luma, hb_time, hb_out;
+    std::map<std::vector<int64_t>, trs::BatchGraph> graphs;
+};
+
+namespace trs {
+
+// Records the CUDA error text for trs_last_error(); returns TRS_ECUDA.
+int cuda_fail(cudaError_t e, const char *what);
+// Grows a device buffer to at least `bytes` (synchronising the device first
+// if it must free the old one); *total tracks the context's bytes.
+int dev_alloc(DevBuf &b, size_t bytes, size_t *total);
+void dev_free(DevBuf &b);
+uint32_t lambda_to_q(float lambda);
+int check_frame(const trs_ctx *ctx, int W, int H);
+int get_plan(trs_ctx *ctx, int W, int H, int n, PlanEntry **out);
+size_t stats_bytes(int C, int R);
+void drop_graphs(trs_ctx *ctx);
+// Launch geometry of one batch: the descriptor blob (DevFrame[nf] and the
+// work prefix sums) written in pinned host memory hb, to be copied to db.
+struct BatchLaunch {
+    uint8_t *hb = nullptr, *db = nullptr;
+    size_t blob = 0, fr_bytes = 0, pre_bytes = 0;
+    int nf = 0, ctus = 0, groups = 0, bands = 0, windows = 0, maxC = 1, maxR = 1, maxN = 1;
+    uint32_t *flags_dev = nullptr;  // nf words, zeroed by the launch
+    uint64_t *scal_dev = nullptr;   // nf * 4 words, reset by the launch
+};
+size_t batch_blob_bytes(int nf);
+// Points a frame's search fields at the plan and at the scratch starting at p.
+void set_search_scratch(DevFrame &f, const PlanEntry &pe, uint8_t *p, int n, float lambda);
+// Writes the work prefix sums after the DevFrame array already placed in hb.
+void batch_describe(BatchLaunch &bl, uint8_t *hb, uint8_t *db, int nf, PlanEntry *const *pe, uint32_t *flags_dev,
+                    uint64_t *scal_dev);
+// Enqueues the descriptor copy (then records `copied`), the flag reset and
+// every kernel of the hot path on cs; stage events (9) when stage != nullptr.
+cudaError_t batch_enqueue(const BatchLaunch &bl, cudaStream_t cs, cudaEvent_t copied, cudaEvent_t *stage);
+
+// Decides nf frames described by device pointers in one launch of each
+// kernel on `stream`, through a cached CUDA graph or by direct launches.
+int batch_run(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partition *out, cudaStream_t stream,
+              bool use_graph);
+
+}  // namespace trs

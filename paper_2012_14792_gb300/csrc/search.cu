@@ -503,6 +503,10 @@ __global__ void __launch_bounds__(32) finish_kernel(LaunchArgs args) {
     if (status == TRS_OK && t_min == kInf) status = TRS_EINFEASIBLE;
     const uint64_t qstar = fr.scal[1];
     if (status == TRS_OK && qstar == kInf) status = TRS_EINFEASIBLE;  // cannot happen: P(T_min) meets Eq. 4
+    // the whole record is rewritten: entries past the used ones read as zero
+    uint64_t *words = reinterpret_cast<uint64_t *>(out);
+    for (int i = lane; i < (int)(sizeof(trs_partition) / 8); i += 32) words[i] = 0;
+    __syncwarp();
     if (lane != 0) return;
     out->status = status;
     out->n_regions = n;
@@ -510,13 +514,7 @@ __global__ void __launch_bounds__(32) finish_kernel(LaunchArgs args) {
     out->rows = R;
     out->n_windows = pl.nwin;
     out->reserved = 0;
-    if (status != TRS_OK) {
-        out->n_tile_cols = out->n_tile_rows = 0;
-        out->t_min_q = out->thr_q = out->t_q = out->q = 0;
-        out->t_min = out->t = out->sse = 0.0;
-        out->tile_row_mask = 0;
-        return;
-    }
+    if (status != TRS_OK) return;
     int bw = -1;
     for (int w = 0; w < pl.nwin; ++w) {
         if (fr.codes[w].c <= 0) continue;
@@ -570,7 +568,6 @@ __global__ void __launch_bounds__(32) finish_kernel(LaunchArgs args) {
             y0 = y;
         }
     }
-    for (int b = best.c; b < kMaxC; ++b) out->slice_cuts[b] = 0;
     out->t_min_q = t_min;
     out->thr_q = thr;
     out->t_q = tmax;

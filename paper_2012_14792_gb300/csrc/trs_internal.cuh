@@ -14,6 +14,8 @@
 
 #include "../../include/trs.h"
 
+static_assert(sizeof(trs_partition) % 8 == 0, "trs_partition is cleared as 8-byte words");
+
 namespace trs {
 
 constexpr uint64_t kInf = ~0ull;

@@ -73,6 +73,23 @@ class trs_frame_desc(ct.Structure):
                 ("n_regions", ct.c_int), ("lambda", ct.c_float)]
 
 
+class trs_server_opts(ct.Structure):
+    _fields_ = [("max_width", ct.c_int), ("max_height", ct.c_int), ("max_regions", ct.c_int),
+                ("max_streams", ct.c_int), ("max_batch", ct.c_int), ("max_inflight", ct.c_int),
+                ("mem_budget_bytes", ct.c_size_t), ("k_area", ct.c_int), ("device", ct.c_int)]
+
+
+class trs_decision(ct.Structure):
+    _fields_ = [("ticket", ct.c_uint64), ("tag", ct.c_uint64), ("stream_id", ct.c_int32), ("status", ct.c_int32),
+                ("latency_us", ct.c_double), ("partition", trs_partition)]
+
+
+class trs_server_stats(ct.Structure):
+    _fields_ = [("batches", ct.c_uint64), ("frames", ct.c_uint64), ("decided", ct.c_uint64),
+                ("mem_used_bytes", ct.c_size_t), ("streams_open", ct.c_int), ("pending", ct.c_int),
+                ("inflight", ct.c_int), ("status", ct.c_int)]
+
+
 PARTITION_BYTES = ct.sizeof(trs_partition)
 
 
@@ -103,6 +120,14 @@ def _load():
         "trs_batch_decide": ([vp, ct.POINTER(trs_frame_desc), i, vp, vp], i),
         "trs_batch_decide_host": ([vp, ct.POINTER(trs_frame_desc), i, ct.POINTER(trs_partition), vp], i),
         "trs_batch_stage_ms": ([vp, ct.POINTER(ct.c_float), i], i),
+        "trs_server_create": ([ct.POINTER(vp), ct.POINTER(trs_server_opts)], i),
+        "trs_server_destroy": ([vp], i),
+        "trs_server_open_stream": ([vp, i, i, i, i, f, ct.POINTER(i)], i),
+        "trs_server_close_stream": ([vp, i], i),
+        "trs_server_update_times": ([vp, i, vp], i),
+        "trs_server_submit": ([vp, i, vp, sz, ct.c_uint64, ct.POINTER(ct.c_uint64)], i),
+        "trs_server_poll": ([vp, ct.POINTER(trs_decision), i, i, ct.POINTER(i)], i),
+        "trs_server_info": ([vp, ct.POINTER(trs_server_stats)], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -256,3 +281,55 @@ def trs_batch_stage_ms(ctx) -> dict:
 
 def partitions_from_bytes(buf: bytes, count: int = 1) -> list[trs_partition]:
     return [trs_partition.from_buffer_copy(buf, i * PARTITION_BYTES) for i in range(count)]
+
+
+# --- serving ---------------------------------------------------------------
+
+def trs_server_create(max_width, max_height, max_regions=16, max_streams=32, max_batch=64, max_inflight=2,
+                      mem_budget_bytes=0, k_area=3, device=0) -> int:
+    o = trs_server_opts(max_width, max_height, max_regions, max_streams, max_batch, max_inflight,
+                        mem_budget_bytes, k_area, device)
+    h = ct.c_void_p()
+    _check(_lib.trs_server_create(ct.byref(h), ct.byref(o)), "trs_server_create")
+    return h.value
+
+
+def trs_server_destroy(srv) -> None:
+    _check(_lib.trs_server_destroy(srv), "trs_server_destroy")
+
+
+def trs_server_open_stream(srv, width, height, bit_depth, n_regions, lam) -> int:
+    sid = ct.c_int(-1)
+    _check(_lib.trs_server_open_stream(srv, width, height, bit_depth, n_regions, lam, ct.byref(sid)),
+           "trs_server_open_stream")
+    return sid.value
+
+
+def trs_server_close_stream(srv, sid) -> None:
+    _check(_lib.trs_server_close_stream(srv, sid), "trs_server_close_stream")
+
+
+def trs_server_update_times(srv, sid, times_host) -> None:
+    _check(_lib.trs_server_update_times(srv, sid, _ptr(times_host)), "trs_server_update_times")
+
+
+def trs_server_submit(srv, sid, luma_host, pitch_bytes, tag=0) -> int:
+    """Returns the ticket; raises TrsError(EBUSY) when the stream's slots are taken."""
+    t = ct.c_uint64(0)
+    _check(_lib.trs_server_submit(srv, sid, _ptr(luma_host), pitch_bytes, tag, ct.byref(t)), "trs_server_submit")
+    return t.value
+
+
+def trs_server_poll(srv, max_out=64, timeout_us=1000) -> list:
+    buf = (trs_decision * max_out)()
+    n = ct.c_int(0)
+    st = _lib.trs_server_poll(srv, buf, max_out, timeout_us, ct.byref(n))
+    if st not in (OK, ETIMEOUT):
+        raise TrsError(st, "trs_server_poll")
+    return [buf[i] for i in range(n.value)]
+
+
+def trs_server_info(srv) -> trs_server_stats:
+    out = trs_server_stats()
+    _check(_lib.trs_server_info(srv, ct.byref(out)), "trs_server_info")
+    return out
