@@ -157,7 +157,7 @@ typedef struct trs_frame_desc {
 
 /* Size in bytes of the ABI structure called `name` ("trs_opts",
  * "trs_ctu_stats", "trs_tables_layout", "trs_partition", "trs_frame_desc",
- * "trs_server_opts", "trs_decision", "trs_server_stats"),
+ * "trs_server_opts", "trs_decision", "trs_server_stats", "trs_tune_report"),
  * 0 for an unknown name; lets bindings check their copies of the layouts. */
 size_t trs_sizeof(const char *name);
 
@@ -266,10 +266,35 @@ int trs_batch_decide(trs_ctx *ctx, const trs_frame_desc *frames_host, int nframe
 int trs_batch_decide_host(trs_ctx *ctx, const trs_frame_desc *frames_host, int nframes, trs_partition *out_host,
                           void *stream);
 
+/* Launch shapes of the search kernels picked by trs_autotune, and the
+ * timings that chose them. */
+typedef struct trs_tune_report {
+    int band_warps;      /* warps per block of the row-DP kernels */
+    int col_warps;       /* warps per block of the column-DP kernels */
+    int col_batch;       /* V rows a column-DP warp loads together */
+    int n_candidates;
+    int cand_band_warps[6], cand_col_warps[6], cand_col_batch[6];
+    float rows_ms[6];    /* both row-DP stages, fastest of three runs */
+    float cols_ms[6];    /* both column-DP stages, fastest of three runs */
+} trs_tune_report;
+
+/* Times six launch-shape candidates of the search kernels on this batch
+ * (direct launches, CUDA events around each kernel), keeps the fastest
+ * row-DP and column-DP shapes in the context for every later call, and
+ * drops captured batch graphs so they are captured again with them.
+ * Synchronises on each timed run.  The decisions themselves do not depend
+ * on the shapes. */
+int trs_autotune(trs_ctx *ctx, const trs_frame_desc *frames_host, int nframes, trs_tune_report *out, void *stream);
+
+/* Sets the search kernels' launch shapes directly: band_warps and
+ * col_warps in {2, 4, 8}, col_batch in {4, 8}; TRS_EINVAL otherwise.
+ * Drops captured batch graphs. */
+int trs_set_tune(trs_ctx *ctx, int band_warps, int col_warps, int col_batch);
+
 /* Device time in milliseconds of each stage of the most recent batched call
  * (texture, tables, step-1 rows, step-1 columns, step-2 rows, step-2
  * columns, rebuild of the smallest code, decode), read from CUDA events
- * recorded inside its graph.
+ * recorded around each kernel (inside its graph when it was replayed).
  * Synchronises on that call.  Returns the number of stages written. */
 int trs_batch_stage_ms(trs_ctx *ctx, float *ms, int max_stages);
 

@@ -134,6 +134,7 @@ size_t trs_sizeof(const char *name) {
     if (!std::strcmp(name, "trs_server_opts")) return sizeof(trs_server_opts);
     if (!std::strcmp(name, "trs_decision")) return sizeof(trs_decision);
     if (!std::strcmp(name, "trs_server_stats")) return sizeof(trs_server_stats);
+    if (!std::strcmp(name, "trs_tune_report")) return sizeof(trs_tune_report);
     return 0;
 }
 
@@ -334,7 +335,7 @@ static int search_one(trs_ctx *ctx, const void *tables, int W, int H, int n, flo
     a.single_items = nitems;
     a.single_windows = nwin;
     a.single_bands = pe->host.nb;
-    TRS_CK((cudaError_t)launch_search(a, pe->host.nb, nwin, f.C, f.R, n, f.scal, 4, stream));
+    TRS_CK((cudaError_t)launch_search(a, pe->host.nb, nwin, f.C, f.R, n, f.scal, 4, stream, nullptr, &ctx->tune));
     return TRS_OK;
 }
 
@@ -468,10 +469,11 @@ int batch_run(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partition *out
     BatchLaunch bl;
     batch_describe(bl, hb, (uint8_t *)ctx->desc.p, nf, pe.data(), (uint32_t *)(ab + flags_off),
                    (uint64_t *)(ab + scal_off));
+    bl.tune = ctx->tune;
     if (!use_graph) {
-        cudaError_t e = batch_enqueue(bl, stream, ctx->copied, nullptr);
+        cudaError_t e = batch_enqueue(bl, stream, ctx->copied, ctx->stage);
         if (e != cudaSuccess) return cuda_fail(e, "batch launch");
-        ctx->stage_valid = false;
+        ctx->stage_valid = true;
         return TRS_OK;
     }
     BatchGraph &g = ctx->graphs[key];
@@ -557,12 +559,11 @@ cudaError_t batch_enqueue(const BatchLaunch &bl, cudaStream_t cs, cudaEvent_t co
     a.pre.bands = (const int32_t *)(bl.db + bl.fr_bytes + 4 * bl.pre_bytes);
     const bool events = stage != nullptr;
     auto mark = [&](int i, cudaError_t e) {
-        if (events && e == cudaSuccess) e = cudaEventRecordWithFlags(stage[i], cs, cudaEventRecordExternal);
+        if (events && e == cudaSuccess) e = record_event(stage[i], cs);
         return e;
     };
     cudaError_t e = cudaMemcpyAsync(bl.db, bl.hb, bl.blob, cudaMemcpyHostToDevice, cs);
-    if (e == cudaSuccess && copied)
-        e = events ? cudaEventRecordWithFlags(copied, cs, cudaEventRecordExternal) : cudaEventRecord(copied, cs);
+    if (e == cudaSuccess && copied) e = record_event(copied, cs);
     if (e == cudaSuccess) e = cudaMemsetAsync(bl.flags_dev, 0, (size_t)bl.nf * 4, cs);
     e = mark(0, e);
     if (e == cudaSuccess) e = (cudaError_t)launch_texture(a, bl.ctus, cs);
@@ -571,7 +572,7 @@ cudaError_t batch_enqueue(const BatchLaunch &bl, cudaStream_t cs, cudaEvent_t co
     e = mark(2, e);
     if (e == cudaSuccess)
         e = (cudaError_t)launch_search(a, bl.bands, bl.windows, bl.maxC, bl.maxR, bl.maxN, bl.scal_dev,
-                                       (size_t)bl.nf * 4, cs, events ? stage + 3 : nullptr);
+                                       (size_t)bl.nf * 4, cs, events ? stage + 3 : nullptr, &bl.tune);
     return e;
 }
 
@@ -581,6 +582,73 @@ extern "C" {
 
 int trs_batch_decide(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partition *out, void *stream) {
     return batch_run(ctx, fd, nf, out, (cudaStream_t)stream, true);
+}
+
+int trs_autotune(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_tune_report *rep, void *stream) {
+    if (!ctx || !fd || !rep || nf < 1 || nf > ctx->o.max_batch) return TRS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    TRS_TRY(dev_alloc(ctx->hb_out, (size_t)ctx->o.max_batch * sizeof(trs_partition), &ctx->total));
+    static const int bws[3] = {2, 4, 8};
+    static const int cws[3] = {2, 4, 8};
+    static const int cbs[2] = {4, 8};
+    const SearchTune keep = ctx->tune;
+    SearchTune cand[6];
+    for (int j = 0; j < 6; ++j) {
+        cand[j].band_warps = bws[j % 3];
+        cand[j].col_warps = cws[j / 2];
+        cand[j].col_batch = cbs[j % 2];
+    }
+    float rows[6], cols[6];
+    for (int j = 0; j < 6; ++j) rows[j] = cols[j] = 1e30f;
+    // one warm-up round, then three timed rounds; the fastest time of each candidate counts
+    for (int round = 0; round < 4; ++round)
+        for (int j = 0; j < 6; ++j) {
+            ctx->tune = cand[j];
+            int rc = batch_run(ctx, fd, nf, (trs_partition *)ctx->hb_out.p, s, false);
+            if (rc != TRS_OK) {
+                ctx->tune = keep;
+                return rc;
+            }
+            float ms[trs_ctx::kStages] = {};
+            if (trs_batch_stage_ms(ctx, ms, trs_ctx::kStages) != trs_ctx::kStages) {
+                ctx->tune = keep;
+                return cuda_fail(cudaErrorUnknown, "autotune stage events");
+            }
+            if (round == 0) continue;
+            rows[j] = std::fmin(rows[j], ms[2] + ms[4]);
+            cols[j] = std::fmin(cols[j], ms[3] + ms[5]);
+        }
+    int jb = 0, jc = 0;
+    for (int j = 1; j < 6; ++j) {
+        if (rows[j] < rows[jb]) jb = j;
+        if (cols[j] < cols[jc]) jc = j;
+    }
+    ctx->tune.band_warps = cand[jb].band_warps;
+    ctx->tune.col_warps = cand[jc].col_warps;
+    ctx->tune.col_batch = cand[jc].col_batch;
+    drop_graphs(ctx);  // graphs are captured again with the chosen shapes
+    rep->band_warps = ctx->tune.band_warps;
+    rep->col_warps = ctx->tune.col_warps;
+    rep->col_batch = ctx->tune.col_batch;
+    rep->n_candidates = 6;
+    for (int j = 0; j < 6; ++j) {
+        rep->cand_band_warps[j] = cand[j].band_warps;
+        rep->cand_col_warps[j] = cand[j].col_warps;
+        rep->cand_col_batch[j] = cand[j].col_batch;
+        rep->rows_ms[j] = rows[j];
+        rep->cols_ms[j] = cols[j];
+    }
+    return TRS_OK;
+}
+
+int trs_set_tune(trs_ctx *ctx, int band_warps, int col_warps, int col_batch) {
+    auto ok_w = [](int w) { return w == 2 || w == 4 || w == 8; };
+    if (!ctx || !ok_w(band_warps) || !ok_w(col_warps) || (col_batch != 4 && col_batch != 8)) return TRS_EINVAL;
+    ctx->tune.band_warps = band_warps;
+    ctx->tune.col_warps = col_warps;
+    ctx->tune.col_batch = col_batch;
+    drop_graphs(ctx);
+    return TRS_OK;
 }
 
 int trs_batch_stage_ms(trs_ctx *ctx, float *ms, int max_stages) {

@@ -65,6 +65,7 @@ struct trs_ctx {
     bool stage_valid = false;
     // host-buffer batches: device staging of planes, times and partitions
     trs::DevBuf hb_luma, hb_time, hb_out;
+    trs::SearchTune tune;  // launch shapes of the search kernels (trs_autotune)
     std::map<std::vector<int64_t>, trs::BatchGraph> graphs;
 };
 
@@ -89,6 +90,7 @@ struct BatchLaunch {
     int nf = 0, ctus = 0, groups = 0, bands = 0, windows = 0, maxC = 1, maxR = 1, maxN = 1;
     uint32_t *flags_dev = nullptr;  // nf words, zeroed by the launch
     uint64_t *scal_dev = nullptr;   // nf * 4 words, reset by the launch
+    SearchTune tune;
 };
 size_t batch_blob_bytes(int nf);
 // Points a frame's search fields at the plan and at the scratch starting at p.

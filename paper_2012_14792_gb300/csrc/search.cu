@@ -40,9 +40,7 @@ namespace trs {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kBandWarps = 4;   // warps per block of band_kernel
-constexpr int kColWarps = 4;    // warps per block of column_kernel
-constexpr int kBatch = 8;       // candidate edges whose V rows column_kernel loads together
+constexpr int kMaxWarps = 8;    // largest warps per block of band_kernel / column_kernel (tunable)
 // Saturating infinity inside the DPs: sums of a value below 2^44 and kSoft
 // stay below 2^63, so the relaxations need no infinity branches.
 constexpr uint64_t kSoft = 1ull << 62;
@@ -178,10 +176,10 @@ __device__ __forceinline__ uint64_t item_rows(const uint64_t *st, int nd, int dm
 // shuffles G_{k-1}[y+d] from lane y+d and relaxes.  V[k] = G_k[0] is
 // collected in lane k and stored with one coalesced write per item.
 template <int STEP>
-__global__ void __launch_bounds__(kBandWarps * 32) band_kernel(LaunchArgs args, int total, int stage_words) {
+__global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, int total, int stage_words) {
     extern __shared__ uint64_t bsm[];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * kBandWarps + wib;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
     if (gw >= total) return;
     int b;
     const int f = locate(args, args.pre.bands, args.single_bands, gw, &b);
@@ -257,7 +255,7 @@ __global__ void __launch_bounds__(kBandWarps * 32) band_kernel(LaunchArgs args, 
 // the warp's shared-memory table Hraw ((C+1)*(n+1) words of 8 bytes).
 // Returns H[0][n] with kInf where no partition exists; for 64-bit values
 // the table keeps every entry (kSoft for none) for the rebuild.
-template <int STEP, typename VT>
+template <int STEP, typename VT, int kBatch>
 __device__ uint64_t column_dp(uint64_t *Hraw, const uint64_t *V, const int32_t *slot_row, int C, int n) {
     const int lane = threadIdx.x & 31;
     const int stride = n + 1;
@@ -315,11 +313,11 @@ __device__ uint64_t column_dp(uint64_t *Hraw, const uint64_t *V, const int32_t *
 // edges at a time (lanes over k, loads of a batch in flight together) and
 // each edge contributes only the slice counts whose V is finite (a ballot
 // per row).
-template <int STEP>
-__global__ void __launch_bounds__(kColWarps * 32) column_kernel(LaunchArgs args, int total, int h_words) {
+template <int STEP, int kBatch>
+__global__ void __launch_bounds__(kMaxWarps * 32) column_kernel(LaunchArgs args, int total, int h_words) {
     extern __shared__ uint64_t csm[];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * kColWarps + wib;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
     if (gw >= total) return;
     int w;
     const int f = locate(args, args.pre.windows, args.single_windows, gw, &w);
@@ -343,9 +341,9 @@ __global__ void __launch_bounds__(kColWarps * 32) column_kernel(LaunchArgs args,
     const int32_t *slot_row = pl.slot_of + (size_t)w * nb;
     uint64_t res;
     if (STEP == 1 && frame_t32(fr))
-        res = column_dp<1, uint32_t>(csm + (size_t)wib * h_words, V, slot_row, C, n);
+        res = column_dp<1, uint32_t, kBatch>(csm + (size_t)wib * h_words, V, slot_row, C, n);
     else
-        res = column_dp<STEP, uint64_t>(csm + (size_t)wib * h_words, V, slot_row, C, n);
+        res = column_dp<STEP, uint64_t, kBatch>(csm + (size_t)wib * h_words, V, slot_row, C, n);
     if (lane == 0) {
         wres[w] = res;
         if (res != kInf) atomicMin(reinterpret_cast<unsigned long long *>(&fr.scal[STEP == 1 ? 0 : 1]), res);
@@ -583,45 +581,54 @@ __global__ void __launch_bounds__(32) finish_kernel(LaunchArgs args) {
 // Raises the dynamic shared-memory limit of the search kernels to what the
 // largest shapes need (once per device, before any capture).
 int prepare_search_kernels() {
-    const int band_smem = kBandWarps * kMaxR * 32 * (int)sizeof(uint64_t);
-    const int col_smem = kColWarps * (kMaxC + 1) * (kMaxN + 1) * (int)sizeof(uint64_t);
-    cudaError_t e = cudaFuncSetAttribute(band_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, band_smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(band_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, band_smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(column_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(column_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, col_smem);
+    const int band_smem = kMaxWarps * kMaxR * 32 * (int)sizeof(uint64_t);
+    const int col_smem = kMaxWarps * (kMaxC + 1) * (kMaxN + 1) * (int)sizeof(uint64_t);
     const int rb_smem = ((kMaxN + 1) * 32 + kMaxR * 32) * (int)sizeof(uint64_t);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(rebuild_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, rb_smem);
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(band_kernel<1>, A, band_smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(band_kernel<2>, A, band_smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(column_kernel<1, 4>, A, col_smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(column_kernel<1, 8>, A, col_smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(column_kernel<2, 4>, A, col_smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(column_kernel<2, 8>, A, col_smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(rebuild_kernel, A, rb_smem);
     return (int)e;
 }
 
 int launch_search(const LaunchArgs &a, int total_bands, int total_windows, int maxC, int maxR, int maxN,
-                  uint64_t *scal, size_t nscal, void *stream, cudaEvent_t *ev) {
+                  uint64_t *scal, size_t nscal, void *stream, cudaEvent_t *ev, const SearchTune *tune) {
+    const SearchTune t = tune ? *tune : SearchTune{};
     cudaStream_t s = (cudaStream_t)stream;
     // T_min and Q* start at +infinity; the column kernels reduce into them
     cudaError_t e = cudaMemsetAsync(scal, 0xff, nscal * sizeof(uint64_t), s);
     if (e != cudaSuccess) return (int)e;
+    const int bw = t.band_warps, cw = t.col_warps;
     const int stage_words = maxR * 32;
-    const size_t band_smem = (size_t)kBandWarps * stage_words * sizeof(uint64_t);
+    const size_t band_smem = (size_t)bw * stage_words * sizeof(uint64_t);
     const int h_words = (maxC + 1) * (maxN + 1);
-    const size_t col_smem = (size_t)kColWarps * h_words * sizeof(uint64_t);
-    const int bb = (total_bands + kBandWarps - 1) / kBandWarps;
-    const int cb = (total_windows + kColWarps - 1) / kColWarps;
+    const size_t col_smem = (size_t)cw * h_words * sizeof(uint64_t);
+    const int bb = (total_bands + bw - 1) / bw;
+    const int cb = (total_windows + cw - 1) / cw;
     auto mark = [&](int i) {
-        if (ev && e == cudaSuccess) e = cudaEventRecordWithFlags(ev[i], s, cudaEventRecordExternal);
+        if (ev && e == cudaSuccess) e = record_event(ev[i], s);
     };
-    if (total_bands > 0) band_kernel<1><<<bb, kBandWarps * 32, band_smem, s>>>(a, total_bands, stage_words);
+    auto columns = [&](int step) {
+        if (total_windows <= 0) return;
+        if (step == 1) {
+            if (t.col_batch == 4) column_kernel<1, 4><<<cb, cw * 32, col_smem, s>>>(a, total_windows, h_words);
+            else column_kernel<1, 8><<<cb, cw * 32, col_smem, s>>>(a, total_windows, h_words);
+        } else {
+            if (t.col_batch == 4) column_kernel<2, 4><<<cb, cw * 32, col_smem, s>>>(a, total_windows, h_words);
+            else column_kernel<2, 8><<<cb, cw * 32, col_smem, s>>>(a, total_windows, h_words);
+        }
+    };
+    if (total_bands > 0) band_kernel<1><<<bb, bw * 32, band_smem, s>>>(a, total_bands, stage_words);
     mark(0);
-    if (total_windows > 0)
-        column_kernel<1><<<cb, kColWarps * 32, col_smem, s>>>(a, total_windows, h_words);
+    columns(1);
     mark(1);
-    if (total_bands > 0) band_kernel<2><<<bb, kBandWarps * 32, band_smem, s>>>(a, total_bands, stage_words);
+    if (total_bands > 0) band_kernel<2><<<bb, bw * 32, band_smem, s>>>(a, total_bands, stage_words);
     mark(2);
-    if (total_windows > 0)
-        column_kernel<2><<<cb, kColWarps * 32, col_smem, s>>>(a, total_windows, h_words);
+    columns(2);
     mark(3);
     const int layer_words = (maxN + 1) * 32;
     const size_t rb_smem = (size_t)(layer_words + stage_words) * sizeof(uint64_t);

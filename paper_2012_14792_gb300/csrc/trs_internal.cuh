@@ -182,6 +182,17 @@ __device__ inline int locate(const LaunchArgs &a, const int32_t *pre, int single
     return lo;
 }
 
+// Records an event on s: as an external event node when s is being
+// captured into a graph (so the event is recorded on every replay), as a
+// plain record otherwise.
+inline cudaError_t record_event(cudaEvent_t ev, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal)
+                                               : cudaEventRecord(ev, s);
+}
+
 // Kernel attributes for the largest shapes; call once per device before launching.
 int prepare_tables_kernel();
 int prepare_search_kernels();
@@ -189,10 +200,18 @@ int prepare_search_kernels();
 // Launchers (return cudaError_t as int).
 int launch_texture(const LaunchArgs &a, int total_ctus, void *stream);
 int launch_tables(const LaunchArgs &a, int total_groups, int maxC, int maxR, void *stream);
+// Launch shapes of the search kernels, chosen by trs_autotune.
+struct SearchTune {
+    int band_warps = 4;  // warps per block of the row-DP kernels (2, 4 or 8)
+    int col_warps = 4;   // warps per block of the column-DP kernels (2, 4 or 8)
+    int col_batch = 8;   // candidate edges whose V rows a column-DP warp loads together (4 or 8)
+};
+
 // scal: the T_min / Q* words of every frame of the launch (reset to +inf first).
 // ev (optional, 6 events): recorded after each of the six search kernels.
 // maxC / maxR / maxN: largest C, R and n over the frames of the launch (shared-memory sizing).
 int launch_search(const LaunchArgs &a, int total_bands, int total_windows, int maxC, int maxR, int maxN,
-                  uint64_t *scal, size_t nscal, void *stream, cudaEvent_t *ev = nullptr);
+                  uint64_t *scal, size_t nscal, void *stream, cudaEvent_t *ev = nullptr,
+                  const SearchTune *tune = nullptr);
 
 }  // namespace trs

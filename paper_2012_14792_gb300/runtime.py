@@ -92,6 +92,11 @@ class Decider:
         trs.trs_batch_decide(self.ctx, descs, out)
         return out
 
+    def autotune(self, frames: list) -> dict:
+        """Picks the search kernels' launch shapes on this batch (see trs_autotune)."""
+        descs = [trs.frame_desc(l, t, w, h, p, bd, n, lam) for (l, p, w, h, bd, t, n, lam) in frames]
+        return trs.trs_autotune(self.ctx, descs).as_dict()
+
     # ---- reading results ----------------------------------------------------
     @staticmethod
     def partitions(out: torch.Tensor, count: int = 1) -> list:

@@ -90,6 +90,18 @@ class trs_server_stats(ct.Structure):
                 ("inflight", ct.c_int), ("status", ct.c_int)]
 
 
+class trs_tune_report(ct.Structure):
+    _fields_ = [("band_warps", ct.c_int), ("col_warps", ct.c_int), ("col_batch", ct.c_int),
+                ("n_candidates", ct.c_int), ("cand_band_warps", ct.c_int * 6), ("cand_col_warps", ct.c_int * 6),
+                ("cand_col_batch", ct.c_int * 6), ("rows_ms", ct.c_float * 6), ("cols_ms", ct.c_float * 6)]
+
+    def as_dict(self) -> dict:
+        return {"band_warps": self.band_warps, "col_warps": self.col_warps, "col_batch": self.col_batch,
+                "candidates": [{"band_warps": self.cand_band_warps[j], "col_warps": self.cand_col_warps[j],
+                                "col_batch": self.cand_col_batch[j], "rows_ms": round(self.rows_ms[j], 4),
+                                "cols_ms": round(self.cols_ms[j], 4)} for j in range(self.n_candidates)]}
+
+
 PARTITION_BYTES = ct.sizeof(trs_partition)
 
 
@@ -120,6 +132,8 @@ def _load():
         "trs_batch_decide": ([vp, ct.POINTER(trs_frame_desc), i, vp, vp], i),
         "trs_batch_decide_host": ([vp, ct.POINTER(trs_frame_desc), i, ct.POINTER(trs_partition), vp], i),
         "trs_batch_stage_ms": ([vp, ct.POINTER(ct.c_float), i], i),
+        "trs_autotune": ([vp, ct.POINTER(trs_frame_desc), i, ct.POINTER(trs_tune_report), vp], i),
+        "trs_set_tune": ([vp, i, i, i], i),
         "trs_server_create": ([ct.POINTER(vp), ct.POINTER(trs_server_opts)], i),
         "trs_server_destroy": ([vp], i),
         "trs_server_open_stream": ([vp, i, i, i, i, f, ct.POINTER(i)], i),
@@ -277,6 +291,17 @@ def trs_batch_stage_ms(ctx) -> dict:
     ms = (ct.c_float * len(STAGES))()
     k = _lib.trs_batch_stage_ms(ctx, ms, len(STAGES))
     return {STAGES[i]: float(ms[i]) for i in range(k)}
+
+
+def trs_autotune(ctx, descs: list[trs_frame_desc], stream=None) -> trs_tune_report:
+    arr = (trs_frame_desc * len(descs))(*descs)
+    rep = trs_tune_report()
+    _check(_lib.trs_autotune(ctx, arr, len(descs), ct.byref(rep), _stream(stream)), "trs_autotune")
+    return rep
+
+
+def trs_set_tune(ctx, band_warps: int, col_warps: int, col_batch: int) -> None:
+    _check(_lib.trs_set_tune(ctx, band_warps, col_warps, col_batch), "trs_set_tune")
 
 
 def partitions_from_bytes(buf: bytes, count: int = 1) -> list[trs_partition]:

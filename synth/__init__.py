@@ -16,6 +16,8 @@ from .frames import (  # noqa: F401
     StreamSpec,
     make_frame,
     mixed_batch,
+    mixed_batch_frame,
+    mixed_batch_layout,
     poisson_arrivals,
     sequence_2160p_blob,
     sequence_2160p_frame,

@@ -202,9 +202,10 @@ class BatchItem:
     lam: float
 
 
-def mixed_batch(nframes: int = 256, seed: int = 4, lam: float = 0.1) -> list[BatchItem]:
-    """Mixed-resolution batch: 480p8 / 1080p10 / 2160p10 in ratio 4:2:1
-    (146 / 73 / 37 of 256), n drawn uniformly from {4, 8, 16}, shuffled."""
+def mixed_batch_layout(nframes: int = 256, seed: int = 4) -> list[tuple[FrameSpec, int]]:
+    """(spec, n) of each frame of the mixed-resolution batch: 480p8 / 1080p10
+    / 2160p10 in ratio 4:2:1 (146 / 73 / 37 of 256), n drawn uniformly from
+    {4, 8, 16}, shuffled."""
     n480 = round(nframes * 4 / 7)
     n1080 = round(nframes * 2 / 7)
     n2160 = nframes - n480 - n1080
@@ -212,11 +213,21 @@ def mixed_batch(nframes: int = 256, seed: int = 4, lam: float = 0.1) -> list[Bat
     rng = _rng(_WORKLOAD_IDS["mixed"], seed, 0, 0, 3)
     order = rng.permutation(len(specs))
     ns = rng.choice([4, 8, 16], size=len(specs))
+    return [(specs[j], int(ns[i])) for i, j in enumerate(order)]
+
+
+def mixed_batch_frame(i: int, nframes: int = 256, seed: int = 4, lam: float = 0.1) -> BatchItem:
+    spec, n = mixed_batch_layout(nframes, seed)[i]
+    plane, times = make_frame(spec, seed, stream=0, frame=i, workload="mixed")
+    return BatchItem(spec, plane, times, n, lam)
+
+
+def mixed_batch(nframes: int = 256, seed: int = 4, lam: float = 0.1) -> list[BatchItem]:
+    """The whole mixed-resolution batch (see mixed_batch_layout)."""
     out = []
-    for i, j in enumerate(order):
-        spec = specs[j]
+    for i, (spec, n) in enumerate(mixed_batch_layout(nframes, seed)):
         plane, times = make_frame(spec, seed, stream=0, frame=i, workload="mixed")
-        out.append(BatchItem(spec, plane, times, int(ns[i]), lam))
+        out.append(BatchItem(spec, plane, times, n, lam))
     return out
 
 

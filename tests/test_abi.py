@@ -37,7 +37,8 @@ def test_every_declared_symbol_is_exported(trs):
 
 
 @pytest.mark.parametrize("name", ["trs_opts", "trs_ctu_stats", "trs_tables_layout", "trs_partition",
-                                  "trs_frame_desc", "trs_server_opts", "trs_decision", "trs_server_stats"])
+                                  "trs_frame_desc", "trs_server_opts", "trs_decision", "trs_server_stats",
+                                  "trs_tune_report"])
 def test_struct_sizes_match_binding(trs, name):
     import ctypes
     assert trs.trs_sizeof(name) == ctypes.sizeof(getattr(trs, name))

@@ -286,3 +286,25 @@ def test_step1_value_width_paths(dec, oracle, scale, flag):
         assert int(dec.read_tables(tab, 1920, 1080)["status"][3]) == flag
         d, _, _ = oracle.decide(plane, times, 10, 8, 0.1)
         assert_partition_equal(p, d, 9)
+
+
+def test_launch_shapes_do_not_change_decisions(dec, oracle):
+    """Every launch shape the autotuner may pick gives the same bytes; the
+    autotuner picks one of them and keeps the decisions."""
+    from paper_2012_14792_gb300 import trs
+    items = synth.mixed_batch(256, seed=4)[:16]
+    ins, keep = _batch_inputs(items)
+    trs.trs_set_tune(dec.ctx, 4, 4, 8)
+    ref = bytes(dec.batch_decide(ins).cpu().numpy())
+    for bw in (2, 4, 8):
+        for cw in (2, 4, 8):
+            for cb in (4, 8):
+                trs.trs_set_tune(dec.ctx, bw, cw, cb)
+                assert bytes(dec.batch_decide(ins).cpu().numpy()) == ref, (bw, cw, cb)
+    rep = dec.autotune(ins)
+    assert rep["band_warps"] in (2, 4, 8) and rep["col_warps"] in (2, 4, 8) and rep["col_batch"] in (4, 8)
+    assert len(rep["candidates"]) == 6 and all(c["rows_ms"] > 0 and c["cols_ms"] > 0 for c in rep["candidates"])
+    assert bytes(dec.batch_decide(ins).cpu().numpy()) == ref
+    with pytest.raises(trs.TrsError):
+        trs.trs_set_tune(dec.ctx, 3, 4, 8)
+    trs.trs_set_tune(dec.ctx, 4, 4, 8)
