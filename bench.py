@@ -96,6 +96,22 @@ def run_mixed(runtime, trs, items, device: int, steps: int, warmup: int):
             "texture_gbs": luma_bytes / (stage["texture"] / 1e3) / 1e9, "autotune": tune}
 
 
+def max_over_ranks(x: float, dist, device=None) -> float:
+    """The slowest rank's time (every rank calls this with its own)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: every rank processed units_per_rank in the
+    slowest rank's time (weak scaling, replicas)."""
+    return world * units_per_rank / seconds
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -369,11 +385,8 @@ def main():
         sync_all()
     ms = ev0.elapsed_time(ev1)
     stage = trs.trs_batch_stage_ms(dec.ctx)  # CUDA events inside the graph, last timed step
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * nfr * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ms, dist, dev)
+    value = job_throughput(nfr * args.steps, world, ms / 1e3)
     parts = dec.partitions(out, nfr)
     assert all(p.status == 0 for p in parts), [p.status for p in parts]
 
@@ -405,13 +418,9 @@ def main():
     for _ in range(e_steps):
         hp = trs.trs_batch_decide_host(dec.ctx, hdescs)
     sync_all()
-    e2e_dt = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_dt], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_dt = float(t.item())
+    e2e_dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
     assert bytes(hp[0]) == bytes(parts[0])
-    e2e = {"value": world * nfr * e_steps / e2e_dt, "unit": UNIT,
+    e2e = {"value": job_throughput(nfr * e_steps, world, e2e_dt), "unit": UNIT,
            "h2d_bytes_per_step": int(sum(p.numel() for p in pinned) + sum(t.numel() * 4 for t in pinned_t)),
            "d2h_bytes_per_step": nfr * trs.PARTITION_BYTES}
 
