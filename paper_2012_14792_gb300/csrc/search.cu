@@ -138,31 +138,37 @@ __device__ void item_dp(const DevFrame &fr, const PlanItem &it, uint64_t thr, in
     __syncwarp();
 }
 
-// k loop of one item (see band_kernel).  Lane y holds G_{k-1}[y]; lane R
-// (or the edge value when R == 32) holds the empty remainder.  Returns, in
+// k loop of one item (see band_kernel), on values of type VT.  sv[i*32 + y]
+// holds the value of the slice [y, y+dmin+i) with the saturating infinity
+// for heights the item does not admit; G (64 words) holds G_{k-1}[y] for
+// y = 0..63, the saturating infinity past the frame except G_0[R] = 0.
+// Lane y reads G[y+d] (consecutive words, no bank conflicts), so a step is
+// two shared loads, a max (step 1) or add (step 2) and a min.  Returns, in
 // lane k (lane 0 for k = 32), V[k] = G_k[0] with kInf where no split exists.
 template <int STEP, typename VT>
-__device__ __forceinline__ uint64_t item_rows(const uint64_t *st, int nd, int dmin, uint32_t vmask, int kmax,
-                                              int R) {
+__device__ __forceinline__ uint64_t item_rows(const VT *sv, VT *G, int nd, int dmin, int kmax, int R) {
     const int lane = threadIdx.x & 31;
     constexpr VT soft = Soft<VT>::v;
-    VT G = (lane == R) ? VT(0) : soft;  // G_0: only the empty remainder holds zero slices
+    __syncwarp();  // every lane is done with the previous item's G
+    G[lane] = lane == R ? VT(0) : soft;
+    G[lane + 32] = lane + 32 == R ? VT(0) : soft;
+    __syncwarp();
     uint64_t vreg = kInf;
+    const VT *gp = G + lane + dmin;
+    const VT *sp = sv + lane;
     for (int k = 1; k <= kmax; ++k) {
-        const VT edge = (k == 1) ? VT(0) : soft;  // G_{k-1}[R] when R == 32
         VT best = soft;
+#pragma unroll 4
         for (int i = 0; i < nd; ++i) {
-            const int src = lane + dmin + i;
-            VT prev = __shfl_sync(kFull, G, src & 31);
-            if (src >= 32) prev = edge;
-            if ((vmask >> i) & 1u) {
-                const VT val = (VT)st[i * 32];
-                const VT c = STEP == 1 ? (prev > val ? prev : val) : VT(prev + val);
-                best = c < best ? c : best;
-            }
+            const VT prev = gp[i], val = sp[i * 32];
+            const VT c = STEP == 1 ? (prev > val ? prev : val) : VT(prev + val);
+            best = c < best ? c : best;
         }
-        G = best < soft ? best : soft;
-        const VT g0 = __shfl_sync(kFull, G, 0);
+        __syncwarp();
+        G[lane] = best < soft ? best : soft;  // lanes at or past R find no slice: soft
+        if (lane == 0) G[32] = soft;          // G_k[32] of a 32-row frame (k >= 1)
+        __syncwarp();
+        const VT g0 = G[0];
         if (lane == (k & 31)) vreg = g0 >= soft ? kInf : (uint64_t)g0;
     }
     return vreg;
@@ -200,7 +206,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, i
     const size_t base = (size_t)b * R * R;
     const uint64_t *RT = reinterpret_cast<const uint64_t *>(fr.tables + off.rect_t) + base;
     const uint64_t *RQ = reinterpret_cast<const uint64_t *>(fr.tables + off.rect_q) + base;
-    uint64_t *stage = bsm + (size_t)wib * stage_words;
+    // per warp: the column's slice values by height, one item's admitted
+    // values, and the 64-word G table
+    uint64_t *stage = bsm + (size_t)wib * (2 * stage_words + 64);
+    uint64_t *itm = stage + stage_words;
+    uint64_t *gbuf = itm + stage_words;
     uint32_t tok = 0;  // step 2: bit d-1 set if the slice [lane, lane+d) meets the Eq. 4 bound
 #pragma unroll 4
     for (int d = 1; d <= R; ++d) {
@@ -231,17 +241,27 @@ __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, i
         const int dmin = max(1, (int)((it.hlo + kCtu - 1) / kCtu));
         const int dmax = min(R, (int)(it.hhi / kCtu) + 1);
         const int nd = dmax - dmin + 1;
-        uint32_t vmask = 0;
-        for (int i = 0; i < nd; ++i) {
-            const int d = dmin + i, y1 = lane + d;
-            const uint32_t h = line_px(y1, H) - ytop;
-            const bool ok = lane < R && y1 <= R && h >= it.hlo && h <= it.hhi &&
-                            (STEP == 1 || ((tok >> (d - 1)) & 1u));
-            vmask |= (ok ? 1u : 0u) << i;
+        // this item's slice values, the saturating infinity where a height is not admitted
+        uint64_t vreg;
+        if (STEP == 1 && t32) {
+            uint32_t *sv = reinterpret_cast<uint32_t *>(itm);
+            for (int i = 0; i < nd; ++i) {
+                const int d = dmin + i, y1 = lane + d;
+                const uint32_t h = line_px(y1, H) - ytop;
+                const bool ok = lane < R && y1 <= R && h >= it.hlo && h <= it.hhi;
+                sv[i * 32 + lane] = ok ? (uint32_t)stage[(d - 1) * 32 + lane] : Soft<uint32_t>::v;
+            }
+            vreg = item_rows<1, uint32_t>(sv, reinterpret_cast<uint32_t *>(gbuf), nd, dmin, it.kmax, R);
+        } else {
+            for (int i = 0; i < nd; ++i) {
+                const int d = dmin + i, y1 = lane + d;
+                const uint32_t h = line_px(y1, H) - ytop;
+                const bool ok = lane < R && y1 <= R && h >= it.hlo && h <= it.hhi &&
+                                (STEP == 1 || ((tok >> (d - 1)) & 1u));
+                itm[i * 32 + lane] = ok ? stage[(d - 1) * 32 + lane] : kSoft;
+            }
+            vreg = item_rows<STEP, uint64_t>(itm, gbuf, nd, dmin, it.kmax, R);
         }
-        const uint64_t *st = stage + (dmin - 1) * 32 + lane;
-        const uint64_t vreg = (STEP == 1 && t32) ? item_rows<1, uint32_t>(st, nd, dmin, vmask, it.kmax, R)
-                                                 : item_rows<STEP, uint64_t>(st, nd, dmin, vmask, it.kmax, R);
         if (lane == 0) {
             V[0] = kInf;
             if (n == 32) V[32] = vreg;
@@ -581,7 +601,7 @@ __global__ void __launch_bounds__(32) finish_kernel(LaunchArgs args) {
 // Raises the dynamic shared-memory limit of the search kernels to what the
 // largest shapes need (once per device, before any capture).
 int prepare_search_kernels() {
-    const int band_smem = kMaxWarps * kMaxR * 32 * (int)sizeof(uint64_t);
+    const int band_smem = kMaxWarps * (2 * kMaxR * 32 + 64) * (int)sizeof(uint64_t);
     const int col_smem = kMaxWarps * (kMaxC + 1) * (kMaxN + 1) * (int)sizeof(uint64_t);
     const int rb_smem = ((kMaxN + 1) * 32 + kMaxR * 32) * (int)sizeof(uint64_t);
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
@@ -604,7 +624,7 @@ int launch_search(const LaunchArgs &a, int total_bands, int total_windows, int m
     if (e != cudaSuccess) return (int)e;
     const int bw = t.band_warps, cw = t.col_warps;
     const int stage_words = maxR * 32;
-    const size_t band_smem = (size_t)bw * stage_words * sizeof(uint64_t);
+    const size_t band_smem = (size_t)bw * (2 * stage_words + 64) * sizeof(uint64_t);
     const int h_words = (maxC + 1) * (maxN + 1);
     const size_t col_smem = (size_t)cw * h_words * sizeof(uint64_t);
     const int bb = (total_bands + bw - 1) / bw;
