@@ -506,9 +506,10 @@ __global__ void __launch_bounds__(32) rebuild_kernel(LaunchArgs args, int total,
     }
 }
 
-// One warp per frame: the smallest code over the windows reaching Q*, then
-// its decoding into trs_partition (one tile row, tile columns = bands,
-// slices top to bottom).
+// One warp per frame: the smallest code over the windows reaching Q* (lanes
+// scan the windows, then a shuffle reduction), then its decoding into
+// trs_partition (one tile row, tile columns = bands, slices top to bottom),
+// one lane per tile column with a warp prefix sum for the region indices.
 __global__ void __launch_bounds__(32) finish_kernel(LaunchArgs args) {
     const int f = blockIdx.x;
     const DevFrame &fr = frame_at(args, f);
@@ -525,46 +526,57 @@ __global__ void __launch_bounds__(32) finish_kernel(LaunchArgs args) {
     uint64_t *words = reinterpret_cast<uint64_t *>(out);
     for (int i = lane; i < (int)(sizeof(trs_partition) / 8); i += 32) words[i] = 0;
     __syncwarp();
-    if (lane != 0) return;
-    out->status = status;
-    out->n_regions = n;
-    out->cols = C;
-    out->rows = R;
-    out->n_windows = pl.nwin;
-    out->reserved = 0;
-    if (status != TRS_OK) return;
     int bw = -1;
-    for (int w = 0; w < pl.nwin; ++w) {
-        if (fr.codes[w].c <= 0) continue;
-        if (bw < 0 || code_less_g(fr.codes[w], fr.codes[bw])) bw = w;
+    if (status == TRS_OK) {
+        for (int w = lane; w < pl.nwin; w += 32)
+            if (fr.codes[w].c > 0 && (bw < 0 || code_less_g(fr.codes[w], fr.codes[bw]))) bw = w;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int other = __shfl_xor_sync(kFull, bw, o);
+            if (other >= 0 && (bw < 0 || code_less_g(fr.codes[other], fr.codes[bw]) ||
+                               (other < bw && !code_less_g(fr.codes[bw], fr.codes[other]))))
+                bw = other;
+        }
+        if (bw < 0) status = TRS_EINFEASIBLE;
     }
-    if (bw < 0) {
-        out->status = TRS_EINFEASIBLE;
+    if (status != TRS_OK) {
+        if (lane == 0) {
+            out->status = status;
+            out->n_regions = n;
+            out->cols = C;
+            out->rows = R;
+            out->n_windows = pl.nwin;
+        }
         return;
     }
     const WinCode &best = fr.codes[bw];
-    const uint64_t thr = eq4_threshold(t_min, fr.lambda_q);
+    const int c = best.c;
     const TablesOffsets off = tables_offsets(C, R);
     const uint64_t *RT = reinterpret_cast<const uint64_t *>(fr.tables + off.rect_t);
     const uint64_t *RQ = reinterpret_cast<const uint64_t *>(fr.tables + off.rect_q);
     const uint64_t *sat1 = reinterpret_cast<const uint64_t *>(fr.tables + off.sat_s1);
+    // lane b decodes tile column b (c <= n <= 32)
+    const int b = lane;
+    const uint32_t cut = b < c ? best.cut[b] : 0u;
+    const int ns = b < c ? __popc(cut) + 1 : 0;
+    int r = ns;  // inclusive prefix sum of slice counts
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(kFull, r, o);
+        if (lane >= o) r += v;
+    }
+    r -= ns;  // first region index of this tile column
     uint64_t tmax = 0, qsum = 0;
     double sse = 0.0;
-    int r = 0;
-    out->n_tile_cols = best.c;
-    out->n_tile_rows = 1;
-    out->tile_row_mask = 0;
-    out->row_bd[0] = 0;
-    out->row_bd[1] = (int16_t)R;
-    for (int i = 0; i <= best.c; ++i) out->col_bd[i] = best.xe[i];
-    for (int b = 0; b < best.c; ++b) {
+    if (b < c) {
         const int x0 = best.xe[b], x1 = best.xe[b + 1];
         const int bi = band_index(C, x0, x1);
-        out->slice_cuts[b] = best.cut[b];
-        out->tile_slices[b] = (uint8_t)(__popc(best.cut[b]) + 1);
+        out->col_bd[b + 1] = (int16_t)x1;
+        out->slice_cuts[b] = cut;
+        out->tile_slices[b] = (uint8_t)ns;
         int y0 = 0;
         for (int y = 1; y <= R; ++y) {
-            if (y < R && !((best.cut[b] >> (y - 1)) & 1u)) continue;
+            if (y < R && !((cut >> (y - 1)) & 1u)) continue;
             const size_t e = ((size_t)bi * R + (y - y0 - 1)) * R + y0;
             const uint64_t tv = RT[e], qv = RQ[e];
             tmax = tv > tmax ? tv : tmax;
@@ -586,14 +598,37 @@ __global__ void __launch_bounds__(32) finish_kernel(LaunchArgs args) {
             y0 = y;
         }
     }
-    out->t_min_q = t_min;
-    out->thr_q = thr;
-    out->t_q = tmax;
-    out->q = qsum;
-    out->t_min = (double)t_min / 65536.0;
-    out->t = (double)tmax / 65536.0;
-    out->sse = sse;
-    if (r != n || qsum != qstar || tmax > thr) out->status = TRS_EINFEASIBLE;  // internal consistency guard
+    int nreg = ns;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t tm = __shfl_xor_sync(kFull, tmax, o);
+        tmax = tm > tmax ? tm : tmax;
+        qsum += __shfl_xor_sync(kFull, qsum, o);
+        sse += __shfl_xor_sync(kFull, sse, o);
+        nreg += __shfl_xor_sync(kFull, nreg, o);
+    }
+    if (lane == 0) {
+        const uint64_t thr = eq4_threshold(t_min, fr.lambda_q);
+        out->n_regions = n;
+        out->cols = C;
+        out->rows = R;
+        out->n_windows = pl.nwin;
+        out->n_tile_cols = c;
+        out->n_tile_rows = 1;
+        out->tile_row_mask = 0;
+        out->row_bd[0] = 0;
+        out->row_bd[1] = (int16_t)R;
+        out->col_bd[0] = 0;
+        out->t_min_q = t_min;
+        out->thr_q = thr;
+        out->t_q = tmax;
+        out->q = qsum;
+        out->t_min = (double)t_min / 65536.0;
+        out->t = (double)tmax / 65536.0;
+        out->sse = sse;
+        // internal consistency guard
+        out->status = (nreg != n || qsum != qstar || tmax > thr) ? TRS_EINFEASIBLE : TRS_OK;
+    }
 }
 
 }  // namespace

@@ -62,7 +62,7 @@ __host__ __device__ inline TablesOffsets tables_offsets(int C, int R) {
 __device__ inline uint64_t ceil_square_div(uint64_t s1, uint32_t n, uint32_t *rem) {
     const uint64_t lo = s1 * s1;
     const uint64_t hi = __umul64hi(s1, s1);
-    uint64_t r = hi % n;
+    uint64_t r = hi;  // the quotient fits 64 bits, so hi < n: hi is the first remainder
     const uint64_t t1 = (r << 32) | (lo >> 32);
     const uint64_t q1 = t1 / n;
     r = t1 - q1 * n;
