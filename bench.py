@@ -121,6 +121,22 @@ def peaks():
         return 6800.0, 2070.0, "fallback"
 
 
+def ncu_traffic(stage: str, frames: int):
+    """DRAM bytes per launch of a stage's kernel from the committed ncu
+    capture (profiles/ncu_traffic.json), scaled to `frames`; None when there
+    is none or the kernel's source changed since it was taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            k = json.load(f)["kernels"][stage]
+        with open(os.path.join(ROOT, k["source"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest()[:16] != k["source_sha256_16"]:
+                return None
+        return (k["dram_read_bytes"] + k["dram_write_bytes"]) * frames / k["frames"]
+    except Exception:
+        return None
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -430,23 +446,29 @@ def main():
     tex_ms = stage.get("texture", 0.0)
     tex_gbs = tex_bytes / (tex_ms / 1e3) / 1e9 if tex_ms > 0 else 0.0
     row_relax, col_relax = trs.trs_plan_work(3840, 2160, N_REGIONS)
-    # INT32 issue peak: 152 SMs x 128 lanes x max SM clock; a relaxation is a
-    # 64-bit combine + a 64-bit minimum, at least 6 INT32 lane operations
-    alu_peak = 152 * 128 * sm_max * 1e6 / 6.0 / 1e12  # T relaxations / s
+    # each DP transition is one combine (max or +) and one minimum: 2 INT32 operations
+    # (step 1 runs on 32-bit values for these frames); the peak is this GPU's
+    # measured INT32 add/min/max throughput
+    alu_peak = trs.trs_alu_peak(local) / 1e12  # T INT32 ops / s
     kinds = {"step1_rows": row_relax, "step2_rows": row_relax, "step1_columns": col_relax,
              "step2_columns": col_relax}
+    kernels = {"texture": "texture_kernel", "tables": "tables_kernel", "step1_rows": "band_kernel<1>",
+               "step1_columns": "column_kernel<1>", "step2_rows": "band_kernel<2>",
+               "step2_columns": "column_kernel<2>", "rebuild": "rebuild_kernel", "decode": "finish_kernel"}
     dominant = max(stage, key=stage.get) if stage else "texture"
+    traffic = ncu_traffic(dominant, nfr)
     if dominant == "texture":
-        roof = {"kernel": "texture_kernel", "bound": "hbm", "achieved": tex_gbs, "peak": hbm, "unit": "GB/s",
-                "frac": tex_gbs / hbm, "traffic": None, "peak_source": src}
+        roof = {"kernel": kernels[dominant], "bound": "hbm", "achieved": tex_gbs, "peak": hbm, "unit": "GB/s",
+                "frac": tex_gbs / hbm, "traffic": traffic, "algorithmic_bytes": tex_bytes, "peak_source": src}
     else:
-        work = kinds.get(dominant, row_relax + col_relax) * nfr
-        ach = work / (stage[dominant] / 1e3) / 1e12
-        roof = {"kernel": dominant, "bound": "alu", "achieved": ach, "peak": alu_peak,
-                "unit": "T relaxations/s", "frac": ach / alu_peak, "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 INT32 lanes x %.0f MHz / 6 ops" % sm_max}
+        ops = 2.0 * kinds.get(dominant, row_relax + col_relax) * nfr
+        ach = ops / (stage[dominant] / 1e3) / 1e12
+        roof = {"kernel": kernels[dominant], "bound": "alu", "achieved": ach, "peak": alu_peak,
+                "unit": "T INT32 ops/s", "frac": ach / alu_peak, "traffic": traffic, "algorithmic_ops": ops,
+                "peak_source": "measured: trs_alu_peak (32-bit add/min/max chains on every SM)"}
     tex_roof = {"kernel": "texture_kernel", "bound": "hbm", "achieved": tex_gbs, "peak": hbm, "unit": "GB/s",
-                "frac": tex_gbs / hbm, "peak_source": src}
+                "frac": tex_gbs / hbm, "traffic": ncu_traffic("texture", nfr), "algorithmic_bytes": tex_bytes,
+                "peak_source": src}
 
     serving = None
     if not args.no_serving:

@@ -168,12 +168,19 @@ size_t trs_sizeof(const char *name);
 int trs_plan_stats(int width, int height, int n_regions, int k_area, int *n_windows, int *n_items);
 
 /* Algorithmic work of one search step of a frame shape, counted from the
- * plan: row_relax = candidate slices examined by the row DPs (for every
- * item and slice count k <= kmax, every admissible slice [y, y+d)),
- * col_relax = candidate (tile column, k, m) triples examined by the column
- * DPs of all windows.  Each relaxation is one 64-bit combine (max for Eq. 1,
- * + for Eq. 2) and one 64-bit minimum.  Pure host arithmetic. */
+ * loop bounds of its DPs: row_relax = for every row-DP unit, kmax slice
+ * counts x the unit's slice heights x R start rows (a transition G_k[y] <-
+ * G_{k-1}[y+d] combined with the slice value, inadmissible ones included,
+ * as the DP evaluates them); col_relax = for every window and tile column
+ * with slices there, kmax x n transitions H[x][m] <- V[k], H[x1][m-k].
+ * Each transition is one combine (max for Eq. 1, + for Eq. 2) and one
+ * minimum.  Pure host arithmetic. */
 int trs_plan_work(int width, int height, int n_regions, int k_area, double *row_relax, double *col_relax);
+
+/* Measured INT32 throughput of the device (32-bit add / min / max chains
+ * over every SM, CUDA-event timed, best of three), in operations per
+ * second: the peak the search kernels' arithmetic is compared with. */
+int trs_alu_peak(int device, double *ops_per_s);
 
 /* --- context ------------------------------------------------------------ */
 

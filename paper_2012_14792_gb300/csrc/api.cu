@@ -2,6 +2,7 @@
 // the launch sequences of the one-frame and batched paths.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -144,20 +145,14 @@ int trs_plan_work(int width, int height, int n, int k, double *row_relax, double
     TRS_TRY(build_plan(width, height, n, k, &p));
     double rows = 0.0, cols = 0.0;
     for (const PlanItem &it : p.items) {
-        double per_k = 0.0;
-        for (int y = 0; y < p.R; ++y)
-            for (int y1 = y + 1; y1 <= p.R; ++y1) {
-                const uint32_t h = line_px(y1, p.H) - line_px(y, p.H);
-                if (h >= it.hlo && h <= it.hhi) per_k += 1.0;
-            }
-        rows += per_k * it.kmax;
+        const int dmin = std::max(1, (int)((it.hlo + kCtu - 1) / kCtu));
+        const int dmax = std::min(p.R, (int)(it.hhi / kCtu) + 1);
+        rows += (double)it.kmax * (dmax - dmin + 1) * p.R;
     }
     for (size_t w = 0; w < p.win_a.size(); ++w)
         for (int b = 0; b < p.nb; ++b) {
             const int32_t slot = p.slot_of[w * p.nb + b];
-            if (slot < 0) continue;
-            const int km = p.items[slot].kmax;
-            for (int kk = 1; kk <= km; ++kk) cols += (double)(p.n - kk + 1);
+            if (slot >= 0) cols += (double)p.items[slot].kmax * p.n;
         }
     *row_relax = rows;
     *col_relax = cols;

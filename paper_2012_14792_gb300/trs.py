@@ -119,6 +119,7 @@ def _load():
         "trs_sizeof": ([ct.c_char_p], sz),
         "trs_plan_stats": ([i, i, i, i, ct.POINTER(i), ct.POINTER(i)], i),
         "trs_plan_work": ([i, i, i, i, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)], i),
+        "trs_alu_peak": ([i, ct.POINTER(ct.c_double)], i),
         "trs_create": ([ct.POINTER(vp), ct.POINTER(trs_opts)], i),
         "trs_destroy": ([vp], i),
         "trs_ctx_bytes": ([vp], sz),
@@ -203,6 +204,12 @@ def trs_plan_work(width: int, height: int, n_regions: int, k_area: int = 3) -> t
     r, c = ct.c_double(0), ct.c_double(0)
     _check(_lib.trs_plan_work(width, height, n_regions, k_area, ct.byref(r), ct.byref(c)), "trs_plan_work")
     return r.value, c.value
+
+
+def trs_alu_peak(device: int = 0) -> float:
+    v = ct.c_double(0)
+    _check(_lib.trs_alu_peak(device, ct.byref(v)), "trs_alu_peak")
+    return v.value
 
 
 def trs_create(max_width: int, max_height: int, max_regions: int = 16, max_batch: int = 1,
