@@ -226,6 +226,16 @@ int trs_region_tables(trs_ctx *ctx, const trs_ctu_stats *stats, const float *ctu
 int trs_search(trs_ctx *ctx, const void *tables_dev, int width, int height, int n_regions, float lambda,
                trs_partition *out_dev, void *stream);
 
+/* Both search steps for several trade-offs at once: the paper tries
+ * lambda in {0, 0.1, 0.3} and keeps the best per resolution and thread
+ * count (Sec. 3.2).  Step 1 (T_min, Eq. 3) does not depend on lambda and
+ * runs once; step 2 (Eq. 2 under Eq. 4) runs for each lambda.  out_dev
+ * receives n_lambdas partitions, identical to n_lambdas trs_search calls.
+ * n_lambdas in 1..TRS_MAX_LAMBDAS. */
+#define TRS_MAX_LAMBDAS 8
+int trs_search_lambdas(trs_ctx *ctx, const void *tables_dev, int width, int height, int n_regions,
+                       const float *lambdas_host, int n_lambdas, trs_partition *out_dev, void *stream);
+
 /* a1-a5 in one call, with the context's own statistics and table buffers. */
 int trs_decide(trs_ctx *ctx, const void *luma_dev, int width, int height, size_t pitch_bytes, int bit_depth,
                const float *ctu_time_dev, int n_regions, float lambda, trs_partition *out_dev,

@@ -334,6 +334,76 @@ static int search_one(trs_ctx *ctx, const void *tables, int W, int H, int n, flo
     return TRS_OK;
 }
 
+int trs_search_lambdas(trs_ctx *ctx, const void *tables, int W, int H, int n, const float *lambdas, int nl,
+                       trs_partition *out, void *stream) {
+    if (!ctx || !tables || !out || !lambdas || (uintptr_t)tables % 256) return TRS_EINVAL;
+    if (nl < 1 || nl > TRS_MAX_LAMBDAS) return TRS_EINVAL;
+    TRS_TRY(check_frame(ctx, W, H));
+    if (n < 1 || n > ctx->o.max_regions) return TRS_EINVAL;
+    for (int i = 0; i < nl; ++i)
+        if (!std::isfinite(lambdas[i]) || lambdas[i] < 0.0f || lambdas[i] > 1000.0f) return TRS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    PlanEntry *pe;
+    TRS_TRY(get_plan(ctx, W, H, n, &pe));
+    const size_t per = align256(pe->scr.bytes);
+    TRS_TRY(dev_alloc(ctx->scratch, per * nl, &ctx->total));
+    const size_t blob = batch_blob_bytes(nl);
+    TRS_TRY(dev_alloc(ctx->desc, blob * 2, &ctx->total));
+    if (ctx->staging_n < blob) {
+        TRS_CK(cudaEventSynchronize(ctx->copied));
+        if (ctx->staging) cudaFreeHost(ctx->staging);
+        ctx->staging = nullptr;
+        ctx->staging_n = 0;
+        drop_graphs(ctx);
+        TRS_CK(cudaMallocHost(&ctx->staging, blob * 2));
+        ctx->staging_n = blob * 2;
+    }
+    TRS_CK(cudaEventSynchronize(ctx->copied));  // the staging blob is free again
+    uint8_t *hb = (uint8_t *)ctx->staging;
+    DevFrame *hf = (DevFrame *)hb;
+    uint8_t *scr = (uint8_t *)ctx->scratch.p;
+    uint64_t *scal = (uint64_t *)ctx->scal.p;  // 4 words per lambda
+    for (int i = 0; i < nl; ++i) {
+        DevFrame f{};
+        f.W = W;
+        f.H = H;
+        f.tables = (uint8_t *)tables;
+        set_search_scratch(f, *pe, scr + i * per, n, lambdas[i]);
+        f.scal = scal + 4 * i;
+        f.out = out + i;
+        hf[i] = f;
+    }
+    for (int i = 1; i < nl; ++i) {  // step 1 is shared: every lambda reads the first one's results
+        hf[i].V1 = hf[0].V1;
+        hf[i].wres1 = hf[0].wres1;
+    }
+    std::vector<PlanEntry *> pes(nl, pe);
+    BatchLaunch bl;
+    batch_describe(bl, hb, (uint8_t *)ctx->desc.p, nl, pes.data(), nullptr, scal);
+    TRS_CK(cudaMemcpyAsync(bl.db, hb, bl.blob, cudaMemcpyHostToDevice, s));
+    TRS_CK(cudaEventRecord(ctx->copied, s));
+    TRS_CK(cudaMemsetAsync(scal, 0xff, (size_t)nl * 4 * sizeof(uint64_t), s));
+    LaunchArgs one{};
+    one.single = hf[0];
+    one.nframes = 1;
+    one.single_items = (int)pe->host.items.size();
+    one.single_windows = (int)pe->host.win_a.size();
+    one.single_bands = pe->host.nb;
+    TRS_CK((cudaError_t)launch_search(one, pe->host.nb, one.single_windows, pe->host.C, pe->host.R, n, scal, 4, s,
+                                      nullptr, &ctx->tune, 1));
+    for (int i = 1; i < nl; ++i)  // T_min of step 1 for every lambda
+        TRS_CK(cudaMemcpyAsync(scal + 4 * i, scal, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    LaunchArgs all{};
+    all.frames = (const DevFrame *)bl.db;
+    all.nframes = nl;
+    all.pre.items = (const int32_t *)(bl.db + bl.fr_bytes + 2 * bl.pre_bytes);
+    all.pre.windows = (const int32_t *)(bl.db + bl.fr_bytes + 3 * bl.pre_bytes);
+    all.pre.bands = (const int32_t *)(bl.db + bl.fr_bytes + 4 * bl.pre_bytes);
+    TRS_CK((cudaError_t)launch_search(all, bl.bands, bl.windows, pe->host.C, pe->host.R, n, scal, (size_t)nl * 4, s,
+                                      nullptr, &ctx->tune, 2));
+    return TRS_OK;
+}
+
 int trs_search(trs_ctx *ctx, const void *tables, int W, int H, int n, float lambda, trs_partition *out,
                void *stream) {
     return search_one(ctx, tables, W, H, n, lambda, out, stream);

@@ -651,11 +651,12 @@ int prepare_search_kernels() {
 }
 
 int launch_search(const LaunchArgs &a, int total_bands, int total_windows, int maxC, int maxR, int maxN,
-                  uint64_t *scal, size_t nscal, void *stream, cudaEvent_t *ev, const SearchTune *tune) {
+                  uint64_t *scal, size_t nscal, void *stream, cudaEvent_t *ev, const SearchTune *tune, int steps) {
     const SearchTune t = tune ? *tune : SearchTune{};
     cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
     // T_min and Q* start at +infinity; the column kernels reduce into them
-    cudaError_t e = cudaMemsetAsync(scal, 0xff, nscal * sizeof(uint64_t), s);
+    if ((steps & 1) && scal) e = cudaMemsetAsync(scal, 0xff, nscal * sizeof(uint64_t), s);
     if (e != cudaSuccess) return (int)e;
     const int bw = t.band_warps, cw = t.col_warps;
     const int stage_words = maxR * 32;
@@ -677,10 +678,13 @@ int launch_search(const LaunchArgs &a, int total_bands, int total_windows, int m
             else column_kernel<2, 8><<<cb, cw * 32, col_smem, s>>>(a, total_windows, h_words);
         }
     };
-    if (total_bands > 0) band_kernel<1><<<bb, bw * 32, band_smem, s>>>(a, total_bands, stage_words);
-    mark(0);
-    columns(1);
-    mark(1);
+    if (steps & 1) {
+        if (total_bands > 0) band_kernel<1><<<bb, bw * 32, band_smem, s>>>(a, total_bands, stage_words);
+        mark(0);
+        columns(1);
+        mark(1);
+    }
+    if (!(steps & 2)) return e != cudaSuccess ? (int)e : (int)cudaGetLastError();
     if (total_bands > 0) band_kernel<2><<<bb, bw * 32, band_smem, s>>>(a, total_bands, stage_words);
     mark(2);
     columns(2);

@@ -212,6 +212,8 @@ struct SearchTune {
 // maxC / maxR / maxN: largest C, R and n over the frames of the launch (shared-memory sizing).
 int launch_search(const LaunchArgs &a, int total_bands, int total_windows, int maxC, int maxR, int maxN,
                   uint64_t *scal, size_t nscal, void *stream, cudaEvent_t *ev = nullptr,
-                  const SearchTune *tune = nullptr);
+                  const SearchTune *tune = nullptr, int steps = 3);
+// steps: 1 = step 1 only (resets scal first), 2 = step 2, rebuild and decode
+// only (scal[0] must already hold T_min and scal[1] +infinity), 3 = both.
 
 }  // namespace trs

@@ -68,6 +68,11 @@ class Decider:
         trs.trs_search(self.ctx, tables, width, height, n, lam, out)
         return out
 
+    def search_lambdas(self, tables: torch.Tensor, width: int, height: int, n: int, lams: list) -> torch.Tensor:
+        out = torch.zeros(len(lams) * trs.PARTITION_BYTES, dtype=torch.uint8, device=self.device)
+        trs.trs_search_lambdas(self.ctx, tables, width, height, n, list(lams), out)
+        return out
+
     # ---- one frame, whole path ------------------------------------------
     def decide(self, luma: torch.Tensor, pitch: int, width: int, height: int, bit_depth: int,
                times: torch.Tensor, n: int, lam: float, out: torch.Tensor | None = None) -> torch.Tensor:

@@ -128,6 +128,7 @@ def _load():
         "trs_region_tables": ([vp, ct.POINTER(trs_ctu_stats), vp, i, i, vp, sz, vp], i),
         "trs_search": ([vp, vp, i, i, i, f, vp, vp], i),
         "trs_search_noalloc": ([vp, i, i, i, i, f, vp, vp], i),
+        "trs_search_lambdas": ([vp, vp, i, i, i, ct.POINTER(ct.c_float), i, vp, vp], i),
         "trs_decide": ([vp, vp, i, i, sz, i, vp, i, f, vp, vp], i),
         "trs_decide_host": ([vp, vp, i, i, sz, i, vp, i, f, ct.POINTER(trs_partition), vp], i),
         "trs_batch_decide": ([vp, ct.POINTER(trs_frame_desc), i, vp, vp], i),
@@ -252,6 +253,12 @@ def trs_region_tables(ctx, stats: trs_ctu_stats, ctu_time, width, height, tables
 def trs_search(ctx, tables, width, height, n_regions, lam, out, stream=None) -> None:
     _check(_lib.trs_search(ctx, _ptr(tables), width, height, n_regions, lam, _ptr(out), _stream(stream)),
            "trs_search")
+
+
+def trs_search_lambdas(ctx, tables, width, height, n_regions, lambdas, out, stream=None) -> None:
+    arr = (ct.c_float * len(lambdas))(*lambdas)
+    _check(_lib.trs_search_lambdas(ctx, _ptr(tables), width, height, n_regions, arr, len(lambdas), _ptr(out),
+                                   _stream(stream)), "trs_search_lambdas")
 
 
 def trs_search_noalloc(tables, width, height, n_regions, k_area, lam, out, stream=None) -> None:

@@ -308,3 +308,22 @@ def test_launch_shapes_do_not_change_decisions(dec, oracle):
     with pytest.raises(trs.TrsError):
         trs.trs_set_tune(dec.ctx, 3, 4, 8)
     trs.trs_set_tune(dec.ctx, 4, 4, 8)
+
+
+@pytest.mark.parametrize("spec_name,n,lams", [("SPEC_2160P10", 16, [0.0, 0.1, 0.3]),
+                                              ("SPEC_1080P10", 8, [0.3, 0.0, 2.0, 0.05, 0.1]),
+                                              ("SPEC_480P8", 4, [0.1])])
+def test_search_lambdas_equals_separate_searches(dec, oracle, spec_name, n, lams):
+    """Step 1 shared across lambdas: every partition equals its own trs_search."""
+    spec = getattr(synth, spec_name)
+    plane, times = synth.make_frame(spec, seed=21)
+    W, H = spec.width, spec.height
+    _, st, _keep = _texture(dec, plane, spec.bit_depth)
+    tab = dec.tables_buffer(W, H)
+    dec.region_tables(st, torch.from_numpy(times).cuda(), W, H, tab)
+    many = dec.partitions(dec.search_lambdas(tab, W, H, n, lams), len(lams))
+    for lam, p in zip(lams, many):
+        one = dec.partitions(dec.search(tab, W, H, n, lam))[0]
+        assert bytes(p) == bytes(one)
+        d, _, _ = oracle.decide(plane, times, spec.bit_depth, n, lam)
+        assert_partition_equal(p, d, spec.ctu_rows)
