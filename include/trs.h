@@ -377,6 +377,22 @@ int trs_server_submit(trs_server *srv, int stream_id, const void *luma_host, siz
 /* Returns up to max_out finished decisions, waiting at most timeout_us for
  * the first; TRS_ETIMEOUT when none finished in time. */
 int trs_server_poll(trs_server *srv, trs_decision *out, int max_out, int timeout_us, int *n_out);
+
+/* Temporal layers (random-access GOPs).  Sec. 2.1 takes the estimator from
+ * the co-TL frame: the previously encoded frame of the same temporal layer.
+ * A stream opened with n_layers keeps one resident map per layer;
+ * trs_server_update_times_layer stores the CTU times of a just-encoded
+ * frame of `layer`, and trs_server_submit_layer decides a frame of `layer`
+ * with that layer's map.  Before a layer's first map exists the most recent
+ * map of any layer is used (the paper is silent on this case).  The calls
+ * without _layer act on layer 0.  TRS_EINVAL for a layer outside
+ * 0..n_layers-1; n_layers in 1..TRS_MAX_TEMPORAL_LAYERS. */
+#define TRS_MAX_TEMPORAL_LAYERS 8
+int trs_server_open_stream_layers(trs_server *srv, int width, int height, int bit_depth, int n_regions,
+                                  float lambda, int n_layers, int *stream_id);
+int trs_server_update_times_layer(trs_server *srv, int stream_id, int layer, const float *ctu_time_host);
+int trs_server_submit_layer(trs_server *srv, int stream_id, int layer, const void *luma_host, size_t pitch_bytes,
+                            uint64_t tag, uint64_t *ticket);
 int trs_server_info(trs_server *srv, trs_server_stats *out);
 
 #ifdef __cplusplus

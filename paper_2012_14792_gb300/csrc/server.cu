@@ -1,8 +1,10 @@
 // Continuous-batching decision server over many concurrent streams.
 //
 // Each stream (one video being encoded) keeps on the device, for as long as
-// it is open: its co-located CTU time map (the estimator input of Sec. 2.1,
-// refreshed by trs_server_update_times after each encoded frame) and
+// it is open: one co-located CTU time map per temporal layer (the estimator
+// input of Sec. 2.1: the CTU times of the previously encoded frame of the
+// same temporal layer, the co-TL frame; refreshed by
+// trs_server_update_times_layer after each encoded frame) and
 // kSlotsPerStream request slots (a luma plane buffer plus the statistics,
 // tables and search scratch of one decision).  All of that memory is
 // allocated when the stream is admitted; admission fails with TRS_EBUSY when
@@ -31,6 +33,7 @@ using namespace trs;
 namespace {
 
 constexpr int kSlotsPerStream = 2;
+constexpr int kMaxLayers = TRS_MAX_TEMPORAL_LAYERS;
 
 double now_us() {
     using namespace std::chrono;
@@ -50,8 +53,11 @@ struct Stream {
     int W = 0, H = 0, bd = 0, n = 0;
     float lambda = 0.0f;
     PlanEntry *pe = nullptr;
-    DevBuf times;  // resident co-located CTU time map
-    bool have_times = false;
+    int layers = 1;
+    DevBuf times;                 // layers x R*C resident co-located CTU time maps
+    size_t tmap = 0;              // bytes of one map (256-aligned)
+    bool have[kMaxLayers] = {};   // a map of that layer was given
+    int last = -1;                // layer of the most recent map
     Slot slot[kSlotsPerStream];
     int inflight = 0;
     size_t bytes = 0;
@@ -59,6 +65,7 @@ struct Stream {
 
 struct Request {
     int stream = 0, slot = 0;
+    const float *times = nullptr;  // the map this decision reads
     uint64_t ticket = 0, tag = 0;
     const void *luma = nullptr;
     size_t pitch = 0;
@@ -129,7 +136,7 @@ int launch_batch(trs_server *srv, Batch &b) {
         f.H = st.H;
         f.bd = st.bd;
         f.vec_ok = 1;
-        f.times = (const float *)st.times.p;
+        f.times = r.times;
         f.s1 = (uint32_t *)sl.stats;
         f.cnt = (uint32_t *)(sl.stats + align256((size_t)cells * 4));
         f.vmax = (uint32_t *)(sl.stats + 2 * align256((size_t)cells * 4));
@@ -298,7 +305,12 @@ int trs_server_destroy(trs_server *srv) {
 
 int trs_server_open_stream(trs_server *srv, int width, int height, int bit_depth, int n_regions, float lambda,
                            int *stream_id) {
-    if (!srv || !stream_id) return TRS_EINVAL;
+    return trs_server_open_stream_layers(srv, width, height, bit_depth, n_regions, lambda, 1, stream_id);
+}
+
+int trs_server_open_stream_layers(trs_server *srv, int width, int height, int bit_depth, int n_regions,
+                                  float lambda, int n_layers, int *stream_id) {
+    if (!srv || !stream_id || n_layers < 1 || n_layers > kMaxLayers) return TRS_EINVAL;
     TRS_TRY(check_frame(srv->ctx, width, height));
     if (bit_depth < 8 || bit_depth > 12 || n_regions < 1 || n_regions > srv->o.max_regions) return TRS_EINVAL;
     if (!std::isfinite(lambda) || lambda < 0.0f || lambda > 1000.0f) return TRS_EINVAL;
@@ -318,11 +330,12 @@ int trs_server_open_stream(trs_server *srv, int width, int height, int bit_depth
     st.lambda = lambda;
     TRS_TRY(get_plan(srv->ctx, width, height, n_regions, &st.pe));
     const size_t per_slot = slot_bytes(st);
-    const size_t tmap = align256((size_t)st.pe->host.C * st.pe->host.R * 4);
-    const size_t need = tmap + kSlotsPerStream * per_slot;
+    st.layers = n_layers;
+    st.tmap = align256((size_t)st.pe->host.C * st.pe->host.R * 4);
+    const size_t need = st.tmap * n_layers + kSlotsPerStream * per_slot;
     if (srv->o.mem_budget_bytes && srv->mem_used + need > srv->o.mem_budget_bytes) return TRS_EBUSY;
     size_t used = 0;
-    int rc = dev_alloc(st.times, tmap, &used);
+    int rc = dev_alloc(st.times, st.tmap * n_layers, &used);
     const int bps = bit_depth == 8 ? 1 : 2;
     const int C = st.pe->host.C, R = st.pe->host.R;
     for (Slot &sl : st.slot) {
@@ -368,25 +381,38 @@ int trs_server_close_stream(trs_server *srv, int id) {
 }
 
 int trs_server_update_times(trs_server *srv, int id, const float *times_host) {
+    return trs_server_update_times_layer(srv, id, 0, times_host);
+}
+
+int trs_server_update_times_layer(trs_server *srv, int id, int layer, const float *times_host) {
     if (!srv || !times_host) return TRS_EINVAL;
     std::unique_lock<std::mutex> lk(srv->mu);
     if (id < 0 || id >= (int)srv->streams.size() || !srv->streams[id].open) return TRS_EINVAL;
     Stream &st = srv->streams[id];
+    if (layer < 0 || layer >= st.layers) return TRS_EINVAL;
     TRS_TRY(wait_stream_idle(srv, lk, st));
     const size_t bytes = (size_t)st.pe->host.C * st.pe->host.R * sizeof(float);
-    TRS_CK(cudaMemcpy(st.times.p, times_host, bytes, cudaMemcpyHostToDevice));
-    st.have_times = true;
+    TRS_CK(cudaMemcpy((uint8_t *)st.times.p + st.tmap * layer, times_host, bytes, cudaMemcpyHostToDevice));
+    st.have[layer] = true;
+    st.last = layer;
     return TRS_OK;
 }
 
 int trs_server_submit(trs_server *srv, int id, const void *luma_host, size_t pitch_bytes, uint64_t tag,
                       uint64_t *ticket) {
+    return trs_server_submit_layer(srv, id, 0, luma_host, pitch_bytes, tag, ticket);
+}
+
+int trs_server_submit_layer(trs_server *srv, int id, int layer, const void *luma_host, size_t pitch_bytes,
+                            uint64_t tag, uint64_t *ticket) {
     if (!srv || !luma_host) return TRS_EINVAL;
     std::lock_guard<std::mutex> lk(srv->mu);
     if (id < 0 || id >= (int)srv->streams.size() || !srv->streams[id].open) return TRS_EINVAL;
     if (srv->worker_status != TRS_OK) return srv->worker_status;
     Stream &st = srv->streams[id];
-    if (!st.have_times) return TRS_EINVAL;
+    if (layer < 0 || layer >= st.layers || st.last < 0) return TRS_EINVAL;
+    // the co-TL map; before a layer's first encoded frame, the most recent map of any layer
+    const int use = st.have[layer] ? layer : st.last;
     if (pitch_bytes < (size_t)st.W * (st.bd == 8 ? 1 : 2)) return TRS_EINVAL;
     int s = -1;
     for (int i = 0; i < kSlotsPerStream; ++i)
@@ -400,6 +426,7 @@ int trs_server_submit(trs_server *srv, int id, const void *luma_host, size_t pit
     Request r;
     r.stream = id;
     r.slot = s;
+    r.times = (const float *)((const uint8_t *)st.times.p + st.tmap * use);
     r.ticket = srv->next_ticket++;
     r.tag = tag;
     r.luma = luma_host;

@@ -144,6 +144,9 @@ def _load():
         "trs_server_submit": ([vp, i, vp, sz, ct.c_uint64, ct.POINTER(ct.c_uint64)], i),
         "trs_server_poll": ([vp, ct.POINTER(trs_decision), i, i, ct.POINTER(i)], i),
         "trs_server_info": ([vp, ct.POINTER(trs_server_stats)], i),
+        "trs_server_open_stream_layers": ([vp, i, i, i, i, f, i, ct.POINTER(i)], i),
+        "trs_server_update_times_layer": ([vp, i, i, vp], i),
+        "trs_server_submit_layer": ([vp, i, i, vp, sz, ct.c_uint64, ct.POINTER(ct.c_uint64)], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -372,3 +375,21 @@ def trs_server_info(srv) -> trs_server_stats:
     out = trs_server_stats()
     _check(_lib.trs_server_info(srv, ct.byref(out)), "trs_server_info")
     return out
+
+
+def trs_server_open_stream_layers(srv, width, height, bit_depth, n_regions, lam, n_layers) -> int:
+    sid = ct.c_int(-1)
+    _check(_lib.trs_server_open_stream_layers(srv, width, height, bit_depth, n_regions, lam, n_layers,
+                                              ct.byref(sid)), "trs_server_open_stream_layers")
+    return sid.value
+
+
+def trs_server_update_times_layer(srv, sid, layer, times_host) -> None:
+    _check(_lib.trs_server_update_times_layer(srv, sid, layer, _ptr(times_host)), "trs_server_update_times_layer")
+
+
+def trs_server_submit_layer(srv, sid, layer, luma_host, pitch_bytes, tag=0) -> int:
+    t = ct.c_uint64(0)
+    _check(_lib.trs_server_submit_layer(srv, sid, layer, _ptr(luma_host), pitch_bytes, tag, ct.byref(t)),
+           "trs_server_submit_layer")
+    return t.value

@@ -19,6 +19,8 @@ from .frames import (  # noqa: F401
     mixed_batch_frame,
     mixed_batch_layout,
     poisson_arrivals,
+    ra_coding_order,
+    ra_temporal_layer,
     sequence_2160p_blob,
     sequence_2160p_frame,
     serving_streams,

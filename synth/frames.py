@@ -273,3 +273,34 @@ def small_frame(width: int, height: int, bit_depth: int, seed: int) -> tuple[np.
     """A frame of arbitrary size for parity and edge-case tests."""
     spec = FrameSpec(f"{width}x{height}p{bit_depth}", width, height, bit_depth)
     return make_frame(spec, seed, workload="test")
+
+
+def ra_temporal_layer(poc: int, gop: int = 16) -> int:
+    """Temporal layer of a picture in a hierarchical random-access GOP
+    (GOP 16: layers 0..4): 0 at multiples of the GOP, then one layer per
+    halving of the distance to the nearest anchor."""
+    r = poc % gop
+    if r == 0:
+        return 0
+    layer, step = 1, gop // 2
+    while r % step:
+        step //= 2
+        layer += 1
+    return layer
+
+
+def ra_coding_order(gop: int = 16) -> list[int]:
+    """POCs of the first GOP in coding order: 0, gop, then each layer's
+    pictures depth first (gop/2, gop/4, ... before their right halves)."""
+    order = [0, gop]
+
+    def split(lo: int, hi: int):
+        if hi - lo < 2:
+            return
+        mid = (lo + hi) // 2
+        order.append(mid)
+        split(lo, mid)
+        split(mid, hi)
+
+    split(0, gop)
+    return order

@@ -144,3 +144,39 @@ def test_time_map_update_takes_effect(lib):
     finally:
         trs.trs_server_destroy(srv)
         dec.close()
+
+
+def test_temporal_layer_maps_follow_the_co_tl_frame(lib):
+    """One random-access GOP of 16 in coding order: each frame is decided
+    with the CTU times of the previous frame of its temporal layer (the co-TL
+    frame of Sec. 2.1), or the most recent map before its layer has one."""
+    trs, runtime = lib
+    srv = trs.trs_server_create(1920, 1080, max_regions=8, max_streams=1, max_batch=4, max_inflight=2)
+    dec = runtime.Decider(max_width=1920, max_height=1080, max_regions=8)
+    try:
+        sid = trs.trs_server_open_stream_layers(srv, 1920, 1080, 10, 8, 0.1, 5)
+        spec = synth.SPEC_1080P10
+        _, init = synth.make_frame(spec, seed=30, frame=999, workload="serve")
+        trs.trs_server_update_times_layer(srv, sid, 0, np.ascontiguousarray(init))
+        layer_map, last = {0: init}, init
+        for poc in synth.ra_coding_order(16):
+            L = synth.ra_temporal_layer(poc)
+            plane, encoded_times = synth.make_frame(spec, seed=31, frame=poc, workload="serve")
+            plane = np.ascontiguousarray(plane)
+            expect = layer_map.get(L, last)
+            trs.trs_server_submit_layer(srv, sid, L, plane, plane.strides[0], tag=poc)
+            ds = []
+            deadline = time.time() + 30
+            while not ds and time.time() < deadline:
+                ds = trs.trs_server_poll(srv, 4, 10_000)
+            assert len(ds) == 1 and ds[0].status == 0 and ds[0].tag == poc
+            assert bytes(ds[0].partition) == bytes(_alone(dec, plane, np.ascontiguousarray(expect), 10, 8, 0.1))
+            # the frame is encoded: its CTU times become its layer's co-TL map
+            trs.trs_server_update_times_layer(srv, sid, L, np.ascontiguousarray(encoded_times))
+            layer_map[L] = encoded_times
+            last = encoded_times
+        with pytest.raises(trs.TrsError):
+            trs.trs_server_submit_layer(srv, sid, 5, plane, plane.strides[0])
+    finally:
+        trs.trs_server_destroy(srv)
+        dec.close()

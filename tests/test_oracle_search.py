@@ -227,3 +227,10 @@ def test_infeasible_and_invalid(oracle):
     assert oracle.search_dp(st, Tq, 3).status == oracle.EINFEASIBLE
     assert oracle.search_enum(st, Tq, 3).status == oracle.EINFEASIBLE
     assert oracle.search_dp(st, Tq, 0).status == oracle.EINVAL
+
+
+def test_random_access_gop_layers():
+    import synth
+    order = synth.ra_coding_order(16)
+    assert order[:6] == [0, 16, 8, 4, 2, 1] and sorted(order) == list(range(17))
+    assert [synth.ra_temporal_layer(p) for p in (0, 16, 8, 4, 12, 2, 6, 1, 15)] == [0, 0, 1, 2, 2, 3, 3, 4, 4]
