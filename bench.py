@@ -337,6 +337,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-light", action="store_true")
     ap.add_argument("--frames", type=int, default=NFRAMES,
                     help="frames per step (a smaller case for profiling; the metric uses 64)")
     args = ap.parse_args()
@@ -405,6 +406,31 @@ def main():
     value = job_throughput(nfr * args.steps, world, ms / 1e3)
     parts = dec.partitions(out, nfr)
     assert all(p.status == 0 for p in parts), [p.status for p in parts]
+
+    # --- lightweight search: every 4th area window --------------------------
+    light = None
+    if not args.no_light:
+        trs.trs_set_window_step(dec.ctx, 4)
+        for _ in range(args.warmup):
+            dec.batch_decide(ins, out)
+        torch.cuda.synchronize(dev)
+        l_steps = max(3, args.steps // 4)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(l_steps):
+            dec.batch_decide(ins, out)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        lp = dec.partitions(out, nfr)
+        trs.trs_set_window_step(dec.ctx, 1)
+        tr = np.array([a.t_q / b.t_q for a, b in zip(lp, parts)])
+        qr = np.array([a.q / max(1, b.q) for a, b in zip(lp, parts)])
+        light = {"window_step": 4, "value": nfr * l_steps / (e0.elapsed_time(e1) / 1e3), "unit": UNIT,
+                 "identical_frac": float(np.mean([a.x_edges() == b.x_edges() and a.band_cuts() == b.band_cuts()
+                                                  for a, b in zip(lp, parts)])),
+                 "t_ratio_mean": float(tr.mean()), "t_ratio_max": float(tr.max()),
+                 "q_ratio_mean": float(qr.mean()), "q_ratio_max": float(qr.max()),
+                 "note": "T(P) and Q(P) of the lightweight decision over the exact one, same frames"}
 
     # --- plain: one frame per launch chain ------------------------------
     one = torch.zeros(trs.PARTITION_BYTES, dtype=torch.uint8, device=dev)
@@ -489,7 +515,8 @@ def main():
                            "frames_per_step": nfr, "form": "batched, CUDA graph",
                            "l2": f"inputs {tex_bytes / 1e9:.2f} GB per step > L2, no flush"},
                 "plain": {"value": plain_value, "unit": UNIT, "form": "one frame per launch chain"},
-                "stage_ms": stage, "autotune": tune, "mixed_256": mixed_res, "serving": serving,
+                "stage_ms": stage, "autotune": tune, "mixed_256": mixed_res, "lightweight": light,
+                "serving": serving,
                 "clocks": clk.summary(), "e2e": e2e,
                 "gpu_launches": 8 * args.steps, "roofline": roof, "roofline_texture": tex_roof,
                 "cpu_baseline": cpu}

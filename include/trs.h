@@ -303,6 +303,14 @@ typedef struct trs_tune_report {
  * on the shapes. */
 int trs_autotune(trs_ctx *ctx, const trs_frame_desc *frames_host, int nframes, trs_tune_report *out, void *stream);
 
+/* Lightweight search (the paper leaves cheaper searches to future work,
+ * Sec. 4): with step > 1 later searches of this context evaluate only
+ * every step-th area window [a, 3a-1], counted from the largest a (kept
+ * always, it holds the most balanced partitions).  Results are valid
+ * partitions of S(n), optimal among those windows; T_min and Q may exceed
+ * the exact ones.  step = 1 restores the exact search.  1 <= step <= 64. */
+int trs_set_window_step(trs_ctx *ctx, int step);
+
 /* Sets the search kernels' launch shapes directly: band_warps and
  * col_warps in {2, 4, 8}, col_batch in {4, 8}; TRS_EINVAL otherwise.
  * Drops captured batch graphs. */

@@ -109,6 +109,7 @@ def lib():
         sargs = [ct.c_int, ct.c_int, u64p, u64p, u64p, u32p, ct.c_int, ct.c_int, ct.c_uint32]
         _lib.oracle_search_enum.argtypes = sargs + [ct.c_int, ct.POINTER(_Result)]
         _lib.oracle_search_dp.argtypes = sargs + [ct.POINTER(_Result)]
+        _lib.oracle_search_dp_windows.argtypes = sargs + [ct.c_int, ct.POINTER(_Result)]
         _lib.oracle_count_enum.argtypes = [ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_int, u64p]
         _lib.oracle_evaluate.argtypes = [ct.c_int, ct.c_int, u64p, u64p, u64p, u32p, ct.c_int,
                                          ct.POINTER(ct.c_int), u64p, u64p, u64p, u64p, u64p,
@@ -219,6 +220,17 @@ def search_dp(st: Stats, Tq: np.ndarray, n: int, lam: float = 0.0, k_area: int =
     r = _Result()
     lib().oracle_search_dp(st.width, st.height, _p64(S1), _p64(S2), _p64(N), _p32(T), n, k_area,
                            lq, ct.byref(r))
+    return _decision(r)
+
+
+def search_dp_windows(st: Stats, Tq: np.ndarray, n: int, lam: float = 0.0, window_step: int = 1,
+                      k_area: int = 3, lam_q: int | None = None) -> Decision:
+    """O2 over every window_step-th area window (largest kept): the lightweight search."""
+    S1, S2, N, T = _search_args(st, Tq)
+    lq = lambda_q(lam) if lam_q is None else lam_q
+    r = _Result()
+    lib().oracle_search_dp_windows(st.width, st.height, _p64(S1), _p64(S2), _p64(N), _p32(T), n, k_area, lq,
+                                   window_step, ct.byref(r))
     return _decision(r)
 
 

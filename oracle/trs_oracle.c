@@ -747,9 +747,35 @@ static int list_windows(const frame_t *f, int n, int k_area, uint64_t **out, int
  * step 1 min over windows of the min-max DP; step 2 min over windows of the
  * min-sum DP under Eq. 4; ties to the lex-smallest code over all windows.
  */
+static int search_dp_windows(int W, int H, const uint64_t *S1, const uint64_t *S2, const uint64_t *N,
+                             const uint32_t *Tq, int n, int k_area, uint32_t lambda_q, int window_step,
+                             oracle_result *res);
+
 int oracle_search_dp(int W, int H, const uint64_t *S1, const uint64_t *S2, const uint64_t *N,
                      const uint32_t *Tq, int n, int k_area, uint32_t lambda_q, oracle_result *res) {
+    return search_dp_windows(W, H, S1, S2, N, Tq, n, k_area, lambda_q, 1, res);
+}
+
+/*
+ * Lightweight variant (the paper's future work on cheaper searches, Sec. 4):
+ * the same DP over every window_step-th area window only, counted from the
+ * largest window down (which always stays).  The result is a partition of
+ * S(n) that is optimal among the partitions of those windows; step 1 is O2.
+ */
+int oracle_search_dp_windows(int W, int H, const uint64_t *S1, const uint64_t *S2, const uint64_t *N,
+                             const uint32_t *Tq, int n, int k_area, uint32_t lambda_q, int window_step,
+                             oracle_result *res) {
+    return search_dp_windows(W, H, S1, S2, N, Tq, n, k_area, lambda_q, window_step, res);
+}
+
+static int search_dp_windows(int W, int H, const uint64_t *S1, const uint64_t *S2, const uint64_t *N,
+                             const uint32_t *Tq, int n, int k_area, uint32_t lambda_q, int window_step,
+                             oracle_result *res) {
     memset(res, 0, sizeof(*res));
+    if (window_step < 1) {
+        res->status = OR_EINVAL;
+        return OR_EINVAL;
+    }
     int st = check_inputs(W, H, n, k_area);
     if (st) {
         res->status = st;
@@ -768,6 +794,12 @@ int oracle_search_dp(int W, int H, const uint64_t *S1, const uint64_t *S2, const
         memo_free(&m);
         res->status = OR_ENOMEM;
         return OR_ENOMEM;
+    }
+    if (window_step > 1) { /* keep windows nw-1, nw-1-step, ... */
+        int kept = 0;
+        for (int i = 0; i < nw; ++i)
+            if ((nw - 1 - i) % window_step == 0) win[kept++] = win[i];
+        nw = kept;
     }
     res->n = n;
     res->n_windows = (uint64_t)nw;

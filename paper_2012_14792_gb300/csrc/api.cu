@@ -60,14 +60,14 @@ int check_frame(const trs_ctx *ctx, int W, int H) {
 }
 
 int get_plan(trs_ctx *ctx, int W, int H, int n, PlanEntry **out) {
-    auto key = std::make_tuple(W, H, n);
+    auto key = std::make_tuple(W, H, n, ctx->window_step);
     auto it = ctx->plans.find(key);
     if (it != ctx->plans.end()) {
         *out = it->second;
         return TRS_OK;
     }
     PlanEntry *e = new PlanEntry();
-    int s = build_plan(W, H, n, ctx->o.k_area, &e->host);
+    int s = build_plan(W, H, n, ctx->o.k_area, &e->host, ctx->window_step);
     if (s != TRS_OK) {
         delete e;
         return s;
@@ -703,6 +703,13 @@ int trs_autotune(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_tune_report
         rep->rows_ms[j] = rows[j];
         rep->cols_ms[j] = cols[j];
     }
+    return TRS_OK;
+}
+
+int trs_set_window_step(trs_ctx *ctx, int step) {
+    if (!ctx || step < 1 || step > 64) return TRS_EINVAL;
+    ctx->window_step = step;
+    drop_graphs(ctx);
     return TRS_OK;
 }
 

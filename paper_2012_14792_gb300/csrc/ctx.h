@@ -52,8 +52,9 @@ struct trs_ctx {
     int maxC = 0, maxR = 0;
     // one-frame path
     trs::DevBuf s1, s2, cnt, vmax, flags, tables, scratch, scal, part, luma_stage, time_stage;
-    // plans by (W, H, n)
-    std::map<std::tuple<int, int, int>, trs::PlanEntry *> plans;
+    // plans by (W, H, n, window step)
+    std::map<std::tuple<int, int, int, int>, trs::PlanEntry *> plans;
+    int window_step = 1;  // 1: exact search; > 1: every window_step-th area window (trs_set_window_step)
     // batched path
     trs::DevBuf arena, desc;
     void *staging = nullptr;  // pinned host copy of the descriptor blob

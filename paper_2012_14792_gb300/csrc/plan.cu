@@ -29,8 +29,8 @@ static std::vector<uint32_t> extents(int cells, int total) {
     return std::vector<uint32_t>(s.begin(), s.end());
 }
 
-int build_plan(int W, int H, int n, int k, HostPlan *p) {
-    if (W <= 0 || H <= 0 || n < 1 || n > kMaxN || k < 1) return TRS_EINVAL;
+int build_plan(int W, int H, int n, int k, HostPlan *p, int window_step) {
+    if (W <= 0 || H <= 0 || n < 1 || n > kMaxN || k < 1 || window_step < 1) return TRS_EINVAL;
     const int C = (W + kCtu - 1) / kCtu, R = (H + kCtu - 1) / kCtu;
     if (C > kMaxC || R > kMaxR) return TRS_EINVAL;
     p->W = W;
@@ -49,6 +49,13 @@ int build_plan(int W, int H, int n, int k, HostPlan *p) {
             if (a * (uint64_t)n <= p->A && ((uint64_t)k * a - 1) * (uint64_t)n >= p->A) wins.insert(a);
         }
     p->win_a.assign(wins.begin(), wins.end());
+    if (window_step > 1) {
+        std::vector<uint64_t> kept;
+        const int all = (int)p->win_a.size();
+        for (int i = 0; i < all; ++i)
+            if ((all - 1 - i) % window_step == 0) kept.push_back(p->win_a[i]);
+        p->win_a.swap(kept);
+    }
     const int nwin = (int)p->win_a.size();
     p->band_x0.resize(p->nb);
     p->band_x1.resize(p->nb);

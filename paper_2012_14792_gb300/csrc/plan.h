@@ -22,7 +22,9 @@ struct SearchScratch {
     size_t V1, V2, w1, w2, H2, codes, bytes;
 };
 
-int build_plan(int W, int H, int n, int k, HostPlan *p);
+// window_step > 1 keeps every window_step-th area window only, counted from
+// the largest (the lightweight search); 1 is the exact search.
+int build_plan(int W, int H, int n, int k, HostPlan *p, int window_step = 1);
 size_t plan_blob_bytes(const HostPlan &p);
 // Lays the plan out as a device blob whose pointers assume it will be copied to dev_base.
 void plan_serialize(const HostPlan &p, uint8_t *dev_base, std::vector<uint8_t> &blob);

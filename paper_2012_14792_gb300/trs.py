@@ -136,6 +136,7 @@ def _load():
         "trs_batch_stage_ms": ([vp, ct.POINTER(ct.c_float), i], i),
         "trs_autotune": ([vp, ct.POINTER(trs_frame_desc), i, ct.POINTER(trs_tune_report), vp], i),
         "trs_set_tune": ([vp, i, i, i], i),
+        "trs_set_window_step": ([vp, i], i),
         "trs_server_create": ([ct.POINTER(vp), ct.POINTER(trs_server_opts)], i),
         "trs_server_destroy": ([vp], i),
         "trs_server_open_stream": ([vp, i, i, i, i, f, ct.POINTER(i)], i),
@@ -315,6 +316,10 @@ def trs_autotune(ctx, descs: list[trs_frame_desc], stream=None) -> trs_tune_repo
     rep = trs_tune_report()
     _check(_lib.trs_autotune(ctx, arr, len(descs), ct.byref(rep), _stream(stream)), "trs_autotune")
     return rep
+
+
+def trs_set_window_step(ctx, step: int) -> None:
+    _check(_lib.trs_set_window_step(ctx, step), "trs_set_window_step")
 
 
 def trs_set_tune(ctx, band_warps: int, col_warps: int, col_batch: int) -> None:

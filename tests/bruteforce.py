@@ -97,3 +97,35 @@ def count(W, H, n, k=3, area_rule=True):
                 continue
         c += 1
     return c
+
+
+def search_in_windows(W, H, S1, S2, Tq, n, lam_q, window_step, k=3):
+    """The lightweight search by brute force: the candidates are the
+    configurations whose slice areas all fit one kept window [a, k*a-1], the
+    kept a being every window_step-th admissible slice area counted from the
+    largest."""
+    C, R, cw, ch = geometry(W, H)
+    A = W * H
+    widths = {sum(cw[i:j]) for i in range(C) for j in range(i + 1, C + 1)}
+    heights = {sum(ch[i:j]) for i in range(R) for j in range(i + 1, R + 1)}
+    wins = sorted({w * h for w in widths for h in heights if w * h * n <= A and (k * w * h - 1) * n >= A})
+    kept = [a for i, a in enumerate(wins) if (len(wins) - 1 - i) % window_step == 0]
+
+    def rsum(a, r):
+        x0, x1, y0, y1 = r
+        return sum(a[y][x] for y in range(y0, y1) for x in range(x0, x1))
+
+    cands = []
+    for code, regions, Y in configurations(W, H, n):
+        areas = [sum(cw[r[0]:r[1]]) * sum(ch[r[2]:r[3]]) for r in regions]
+        if not any(all(a <= x <= k * a - 1 for x in areas) for a in kept):
+            continue
+        t = max(rsum(Tq, r) for r in regions)
+        q = sum(rsum(S2, r) - (-(-rsum(S1, r) ** 2 // ar)) for r, ar in zip(regions, areas))
+        cands.append((code, regions, t, q))
+    if not cands:
+        return None
+    t_min = min(c[2] for c in cands)
+    feas = [c for c in cands if c[2] * 65536 <= t_min * (65536 + lam_q)]
+    best = min(feas, key=lambda c: (c[3], c[0]))
+    return dict(t_min=t_min, t=best[2], q=best[3], regions=best[1], n_windows=len(kept))

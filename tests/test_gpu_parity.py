@@ -327,3 +327,22 @@ def test_search_lambdas_equals_separate_searches(dec, oracle, spec_name, n, lams
         assert bytes(p) == bytes(one)
         d, _, _ = oracle.decide(plane, times, spec.bit_depth, n, lam)
         assert_partition_equal(p, d, spec.ctu_rows)
+
+
+@pytest.mark.parametrize("spec_name,n,step", [("SPEC_2160P10", 16, 4), ("SPEC_2160P10", 16, 8),
+                                              ("SPEC_1080P10", 8, 2), ("SPEC_480P8", 4, 3)])
+def test_windowed_search_matches_oracle(dec, oracle, spec_name, n, step):
+    from paper_2012_14792_gb300 import trs
+    spec = getattr(synth, spec_name)
+    trs.trs_set_window_step(dec.ctx, step)
+    try:
+        for seed in range(2):
+            plane, times = synth.make_frame(spec, seed=60 + seed)
+            p = _decide(dec, plane, times, spec.bit_depth, n, 0.1)
+            st = oracle.texture(plane, spec.bit_depth)
+            Tq, _ = oracle.time_q(times)
+            d = oracle.search_dp_windows(st, Tq, n, 0.1, window_step=step)
+            assert p.n_windows == d.n_windows
+            assert_partition_equal(p, d, spec.ctu_rows)
+    finally:
+        trs.trs_set_window_step(dec.ctx, 1)

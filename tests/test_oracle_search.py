@@ -234,3 +234,43 @@ def test_random_access_gop_layers():
     order = synth.ra_coding_order(16)
     assert order[:6] == [0, 16, 8, 4, 2, 1] and sorted(order) == list(range(17))
     assert [synth.ra_temporal_layer(p) for p in (0, 16, 8, 4, 12, 2, 6, 1, 15)] == [0, 0, 1, 2, 2, 3, 3, 4, 4]
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_windowed_search_matches_bruteforce(oracle, seed):
+    """The lightweight search (every s-th area window) against an independent
+    brute force over the configurations that fit a kept window."""
+    rng = np.random.default_rng(3000 + seed)
+    C, R = int(rng.integers(2, 4)), int(rng.integers(2, 4))
+    W = (C - 1) * 128 + int(rng.integers(1, 129))
+    H = (R - 1) * 128 + int(rng.integers(1, 129))
+    n = int(rng.integers(2, 6))
+    step = int(rng.integers(1, 4))
+    S1, S2, N, Tq = random_instance(rng, W, H, ["random", "flat", "uniform"][seed % 3])
+    st = stats_from(oracle, W, H, S1, S2, N)
+    lam_q = int(rng.choice([0, 6554, 65536]))
+    d = oracle.search_dp_windows(st, Tq, n, window_step=step, lam_q=lam_q)
+    ref = bruteforce.search_in_windows(W, H, S1.tolist(), S2.tolist(), Tq.astype(np.int64).tolist(), n, lam_q, step)
+    if ref is None:
+        assert d.status == oracle.EINFEASIBLE
+        return
+    assert d.status == oracle.OK
+    assert (d.t_min, d.t, d.q, d.n_windows) == (ref["t_min"], ref["t"], ref["q"], ref["n_windows"])
+    assert sorted(d.regions(R)) == sorted(ref["regions"])
+
+
+def test_windowed_search_step_one_is_exact_and_never_better(oracle):
+    import synth
+    plane, times = synth.make_frame(synth.SPEC_1080P10, seed=8)
+    st = oracle.texture(plane, 10)
+    Tq, _ = oracle.time_q(times)
+    exact = oracle.search_dp(st, Tq, 8, 0.1)
+    one = oracle.search_dp_windows(st, Tq, 8, 0.1, window_step=1)
+    assert (one.t_min, one.t, one.q, one.x_edges, one.band_cuts) == (exact.t_min, exact.t, exact.q, exact.x_edges,
+                                                                       exact.band_cuts)
+    for step in (2, 4, 8):
+        h = oracle.search_dp_windows(st, Tq, 8, 0.1, window_step=step)
+        assert h.status == oracle.OK and h.t_min >= exact.t_min
+        assert h.n_windows == -(-exact.n_windows // step)
+        ev = oracle.evaluate(st, Tq, h.x_edges, h.band_cuts)
+        assert ev["n"] == 8 and 3 * ev["amin"] > ev["amax"] and ev["t"] == h.t and ev["q"] == h.q
