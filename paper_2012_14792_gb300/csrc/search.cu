@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, i
 // the warp's shared-memory table Hraw ((C+1)*(n+1) words of 8 bytes).
 // Returns H[0][n] with kInf where no partition exists; for 64-bit values
 // the table keeps every entry (kSoft for none) for the rebuild.
-template <int STEP, typename VT, int kBatch>
+template <int STEP, typename VT, int kBatch, bool PAIR>
 __device__ uint64_t column_dp(uint64_t *Hraw, const uint64_t *V, const int32_t *slot_row, int C, int n) {
     const int lane = threadIdx.x & 31;
     const int stride = n + 1;
@@ -285,32 +285,40 @@ __device__ uint64_t column_dp(uint64_t *Hraw, const uint64_t *V, const int32_t *
     __syncwarp();
     if (lane == 0) Hs[C * stride] = 0;
     __syncwarp();
-    const int m = lane + 1;
+    // PAIR (n <= 16): lanes 0-15 relax one candidate edge and lanes 16-31 the
+    // next, each half over m = 1..16; otherwise the whole warp takes one edge
+    const int half = PAIR ? lane >> 4 : 0;
+    const int kl = PAIR ? lane & 15 : lane;  // lane kl holds V[kl+1] of its half's edge
+    const int m = kl + 1;
+    constexpr int kPer = PAIR ? 2 : 1;       // edges per step
     for (int x = C - 1; x >= 0; --x) {
         VT acc = soft;
         const int32_t *srow = slot_row + band_index(C, x, x + 1);  // edges x+1.. are consecutive bands
         for (int base = 0; base < C - x; base += 32) {
             const int ncand = min(32, C - x - base);
             const int sl = lane < ncand ? srow[base + lane] : -1;
-            // edges in batches of kBatch: all V-row loads of a batch are in flight together
-            for (int j0 = 0; j0 < ncand; j0 += kBatch) {
+            // edges in batches: all V-row loads of a batch are in flight together
+            for (int j0 = 0; j0 < ncand; j0 += kBatch * kPer) {
                 uint64_t vb[kBatch];
 #pragma unroll
                 for (int u = 0; u < kBatch; ++u) {
-                    const int sj = __shfl_sync(kFull, sl, (j0 + u) & 31);
-                    vb[u] = (j0 + u < ncand && sj >= 0 && lane < n) ? __ldg(V + (size_t)sj * stride + lane + 1)
-                                                                     : kInf;
+                    const int jj = j0 + u * kPer + half;
+                    const int sj = __shfl_sync(kFull, sl, jj & 31);
+                    vb[u] = (jj < ncand && sj >= 0 && kl < n) ? __ldg(V + (size_t)sj * stride + kl + 1) : kInf;
                 }
 #pragma unroll
                 for (int u = 0; u < kBatch; ++u) {
-                    unsigned fin = __ballot_sync(kFull, vb[u] != kInf);
-                    const VT *Hrow = Hs + (size_t)(x + 1 + base + j0 + u) * stride;
+                    const unsigned fin = __ballot_sync(kFull, vb[u] != kInf);
+                    const unsigned mine = PAIR ? (half ? fin >> 16 : fin & 0xffffu) : fin;
+                    unsigned any = PAIR ? ((fin & 0xffffu) | (fin >> 16)) : fin;
+                    const int jj = j0 + u * kPer + half;
+                    const VT *Hrow = Hs + (size_t)(x + 1 + base + (jj < ncand ? jj : 0)) * stride;
                     const VT vv = (VT)vb[u];
-                    while (fin) {
-                        const int k = __ffs(fin);
-                        fin &= fin - 1;
-                        const VT v = __shfl_sync(kFull, vv, k - 1);
-                        if (m >= k && m <= n) {
+                    while (any) {
+                        const int k = __ffs(any);
+                        any &= any - 1;
+                        const VT v = __shfl_sync(kFull, vv, (half << 4) + k - 1);
+                        if (((mine >> (k - 1)) & 1u) && m >= k && m <= n) {
                             const VT h = Hrow[m - k];
                             const VT c = STEP == 1 ? (v > h ? v : h) : VT(v + h);
                             acc = c < acc ? c : acc;
@@ -319,7 +327,11 @@ __device__ uint64_t column_dp(uint64_t *Hraw, const uint64_t *V, const int32_t *
                 }
             }
         }
-        if (m <= n) Hs[x * stride + m] = acc < soft ? acc : soft;
+        if (PAIR) {
+            const VT o = __shfl_xor_sync(kFull, acc, 16);
+            acc = o < acc ? o : acc;
+        }
+        if (half == 0 && m <= n) Hs[x * stride + m] = acc < soft ? acc : soft;
         __syncwarp();
     }
     const VT r = Hs[n];
@@ -360,10 +372,13 @@ __global__ void __launch_bounds__(kMaxWarps * 32) column_kernel(LaunchArgs args,
     }
     const int32_t *slot_row = pl.slot_of + (size_t)w * nb;
     uint64_t res;
+    uint64_t *Hraw = csm + (size_t)wib * h_words;
     if (STEP == 1 && frame_t32(fr))
-        res = column_dp<1, uint32_t, kBatch>(csm + (size_t)wib * h_words, V, slot_row, C, n);
+        res = n <= 16 ? column_dp<1, uint32_t, kBatch, true>(Hraw, V, slot_row, C, n)
+                      : column_dp<1, uint32_t, kBatch, false>(Hraw, V, slot_row, C, n);
     else
-        res = column_dp<STEP, uint64_t, kBatch>(csm + (size_t)wib * h_words, V, slot_row, C, n);
+        res = n <= 16 ? column_dp<STEP, uint64_t, kBatch, true>(Hraw, V, slot_row, C, n)
+                      : column_dp<STEP, uint64_t, kBatch, false>(Hraw, V, slot_row, C, n);
     if (lane == 0) {
         wres[w] = res;
         if (res != kInf) atomicMin(reinterpret_cast<unsigned long long *>(&fr.scal[STEP == 1 ? 0 : 1]), res);
