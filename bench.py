@@ -36,6 +36,7 @@ sys.path.insert(0, ROOT)
 METRIC = "TRS partition decisions/sec at 2160p (batched vs plain); p50/p99 latency; % HBM peak"
 UNIT = "decisions/s"
 NFRAMES = 64
+PARTS = 2  # chunks a captured batch is pipelined in (trs_set_batch_parts)
 N_REGIONS = 16
 LAMBDA = 0.1
 WORKLOAD = "3840x2160p10 moving-blob sequence, 64 frames, n=16, lambda=0.1, k=3"
@@ -60,7 +61,7 @@ def make_inputs(nframes: int, mixed: bool = False):
     return seq, mix
 
 
-def run_mixed(runtime, trs, items, device: int, steps: int, warmup: int):
+def run_mixed(runtime, trs, items, device: int, steps: int, warmup: int, n_parts: int):
     """The 256-frame mixed batch (146 x 480p8, 73 x 1080p10, 37 x 2160p10,
     n from {4, 8, 16}, lambda 0.1) in one graph launch per step."""
     import torch
@@ -74,6 +75,7 @@ def run_mixed(runtime, trs, items, device: int, steps: int, warmup: int):
         keep += [l, t]
         ins.append((l, raw.strides[0], it.spec.width, it.spec.height, it.spec.bit_depth, t, it.n_regions, it.lam))
     tune = dec.autotune(ins)
+    trs.trs_set_batch_parts(dec.ctx, n_parts)
     out = torch.zeros(len(items) * trs.PARTITION_BYTES, dtype=torch.uint8, device=dev)
     for _ in range(warmup):
         dec.batch_decide(ins, out)
@@ -89,11 +91,13 @@ def run_mixed(runtime, trs, items, device: int, steps: int, warmup: int):
     parts = dec.partitions(out, len(items))
     assert all(p.status == 0 for p in parts)
     stage = trs.trs_batch_stage_ms(dec.ctx)
+    sf = trs.trs_batch_stage_frames(dec.ctx)
     dec.close()
     luma_bytes = sum(it.spec.frame_bytes for it in items)
+    half_bytes = sum(it.spec.frame_bytes for it in items[:sf])
     return {"value": len(items) * steps / (ms / 1e3), "unit": UNIT, "frames_per_step": len(items),
             "ms_per_step": ms / steps, "luma_gb_per_step": luma_bytes / 1e9, "stage_ms": stage,
-            "texture_gbs": luma_bytes / (stage["texture"] / 1e3) / 1e9, "autotune": tune}
+            "parts": n_parts, "stage_frames": sf, "texture_gbs": half_bytes / (stage["texture"] / 1e3) / 1e9, "autotune": tune}
 
 
 def max_over_ranks(x: float, dist, device=None) -> float:
@@ -338,6 +342,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-light", action="store_true")
+    ap.add_argument("--parts", type=int, default=PARTS, choices=[1, 2, 3, 4],
+                    help="chunks a captured batch is pipelined in")
     ap.add_argument("--frames", type=int, default=NFRAMES,
                     help="frames per step (a smaller case for profiling; the metric uses 64)")
     args = ap.parse_args()
@@ -390,10 +396,12 @@ def main():
 
     # --- batched, timed --------------------------------------------------
     tune = dec.autotune(ins)  # launch shapes of the search kernels, picked on this workload
+    trs.trs_set_batch_parts(dec.ctx, args.parts)
     for _ in range(args.warmup):
         dec.batch_decide(ins, out)
     sync_all()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = trs.trs_batch_kernels(dec.ctx) * args.steps  # the same graph every step
     with ClockSampler(local) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
@@ -401,11 +409,34 @@ def main():
         ev1.record(stream)
         sync_all()
     ms = ev0.elapsed_time(ev1)
-    stage = trs.trs_batch_stage_ms(dec.ctx)  # CUDA events inside the graph, last timed step
+    stage_overlap = trs.trs_batch_stage_ms(dec.ctx)  # CUDA events inside the graph, last timed step
+    overlap_frames = trs.trs_batch_stage_frames(dec.ctx)  # the first half of the batch
     ms = max_over_ranks(ms, dist, dev)
     value = job_throughput(nfr * args.steps, world, ms / 1e3)
     parts = dec.partitions(out, nfr)
     assert all(p.status == 0 for p in parts), [p.status for p in parts]
+
+    # --- kernels alone: the batch as one launch chain, no second half running
+    # beside it; the per-kernel durations of the roofline, averaged over steps
+    trs.trs_set_batch_parts(dec.ctx, 1)
+    for _ in range(3):
+        dec.batch_decide(ins, out)
+    iso_steps = max(5, args.steps // 10)
+    acc = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(iso_steps):
+        dec.batch_decide(ins, out)
+        torch.cuda.synchronize(dev)
+        for k, v in trs.trs_batch_stage_ms(dec.ctx).items():
+            acc[k] = acc.get(k, 0.0) + v / iso_steps
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    stage, stage_frames = acc, trs.trs_batch_stage_frames(dec.ctx)
+    no_overlap = {"value": nfr * iso_steps / (e0.elapsed_time(e1) / 1e3), "unit": UNIT,
+                  "note": "one launch chain over all frames, a host sync per step"}
+    trs.trs_set_batch_parts(dec.ctx, args.parts)
+    assert bytes(dec.partitions(out, 1)[0]) == bytes(parts[0])
 
     # --- lightweight search: every 4th area window --------------------------
     light = None
@@ -468,7 +499,7 @@ def main():
 
     # --- roofline -----------------------------------------------------------
     hbm, sm_max, src = peaks()
-    tex_bytes = sum(p.numel() for p in pinned)  # each luma sample read once
+    tex_bytes = sum(p.numel() for p in pinned[:stage_frames])  # each luma sample read once
     tex_ms = stage.get("texture", 0.0)
     tex_gbs = tex_bytes / (tex_ms / 1e3) / 1e9 if tex_ms > 0 else 0.0
     row_relax, col_relax = trs.trs_plan_work(3840, 2160, N_REGIONS)
@@ -482,18 +513,18 @@ def main():
                "step1_columns": "column_kernel<1>", "step2_rows": "band_kernel<2>",
                "step2_columns": "column_kernel<2>", "rebuild": "rebuild_kernel", "decode": "finish_kernel"}
     dominant = max(stage, key=stage.get) if stage else "texture"
-    traffic = ncu_traffic(dominant, nfr)
+    traffic = ncu_traffic(dominant, stage_frames)
     if dominant == "texture":
         roof = {"kernel": kernels[dominant], "bound": "hbm", "achieved": tex_gbs, "peak": hbm, "unit": "GB/s",
                 "frac": tex_gbs / hbm, "traffic": traffic, "algorithmic_bytes": tex_bytes, "peak_source": src}
     else:
-        ops = 2.0 * kinds.get(dominant, row_relax + col_relax) * nfr
+        ops = 2.0 * kinds.get(dominant, row_relax + col_relax) * stage_frames
         ach = ops / (stage[dominant] / 1e3) / 1e12
         roof = {"kernel": kernels[dominant], "bound": "alu", "achieved": ach, "peak": alu_peak,
                 "unit": "T INT32 ops/s", "frac": ach / alu_peak, "traffic": traffic, "algorithmic_ops": ops,
                 "peak_source": "measured: trs_alu_peak (32-bit add/min/max chains on every SM)"}
     tex_roof = {"kernel": "texture_kernel", "bound": "hbm", "achieved": tex_gbs, "peak": hbm, "unit": "GB/s",
-                "frac": tex_gbs / hbm, "traffic": ncu_traffic("texture", nfr), "algorithmic_bytes": tex_bytes,
+                "frac": tex_gbs / hbm, "traffic": ncu_traffic("texture", stage_frames), "algorithmic_bytes": tex_bytes,
                 "peak_source": src}
 
     serving = None
@@ -501,7 +532,7 @@ def main():
         serving = run_serving(trs, local)
     mixed_res = None
     if mixed is not None:
-        mixed_res = run_mixed(runtime, trs, mixed, local, max(3, args.steps // 20), args.warmup)
+        mixed_res = run_mixed(runtime, trs, mixed, local, max(3, args.steps // 20), args.warmup, args.parts)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -512,13 +543,15 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
                 "config": {"workload": WORKLOAD if nfr == NFRAMES else f"{WORKLOAD} (first {nfr} frames)",
-                           "frames_per_step": nfr, "form": "batched, CUDA graph",
-                           "l2": f"inputs {tex_bytes / 1e9:.2f} GB per step > L2, no flush"},
+                           "frames_per_step": nfr, "form": f"batched, CUDA graph, {args.parts} pipelined chunks",
+                           "l2": f"inputs {nfr * 16588800 / 1e9:.2f} GB per step > L2, no flush"},
                 "plain": {"value": plain_value, "unit": UNIT, "form": "one frame per launch chain"},
-                "stage_ms": stage, "autotune": tune, "mixed_256": mixed_res, "lightweight": light,
+                "stage_ms": stage, "stage_frames": stage_frames,
+                "stage_ms_overlapped": stage_overlap, "stage_frames_overlapped": overlap_frames,
+                "no_overlap": no_overlap, "autotune": tune, "mixed_256": mixed_res, "lightweight": light,
                 "serving": serving,
                 "clocks": clk.summary(), "e2e": e2e,
-                "gpu_launches": 8 * args.steps, "roofline": roof, "roofline_texture": tex_roof,
+                "gpu_launches": launches, "roofline": roof, "roofline_texture": tex_roof,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     dec.close()

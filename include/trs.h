@@ -269,9 +269,10 @@ int trs_search_noalloc(const void *tables_dev, int width, int height, int n_regi
 /* --- batched form -------------------------------------------------------- */
 
 /* Decides nframes frames (1..opts.max_batch) of any sizes, depths, n and
- * lambda with one launch of each kernel over all of them; out_dev holds
- * nframes partitions.  The launch sequence is captured in a CUDA graph the
- * first time a batch of a given composition is seen and replayed after. */
+ * lambda with one launch of each kernel over all of them (over each chunk
+ * of them: see trs_set_batch_parts); out_dev holds nframes partitions.  The launch sequence is captured in a
+ * CUDA graph the first time a batch of a given composition is seen and
+ * replayed after. */
 int trs_batch_decide(trs_ctx *ctx, const trs_frame_desc *frames_host, int nframes, trs_partition *out_dev,
                      void *stream);
 
@@ -315,6 +316,23 @@ int trs_set_window_step(trs_ctx *ctx, int step);
  * col_warps in {2, 4, 8}, col_batch in {4, 8}; TRS_EINVAL otherwise.
  * Drops captured batch graphs. */
 int trs_set_tune(trs_ctx *ctx, int band_warps, int col_warps, int col_batch);
+
+/* Frames covered by the stage times of trs_batch_stage_ms: the first chunk
+ * of a captured batch (see trs_set_batch_parts), or the whole batch of a
+ * call that runs as one launch chain.  0 before the first batched call. */
+int trs_batch_stage_frames(const trs_ctx *ctx);
+
+/* Kernels launched by the most recent batched call (8 per chunk; 0 before
+ * the first call). */
+int trs_batch_kernels(const trs_ctx *ctx);
+
+/* parts in 1..4 (default 2): a captured batch of nframes frames runs as
+ * min(parts, nframes / 4) chunks (at least one) of consecutive frames,
+ * pipelined on two streams so that each chunk's texture map (bound by HBM
+ * bandwidth) overlaps the previous chunk's search (bound by the ALUs).
+ * Decisions are the same bytes for every value; each chunking is captured
+ * as its own graph.  TRS_EINVAL outside 1..4. */
+int trs_set_batch_parts(trs_ctx *ctx, int parts);
 
 /* Device time in milliseconds of each stage of the most recent batched call
  * (texture, tables, step-1 rows, step-1 columns, step-2 rows, step-2

@@ -196,6 +196,10 @@ int trs_create(trs_ctx **out, const trs_opts *o) {
     s = s ? s : dev_alloc(c->time_stage, cells * 4, &c->total);
     if (s == TRS_OK && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) s = TRS_ECUDA;
     if (s == TRS_OK && cudaEventCreateWithFlags(&c->copied, cudaEventDisableTiming) != cudaSuccess) s = TRS_ECUDA;
+    if (s == TRS_OK && cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking) != cudaSuccess) s = TRS_ECUDA;
+    for (int i = 0; i < kMaxParts && s == TRS_OK; ++i)
+        if (cudaEventCreateWithFlags(&c->tex_done[i], cudaEventDisableTiming) != cudaSuccess) s = TRS_ECUDA;
+    if (s == TRS_OK && cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess) s = TRS_ECUDA;
     for (int i = 0; i <= trs_ctx::kStages && s == TRS_OK; ++i)
         if (cudaEventCreate(&c->stage[i]) != cudaSuccess) s = TRS_ECUDA;
     if (s != TRS_OK) {
@@ -221,6 +225,10 @@ int trs_destroy(trs_ctx *c) {
     if (c->staging) cudaFreeHost(c->staging);
     if (c->cap) cudaStreamDestroy(c->cap);
     if (c->copied) cudaEventDestroy(c->copied);
+    if (c->cap2) cudaStreamDestroy(c->cap2);
+    for (int i = 0; i < kMaxParts; ++i)
+        if (c->tex_done[i]) cudaEventDestroy(c->tex_done[i]);
+    if (c->join) cudaEventDestroy(c->join);
     for (int i = 0; i <= trs_ctx::kStages; ++i)
         if (c->stage[i]) cudaEventDestroy(c->stage[i]);
     delete c;
@@ -348,7 +356,10 @@ int trs_search_lambdas(trs_ctx *ctx, const void *tables, int W, int H, int n, co
     const size_t per = align256(pe->scr.bytes);
     TRS_TRY(dev_alloc(ctx->scratch, per * nl, &ctx->total));
     const size_t blob = batch_blob_bytes(nl);
-    TRS_TRY(dev_alloc(ctx->desc, blob * 2, &ctx->total));
+    if (ctx->desc.n < blob) {  // captured batches hold the old descriptor address
+        drop_graphs(ctx);
+        TRS_TRY(dev_alloc(ctx->desc, blob * 2, &ctx->total));
+    }
     if (ctx->staging_n < blob) {
         TRS_CK(cudaEventSynchronize(ctx->copied));
         if (ctx->staging) cudaFreeHost(ctx->staging);
@@ -486,7 +497,9 @@ int batch_run(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partition *out
         drop_graphs(ctx);
         TRS_TRY(dev_alloc(ctx->arena, off + off / 4, &ctx->total));
     }
-    const size_t blob = batch_blob_bytes(nf);
+    // a graph batch in chunks keeps one descriptor blob per chunk; each adds
+    // at most 6 x 256 bytes of alignment and one prefix entry per table
+    const size_t blob = batch_blob_bytes(nf) + (size_t)kMaxParts * 1600;
     if (ctx->desc.n < blob) {
         drop_graphs(ctx);
         TRS_TRY(dev_alloc(ctx->desc, blob * 2, &ctx->total));
@@ -531,21 +544,61 @@ int batch_run(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partition *out
         f.out = out + i;
         hf[i] = f;
     }
-    BatchLaunch bl;
-    batch_describe(bl, hb, (uint8_t *)ctx->desc.p, nf, pe.data(), (uint32_t *)(ab + flags_off),
-                   (uint64_t *)(ab + scal_off));
-    bl.tune = ctx->tune;
+    uint32_t *flags = (uint32_t *)(ab + flags_off);
+    uint64_t *scal = (uint64_t *)(ab + scal_off);
     if (!use_graph) {
+        BatchLaunch bl;
+        batch_describe(bl, hb, (uint8_t *)ctx->desc.p, nf, pe.data(), flags, scal);
+        bl.tune = ctx->tune;
         cudaError_t e = batch_enqueue(bl, stream, ctx->copied, ctx->stage);
         if (e != cudaSuccess) return cuda_fail(e, "batch launch");
         ctx->stage_valid = true;
+        ctx->stage_frames = nf;
+        ctx->last_kernels = kKernelsPerBatch;
         return TRS_OK;
+    }
+    // Graph batches run as P chunks of at least kChunkMin frames each, software
+    // pipelined on two streams (chunk c on stream c % 2): chunk c's texture
+    // kernel (bound by HBM) starts once chunk c-1's has finished and runs
+    // beside chunk c-1's tables and search (bound by the ALUs).  Stage events
+    // time chunk 0.
+    const int parts = std::max(1, std::min(ctx->parts, nf / kChunkMin));
+    key.push_back(parts);
+    BatchLaunch bl[kMaxParts];
+    int first[kMaxParts + 1];
+    size_t off_c[kMaxParts + 1];
+    first[0] = 0;
+    off_c[0] = 0;
+    for (int c = 0; c < parts; ++c) {
+        first[c + 1] = (int)((int64_t)nf * (c + 1) / parts);
+        off_c[c + 1] = off_c[c] + batch_blob_bytes(first[c + 1] - first[c]);
+    }
+    // each chunk's descriptors at the start of its own blob; the last chunk
+    // first, so that no move overwrites descriptors not yet moved
+    for (int c = parts - 1; c > 0; --c)
+        std::memmove(hb + off_c[c], hb + (size_t)first[c] * sizeof(DevFrame),
+                     (size_t)(first[c + 1] - first[c]) * sizeof(DevFrame));
+    for (int c = 0; c < parts; ++c) {
+        batch_describe(bl[c], hb + off_c[c], (uint8_t *)ctx->desc.p + off_c[c], first[c + 1] - first[c],
+                       pe.data() + first[c], flags + first[c], scal + 4 * first[c]);
+        bl[c].tune = ctx->tune;
     }
     BatchGraph &g = ctx->graphs[key];
     if (!g.exec) {
-        cudaStream_t cs = ctx->cap;
+        cudaStream_t cs = ctx->cap, st[2] = {ctx->cap, ctx->cap2};
         TRS_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = batch_enqueue(bl, cs, ctx->copied, ctx->stage);
+        cudaError_t e = cudaMemcpyAsync(bl[0].db, bl[0].hb, off_c[parts], cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = record_event(ctx->copied, cs);
+        for (int c = 0; c < parts && e == cudaSuccess; ++c) {
+            if (c > 0) e = cudaStreamWaitEvent(st[c % 2], ctx->tex_done[c - 1], 0);
+            if (e == cudaSuccess)
+                e = batch_enqueue_work(bl[c], st[c % 2], c == 0 ? ctx->stage : nullptr,
+                                       c + 1 < parts ? ctx->tex_done[c] : nullptr);
+        }
+        if (parts > 1) {
+            if (e == cudaSuccess) e = cudaEventRecord(ctx->join, ctx->cap2);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->join, 0);
+        }
         cudaGraph_t graph = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
         if (e == cudaSuccess) e = e2;
@@ -559,6 +612,8 @@ int batch_run(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partition *out
     }
     TRS_CK(cudaGraphLaunch(g.exec, stream));
     ctx->stage_valid = true;
+    ctx->stage_frames = first[1];
+    ctx->last_kernels = parts * kKernelsPerBatch;
     return TRS_OK;
 }
 
@@ -613,7 +668,7 @@ void batch_describe(BatchLaunch &bl, uint8_t *hb, uint8_t *db, int nf, PlanEntry
     bl.windows = pw[nf];
 }
 
-cudaError_t batch_enqueue(const BatchLaunch &bl, cudaStream_t cs, cudaEvent_t copied, cudaEvent_t *stage) {
+cudaError_t batch_enqueue_work(const BatchLaunch &bl, cudaStream_t cs, cudaEvent_t *stage, cudaEvent_t after_texture) {
     LaunchArgs a{};
     a.frames = (const DevFrame *)bl.db;
     a.nframes = bl.nf;
@@ -627,17 +682,23 @@ cudaError_t batch_enqueue(const BatchLaunch &bl, cudaStream_t cs, cudaEvent_t co
         if (events && e == cudaSuccess) e = record_event(stage[i], cs);
         return e;
     };
-    cudaError_t e = cudaMemcpyAsync(bl.db, bl.hb, bl.blob, cudaMemcpyHostToDevice, cs);
-    if (e == cudaSuccess && copied) e = record_event(copied, cs);
-    if (e == cudaSuccess) e = cudaMemsetAsync(bl.flags_dev, 0, (size_t)bl.nf * 4, cs);
+    cudaError_t e = cudaMemsetAsync(bl.flags_dev, 0, (size_t)bl.nf * 4, cs);
     e = mark(0, e);
     if (e == cudaSuccess) e = (cudaError_t)launch_texture(a, bl.ctus, cs);
     e = mark(1, e);
+    if (e == cudaSuccess && after_texture) e = cudaEventRecord(after_texture, cs);
     if (e == cudaSuccess) e = (cudaError_t)launch_tables(a, bl.groups, bl.maxC, bl.maxR, cs);
     e = mark(2, e);
     if (e == cudaSuccess)
         e = (cudaError_t)launch_search(a, bl.bands, bl.windows, bl.maxC, bl.maxR, bl.maxN, bl.scal_dev,
                                        (size_t)bl.nf * 4, cs, events ? stage + 3 : nullptr, &bl.tune);
+    return e;
+}
+
+cudaError_t batch_enqueue(const BatchLaunch &bl, cudaStream_t cs, cudaEvent_t copied, cudaEvent_t *stage) {
+    cudaError_t e = cudaMemcpyAsync(bl.db, bl.hb, bl.blob, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess && copied) e = record_event(copied, cs);
+    if (e == cudaSuccess) e = batch_enqueue_work(bl, cs, stage, nullptr);
     return e;
 }
 
@@ -720,6 +781,16 @@ int trs_set_tune(trs_ctx *ctx, int band_warps, int col_warps, int col_batch) {
     ctx->tune.col_warps = col_warps;
     ctx->tune.col_batch = col_batch;
     drop_graphs(ctx);
+    return TRS_OK;
+}
+
+int trs_batch_stage_frames(const trs_ctx *ctx) { return ctx && ctx->stage_valid ? ctx->stage_frames : 0; }
+
+int trs_batch_kernels(const trs_ctx *ctx) { return ctx && ctx->stage_valid ? ctx->last_kernels : 0; }
+
+int trs_set_batch_parts(trs_ctx *ctx, int parts) {
+    if (!ctx || parts < 1 || parts > kMaxParts) return TRS_EINVAL;
+    ctx->parts = parts;
     return TRS_OK;
 }
 

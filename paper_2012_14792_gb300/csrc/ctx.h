@@ -44,6 +44,10 @@ struct BatchGraph {
     size_t staged_bytes = 0;
 };
 
+constexpr int kKernelsPerBatch = 8;  // texture, tables, 2 x (rows, columns), rebuild, finish
+constexpr int kMaxParts = 4;         // most chunks a captured batch is pipelined in
+constexpr int kChunkMin = 4;         // fewest frames in a chunk
+
 }  // namespace trs
 
 struct trs_ctx {
@@ -59,11 +63,15 @@ struct trs_ctx {
     trs::DevBuf arena, desc;
     void *staging = nullptr;  // pinned host copy of the descriptor blob
     size_t staging_n = 0;
-    cudaStream_t cap = nullptr;
-    cudaEvent_t copied = nullptr;
+    cudaStream_t cap = nullptr, cap2 = nullptr;  // capture streams (second: the batch's second half)
+    cudaEvent_t copied = nullptr, join = nullptr;
+    cudaEvent_t tex_done[trs::kMaxParts] = {};  // chunk c's texture kernel has run
     static constexpr int kStages = 8;
     cudaEvent_t stage[kStages + 1] = {};  // timing events recorded inside batch graphs
     bool stage_valid = false;
+    int stage_frames = 0;  // frames the stage events covered
+    int last_kernels = 0;  // kernels the most recent batched call launched
+    int parts = 2;         // chunks of a captured batch (trs_set_batch_parts)
     // host-buffer batches: device staging of planes, times and partitions
     trs::DevBuf hb_luma, hb_time, hb_out;
     trs::SearchTune tune;  // launch shapes of the search kernels (trs_autotune)
@@ -102,6 +110,10 @@ void batch_describe(BatchLaunch &bl, uint8_t *hb, uint8_t *db, int nf, PlanEntry
 // Enqueues the descriptor copy (then records `copied`), the flag reset and
 // every kernel of the hot path on cs; stage events (9) when stage != nullptr.
 cudaError_t batch_enqueue(const BatchLaunch &bl, cudaStream_t cs, cudaEvent_t copied, cudaEvent_t *stage);
+// The same without the descriptor copy; records after_texture (if given)
+// once the texture kernel is enqueued.
+cudaError_t batch_enqueue_work(const BatchLaunch &bl, cudaStream_t cs, cudaEvent_t *stage, cudaEvent_t after_texture);
+
 
 // Decides nf frames described by device pointers in one launch of each
 // kernel on `stream`, through a cached CUDA graph or by direct launches.

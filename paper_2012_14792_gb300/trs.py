@@ -134,6 +134,9 @@ def _load():
         "trs_batch_decide": ([vp, ct.POINTER(trs_frame_desc), i, vp, vp], i),
         "trs_batch_decide_host": ([vp, ct.POINTER(trs_frame_desc), i, ct.POINTER(trs_partition), vp], i),
         "trs_batch_stage_ms": ([vp, ct.POINTER(ct.c_float), i], i),
+        "trs_batch_stage_frames": ([vp], i),
+        "trs_batch_kernels": ([vp], i),
+        "trs_set_batch_parts": ([vp, i], i),
         "trs_autotune": ([vp, ct.POINTER(trs_frame_desc), i, ct.POINTER(trs_tune_report), vp], i),
         "trs_set_tune": ([vp, i, i, i], i),
         "trs_set_window_step": ([vp, i], i),
@@ -303,6 +306,18 @@ def trs_batch_decide_host(ctx, descs: list[trs_frame_desc], stream=None) -> list
 
 
 STAGES = ("texture", "tables", "step1_rows", "step1_columns", "step2_rows", "step2_columns", "rebuild", "decode")
+
+
+def trs_batch_stage_frames(ctx) -> int:
+    return _lib.trs_batch_stage_frames(ctx)
+
+
+def trs_batch_kernels(ctx) -> int:
+    return _lib.trs_batch_kernels(ctx)
+
+
+def trs_set_batch_parts(ctx, parts: int) -> None:
+    _check(_lib.trs_set_batch_parts(ctx, parts), "trs_set_batch_parts")
 
 
 def trs_batch_stage_ms(ctx) -> dict:

@@ -272,6 +272,53 @@ def test_batch_graph_replay_with_new_frames(dec, oracle):
             assert_partition_equal(p, d, it.spec.ctu_rows)
 
 
+@pytest.mark.parametrize("nf", [1, 7, 8, 9, 33])
+def test_batch_chunks_equal_alone(dec, nf):
+    """Captured batches run as pipelined chunks on two streams; every
+    partition equals the frame decided alone for every chunking, and the
+    stage times cover the first chunk."""
+    from paper_2012_14792_gb300 import trs
+    items = synth.mixed_batch(256, seed=6)[:nf]
+    ins, keep = _batch_inputs(items)
+    alone = [bytes(dec.partitions(dec.decide(ptr, pitch, W, H, bd, tt, n, lam))[0])
+             for (ptr, pitch, W, H, bd, tt, n, lam) in ins]
+    try:
+        for parts in (2, 1, 3, 4):
+            trs.trs_set_batch_parts(dec.ctx, parts)
+            P = max(1, min(parts, nf // 4))
+            for _ in range(2):  # capture, then replay
+                ps = dec.partitions(dec.batch_decide(ins), nf)
+                assert trs.trs_batch_stage_frames(dec.ctx) == nf // P
+                assert trs.trs_batch_kernels(dec.ctx) == 8 * P
+                assert [bytes(p) for p in ps] == alone, parts
+    finally:
+        trs.trs_set_batch_parts(dec.ctx, 2)
+    for bad in (0, 5):
+        with pytest.raises(trs.TrsError):
+            trs.trs_set_batch_parts(dec.ctx, bad)
+
+
+def test_batch_replay_after_descriptor_growth(dec):
+    """A multi-lambda search that needs a larger descriptor buffer drops the
+    captured batches that pointed at the old one; replays stay correct."""
+    from paper_2012_14792_gb300 import runtime
+    fresh = runtime.Decider(max_width=3840, max_height=2160, max_regions=32, max_batch=4)
+    try:
+        items = synth.mixed_batch(256, seed=7)[:1]
+        ins, keep = _batch_inputs(items)
+        ref = bytes(dec.batch_decide(ins).cpu().numpy())
+        assert bytes(fresh.batch_decide(ins).cpu().numpy()) == ref
+        it = items[0]
+        W, H = it.spec.width, it.spec.height
+        _, st, _keep = _texture(fresh, it.plane, it.spec.bit_depth)
+        tab = fresh.tables_buffer(W, H)
+        fresh.region_tables(st, torch.from_numpy(it.times).cuda(), W, H, tab)
+        fresh.search_lambdas(tab, W, H, it.n_regions, [0.0, 0.05, 0.1, 0.2, 0.3, 0.5, 1.0, 2.0])
+        assert bytes(fresh.batch_decide(ins).cpu().numpy()) == ref
+    finally:
+        fresh.close()
+
+
 @pytest.mark.parametrize("scale,flag", [(1.0, 1), (2000.0, 0)])
 def test_step1_value_width_paths(dec, oracle, scale, flag):
     """Frames whose total Q16 time is below 2^31 run step 1 on 32-bit values,
