@@ -17,8 +17,8 @@
 //  band_kernel<STEP>    one warp per (frame, tile column), running all of
 //                       the column's items: lanes are the start row y of
 //                       the remaining rows [y, R); for k = 1..kmax it
-//                       relaxes every admissible slice height d, pulling
-//                       G_{k-1}[y+d] from lane y+d with a shuffle.  Step 1
+//                       relaxes every admissible slice height d, reading
+//                       G_{k-1}[y+d] from the warp's shared-memory table.  Step 1
 //                       combines with max (Eq. 1), step 2 with + (Eq. 2) and
 //                       drops slices whose time exceeds the Eq. 4 bound.
 //  column_kernel<STEP>  one warp per (frame, window): DP over tile-column
@@ -175,116 +175,128 @@ __device__ __forceinline__ uint64_t item_rows(const VT *sv, VT *G, int nd, int d
 }
 
 // Two items of one tile column per warp, for frames of at most 17 CTU rows
-// and n <= 16 (every workload of the paper): half h = lane / 16 runs item
-// i + h with its lane l on start row y = l + 1.  Row 0 is never a source of
-// the recursion (sources are rows y + d > y), only the output V[k] = G_k[0],
-// so each half computes it per k as a 16-lane min-reduction over the
-// slice heights.  Loops run to the larger of the two items' bounds (extra
-// heights hold the saturating infinity), so both halves stay in step.
+// and n <= 16 (every workload of the paper): half h = lane / 16 runs one
+// item with its lane l on start row y = l.  Row 16, the last row of a
+// 17-row frame, needs no lane: a slice starting there ends at the frame's
+// bottom, so G_1[16] is that slice's value and G_k[16] (k >= 2) is empty.
+// G_{k-1} and G_k alternate between two 64-word buffers per half, so one
+// warp barrier per k suffices.  Loops run to the larger of the two items'
+// bounds (extra heights hold the saturating infinity), so both halves stay
+// in step.  Half 0 runs item ia, half 1 item ib (none if ib is negative).
 template <int STEP, typename VT>
-__device__ void items_paired(const DevFrame &fr, const DevPlan &pl, int i0, int i1, uint64_t *Vall,
-                             const uint64_t *stage, VT *sv, VT *G, VT *r0, const uint32_t *tokbuf, uint64_t thr) {
-    const int lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15, y = l + 1;
+__device__ void item_pair(const DevFrame &fr, const DevPlan &pl, int ia, int ib, uint64_t *Vall,
+                          const uint64_t *stage, VT *sv, VT *G, const uint32_t *tokbuf) {
+    const int lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15, y = l;
     const int n = pl.n, R = fr.R, H = fr.H;
     constexpr VT soft = Soft<VT>::v;
     const uint32_t ytop = line_px(y, H);
     const uint32_t tok_y = STEP == 2 ? tokbuf[y] : ~0u;
-    const uint32_t tok_0 = STEP == 2 ? tokbuf[0] : ~0u;
-    VT *Gh = G + h * 64;
-    for (int ii = i0; ii < i1; ii += 2) {
-        const int mi = ii + h;
-        const bool have = mi < i1;
-        PlanItem it{0, 0, 1u, 0u, 0, -1};
-        if (have) it = pl.items[mi];
-        bool live = have;
-        if (STEP == 2) {
-            // an item only matters if one of its windows still meets Eq. 4
-            const PlanItem a = pl.items[ii];
-            bool na = false, nb = false;
-            for (int w = a.w_first + lane; w <= a.w_last; w += 32) na |= fr.wres1[w] <= thr;
-            if (ii + 1 < i1) {
-                const PlanItem b = pl.items[ii + 1];
-                for (int w = b.w_first + lane; w <= b.w_last; w += 32) nb |= fr.wres1[w] <= thr;
-            }
-            na = __any_sync(kFull, na);
-            nb = __any_sync(kFull, nb);
-            live = have && (h ? nb : na);
-        }
-        const int kmax = live ? it.kmax : 0;
-        const int dmin = max(1, (int)((it.hlo + kCtu - 1) / kCtu));
-        const int nd = live ? min(R, (int)(it.hhi / kCtu) + 1) - dmin + 1 : 0;
-        const int ndm = max(nd, __shfl_xor_sync(kFull, nd, 16));
-        const int kmm = max(kmax, __shfl_xor_sync(kFull, kmax, 16));
+    VT *Ga = G + h * 128, *Gb = Ga + 64;  // G_{k-1} in Ga, G_k into Gb, then swapped
+    const int mi = h ? ib : ia;
+    const bool have = mi >= 0;
+    PlanItem it{0, 0, 1u, 0u, 0, -1};
+    if (have) it = pl.items[mi];
+    const int kmax = have ? it.kmax : 0;
+    const int dmin = max(1, (int)((it.hlo + kCtu - 1) / kCtu));
+    const int nd = have ? min(R, (int)(it.hhi / kCtu) + 1) - dmin + 1 : 0;
+    const int ndm = max(nd, __shfl_xor_sync(kFull, nd, 16));
+    const int kmm = max(kmax, __shfl_xor_sync(kFull, kmax, 16));
+    __syncwarp();  // every lane is done with the previous pair's tables
+    for (int i = 0; i < ndm; ++i) {
+        const int d = dmin + i, y1 = y + d;
+        const uint32_t hh = line_px(y1, H) - ytop;
+        const bool ok = i < nd && y < R && y1 <= R && hh >= it.hlo && hh <= it.hhi &&
+                        (STEP == 1 || ((tok_y >> (d - 1)) & 1u));
+        sv[i * 32 + lane] = ok ? (VT)stage[(d - 1) * 32 + y] : soft;
+    }
+    // G_1[16]: the one-row slice [16, 17) of a 17-row frame
+    const uint32_t h16 = (uint32_t)H - line_px(16, H);
+    const bool ok16 = have && R == 17 && dmin == 1 && h16 >= it.hlo && h16 <= it.hhi &&
+                      (STEP == 1 || (tokbuf[16] & 1u));
+    const VT g16 = ok16 ? (VT)stage[16] : soft;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int e = l + 16 * q;
+        Ga[e] = e == R ? VT(0) : soft;  // G_0: only the empty remainder holds zero slices
+        Gb[e] = soft;
+    }
+    __syncwarp();
+    uint64_t vreg = kInf;
+    const VT *sp = sv + lane;
+    for (int k = 1; k <= kmm; ++k) {
+        const VT *gp = Ga + y + dmin;
+        VT best = soft;
+#pragma unroll 4
         for (int i = 0; i < ndm; ++i) {
-            const int d = dmin + i, y1 = y + d;
-            const uint32_t hh = line_px(y1, H) - ytop;
-            const bool ok = i < nd && y < R && y1 <= R && hh >= it.hlo && hh <= it.hhi &&
-                            (STEP == 1 || ((tok_y >> (d - 1)) & 1u));
-            sv[i * 32 + lane] = ok ? (VT)stage[(d - 1) * 32 + y] : soft;
+            const VT prev = gp[i], val = sp[i * 32];
+            const VT c = STEP == 1 ? (prev > val ? prev : val) : VT(prev + val);
+            best = c < best ? c : best;
         }
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {  // row 0: lane l takes heights l and l + 16
-            const int j = l + 16 * q, d = dmin + j;
-            const uint32_t hh = line_px(d, H);
-            const bool ok = j < nd && d <= R && hh >= it.hlo && hh <= it.hhi &&
-                            (STEP == 1 || ((tok_0 >> (d - 1)) & 1u));
-            r0[h * 32 + j] = ok ? (VT)stage[(d - 1) * 32] : soft;
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int e = l + 16 * q;
-            Gh[e] = e == R ? VT(0) : soft;  // G_0: only the empty remainder holds zero slices
+        if (k <= kmax) {  // a half past its kmax runs on, unread
+            Gb[y] = best < soft ? best : soft;
+            if (l == 0) {
+                Gb[16] = k == 1 ? g16 : soft;
+                Gb[17] = soft;  // G_k[R] of a 17-row frame, k >= 1
+            }
         }
         __syncwarp();
-        uint64_t vreg = kInf;
-        const VT *gp = Gh + y + dmin;
-        const VT *sp = sv + lane;
-        for (int k = 1; k <= kmm; ++k) {
-            VT best = soft;
-#pragma unroll 4
-            for (int i = 0; i < ndm; ++i) {
-                const VT prev = gp[i], val = sp[i * 32];
-                const VT c = STEP == 1 ? (prev > val ? prev : val) : VT(prev + val);
-                best = c < best ? c : best;
-            }
-            VT t = soft;
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int j = l + 16 * q;
-                if (j < ndm) {
-                    const VT prev = Gh[dmin + j], val = r0[h * 32 + j];
-                    const VT c = STEP == 1 ? (prev > val ? prev : val) : VT(prev + val);
-                    t = c < t ? c : t;
-                }
-            }
-#pragma unroll
-            for (int o = 8; o > 0; o >>= 1) {
-                const VT u = __shfl_xor_sync(kFull, t, o);
-                t = u < t ? u : t;
-            }
-            __syncwarp();
-            if (k <= kmax) {
-                Gh[y] = best < soft ? best : soft;
-                if (l == 0) Gh[R] = soft;  // G_k[R] for k >= 1 (no lane holds row 17)
-                if (l == k - 1) vreg = t >= soft ? kInf : (uint64_t)t;
-            }
-            __syncwarp();
+        if (l == k - 1 && k <= kmax) {
+            const VT g0 = Gb[0];
+            vreg = g0 >= soft ? kInf : (uint64_t)g0;
         }
-        if (have) {
-            uint64_t *V = Vall + (size_t)mi * (n + 1);
-            if (l == 0) V[0] = kInf;
-            if (l < n) V[l + 1] = vreg;
+        VT *t = Ga;
+        Ga = Gb;
+        Gb = t;
+    }
+    if (have) {
+        uint64_t *V = Vall + (size_t)mi * (n + 1);
+        if (l == 0) V[0] = kInf;
+        if (l < n) V[l + 1] = vreg;
+    }
+}
+
+// The items of one tile column two at a time (see item_pair).  Step 2 runs
+// only the items with a window whose step-1 best time meets Eq. 4 (no other
+// window is read again) and pairs them up after that filter.
+template <int STEP, typename VT>
+__device__ void items_paired(const DevFrame &fr, const DevPlan &pl, int i0, int i1, uint64_t *Vall,
+                             const uint64_t *stage, VT *sv, VT *G, const uint32_t *tokbuf, uint64_t thr) {
+    const int lane = threadIdx.x & 31;
+    if (STEP == 1) {
+        for (int ii = i0; ii < i1; ii += 2)
+            item_pair<STEP, VT>(fr, pl, ii, ii + 1 < i1 ? ii + 1 : -1, Vall, stage, sv, G, tokbuf);
+        return;
+    }
+    int held = -1;  // a live item waiting for its partner
+    for (int base = i0; base < i1; base += 32) {
+        bool live = false;
+        if (base + lane < i1) {
+            const PlanItem it = pl.items[base + lane];
+            for (int w = it.w_first; w <= it.w_last && !live; ++w) live = fr.wres1[w] <= thr;
+        }
+        unsigned m = __ballot_sync(kFull, live);
+        while (m) {
+            const int i = base + __ffs(m) - 1;
+            m &= m - 1;
+            if (held < 0) {
+                held = i;
+            } else {
+                item_pair<STEP, VT>(fr, pl, held, i, Vall, stage, sv, G, tokbuf);
+                held = -1;
+            }
         }
     }
+    if (held >= 0) item_pair<STEP, VT>(fr, pl, held, -1, Vall, stage, sv, G, tokbuf);
 }
 
 // Row DPs, one warp per (frame, tile column): the column's slice values
 // for every height d are staged once in shared memory (stage[(d-1)*32 + y];
 // step 2 also keeps, per lane, a bit per height for the Eq. 4 bound on the
 // slice time), then every item of the column runs from there: its
-// admissible heights become a per-lane bit mask and the k loop only
-// shuffles G_{k-1}[y+d] from lane y+d and relaxes.  V[k] = G_k[0] is
+// admitted slice values are staged per lane and the k loop only reads
+// G_{k-1}[y+d] from shared memory and relaxes.  V[k] = G_k[0] is
 // collected in lane k and stored with one coalesced write per item.
+constexpr int kBandTail = 272;  // per warp after the two staging areas: G tables and tok bits
 template <int STEP>
 __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, int total, int stage_words) {
     extern __shared__ uint64_t bsm[];
@@ -312,9 +324,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, i
     const uint64_t *RQ = reinterpret_cast<const uint64_t *>(fr.tables + off.rect_q) + base;
     // per warp: the column's slice values by height, one item's admitted
     // values, and the 64-word G table
-    uint64_t *stage = bsm + (size_t)wib * (2 * stage_words + 256);
+    uint64_t *stage = bsm + (size_t)wib * (2 * stage_words + kBandTail);
     uint64_t *itm = stage + stage_words;
-    uint64_t *gbuf = itm + stage_words;  // 256 words: G tables, row-0 values, tok per row
+    uint64_t *gbuf = itm + stage_words;  // G tables (256 words), then tok per row (16 words)
     uint32_t tok = 0;  // step 2: bit d-1 set if the slice [lane, lane+d) meets the Eq. 4 bound
 #pragma unroll 4
     for (int d = 1; d <= R; ++d) {
@@ -328,16 +340,15 @@ __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, i
             stage[(d - 1) * 32 + lane] = tv;
         }
     }
-    uint32_t *tokbuf = reinterpret_cast<uint32_t *>(gbuf + 224);
+    uint32_t *tokbuf = reinterpret_cast<uint32_t *>(gbuf + 256);
     tokbuf[lane] = tok;
     __syncwarp();
     if (R <= 17 && n <= 16) {
         if (STEP == 1 && t32)
             items_paired<1, uint32_t>(fr, pl, i0, i1, Vall, stage, reinterpret_cast<uint32_t *>(itm),
-                                      reinterpret_cast<uint32_t *>(gbuf), reinterpret_cast<uint32_t *>(gbuf) + 128,
-                                      tokbuf, thr);
+                                      reinterpret_cast<uint32_t *>(gbuf), tokbuf, thr);
         else
-            items_paired<STEP, uint64_t>(fr, pl, i0, i1, Vall, stage, itm, gbuf, gbuf + 128, tokbuf, thr);
+            items_paired<STEP, uint64_t>(fr, pl, i0, i1, Vall, stage, itm, gbuf, tokbuf, thr);
         return;
     }
     const uint32_t ytop = line_px(lane, H);
@@ -766,7 +777,7 @@ __global__ void __launch_bounds__(32) finish_kernel(LaunchArgs args) {
 // Raises the dynamic shared-memory limit of the search kernels to what the
 // largest shapes need (once per device, before any capture).
 int prepare_search_kernels() {
-    const int band_smem = kMaxWarps * (2 * kMaxR * 32 + 256) * (int)sizeof(uint64_t);
+    const int band_smem = kMaxWarps * (2 * kMaxR * 32 + kBandTail) * (int)sizeof(uint64_t);
     const int col_smem = kMaxWarps * (kMaxC + 1) * (kMaxN + 1) * (int)sizeof(uint64_t);
     const int rb_smem = ((kMaxN + 1) * 32 + kMaxR * 32) * (int)sizeof(uint64_t);
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
@@ -790,7 +801,7 @@ int launch_search(const LaunchArgs &a, int total_bands, int total_windows, int m
     if (e != cudaSuccess) return (int)e;
     const int bw = t.band_warps, cw = t.col_warps;
     const int stage_words = maxR * 32;
-    const size_t band_smem = (size_t)bw * (2 * stage_words + 256) * sizeof(uint64_t);
+    const size_t band_smem = (size_t)bw * (2 * stage_words + kBandTail) * sizeof(uint64_t);
     const int h_words = (maxC + 1) * (maxN + 1);
     const size_t col_smem = (size_t)cw * h_words * sizeof(uint64_t);
     const int bb = (total_bands + bw - 1) / bw;
