@@ -342,6 +342,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-light", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default launch shapes (short profiling runs)")
     ap.add_argument("--parts", type=int, default=PARTS, choices=[1, 2, 3, 4],
                     help="chunks a captured batch is pipelined in")
     ap.add_argument("--frames", type=int, default=NFRAMES,
@@ -395,7 +397,7 @@ def main():
             dist.barrier()
 
     # --- batched, timed --------------------------------------------------
-    tune = dec.autotune(ins)  # launch shapes of the search kernels, picked on this workload
+    tune = None if args.no_tune else dec.autotune(ins)  # launch shapes picked on this workload
     trs.trs_set_batch_parts(dec.ctx, args.parts)
     for _ in range(args.warmup):
         dec.batch_decide(ins, out)

@@ -288,8 +288,8 @@ int trs_batch_decide_host(trs_ctx *ctx, const trs_frame_desc *frames_host, int n
  * timings that chose them. */
 typedef struct trs_tune_report {
     int band_warps;      /* warps per block of the row-DP kernels */
-    int col_warps;       /* warps per block of the column-DP kernels */
-    int col_batch;       /* V rows a column-DP warp loads together */
+    int col_warps;       /* warps sharing one window's column DP (one block per window) */
+    int col_batch;       /* candidate steps whose V rows a column-DP warp loads together */
     int n_candidates;
     int cand_band_warps[6], cand_col_warps[6], cand_col_batch[6];
     float rows_ms[6];    /* both row-DP stages, fastest of three runs */
@@ -312,8 +312,8 @@ int trs_autotune(trs_ctx *ctx, const trs_frame_desc *frames_host, int nframes, t
  * the exact ones.  step = 1 restores the exact search.  1 <= step <= 64. */
 int trs_set_window_step(trs_ctx *ctx, int step);
 
-/* Sets the search kernels' launch shapes directly: band_warps and
- * col_warps in {2, 4, 8}, col_batch in {4, 8}; TRS_EINVAL otherwise.
+/* Sets the search kernels' launch shapes directly: band_warps in {2, 4, 8},
+ * col_warps in {1, 2, 4, 8}, col_batch in {4, 8}; TRS_EINVAL otherwise.
  * Drops captured batch graphs. */
 int trs_set_tune(trs_ctx *ctx, int band_warps, int col_warps, int col_batch);
 

@@ -715,7 +715,7 @@ int trs_autotune(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_tune_report
     cudaStream_t s = (cudaStream_t)stream;
     TRS_TRY(dev_alloc(ctx->hb_out, (size_t)ctx->o.max_batch * sizeof(trs_partition), &ctx->total));
     static const int bws[3] = {2, 4, 8};
-    static const int cws[3] = {2, 4, 8};
+    static const int cws[3] = {1, 2, 4};
     static const int cbs[2] = {4, 8};
     const SearchTune keep = ctx->tune;
     SearchTune cand[6];
@@ -776,7 +776,8 @@ int trs_set_window_step(trs_ctx *ctx, int step) {
 
 int trs_set_tune(trs_ctx *ctx, int band_warps, int col_warps, int col_batch) {
     auto ok_w = [](int w) { return w == 2 || w == 4 || w == 8; };
-    if (!ctx || !ok_w(band_warps) || !ok_w(col_warps) || (col_batch != 4 && col_batch != 8)) return TRS_EINVAL;
+    if (!ctx || !ok_w(band_warps) || !(col_warps == 1 || ok_w(col_warps)) || (col_batch != 4 && col_batch != 8))
+        return TRS_EINVAL;
     ctx->tune.band_warps = band_warps;
     ctx->tune.col_warps = col_warps;
     ctx->tune.col_batch = col_batch;

@@ -191,7 +191,9 @@ __device__ void item_pair(const DevFrame &fr, const DevPlan &pl, int ia, int ib,
     constexpr VT soft = Soft<VT>::v;
     const uint32_t ytop = line_px(y, H);
     const uint32_t tok_y = STEP == 2 ? tokbuf[y] : ~0u;
-    VT *Ga = G + h * 128, *Gb = Ga + 64;  // G_{k-1} in Ga, G_k into Gb, then swapped
+    // G_{k-1} in Ga, G_k into Gb, then swapped; half 1's pair sits 16 words
+    // further so that the halves' 32-bit reads fall in different banks
+    VT *Ga = G + h * 144, *Gb = Ga + 64;
     const int mi = h ? ib : ia;
     const bool have = mi >= 0;
     PlanItem it{0, 0, 1u, 0u, 0, -1};
@@ -296,7 +298,7 @@ __device__ void items_paired(const DevFrame &fr, const DevPlan &pl, int i0, int 
 // admitted slice values are staged per lane and the k loop only reads
 // G_{k-1}[y+d] from shared memory and relaxes.  V[k] = G_k[0] is
 // collected in lane k and stored with one coalesced write per item.
-constexpr int kBandTail = 272;  // per warp after the two staging areas: G tables and tok bits
+constexpr int kBandTail = 304;  // per warp after the two staging areas: G tables (288 words), tok bits (16)
 template <int STEP>
 __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, int total, int stage_words) {
     extern __shared__ uint64_t bsm[];
@@ -326,7 +328,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, i
     // values, and the 64-word G table
     uint64_t *stage = bsm + (size_t)wib * (2 * stage_words + kBandTail);
     uint64_t *itm = stage + stage_words;
-    uint64_t *gbuf = itm + stage_words;  // G tables (256 words), then tok per row (16 words)
+    uint64_t *gbuf = itm + stage_words;  // G tables (288 words), then tok per row (16 words)
     uint32_t tok = 0;  // step 2: bit d-1 set if the slice [lane, lane+d) meets the Eq. 4 bound
 #pragma unroll 4
     for (int d = 1; d <= R; ++d) {
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, i
             stage[(d - 1) * 32 + lane] = tv;
         }
     }
-    uint32_t *tokbuf = reinterpret_cast<uint32_t *>(gbuf + 256);
+    uint32_t *tokbuf = reinterpret_cast<uint32_t *>(gbuf + 288);
     tokbuf[lane] = tok;
     __syncwarp();
     if (R <= 17 && n <= 16) {
@@ -397,58 +399,71 @@ __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, i
     }
 }
 
-// The column DP of one window (see column_kernel) on values of type VT in
-// the warp's shared-memory table Hraw ((C+1)*(n+1) words of 8 bytes).
-// Returns H[0][n] with kInf where no partition exists; for 64-bit values
-// the table keeps every entry (kSoft for none) for the rebuild.
+__device__ __forceinline__ void smem_min(uint32_t *p, uint32_t v) { atomicMin(p, v); }
+__device__ __forceinline__ void smem_min(uint64_t *p, uint64_t v) {
+    atomicMin(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
+}
+
+// The column DP of one window (see column_kernel) on values of type VT, by
+// the P warps of the block, in the block's shared-memory table Hraw
+// ((C+1)*(n+1) words of 8 bytes); slots holds the window's item of every
+// band.  Returns H[0][n] with kInf where no partition exists; for 64-bit
+// values the table keeps every entry (kSoft for none) for the rebuild.
 template <int STEP, typename VT, int kBatch, bool PAIR>
-__device__ uint64_t column_dp(uint64_t *Hraw, const uint64_t *V, const int32_t *slot_row, int C, int n) {
-    const int lane = threadIdx.x & 31;
+__device__ uint64_t column_dp(uint64_t *Hraw, const int32_t *slots, const uint64_t *V, int C, int n) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, P = blockDim.x >> 5;
     const int stride = n + 1;
     constexpr VT soft = Soft<VT>::v;
     VT *Hs = reinterpret_cast<VT *>(Hraw);
-    for (int i = lane; i < (C + 1) * stride; i += 32) Hs[i] = soft;
-    __syncwarp();
-    if (lane == 0) Hs[C * stride] = 0;
-    __syncwarp();
-    // PAIR (n <= 16): lanes 0-15 relax one candidate edge and lanes 16-31 the
-    // next, each half over m = 1..16; otherwise the whole warp takes one edge
+    // PAIR (n <= 16): lanes 0-15 relax one candidate edge and lanes 16-31
+    // another, each half over m = 1..16; otherwise the whole warp takes one
     const int half = PAIR ? lane >> 4 : 0;
     const int kl = PAIR ? lane & 15 : lane;  // lane kl holds V[kl+1] of its half's edge
     const int m = kl + 1;
-    constexpr int kPer = PAIR ? 2 : 1;       // edges per step
+    constexpr int kPer = PAIR ? 2 : 1;       // edges per warp step
+    // warp w takes, at left edge x, the candidate right edges x + 1 + c with
+    // c = (s * P + w) * kPer + half for its steps s = 0, 1, ...
+    auto cand = [&](int s) { return (s * P + w) * kPer + half; };
+    auto load = [&](int x, int s0, uint64_t (&vb)[kBatch]) {
+        const int32_t *srow = slots + band_index(C, x, x + 1);  // edges x+1.. are consecutive bands
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int c = cand(s0 + u);
+            const int sj = (c < C - x && kl < n) ? srow[c] : -1;
+            vb[u] = sj >= 0 ? __ldg(V + (size_t)sj * stride + kl + 1) : kInf;
+        }
+    };
+    uint64_t cur[kBatch], nxt[kBatch];
+    load(C - 1, 0, cur);
     for (int x = C - 1; x >= 0; --x) {
+        const int ncand = C - x;
+        // the next left edge's first V rows are in flight while this one relaxes
+        if (x > 0) load(x - 1, 0, nxt);
         VT acc = soft;
-        const int32_t *srow = slot_row + band_index(C, x, x + 1);  // edges x+1.. are consecutive bands
-        for (int base = 0; base < C - x; base += 32) {
-            const int ncand = min(32, C - x - base);
-            const int sl = lane < ncand ? srow[base + lane] : -1;
-            // edges in batches: all V-row loads of a batch are in flight together
-            for (int j0 = 0; j0 < ncand; j0 += kBatch * kPer) {
-                uint64_t vb[kBatch];
+        for (int s0 = 0; (s0 * P + w) * kPer < ncand; s0 += kBatch) {
+            uint64_t vb[kBatch];
+            if (s0 == 0) {
 #pragma unroll
-                for (int u = 0; u < kBatch; ++u) {
-                    const int jj = j0 + u * kPer + half;
-                    const int sj = __shfl_sync(kFull, sl, jj & 31);
-                    vb[u] = (jj < ncand && sj >= 0 && kl < n) ? __ldg(V + (size_t)sj * stride + kl + 1) : kInf;
-                }
+                for (int u = 0; u < kBatch; ++u) vb[u] = cur[u];
+            } else {
+                load(x, s0, vb);
+            }
 #pragma unroll
-                for (int u = 0; u < kBatch; ++u) {
-                    const unsigned fin = __ballot_sync(kFull, vb[u] != kInf);
-                    const unsigned mine = PAIR ? (half ? fin >> 16 : fin & 0xffffu) : fin;
-                    unsigned any = PAIR ? ((fin & 0xffffu) | (fin >> 16)) : fin;
-                    const int jj = j0 + u * kPer + half;
-                    const VT *Hrow = Hs + (size_t)(x + 1 + base + (jj < ncand ? jj : 0)) * stride;
-                    const VT vv = (VT)vb[u];
-                    while (any) {
-                        const int k = __ffs(any);
-                        any &= any - 1;
-                        const VT v = __shfl_sync(kFull, vv, (half << 4) + k - 1);
-                        if (((mine >> (k - 1)) & 1u) && m >= k && m <= n) {
-                            const VT h = Hrow[m - k];
-                            const VT c = STEP == 1 ? (v > h ? v : h) : VT(v + h);
-                            acc = c < acc ? c : acc;
-                        }
+            for (int u = 0; u < kBatch; ++u) {
+                const unsigned fin = __ballot_sync(kFull, vb[u] != kInf);
+                const unsigned mine = PAIR ? (half ? fin >> 16 : fin & 0xffffu) : fin;
+                unsigned any = PAIR ? ((fin & 0xffffu) | (fin >> 16)) : fin;
+                const int c = cand(s0 + u);
+                const VT *Hrow = Hs + (size_t)(x + 1 + (c < ncand ? c : 0)) * stride;
+                const VT vv = (VT)vb[u];
+                while (any) {
+                    const int k = __ffs(any);
+                    any &= any - 1;
+                    const VT v = __shfl_sync(kFull, vv, (half << 4) + k - 1);
+                    if (((mine >> (k - 1)) & 1u) && m >= k && m <= n) {
+                        const VT h = Hrow[m - k];
+                        const VT cc = STEP == 1 ? (v > h ? v : h) : VT(v + h);
+                        acc = cc < acc ? cc : acc;
                     }
                 }
             }
@@ -457,62 +472,72 @@ __device__ uint64_t column_dp(uint64_t *Hraw, const uint64_t *V, const int32_t *
             const VT o = __shfl_xor_sync(kFull, acc, 16);
             acc = o < acc ? o : acc;
         }
-        if (half == 0 && m <= n) Hs[x * stride + m] = acc < soft ? acc : soft;
-        __syncwarp();
+        if (half == 0 && m <= n && acc < soft) smem_min(Hs + (size_t)x * stride + m, acc);
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) cur[u] = nxt[u];
+        __syncthreads();  // row x is complete before any warp reads it
     }
     const VT r = Hs[n];
     return r >= soft ? kInf : (uint64_t)r;
 }
 
-// Suffix DP over tile-column edges of one window, one warp:
+// Suffix DP over tile-column edges of one window, one block of P warps:
 //   H[x][m] = min over x1 > x, k of  V[item(w, [x,x1))][k] (+|max) H[x1][m-k],
-// H[C][0] = 0.  Lane m-1 owns slice count m.  For each x the lanes fetch
-// the items of all candidate edges at once; V rows are then loaded eight
-// edges at a time (lanes over k, loads of a batch in flight together) and
-// each edge contributes only the slice counts whose V is finite (a ballot
-// per row).
+// H[C][0] = 0.  Lane m-1 owns slice count m.  At each left edge x the
+// block's warps split the candidate right edges x1 between them, relax the
+// slice counts whose V is finite (a ballot per row) and merge their minima
+// into row x with shared-memory atomics; the V rows of the next left edge
+// are loaded while the current one relaxes.
 template <int STEP, int kBatch>
 __global__ void __launch_bounds__(kMaxWarps * 32) column_kernel(LaunchArgs args, int total, int h_words) {
     extern __shared__ uint64_t csm[];
-    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
-    if (gw >= total) return;
-    int w;
-    const int f = locate(args, args.pre.windows, args.single_windows, gw, &w);
+    const int w = blockIdx.x;
+    if (w >= total) return;
+    int wl;
+    const int f = locate(args, args.pre.windows, args.single_windows, w, &wl);
     const DevFrame &fr = frame_at(args, f);
     const DevPlan &pl = *fr.plan;
     const int C = fr.C, n = pl.n, nb = pl.nb, stride = n + 1;
     uint64_t *wres = STEP == 1 ? fr.wres1 : fr.wres2;
     const uint64_t *V = STEP == 1 ? fr.V1 : fr.V2;
     if (frame_status(fr) != TRS_OK) {
-        if (lane == 0) wres[w] = kInf;
+        if (threadIdx.x == 0) wres[wl] = kInf;
         return;
     }
     if (STEP == 2) {
         // a window whose best time breaks Eq. 4 holds no step-2 candidate
         const uint64_t thr = eq4_threshold(fr.scal[0], fr.lambda_q);
-        if (fr.wres1[w] > thr) {
-            if (lane == 0) wres[w] = kInf;
+        if (fr.wres1[wl] > thr) {
+            if (threadIdx.x == 0) wres[wl] = kInf;
             return;
         }
     }
-    const int32_t *slot_row = pl.slot_of + (size_t)w * nb;
+    uint64_t *Hraw = csm;
+    int32_t *slots = reinterpret_cast<int32_t *>(csm + h_words);
+    const int32_t *slot_row = pl.slot_of + (size_t)wl * nb;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) slots[i] = slot_row[i];
+    const bool t32 = STEP == 1 && frame_t32(fr);
+    if (t32) {
+        uint32_t *Hs = reinterpret_cast<uint32_t *>(Hraw);
+        for (int i = threadIdx.x; i < (C + 1) * stride; i += blockDim.x) Hs[i] = i == C * stride ? 0u : Soft<uint32_t>::v;
+    } else {
+        for (int i = threadIdx.x; i < (C + 1) * stride; i += blockDim.x) Hraw[i] = i == C * stride ? 0ull : kSoft;
+    }
+    __syncthreads();
     uint64_t res;
-    uint64_t *Hraw = csm + (size_t)wib * h_words;
-    if (STEP == 1 && frame_t32(fr))
-        res = n <= 16 ? column_dp<1, uint32_t, kBatch, true>(Hraw, V, slot_row, C, n)
-                      : column_dp<1, uint32_t, kBatch, false>(Hraw, V, slot_row, C, n);
+    if (t32)
+        res = n <= 16 ? column_dp<1, uint32_t, kBatch, true>(Hraw, slots, V, C, n)
+                      : column_dp<1, uint32_t, kBatch, false>(Hraw, slots, V, C, n);
     else
-        res = n <= 16 ? column_dp<STEP, uint64_t, kBatch, true>(Hraw, V, slot_row, C, n)
-                      : column_dp<STEP, uint64_t, kBatch, false>(Hraw, V, slot_row, C, n);
-    if (lane == 0) {
-        wres[w] = res;
+        res = n <= 16 ? column_dp<STEP, uint64_t, kBatch, true>(Hraw, slots, V, C, n)
+                      : column_dp<STEP, uint64_t, kBatch, false>(Hraw, slots, V, C, n);
+    if (threadIdx.x == 0) {
+        wres[wl] = res;
         if (res != kInf) atomicMin(reinterpret_cast<unsigned long long *>(&fr.scal[STEP == 1 ? 0 : 1]), res);
     }
     if (STEP == 2) {
-        const uint64_t *Hs = csm + (size_t)wib * h_words;
-        uint64_t *H2 = fr.H2 + (size_t)w * (C + 1) * stride;
-        for (int i = lane; i < (C + 1) * stride; i += 32) H2[i] = hard_inf(Hs[i]);
+        uint64_t *H2 = fr.H2 + (size_t)wl * (C + 1) * stride;
+        for (int i = threadIdx.x; i < (C + 1) * stride; i += blockDim.x) H2[i] = hard_inf(Hraw[i]);
     }
 }
 
@@ -778,7 +803,7 @@ __global__ void __launch_bounds__(32) finish_kernel(LaunchArgs args) {
 // largest shapes need (once per device, before any capture).
 int prepare_search_kernels() {
     const int band_smem = kMaxWarps * (2 * kMaxR * 32 + kBandTail) * (int)sizeof(uint64_t);
-    const int col_smem = kMaxWarps * (kMaxC + 1) * (kMaxN + 1) * (int)sizeof(uint64_t);
+    const int col_smem = (kMaxC + 1) * (kMaxN + 1) * (int)sizeof(uint64_t) + num_bands(kMaxC) * (int)sizeof(int32_t);
     const int rb_smem = ((kMaxN + 1) * 32 + kMaxR * 32) * (int)sizeof(uint64_t);
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
     cudaError_t e = cudaFuncSetAttribute(band_kernel<1>, A, band_smem);
@@ -803,9 +828,9 @@ int launch_search(const LaunchArgs &a, int total_bands, int total_windows, int m
     const int stage_words = maxR * 32;
     const size_t band_smem = (size_t)bw * (2 * stage_words + kBandTail) * sizeof(uint64_t);
     const int h_words = (maxC + 1) * (maxN + 1);
-    const size_t col_smem = (size_t)cw * h_words * sizeof(uint64_t);
+    const size_t col_smem = (size_t)h_words * sizeof(uint64_t) + (size_t)num_bands(maxC) * sizeof(int32_t);
     const int bb = (total_bands + bw - 1) / bw;
-    const int cb = (total_windows + cw - 1) / cw;
+    const int cb = total_windows;  // one block of cw warps per window
     auto mark = [&](int i) {
         if (ev && e == cudaSuccess) e = record_event(ev[i], s);
     };

@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(kTabThreads) tables_kernel(LaunchArgs args) {
     uint32_t *tq = reinterpret_cast<uint32_t *>(satt + S);
     __shared__ int bad;
     __shared__ int bx0[kBandsPerBlock], bx1[kBandsPerBlock];
+    __shared__ uint16_t slice_dy[kMaxR * (kMaxR + 1) / 2];  // (d - 1) << 8 | y of the band's slices
     const int t = threadIdx.x;
     if (t == 0) bad = 0;
     for (int i = t; i < S; i += kTabThreads) {
@@ -95,6 +96,10 @@ __global__ void __launch_bounds__(kTabThreads) tables_kernel(LaunchArgs args) {
             bx1[t] = x0 + 1 + b;
         }
     }
+    if (t < R) {  // height d = t + 1 has start rows 0 .. R - d, after those of the smaller heights
+        const int first = t * R - t * (t - 1) / 2;
+        for (int y = 0; y < R - t; ++y) slice_dy[first + y] = (uint16_t)(t << 8 | y);
+    }
     __syncthreads();
 
     const TablesOffsets off = tables_offsets(C, R);
@@ -102,16 +107,23 @@ __global__ void __launch_bounds__(kTabThreads) tables_kernel(LaunchArgs args) {
     uint64_t *rect_q = reinterpret_cast<uint64_t *>(fr.tables + off.rect_q);
     const int per_band = R * R;
     const int nloc = min(kBandsPerBlock, nb - b0);
+    // entries past the frame's bottom (y + d > R) hold zeros
     for (int e = t; e < nloc * per_band; e += kTabThreads) {
         const int lb = e / per_band, rem = e - lb * per_band;
         const int dm1 = rem / R, y = rem - dm1 * R;
-        const int y1 = y + dm1 + 1;
-        const size_t gi = (size_t)(b0 + lb) * per_band + rem;
-        if (y1 > R) {
+        if (y + dm1 + 1 > R) {
+            const size_t gi = (size_t)(b0 + lb) * per_band + rem;
             rect_t[gi] = 0;
             rect_q[gi] = 0;
-            continue;
         }
+    }
+    // the R(R+1)/2 slices of a band, enumerated densely so that no lane idles
+    const int per_valid = R * (R + 1) / 2;
+    for (int e = t; e < nloc * per_valid; e += kTabThreads) {
+        const int lb = e / per_valid;
+        const int dy = slice_dy[e - lb * per_valid];
+        const int dm1 = dy >> 8, y = dy & 255, y1 = y + dm1 + 1;
+        const size_t gi = (size_t)(b0 + lb) * per_band + (size_t)dm1 * R + y;
         const int x0 = bx0[lb], x1 = bx1[lb];
         const int i00 = y * (C + 1) + x0, i01 = y * (C + 1) + x1;
         const int i10 = y1 * (C + 1) + x0, i11 = y1 * (C + 1) + x1;

@@ -56,21 +56,34 @@ __host__ __device__ inline TablesOffsets tables_offsets(int C, int R) {
 }
 
 #ifdef __CUDACC__
-// ceil(s1^2 / n) for n < 2^32 when the quotient fits 64 bits (it is at most
-// S2 by Cauchy-Schwarz); *rem = s1^2 mod n.  128-bit square, long division
-// by 32-bit digits.
+// floor(x / n) and *rem = x mod n for 1 <= n < 2^32, without a hardware
+// divide: the schoolbook correction of a trial quotient (Knuth, TAOCP vol. 2,
+// Sec. 4.3.1), the trial quotient taken in single precision with every
+// rounding toward zero and rn <= 1/n, so that it never exceeds x / n; the
+// remainder is then exact in 64-bit integers.  Each round leaves a quotient
+// below 2^-21 of the previous one (plus 1), so x < 2^64 takes at most five.
+__device__ inline uint64_t udivmod_trial(uint64_t x, uint32_t n, float rn, uint64_t *rem) {
+    uint64_t q = 0;
+    while (x >= n) {
+        uint64_t t = __float2ull_rz(__fmul_rz(__ull2float_rz(x), rn));
+        t = t ? t : 1;  // x >= n: at least one n fits
+        q += t;
+        x -= t * n;
+    }
+    *rem = x;
+    return q;
+}
+
+// ceil(s1^2 / n) for 1 <= n < 2^32 when the quotient fits 64 bits (it is at
+// most S2 by Cauchy-Schwarz); *rem = s1^2 mod n.  With s1 = a n + b (b < n):
+// s1^2 = n (a (s1 + b) + c) + r where b^2 = c n + r.
 __device__ inline uint64_t ceil_square_div(uint64_t s1, uint32_t n, uint32_t *rem) {
-    const uint64_t lo = s1 * s1;
-    const uint64_t hi = __umul64hi(s1, s1);
-    uint64_t r = hi;  // the quotient fits 64 bits, so hi < n: hi is the first remainder
-    const uint64_t t1 = (r << 32) | (lo >> 32);
-    const uint64_t q1 = t1 / n;
-    r = t1 - q1 * n;
-    const uint64_t t2 = (r << 32) | (lo & 0xffffffffull);
-    const uint64_t q0 = t2 / n;
-    r = t2 - q0 * n;
+    const float rn = __frcp_rz(__uint2float_ru(n));  // <= 1/n
+    uint64_t b, r;
+    const uint64_t a = udivmod_trial(s1, n, rn, &b);
+    const uint64_t c = udivmod_trial(b * b, n, rn, &r);
     *rem = (uint32_t)r;
-    return (q1 << 32) + q0 + (r != 0 ? 1u : 0u);
+    return a * (s1 + b) + c + (r != 0 ? 1u : 0u);
 }
 
 // Largest T with T * 65536 <= t_min * (65536 + lambda_q)  (Eq. 4).
@@ -203,8 +216,8 @@ int launch_tables(const LaunchArgs &a, int total_groups, int maxC, int maxR, voi
 // Launch shapes of the search kernels, chosen by trs_autotune.
 struct SearchTune {
     int band_warps = 4;  // warps per block of the row-DP kernels (2, 4 or 8)
-    int col_warps = 4;   // warps per block of the column-DP kernels (2, 4 or 8)
-    int col_batch = 8;   // candidate edges whose V rows a column-DP warp loads together (4 or 8)
+    int col_warps = 4;   // warps sharing one window's column DP, one block per window (2, 4 or 8)
+    int col_batch = 8;   // candidate steps whose V rows a column-DP warp loads together (4 or 8)
 };
 
 // scal: the T_min / Q* words of every frame of the launch (reset to +inf first).
