@@ -176,21 +176,27 @@ __device__ __forceinline__ uint64_t item_rows(const VT *sv, VT *G, int nd, int d
 
 // Two items of one tile column per warp, for frames of at most 17 CTU rows
 // and n <= 16 (every workload of the paper): half h = lane / 16 runs one
-// item with its lane l on start row y = l.  Row 16, the last row of a
-// 17-row frame, needs no lane: a slice starting there ends at the frame's
-// bottom, so G_1[16] is that slice's value and G_k[16] (k >= 2) is empty.
-// G_{k-1} and G_k alternate between two 64-word buffers per half, so one
-// warp barrier per k suffices.  Loops run to the larger of the two items'
-// bounds (extra heights hold the saturating infinity), so both halves stay
-// in step.  Half 0 runs item ia, half 1 item ib (none if ib is negative).
+// item with its lane l on start row y = l.
+//  * A slice [y, y+d) that ends above the frame's last row is d full CTU
+//    rows high, so the item admits it iff d lies in [dlo, dhi] (its pixel
+//    range over 128).  The slice ending on the last row (possibly clipped)
+//    only starts a 1-slice remainder: G_{k-1}[R] is empty for k >= 2.  So
+//    G_1[y] is that one slice (if admitted) and, for k >= 2, lane y relaxes
+//    d = dlo..dhi only.
+//  * Row 16, the last row of a 17-row frame, needs no lane: G_1[16] is its
+//    one-row slice and G_k[16] (k >= 2) is empty.
+//  * G_{k-1} and G_k alternate between two 64-word buffers per half, one
+//    warp barrier per k.
+// Loops run to the larger of the two items' bounds (extra heights hold the
+// saturating infinity), so both halves stay in step.  The staged values
+// already hold the saturating infinity for slices past Eq. 4's bound (step
+// 2).  Half 0 runs item ia, half 1 item ib (none if ib is negative).
 template <int STEP, typename VT>
 __device__ void item_pair(const DevFrame &fr, const DevPlan &pl, int ia, int ib, uint64_t *Vall,
-                          const uint64_t *stage, VT *sv, VT *G, const uint32_t *tokbuf) {
+                          const uint64_t *stage, VT *sv, VT *G) {
     const int lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15, y = l;
     const int n = pl.n, R = fr.R, H = fr.H;
     constexpr VT soft = Soft<VT>::v;
-    const uint32_t ytop = line_px(y, H);
-    const uint32_t tok_y = STEP == 2 ? tokbuf[y] : ~0u;
     // G_{k-1} in Ga, G_k into Gb, then swapped; half 1's pair sits 16 words
     // further so that the halves' 32-bit reads fall in different banks
     VT *Ga = G + h * 144, *Gb = Ga + 64;
@@ -199,34 +205,39 @@ __device__ void item_pair(const DevFrame &fr, const DevPlan &pl, int ia, int ib,
     PlanItem it{0, 0, 1u, 0u, 0, -1};
     if (have) it = pl.items[mi];
     const int kmax = have ? it.kmax : 0;
-    const int dmin = max(1, (int)((it.hlo + kCtu - 1) / kCtu));
-    const int nd = have ? min(R, (int)(it.hhi / kCtu) + 1) - dmin + 1 : 0;
+    const int dlo = max(1, (int)((it.hlo + kCtu - 1) / kCtu));
+    const int nd = have ? (int)(it.hhi / kCtu) - dlo + 1 : 0;  // full-height slices admitted (may be <= 0)
     const int ndm = max(nd, __shfl_xor_sync(kFull, nd, 16));
     const int kmm = max(kmax, __shfl_xor_sync(kFull, kmax, 16));
     __syncwarp();  // every lane is done with the previous pair's tables
-    for (int i = 0; i < ndm; ++i) {
-        const int d = dmin + i, y1 = y + d;
-        const uint32_t hh = line_px(y1, H) - ytop;
-        const bool ok = i < nd && y < R && y1 <= R && hh >= it.hlo && hh <= it.hhi &&
-                        (STEP == 1 || ((tok_y >> (d - 1)) & 1u));
-        sv[i * 32 + lane] = ok ? (VT)stage[(d - 1) * 32 + y] : soft;
-    }
-    // G_1[16]: the one-row slice [16, 17) of a 17-row frame
-    const uint32_t h16 = (uint32_t)H - line_px(16, H);
-    const bool ok16 = have && R == 17 && dmin == 1 && h16 >= it.hlo && h16 <= it.hhi &&
-                      (STEP == 1 || (tokbuf[16] & 1u));
-    const VT g16 = ok16 ? (VT)stage[16] : soft;
+    for (int i = 0; i < ndm; ++i)
+        sv[i * 32 + lane] = i < nd ? (VT)stage[(dlo + i - 1) * 32 + y] : soft;
+    // G_1: the single slice [y, R), for y = l and for row 16
+    auto last_slice = [&](int yy) -> VT {
+        const uint32_t hh = (uint32_t)H - line_px(yy, H);
+        return have && yy < R && hh >= it.hlo && hh <= it.hhi ? (VT)stage[(R - yy - 1) * 32 + yy] : soft;
+    };
+    const VT g16 = last_slice(16);
+    Gb[y] = kmax >= 1 ? last_slice(y) : soft;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int e = l + 16 * q;
         Ga[e] = e == R ? VT(0) : soft;  // G_0: only the empty remainder holds zero slices
-        Gb[e] = soft;
+        if (q) Gb[e] = soft;
     }
+    if (l == 0) Gb[16] = g16;
     __syncwarp();
     uint64_t vreg = kInf;
+    if (l == 0 && kmax >= 1) {
+        const VT g0 = Gb[0];
+        vreg = g0 >= soft ? kInf : (uint64_t)g0;
+    }
+    VT *t = Ga;
+    Ga = Gb;
+    Gb = t;
     const VT *sp = sv + lane;
-    for (int k = 1; k <= kmm; ++k) {
-        const VT *gp = Ga + y + dmin;
+    for (int k = 2; k <= kmm; ++k) {
+        const VT *gp = Ga + y + dlo;
         VT best = soft;
 #pragma unroll 4
         for (int i = 0; i < ndm; ++i) {
@@ -237,7 +248,7 @@ __device__ void item_pair(const DevFrame &fr, const DevPlan &pl, int ia, int ib,
         if (k <= kmax) {  // a half past its kmax runs on, unread
             Gb[y] = best < soft ? best : soft;
             if (l == 0) {
-                Gb[16] = k == 1 ? g16 : soft;
+                Gb[16] = soft;  // G_k[16] of a 17-row frame, k >= 2
                 Gb[17] = soft;  // G_k[R] of a 17-row frame, k >= 1
             }
         }
@@ -246,7 +257,7 @@ __device__ void item_pair(const DevFrame &fr, const DevPlan &pl, int ia, int ib,
             const VT g0 = Gb[0];
             vreg = g0 >= soft ? kInf : (uint64_t)g0;
         }
-        VT *t = Ga;
+        t = Ga;
         Ga = Gb;
         Gb = t;
     }
@@ -262,11 +273,11 @@ __device__ void item_pair(const DevFrame &fr, const DevPlan &pl, int ia, int ib,
 // window is read again) and pairs them up after that filter.
 template <int STEP, typename VT>
 __device__ void items_paired(const DevFrame &fr, const DevPlan &pl, int i0, int i1, uint64_t *Vall,
-                             const uint64_t *stage, VT *sv, VT *G, const uint32_t *tokbuf, uint64_t thr) {
+                             const uint64_t *stage, VT *sv, VT *G, uint64_t thr) {
     const int lane = threadIdx.x & 31;
     if (STEP == 1) {
         for (int ii = i0; ii < i1; ii += 2)
-            item_pair<STEP, VT>(fr, pl, ii, ii + 1 < i1 ? ii + 1 : -1, Vall, stage, sv, G, tokbuf);
+            item_pair<STEP, VT>(fr, pl, ii, ii + 1 < i1 ? ii + 1 : -1, Vall, stage, sv, G);
         return;
     }
     int held = -1;  // a live item waiting for its partner
@@ -283,12 +294,12 @@ __device__ void items_paired(const DevFrame &fr, const DevPlan &pl, int i0, int 
             if (held < 0) {
                 held = i;
             } else {
-                item_pair<STEP, VT>(fr, pl, held, i, Vall, stage, sv, G, tokbuf);
+                item_pair<STEP, VT>(fr, pl, held, i, Vall, stage, sv, G);
                 held = -1;
             }
         }
     }
-    if (held >= 0) item_pair<STEP, VT>(fr, pl, held, -1, Vall, stage, sv, G, tokbuf);
+    if (held >= 0) item_pair<STEP, VT>(fr, pl, held, -1, Vall, stage, sv, G);
 }
 
 // Row DPs, one warp per (frame, tile column): the column's slice values
@@ -298,7 +309,7 @@ __device__ void items_paired(const DevFrame &fr, const DevPlan &pl, int i0, int 
 // admitted slice values are staged per lane and the k loop only reads
 // G_{k-1}[y+d] from shared memory and relaxes.  V[k] = G_k[0] is
 // collected in lane k and stored with one coalesced write per item.
-constexpr int kBandTail = 304;  // per warp after the two staging areas: G tables (288 words), tok bits (16)
+constexpr int kBandTail = 288;  // per warp after the two staging areas: the G tables
 template <int STEP>
 __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, int total, int stage_words) {
     extern __shared__ uint64_t bsm[];
@@ -325,10 +336,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, i
     const uint64_t *RT = reinterpret_cast<const uint64_t *>(fr.tables + off.rect_t) + base;
     const uint64_t *RQ = reinterpret_cast<const uint64_t *>(fr.tables + off.rect_q) + base;
     // per warp: the column's slice values by height, one item's admitted
-    // values, and the 64-word G table
+    // values, and the G tables (288 words)
     uint64_t *stage = bsm + (size_t)wib * (2 * stage_words + kBandTail);
     uint64_t *itm = stage + stage_words;
-    uint64_t *gbuf = itm + stage_words;  // G tables (288 words), then tok per row (16 words)
+    uint64_t *gbuf = itm + stage_words;
     uint32_t tok = 0;  // step 2: bit d-1 set if the slice [lane, lane+d) meets the Eq. 4 bound
 #pragma unroll 4
     for (int d = 1; d <= R; ++d) {
@@ -336,21 +347,21 @@ __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, i
         const size_t e = in ? (size_t)(d - 1) * R + lane : 0;
         const uint64_t tv = __ldg(RT + e);
         if (STEP == 2) {
-            stage[(d - 1) * 32 + lane] = __ldg(RQ + e);
-            tok |= (in && tv <= thr ? 1u : 0u) << (d - 1);
+            // slices past the Eq. 4 bound hold the saturating infinity
+            const bool meets = in && tv <= thr;
+            stage[(d - 1) * 32 + lane] = meets ? __ldg(RQ + e) : kSoft;
+            tok |= (meets ? 1u : 0u) << (d - 1);
         } else {
             stage[(d - 1) * 32 + lane] = tv;
         }
     }
-    uint32_t *tokbuf = reinterpret_cast<uint32_t *>(gbuf + 288);
-    tokbuf[lane] = tok;
     __syncwarp();
     if (R <= 17 && n <= 16) {
         if (STEP == 1 && t32)
             items_paired<1, uint32_t>(fr, pl, i0, i1, Vall, stage, reinterpret_cast<uint32_t *>(itm),
-                                      reinterpret_cast<uint32_t *>(gbuf), tokbuf, thr);
+                                      reinterpret_cast<uint32_t *>(gbuf), thr);
         else
-            items_paired<STEP, uint64_t>(fr, pl, i0, i1, Vall, stage, itm, gbuf, tokbuf, thr);
+            items_paired<STEP, uint64_t>(fr, pl, i0, i1, Vall, stage, itm, gbuf, thr);
         return;
     }
     const uint32_t ytop = line_px(lane, H);
