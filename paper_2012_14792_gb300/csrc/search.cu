@@ -462,20 +462,20 @@ __device__ uint64_t column_dp(uint64_t *Hraw, const int32_t *slots, const uint64
 #pragma unroll
             for (int u = 0; u < kBatch; ++u) {
                 const unsigned fin = __ballot_sync(kFull, vb[u] != kInf);
-                const unsigned mine = PAIR ? (half ? fin >> 16 : fin & 0xffffu) : fin;
-                unsigned any = PAIR ? ((fin & 0xffffu) | (fin >> 16)) : fin;
+                const unsigned any = PAIR ? ((fin & 0xffffu) | (fin >> 16)) : fin;
+                if (!any) continue;
                 const int c = cand(s0 + u);
                 const VT *Hrow = Hs + (size_t)(x + 1 + (c < ncand ? c : 0)) * stride;
-                const VT vv = (VT)vb[u];
-                while (any) {
-                    const int k = __ffs(any);
-                    any &= any - 1;
+                // the slice counts between the lowest and highest finite k of
+                // either half; a count this half lacks relaxes its saturating
+                // infinity, which no minimum keeps
+                const VT vv = vb[u] == kInf ? soft : (VT)vb[u];
+                const int khi = 32 - __clz(any);
+                for (int k = __ffs(any); k <= khi; ++k) {
                     const VT v = __shfl_sync(kFull, vv, (half << 4) + k - 1);
-                    if (((mine >> (k - 1)) & 1u) && m >= k && m <= n) {
-                        const VT h = Hrow[m - k];
-                        const VT cc = STEP == 1 ? (v > h ? v : h) : VT(v + h);
-                        acc = cc < acc ? cc : acc;
-                    }
+                    const VT h = (m >= k && m <= n) ? Hrow[m - k] : soft;
+                    const VT cc = STEP == 1 ? (v > h ? v : h) : VT(v + h);
+                    acc = cc < acc ? cc : acc;
                 }
             }
         }
