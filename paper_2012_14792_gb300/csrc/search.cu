@@ -732,7 +732,9 @@ __global__ void __launch_bounds__(32) finish_kernel(LaunchArgs args) {
     const uint64_t *RT = reinterpret_cast<const uint64_t *>(fr.tables + off.rect_t);
     const uint64_t *RQ = reinterpret_cast<const uint64_t *>(fr.tables + off.rect_q);
     const uint64_t *sat1 = reinterpret_cast<const uint64_t *>(fr.tables + off.sat_s1);
-    // lane b decodes tile column b (c <= n <= 32)
+    // lane b lays out tile column b's slices (c <= n <= 32), then lane r
+    // evaluates region r
+    __shared__ int16_t reg[32][4];
     const int b = lane;
     const uint32_t cut = b < c ? best.cut[b] : 0u;
     const int ns = b < c ? __popc(cut) + 1 : 0;
@@ -743,33 +745,19 @@ __global__ void __launch_bounds__(32) finish_kernel(LaunchArgs args) {
         if (lane >= o) r += v;
     }
     r -= ns;  // first region index of this tile column
-    uint64_t tmax = 0, qsum = 0;
-    double sse = 0.0;
     if (b < c) {
         const int x0 = best.xe[b], x1 = best.xe[b + 1];
-        const int bi = band_index(C, x0, x1);
         out->col_bd[b + 1] = (int16_t)x1;
         out->slice_cuts[b] = cut;
         out->tile_slices[b] = (uint8_t)ns;
         int y0 = 0;
         for (int y = 1; y <= R; ++y) {
             if (y < R && !((cut >> (y - 1)) & 1u)) continue;
-            const size_t e = ((size_t)bi * R + (y - y0 - 1)) * R + y0;
-            const uint64_t tv = RT[e], qv = RQ[e];
-            tmax = tv > tmax ? tv : tmax;
-            qsum += qv;
-            const uint64_t s1 = sat1[y * (C + 1) + x1] - sat1[y0 * (C + 1) + x1] - sat1[y * (C + 1) + x0] +
-                                sat1[y0 * (C + 1) + x0];
-            const uint32_t np = (line_px(x1, fr.W) - line_px(x0, fr.W)) * (line_px(y, fr.H) - line_px(y0, fr.H));
-            uint32_t rem;
-            (void)ceil_square_div(s1, np, &rem);
-            // exact SSE = floor + (ceil(S1^2/N) - S1^2/N)
-            sse += (double)qv + (rem ? (double)(np - rem) / (double)np : 0.0);
-            if (r < kMaxN) {
-                out->region[r][0] = (int16_t)x0;
-                out->region[r][1] = (int16_t)y0;
-                out->region[r][2] = (int16_t)x1;
-                out->region[r][3] = (int16_t)y;
+            if (r < 32) {
+                reg[r][0] = (int16_t)x0;
+                reg[r][1] = (int16_t)y0;
+                reg[r][2] = (int16_t)x1;
+                reg[r][3] = (int16_t)y;
             }
             r++;
             y0 = y;
@@ -777,12 +765,34 @@ __global__ void __launch_bounds__(32) finish_kernel(LaunchArgs args) {
     }
     int nreg = ns;
 #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nreg += __shfl_xor_sync(kFull, nreg, o);
+    __syncwarp();
+    uint64_t tmax = 0, qsum = 0;
+    double sse = 0.0;
+    if (lane < nreg && lane < kMaxN) {
+        const int x0 = reg[lane][0], y0 = reg[lane][1], x1 = reg[lane][2], y = reg[lane][3];
+        const size_t e = ((size_t)band_index(C, x0, x1) * R + (y - y0 - 1)) * R + y0;
+        const uint64_t tv = RT[e], qv = RQ[e];
+        tmax = tv;
+        qsum = qv;
+        const uint64_t s1 = sat1[y * (C + 1) + x1] - sat1[y0 * (C + 1) + x1] - sat1[y * (C + 1) + x0] +
+                            sat1[y0 * (C + 1) + x0];
+        const uint32_t np = (line_px(x1, fr.W) - line_px(x0, fr.W)) * (line_px(y, fr.H) - line_px(y0, fr.H));
+        uint32_t rem;
+        (void)ceil_square_div(s1, np, &rem);
+        // exact SSE = floor + (ceil(S1^2/N) - S1^2/N)
+        sse = (double)qv + (rem ? (double)(np - rem) / (double)np : 0.0);
+        out->region[lane][0] = (int16_t)x0;
+        out->region[lane][1] = (int16_t)y0;
+        out->region[lane][2] = (int16_t)x1;
+        out->region[lane][3] = (int16_t)y;
+    }
+#pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const uint64_t tm = __shfl_xor_sync(kFull, tmax, o);
         tmax = tm > tmax ? tm : tmax;
         qsum += __shfl_xor_sync(kFull, qsum, o);
         sse += __shfl_xor_sync(kFull, sse, o);
-        nreg += __shfl_xor_sync(kFull, nreg, o);
     }
     if (lane == 0) {
         const uint64_t thr = eq4_threshold(t_min, fr.lambda_q);
