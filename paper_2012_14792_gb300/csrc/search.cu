@@ -190,9 +190,9 @@ __device__ __forceinline__ uint64_t item_rows(const VT *sv, VT *G, int nd, int d
 // Loops run to the larger of the two items' bounds (extra heights hold the
 // saturating infinity), so both halves stay in step.  The staged values
 // already hold the saturating infinity for slices past Eq. 4's bound (step
-// 2).  Half 0 runs item ia, half 1 item ib (none if ib is negative).
+// 2).  Each half runs its item mi (none if mi is negative), described by it.
 template <int STEP, typename VT>
-__device__ void item_pair(const DevFrame &fr, const DevPlan &pl, int ia, int ib, uint64_t *Vall,
+__device__ void item_pair(const DevFrame &fr, const DevPlan &pl, int mi, const PlanItem &it, uint64_t *Vall,
                           const uint64_t *stage, VT *sv, VT *G) {
     const int lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15, y = l;
     const int n = pl.n, R = fr.R, H = fr.H;
@@ -200,10 +200,7 @@ __device__ void item_pair(const DevFrame &fr, const DevPlan &pl, int ia, int ib,
     // G_{k-1} in Ga, G_k into Gb, then swapped; half 1's pair sits 16 words
     // further so that the halves' 32-bit reads fall in different banks
     VT *Ga = G + h * 144, *Gb = Ga + 64;
-    const int mi = h ? ib : ia;
     const bool have = mi >= 0;
-    PlanItem it{0, 0, 1u, 0u, 0, -1};
-    if (have) it = pl.items[mi];
     const int kmax = have ? it.kmax : 0;
     const int dlo = max(1, (int)((it.hlo + kCtu - 1) / kCtu));
     const int nd = have ? (int)(it.hhi / kCtu) - dlo + 1 : 0;  // full-height slices admitted (may be <= 0)
@@ -238,12 +235,32 @@ __device__ void item_pair(const DevFrame &fr, const DevPlan &pl, int ia, int ib,
     const VT *sp = sv + lane;
     for (int k = 2; k <= kmm; ++k) {
         const VT *gp = Ga + y + dlo;
-        VT best = soft;
+        VT best;
+        if (sizeof(VT) == 4) {
+            VT b0 = soft, b1 = soft;  // 32-bit values: two minima, independent chains
+            int i = 0;
+#pragma unroll 2
+            for (; i + 1 < ndm; i += 2) {
+                const VT p0 = gp[i], v0 = sp[i * 32], p1 = gp[i + 1], v1 = sp[(i + 1) * 32];
+                const VT c0 = STEP == 1 ? (p0 > v0 ? p0 : v0) : VT(p0 + v0);
+                const VT c1 = STEP == 1 ? (p1 > v1 ? p1 : v1) : VT(p1 + v1);
+                b0 = c0 < b0 ? c0 : b0;
+                b1 = c1 < b1 ? c1 : b1;
+            }
+            if (i < ndm) {
+                const VT p0 = gp[i], v0 = sp[i * 32];
+                const VT c0 = STEP == 1 ? (p0 > v0 ? p0 : v0) : VT(p0 + v0);
+                b0 = c0 < b0 ? c0 : b0;
+            }
+            best = b0 < b1 ? b0 : b1;
+        } else {
+            best = soft;
 #pragma unroll 4
-        for (int i = 0; i < ndm; ++i) {
-            const VT prev = gp[i], val = sp[i * 32];
-            const VT c = STEP == 1 ? (prev > val ? prev : val) : VT(prev + val);
-            best = c < best ? c : best;
+            for (int i = 0; i < ndm; ++i) {
+                const VT prev = gp[i], val = sp[i * 32];
+                const VT c = STEP == 1 ? (prev > val ? prev : val) : VT(prev + val);
+                best = c < best ? c : best;
+            }
         }
         if (k <= kmax) {  // a half past its kmax runs on, unread
             Gb[y] = best < soft ? best : soft;
@@ -268,38 +285,43 @@ __device__ void item_pair(const DevFrame &fr, const DevPlan &pl, int ia, int ib,
     }
 }
 
-// The items of one tile column two at a time (see item_pair).  Step 2 runs
-// only the items with a window whose step-1 best time meets Eq. 4 (no other
-// window is read again) and pairs them up after that filter.
+// The items of one tile column two at a time (see item_pair), the next
+// pair's descriptions loaded while the current pair runs.  Step 2 runs only
+// the items with a window whose step-1 best time meets Eq. 4 (no other
+// window is read again), listed in order in `list` first, and pairs them
+// up after that filter.  A column has at most 2 x (distinct slice heights)
+// <= 4R items, so kListMax entries hold them for R <= 17.
+constexpr int kListMax = 128;
 template <int STEP, typename VT>
 __device__ void items_paired(const DevFrame &fr, const DevPlan &pl, int i0, int i1, uint64_t *Vall,
-                             const uint64_t *stage, VT *sv, VT *G, uint64_t thr) {
-    const int lane = threadIdx.x & 31;
-    if (STEP == 1) {
-        for (int ii = i0; ii < i1; ii += 2)
-            item_pair<STEP, VT>(fr, pl, ii, ii + 1 < i1 ? ii + 1 : -1, Vall, stage, sv, G);
-        return;
-    }
-    int held = -1;  // a live item waiting for its partner
-    for (int base = i0; base < i1; base += 32) {
-        bool live = false;
-        if (base + lane < i1) {
-            const PlanItem it = pl.items[base + lane];
-            for (int w = it.w_first; w <= it.w_last && !live; ++w) live = fr.wres1[w] <= thr;
-        }
-        unsigned m = __ballot_sync(kFull, live);
-        while (m) {
-            const int i = base + __ffs(m) - 1;
-            m &= m - 1;
-            if (held < 0) {
-                held = i;
-            } else {
-                item_pair<STEP, VT>(fr, pl, held, i, Vall, stage, sv, G);
-                held = -1;
+                             const uint64_t *stage, VT *sv, VT *G, int16_t *list, uint64_t thr) {
+    const int lane = threadIdx.x & 31, h = lane >> 4;
+    int cnt = i1 - i0;
+    if (STEP == 2) {
+        cnt = 0;
+        for (int base = i0; base < i1; base += 32) {
+            bool live = false;
+            if (base + lane < i1) {
+                const PlanItem it = pl.items[base + lane];
+                for (int w = it.w_first; w <= it.w_last && !live; ++w) live = fr.wres1[w] <= thr;
             }
+            const unsigned m = __ballot_sync(kFull, live);
+            if (live) list[cnt + __popc(m & ((1u << lane) - 1u))] = (int16_t)(base + lane - i0);
+            cnt += __popc(m);
         }
+        __syncwarp();
     }
-    if (held >= 0) item_pair<STEP, VT>(fr, pl, held, -1, Vall, stage, sv, G);
+    auto item_at = [&](int j) { return j < cnt ? i0 + (STEP == 1 ? j : (int)list[j]) : -1; };
+    PlanItem nxt{0, 0, 1u, 0u, 0, -1};
+    int mnext = item_at(h);
+    if (mnext >= 0) nxt = pl.items[mnext];
+    for (int p = 0; p < cnt; p += 2) {
+        const PlanItem cur = nxt;
+        const int mi = mnext;
+        mnext = item_at(p + 2 + h);
+        if (mnext >= 0) nxt = pl.items[mnext];
+        item_pair<STEP, VT>(fr, pl, mi, cur, Vall, stage, sv, G);
+    }
 }
 
 // Row DPs, one warp per (frame, tile column): the column's slice values
@@ -309,7 +331,7 @@ __device__ void items_paired(const DevFrame &fr, const DevPlan &pl, int i0, int 
 // admitted slice values are staged per lane and the k loop only reads
 // G_{k-1}[y+d] from shared memory and relaxes.  V[k] = G_k[0] is
 // collected in lane k and stored with one coalesced write per item.
-constexpr int kBandTail = 288;  // per warp after the two staging areas: the G tables
+constexpr int kBandTail = 352;  // per warp after the two staging areas: G tables (288 words), item list (64)
 template <int STEP>
 __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, int total, int stage_words) {
     extern __shared__ uint64_t bsm[];
@@ -340,8 +362,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, i
     uint64_t *stage = bsm + (size_t)wib * (2 * stage_words + kBandTail);
     uint64_t *itm = stage + stage_words;
     uint64_t *gbuf = itm + stage_words;
+    int16_t *list = reinterpret_cast<int16_t *>(gbuf + 288);
     uint32_t tok = 0;  // step 2: bit d-1 set if the slice [lane, lane+d) meets the Eq. 4 bound
-#pragma unroll 4
+#pragma unroll 8
     for (int d = 1; d <= R; ++d) {
         const bool in = lane < R && lane + d <= R;
         const size_t e = in ? (size_t)(d - 1) * R + lane : 0;
@@ -356,12 +379,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, i
         }
     }
     __syncwarp();
-    if (R <= 17 && n <= 16) {
+    if (R <= 17 && n <= 16 && i1 - i0 <= kListMax) {
         if (STEP == 1 && t32)
             items_paired<1, uint32_t>(fr, pl, i0, i1, Vall, stage, reinterpret_cast<uint32_t *>(itm),
-                                      reinterpret_cast<uint32_t *>(gbuf), thr);
+                                      reinterpret_cast<uint32_t *>(gbuf), list, thr);
         else
-            items_paired<STEP, uint64_t>(fr, pl, i0, i1, Vall, stage, itm, gbuf, thr);
+            items_paired<STEP, uint64_t>(fr, pl, i0, i1, Vall, stage, itm, gbuf, list, thr);
         return;
     }
     const uint32_t ytop = line_px(lane, H);
