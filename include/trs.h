@@ -110,7 +110,8 @@ typedef struct trs_tables_layout {
     size_t off_sat_t;    /* uint64 [(R+1)*(C+1)], of Tq */
     size_t off_rect_t;   /* uint64 [bands][R][R]: entry (b, d-1, y) = time of the slice spanning
                             tile column b, CTU rows [y, y+d) (Eq. 1); band b of columns [x0,x1)
-                            has b = x0*(2C-x0+1)/2 + (x1-x0-1); entries with y+d > R are unused */
+                            has b = x0*(2C-x0+1)/2 + (x1-x0-1); entries with y+d > R are
+                            unused and left unwritten */
     size_t off_rect_q;   /* uint64 [bands][R][R]: floor of the slice's luma SSE (Eq. 2), same index */
     size_t off_status;   /* int32 [4]: [0] data status of this frame (TRS_OK / TRS_ERANGE), [1] W, [2] H,
                             [3] 1 if the frame's total Q16 time is below 2^31 */

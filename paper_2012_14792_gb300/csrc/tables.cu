@@ -5,7 +5,8 @@
 //    frame TRS_ERANGE and count as 0).
 //  * Summed-area tables of S1, S2 and Tq over the CTU grid.
 //  * For every tile column b = [x0, x1) and every slice of CTU rows
-//    [y, y + d): its time T = sum of Tq (Eq. 1) and its quality term
+//    [y, y + d) (y + d <= R; other entries are left unwritten): its time
+//    T = sum of Tq (Eq. 1) and its quality term
 //    Q = S2 - ceil(S1^2 / N), the floor of the slice's luma SSE (Eq. 2),
 //    computed exactly with a 128-bit square.  Stored diagonal-major
 //    ([b][d-1][y]) so that the search, which walks one slice height d at a
@@ -107,21 +108,12 @@ __global__ void __launch_bounds__(kTabThreads) tables_kernel(LaunchArgs args) {
     uint64_t *rect_q = reinterpret_cast<uint64_t *>(fr.tables + off.rect_q);
     const int per_band = R * R;
     const int nloc = min(kBandsPerBlock, nb - b0);
-    // entries past the frame's bottom (y + d > R) hold zeros
-    for (int e = t; e < nloc * per_band; e += kTabThreads) {
-        const int lb = e / per_band, rem = e - lb * per_band;
-        const int dm1 = rem / R, y = rem - dm1 * R;
-        if (y + dm1 + 1 > R) {
-            const size_t gi = (size_t)(b0 + lb) * per_band + rem;
-            rect_t[gi] = 0;
-            rect_q[gi] = 0;
-        }
-    }
-    // the R(R+1)/2 slices of a band, enumerated densely so that no lane idles
+    // the R(R+1)/2 slices of each band, enumerated densely so that no lane
+    // idles; entries past the frame's bottom (y + d > R) are left unwritten
     const int per_valid = R * (R + 1) / 2;
+    int lb = t / per_valid, v = t - lb * per_valid;  // entry e = lb * per_valid + v, stepped by kTabThreads
     for (int e = t; e < nloc * per_valid; e += kTabThreads) {
-        const int lb = e / per_valid;
-        const int dy = slice_dy[e - lb * per_valid];
+        const int dy = slice_dy[v];
         const int dm1 = dy >> 8, y = dy & 255, y1 = y + dm1 + 1;
         const size_t gi = (size_t)(b0 + lb) * per_band + (size_t)dm1 * R + y;
         const int x0 = bx0[lb], x1 = bx1[lb];
@@ -134,6 +126,7 @@ __global__ void __launch_bounds__(kTabThreads) tables_kernel(LaunchArgs args) {
         uint32_t r;
         rect_t[gi] = T;
         rect_q[gi] = s2 - ceil_square_div(s1, n, &r);
+        for (v += kTabThreads; v >= per_valid; v -= per_valid) ++lb;
     }
     if (grp == 0) {
         uint32_t *gtq = reinterpret_cast<uint32_t *>(fr.tables + off.tq);

@@ -166,7 +166,7 @@ struct WorkPrefix {
     const int32_t *bands;    // search rows: tile columns (one warp each, all of its items)
 };
 
-constexpr int kBandsPerBlock = 8;
+constexpr int kBandsPerBlock = 16;
 
 struct LaunchArgs {
     DevFrame single;            // used when frames == nullptr
