@@ -56,6 +56,20 @@ __host__ __device__ inline TablesOffsets tables_offsets(int C, int R) {
 }
 
 #ifdef __CUDACC__
+// A float no larger than x (two 32-bit conversions: no 64-bit one).
+__device__ inline float u64_to_float_rz(uint64_t x) {
+    return __fadd_rz(__fmul_rz(__uint2float_rz((uint32_t)(x >> 32)), 4294967296.0f), __uint2float_rz((uint32_t)x));
+}
+
+// floor(f) for 0 <= f < 2^64, exactly: the multiple of 2^32 below f and
+// the rest are both floats (f has 24 significant bits), so neither step
+// rounds.
+__device__ inline uint64_t float_to_u64_rz(float f) {
+    const uint32_t hi = __float2uint_rz(f * 2.3283064365386963e-10f);  // f / 2^32
+    const float rest = f - __uint2float_rz(hi) * 4294967296.0f;
+    return ((uint64_t)hi << 32) + __float2uint_rz(rest);
+}
+
 // floor(x / n) and *rem = x mod n for 1 <= n < 2^32, without a hardware
 // divide: the schoolbook correction of a trial quotient (Knuth, TAOCP vol. 2,
 // Sec. 4.3.1), the trial quotient taken in single precision with every
@@ -65,7 +79,7 @@ __host__ __device__ inline TablesOffsets tables_offsets(int C, int R) {
 __device__ inline uint64_t udivmod_trial(uint64_t x, uint32_t n, float rn, uint64_t *rem) {
     uint64_t q = 0;
     while (x >= n) {
-        uint64_t t = __float2ull_rz(__fmul_rz(__ull2float_rz(x), rn));
+        uint64_t t = float_to_u64_rz(__fmul_rz(u64_to_float_rz(x), rn));
         t = t ? t : 1;  // x >= n: at least one n fits
         q += t;
         x -= t * n;
