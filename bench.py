@@ -133,9 +133,12 @@ def ncu_traffic(stage: str, frames: int):
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             k = json.load(f)["kernels"][stage]
-        with open(os.path.join(ROOT, k["source"]), "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest()[:16] != k["source_sha256_16"]:
-                return None
+        h = hashlib.sha256()
+        for src in k["sources"]:  # the kernel's file and the headers it compiles with
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest()[:16] != k["sources_sha256_16"]:
+            return None
         return (k["dram_read_bytes"] + k["dram_write_bytes"]) * frames / k["frames"]
     except Exception:
         return None

@@ -228,10 +228,10 @@ int prepare_search_kernels();
 int launch_texture(const LaunchArgs &a, int total_ctus, void *stream);
 int launch_tables(const LaunchArgs &a, int total_groups, int maxC, int maxR, void *stream);
 // Launch shapes of the search kernels, chosen by trs_autotune.
-struct SearchTune {
-    int band_warps = 4;  // warps per block of the row-DP kernels (2, 4 or 8)
-    int col_warps = 4;   // warps sharing one window's column DP, one block per window (2, 4 or 8)
-    int col_batch = 8;   // candidate steps whose V rows a column-DP warp loads together (4 or 8)
+struct SearchTune {  // defaults: what trs_autotune picks for 2160p frames on GB300
+    int band_warps = 2;  // warps per block of the row-DP kernels (2, 4 or 8)
+    int col_warps = 2;   // warps sharing one window's column DP, one block per window (1, 2, 4 or 8)
+    int col_batch = 4;   // candidate steps whose V rows a column-DP warp loads together (4 or 8)
 };
 
 // scal: the T_min / Q* words of every frame of the launch (reset to +inf first).
