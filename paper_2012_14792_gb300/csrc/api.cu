@@ -666,6 +666,15 @@ void batch_describe(BatchLaunch &bl, uint8_t *hb, uint8_t *db, int nf, PlanEntry
     bl.groups = pg[nf];
     bl.bands = pb[nf];
     bl.windows = pw[nf];
+    bl.uniform = 1;
+    for (int i = 1; i < nf && bl.uniform; ++i) bl.uniform = pe[i] == pe[0];
+    if (nf > 0) {
+        bl.u_ctus = pc[1];
+        bl.u_groups = pg[1];
+        bl.u_items = pi[1];
+        bl.u_windows = pw[1];
+        bl.u_bands = pb[1];
+    }
 }
 
 cudaError_t batch_enqueue_work(const BatchLaunch &bl, cudaStream_t cs, cudaEvent_t *stage, cudaEvent_t after_texture) {
@@ -677,6 +686,14 @@ cudaError_t batch_enqueue_work(const BatchLaunch &bl, cudaStream_t cs, cudaEvent
     a.pre.items = (const int32_t *)(bl.db + bl.fr_bytes + 2 * bl.pre_bytes);
     a.pre.windows = (const int32_t *)(bl.db + bl.fr_bytes + 3 * bl.pre_bytes);
     a.pre.bands = (const int32_t *)(bl.db + bl.fr_bytes + 4 * bl.pre_bytes);
+    if (bl.uniform) {
+        a.uniform = 1;
+        a.single_ctus = bl.u_ctus;
+        a.single_bandgrp = bl.u_groups;
+        a.single_items = bl.u_items;
+        a.single_windows = bl.u_windows;
+        a.single_bands = bl.u_bands;
+    }
     const bool events = stage != nullptr;
     auto mark = [&](int i, cudaError_t e) {
         if (events && e == cudaSuccess) e = record_event(stage[i], cs);

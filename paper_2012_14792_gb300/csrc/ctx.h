@@ -97,6 +97,8 @@ struct BatchLaunch {
     uint8_t *hb = nullptr, *db = nullptr;
     size_t blob = 0, fr_bytes = 0, pre_bytes = 0;
     int nf = 0, ctus = 0, groups = 0, bands = 0, windows = 0, maxC = 1, maxR = 1, maxN = 1;
+    // every frame has the same plan: the work units of one frame
+    int uniform = 0, u_ctus = 0, u_groups = 0, u_items = 0, u_windows = 0, u_bands = 0;
     uint32_t *flags_dev = nullptr;  // nf words, zeroed by the launch
     uint64_t *scal_dev = nullptr;   // nf * 4 words, reset by the launch
     SearchTune tune;

@@ -187,18 +187,28 @@ struct LaunchArgs {
     const DevFrame *frames;     // device array of nframes, or nullptr
     int nframes;
     WorkPrefix pre;             // device arrays (unused when nframes == 1 and frames == nullptr)
+    // work units of the single frame; with `uniform` (every frame of the
+    // array has the same plan) the units of each frame of the array
     int single_ctus, single_bandgrp, single_items, single_windows, single_bands;
+    int uniform;
 };
 
 __device__ inline const DevFrame &frame_at(const LaunchArgs &a, int f) {
     return a.frames ? a.frames[f] : a.single;
 }
 
-// Maps a global work index to (frame, local index) through a prefix array.
+// Maps a global work index to (frame, local index): by a division when
+// every frame has the same number of units, else by binary search through
+// the prefix array.
 __device__ inline int locate(const LaunchArgs &a, const int32_t *pre, int single_count, int g, int *local) {
     if (!a.frames) {
         *local = g;
         return 0;
+    }
+    if (a.uniform) {
+        const int f = g / single_count;
+        *local = g - f * single_count;
+        return f;
     }
     int lo = 0, hi = a.nframes - 1;
     while (lo < hi) {
