@@ -191,7 +191,7 @@ __device__ __forceinline__ uint64_t item_rows(const VT *sv, VT *G, int nd, int d
 // saturating infinity), so both halves stay in step.  The staged values
 // already hold the saturating infinity for slices past Eq. 4's bound (step
 // 2).  Each half runs its item mi (none if mi is negative), described by it.
-template <int STEP, typename VT>
+template <int STEP, typename VT, int S>
 __device__ void item_pair(const DevFrame &fr, const DevPlan &pl, int mi, const PlanItem &it, uint64_t *Vall,
                           const uint64_t *stage, VT *sv, VT *G) {
     const int lane = threadIdx.x & 31, h = lane >> 4, l = lane & 15, y = l;
@@ -208,11 +208,11 @@ __device__ void item_pair(const DevFrame &fr, const DevPlan &pl, int mi, const P
     const int kmm = max(kmax, __shfl_xor_sync(kFull, kmax, 16));
     __syncwarp();  // every lane is done with the previous pair's tables
     for (int i = 0; i < ndm; ++i)
-        sv[i * 32 + lane] = i < nd ? (VT)stage[(dlo + i - 1) * 32 + y] : soft;
+        sv[i * 32 + lane] = i < nd ? (VT)stage[(dlo + i - 1) * S + y] : soft;
     // G_1: the single slice [y, R), for y = l and for row 16
     auto last_slice = [&](int yy) -> VT {
         const uint32_t hh = (uint32_t)H - line_px(yy, H);
-        return have && yy < R && hh >= it.hlo && hh <= it.hhi ? (VT)stage[(R - yy - 1) * 32 + yy] : soft;
+        return have && yy < R && hh >= it.hlo && hh <= it.hhi ? (VT)stage[(R - yy - 1) * S + yy] : soft;
     };
     const VT g16 = last_slice(16);
     Gb[y] = kmax >= 1 ? last_slice(y) : soft;
@@ -288,22 +288,44 @@ __device__ void item_pair(const DevFrame &fr, const DevPlan &pl, int mi, const P
 // The items of one tile column two at a time (see item_pair), the next
 // pair's descriptions loaded while the current pair runs.  Step 2 runs only
 // the items with a window whose step-1 best time meets Eq. 4 (no other
-// window is read again), listed in order in `list` first, and pairs them
-// up after that filter.  A column has at most 2 x (distinct slice heights)
-// <= 4R items, so kListMax entries hold them for R <= 17.
+// window is read again): the frame's windows that meet it are first marked
+// in a bit mask, then the live items listed in order in `list` and paired.
+// A column has at most 2 x (distinct slice heights) <= 4R items, so
+// kListMax entries hold them for R <= 17.
 constexpr int kListMax = 128;
-template <int STEP, typename VT>
+constexpr int kMaskWindows = 1024;  // windows the step-2 bit mask covers (more: tested per item)
+template <int STEP, typename VT, int S>
 __device__ void items_paired(const DevFrame &fr, const DevPlan &pl, int i0, int i1, uint64_t *Vall,
-                             const uint64_t *stage, VT *sv, VT *G, int16_t *list, uint64_t thr) {
+                             const uint64_t *stage, VT *sv, VT *G, int16_t *list, uint32_t *wmask,
+                             uint64_t thr) {
     const int lane = threadIdx.x & 31, h = lane >> 4;
     int cnt = i1 - i0;
     if (STEP == 2) {
+        const int nwin = pl.nwin;
+        const bool masked = nwin <= kMaskWindows;
+        if (masked) {
+            for (int w0 = 0; w0 < nwin; w0 += 32) {
+                const bool ok = w0 + lane < nwin && fr.wres1[w0 + lane] <= thr;
+                const unsigned m = __ballot_sync(kFull, ok);
+                if (lane == 0) wmask[w0 >> 5] = m;
+            }
+            __syncwarp();
+        }
         cnt = 0;
         for (int base = i0; base < i1; base += 32) {
             bool live = false;
             if (base + lane < i1) {
                 const PlanItem it = pl.items[base + lane];
-                for (int w = it.w_first; w <= it.w_last && !live; ++w) live = fr.wres1[w] <= thr;
+                if (masked) {
+                    for (int w = it.w_first; w <= it.w_last && !live; w = (w | 31) + 1) {
+                        const int hi = min(it.w_last, w | 31);
+                        const uint32_t bits = wmask[w >> 5] >> (w & 31);
+                        const int span = hi - w + 1;  // 1..32
+                        live = (span == 32 ? bits : bits & ((1u << span) - 1u)) != 0u;
+                    }
+                } else {
+                    for (int w = it.w_first; w <= it.w_last && !live; ++w) live = fr.wres1[w] <= thr;
+                }
             }
             const unsigned m = __ballot_sync(kFull, live);
             if (live) list[cnt + __popc(m & ((1u << lane) - 1u))] = (int16_t)(base + lane - i0);
@@ -320,20 +342,23 @@ __device__ void items_paired(const DevFrame &fr, const DevPlan &pl, int i0, int 
         const int mi = mnext;
         mnext = item_at(p + 2 + h);
         if (mnext >= 0) nxt = pl.items[mnext];
-        item_pair<STEP, VT>(fr, pl, mi, cur, Vall, stage, sv, G);
+        item_pair<STEP, VT, S>(fr, pl, mi, cur, Vall, stage, sv, G);
     }
 }
 
 // Row DPs, one warp per (frame, tile column): the column's slice values
-// for every height d are staged once in shared memory (stage[(d-1)*32 + y];
-// step 2 also keeps, per lane, a bit per height for the Eq. 4 bound on the
-// slice time), then every item of the column runs from there: its
-// admitted slice values are staged per lane and the k loop only reads
-// G_{k-1}[y+d] from shared memory and relaxes.  V[k] = G_k[0] is
+// for every height d are staged once in shared memory (stage[(d-1)*S + y],
+// S = 17 when every frame of the launch has at most 17 CTU rows and n <= 16,
+// else 32; step 2 stages the saturating infinity for slices past Eq. 4's
+// bound), then the column's items run from there (items_paired, or one at a
+// time through item_rows for taller frames or n > 16).  V[k] = G_k[0] is
 // collected in lane k and stored with one coalesced write per item.
-constexpr int kBandTail = 352;  // per warp after the two staging areas: G tables (288 words), item list (64)
-template <int STEP>
-__global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, int total, int stage_words) {
+// per warp after the two staging areas: G tables (288 words), item list
+// (64), step-2 window mask (16)
+constexpr int kBandTail = 368;
+template <int STEP, int S>
+__global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, int total, int stage_words,
+                                                               int itm_words) {
     extern __shared__ uint64_t bsm[];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
@@ -359,10 +384,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, i
     const uint64_t *RQ = reinterpret_cast<const uint64_t *>(fr.tables + off.rect_q) + base;
     // per warp: the column's slice values by height, one item's admitted
     // values, and the G tables (288 words)
-    uint64_t *stage = bsm + (size_t)wib * (2 * stage_words + kBandTail);
+    uint64_t *stage = bsm + (size_t)wib * (stage_words + itm_words + kBandTail);
     uint64_t *itm = stage + stage_words;
-    uint64_t *gbuf = itm + stage_words;
+    uint64_t *gbuf = itm + itm_words;
     int16_t *list = reinterpret_cast<int16_t *>(gbuf + 288);
+    uint32_t *wmask = reinterpret_cast<uint32_t *>(gbuf + 352);
     uint32_t tok = 0;  // step 2: bit d-1 set if the slice [lane, lane+d) meets the Eq. 4 bound
 #pragma unroll 8
     for (int d = 1; d <= R; ++d) {
@@ -372,19 +398,21 @@ __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, i
         if (STEP == 2) {
             // slices past the Eq. 4 bound hold the saturating infinity
             const bool meets = in && tv <= thr;
-            stage[(d - 1) * 32 + lane] = meets ? __ldg(RQ + e) : kSoft;
+            const uint64_t qv = __ldg(RQ + e);
+            if (lane < S) stage[(d - 1) * S + lane] = meets ? qv : kSoft;
             tok |= (meets ? 1u : 0u) << (d - 1);
         } else {
-            stage[(d - 1) * 32 + lane] = tv;
+            if (lane < S) stage[(d - 1) * S + lane] = tv;
         }
     }
     __syncwarp();
+    // with S = 17 every column takes this path (R <= 17 admits at most 68 items)
     if (R <= 17 && n <= 16 && i1 - i0 <= kListMax) {
         if (STEP == 1 && t32)
-            items_paired<1, uint32_t>(fr, pl, i0, i1, Vall, stage, reinterpret_cast<uint32_t *>(itm),
-                                      reinterpret_cast<uint32_t *>(gbuf), list, thr);
+            items_paired<1, uint32_t, S>(fr, pl, i0, i1, Vall, stage, reinterpret_cast<uint32_t *>(itm),
+                                         reinterpret_cast<uint32_t *>(gbuf), list, wmask, thr);
         else
-            items_paired<STEP, uint64_t>(fr, pl, i0, i1, Vall, stage, itm, gbuf, list, thr);
+            items_paired<STEP, uint64_t, S>(fr, pl, i0, i1, Vall, stage, itm, gbuf, list, wmask, thr);
         return;
     }
     const uint32_t ytop = line_px(lane, H);
@@ -411,7 +439,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, i
                 const int d = dmin + i, y1 = lane + d;
                 const uint32_t h = line_px(y1, H) - ytop;
                 const bool ok = lane < R && y1 <= R && h >= it.hlo && h <= it.hhi;
-                sv[i * 32 + lane] = ok ? (uint32_t)stage[(d - 1) * 32 + lane] : Soft<uint32_t>::v;
+                sv[i * 32 + lane] = ok ? (uint32_t)stage[(d - 1) * S + lane] : Soft<uint32_t>::v;
             }
             vreg = item_rows<1, uint32_t>(sv, reinterpret_cast<uint32_t *>(gbuf), nd, dmin, it.kmax, R);
         } else {
@@ -420,7 +448,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, i
                 const uint32_t h = line_px(y1, H) - ytop;
                 const bool ok = lane < R && y1 <= R && h >= it.hlo && h <= it.hhi &&
                                 (STEP == 1 || ((tok >> (d - 1)) & 1u));
-                itm[i * 32 + lane] = ok ? stage[(d - 1) * 32 + lane] : kSoft;
+                itm[i * 32 + lane] = ok ? stage[(d - 1) * S + lane] : kSoft;
             }
             vreg = item_rows<STEP, uint64_t>(itm, gbuf, nd, dmin, it.kmax, R);
         }
@@ -850,8 +878,10 @@ int prepare_search_kernels() {
     const int col_smem = (kMaxC + 1) * (kMaxN + 1) * (int)sizeof(uint64_t) + num_bands(kMaxC) * (int)sizeof(int32_t);
     const int rb_smem = ((kMaxN + 1) * 32 + kMaxR * 32) * (int)sizeof(uint64_t);
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaFuncSetAttribute(band_kernel<1>, A, band_smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(band_kernel<2>, A, band_smem);
+    cudaError_t e = cudaFuncSetAttribute(band_kernel<1, 17>, A, band_smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(band_kernel<1, 32>, A, band_smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(band_kernel<2, 17>, A, band_smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(band_kernel<2, 32>, A, band_smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(column_kernel<1, 4>, A, col_smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(column_kernel<1, 8>, A, col_smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(column_kernel<2, 4>, A, col_smem);
@@ -869,8 +899,10 @@ int launch_search(const LaunchArgs &a, int total_bands, int total_windows, int m
     if ((steps & 1) && scal) e = cudaMemsetAsync(scal, 0xff, nscal * sizeof(uint64_t), s);
     if (e != cudaSuccess) return (int)e;
     const int bw = t.band_warps, cw = t.col_warps;
-    const int stage_words = maxR * 32;
-    const size_t band_smem = (size_t)bw * (2 * stage_words + kBandTail) * sizeof(uint64_t);
+    const int stage_words = maxR * 32;  // rebuild's staging (stride 32)
+    const int S = maxR <= 17 && maxN <= 16 ? 17 : 32;
+    const int band_stage = maxR * S, band_itm = maxR * 32;
+    const size_t band_smem = (size_t)bw * (band_stage + band_itm + kBandTail) * sizeof(uint64_t);
     const int h_words = (maxC + 1) * (maxN + 1);
     const size_t col_smem = (size_t)h_words * sizeof(uint64_t) + (size_t)num_bands(maxC) * sizeof(int32_t);
     const int bb = (total_bands + bw - 1) / bw;
@@ -889,13 +921,19 @@ int launch_search(const LaunchArgs &a, int total_bands, int total_windows, int m
         }
     };
     if (steps & 1) {
-        if (total_bands > 0) band_kernel<1><<<bb, bw * 32, band_smem, s>>>(a, total_bands, stage_words);
+        if (total_bands > 0) {
+            if (S == 17) band_kernel<1, 17><<<bb, bw * 32, band_smem, s>>>(a, total_bands, band_stage, band_itm);
+            else band_kernel<1, 32><<<bb, bw * 32, band_smem, s>>>(a, total_bands, band_stage, band_itm);
+        }
         mark(0);
         columns(1);
         mark(1);
     }
     if (!(steps & 2)) return e != cudaSuccess ? (int)e : (int)cudaGetLastError();
-    if (total_bands > 0) band_kernel<2><<<bb, bw * 32, band_smem, s>>>(a, total_bands, stage_words);
+    if (total_bands > 0) {
+        if (S == 17) band_kernel<2, 17><<<bb, bw * 32, band_smem, s>>>(a, total_bands, band_stage, band_itm);
+        else band_kernel<2, 32><<<bb, bw * 32, band_smem, s>>>(a, total_bands, band_stage, band_itm);
+    }
     mark(2);
     columns(2);
     mark(3);
