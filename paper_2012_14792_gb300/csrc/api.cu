@@ -338,7 +338,8 @@ static int search_one(trs_ctx *ctx, const void *tables, int W, int H, int n, flo
     a.single_items = nitems;
     a.single_windows = nwin;
     a.single_bands = pe->host.nb;
-    TRS_CK((cudaError_t)launch_search(a, pe->host.nb, nwin, f.C, f.R, n, f.scal, 4, stream, nullptr, &ctx->tune));
+    TRS_CK((cudaError_t)launch_search(a, pe->host.nb, nwin, f.C, f.R, n, f.scal, 4, stream, nullptr, &ctx->tune, 3,
+                                      pe->host.max_nd));
     return TRS_OK;
 }
 
@@ -401,7 +402,7 @@ int trs_search_lambdas(trs_ctx *ctx, const void *tables, int W, int H, int n, co
     one.single_windows = (int)pe->host.win_a.size();
     one.single_bands = pe->host.nb;
     TRS_CK((cudaError_t)launch_search(one, pe->host.nb, one.single_windows, pe->host.C, pe->host.R, n, scal, 4, s,
-                                      nullptr, &ctx->tune, 1));
+                                      nullptr, &ctx->tune, 1, pe->host.max_nd));
     for (int i = 1; i < nl; ++i)  // T_min of step 1 for every lambda
         TRS_CK(cudaMemcpyAsync(scal + 4 * i, scal, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
     LaunchArgs all{};
@@ -411,7 +412,7 @@ int trs_search_lambdas(trs_ctx *ctx, const void *tables, int W, int H, int n, co
     all.pre.windows = (const int32_t *)(bl.db + bl.fr_bytes + 3 * bl.pre_bytes);
     all.pre.bands = (const int32_t *)(bl.db + bl.fr_bytes + 4 * bl.pre_bytes);
     TRS_CK((cudaError_t)launch_search(all, bl.bands, bl.windows, pe->host.C, pe->host.R, n, scal, (size_t)nl * 4, s,
-                                      nullptr, &ctx->tune, 2));
+                                      nullptr, &ctx->tune, 2, pe->host.max_nd));
     return TRS_OK;
 }
 
@@ -651,6 +652,7 @@ void batch_describe(BatchLaunch &bl, uint8_t *hb, uint8_t *db, int nf, PlanEntry
     int32_t *pb = (int32_t *)(hb + bl.fr_bytes + 4 * bl.pre_bytes);
     pc[0] = pg[0] = pi[0] = pw[0] = pb[0] = 0;
     bl.maxC = bl.maxR = bl.maxN = 1;
+    bl.maxND = 0;
     for (int i = 0; i < nf; ++i) {
         const HostPlan &hp = pe[i]->host;
         pc[i + 1] = pc[i] + hp.C * hp.R;
@@ -661,6 +663,7 @@ void batch_describe(BatchLaunch &bl, uint8_t *hb, uint8_t *db, int nf, PlanEntry
         bl.maxC = hp.C > bl.maxC ? hp.C : bl.maxC;
         bl.maxR = hp.R > bl.maxR ? hp.R : bl.maxR;
         bl.maxN = hp.n > bl.maxN ? hp.n : bl.maxN;
+        bl.maxND = hp.max_nd > bl.maxND ? hp.max_nd : bl.maxND;
     }
     bl.ctus = pc[nf];
     bl.groups = pg[nf];
@@ -708,7 +711,7 @@ cudaError_t batch_enqueue_work(const BatchLaunch &bl, cudaStream_t cs, cudaEvent
     e = mark(2, e);
     if (e == cudaSuccess)
         e = (cudaError_t)launch_search(a, bl.bands, bl.windows, bl.maxC, bl.maxR, bl.maxN, bl.scal_dev,
-                                       (size_t)bl.nf * 4, cs, events ? stage + 3 : nullptr, &bl.tune);
+                                       (size_t)bl.nf * 4, cs, events ? stage + 3 : nullptr, &bl.tune, 3, bl.maxND);
     return e;
 }
 

@@ -96,7 +96,7 @@ void drop_graphs(trs_ctx *ctx);
 struct BatchLaunch {
     uint8_t *hb = nullptr, *db = nullptr;
     size_t blob = 0, fr_bytes = 0, pre_bytes = 0;
-    int nf = 0, ctus = 0, groups = 0, bands = 0, windows = 0, maxC = 1, maxR = 1, maxN = 1;
+    int nf = 0, ctus = 0, groups = 0, bands = 0, windows = 0, maxC = 1, maxR = 1, maxN = 1, maxND = 0;
     // every frame has the same plan: the work units of one frame
     int uniform = 0, u_ctus = 0, u_groups = 0, u_items = 0, u_windows = 0, u_bands = 0;
     uint32_t *flags_dev = nullptr;  // nf words, zeroed by the launch

@@ -66,6 +66,7 @@ int build_plan(int W, int H, int n, int k, HostPlan *p, int window_step) {
             p->band_x1[b] = (int16_t)x1;
         }
     p->items.clear();
+    p->max_nd = 0;
     p->slot_of.assign((size_t)nwin * p->nb, -1);
     p->band_items.assign(p->nb + 1, 0);
     for (int b = 0; b < p->nb; ++b) {
@@ -91,6 +92,8 @@ int build_plan(int W, int H, int n, int k, HostPlan *p, int window_step) {
             it.hlo = hs[ilo];
             it.hhi = hs[ihi];
             it.kmax = std::min(std::min(n, R), (int)(H / it.hlo));
+            const int dlo = std::max(1, (int)((it.hlo + kCtu - 1) / kCtu));
+            p->max_nd = std::max(p->max_nd, (int)(it.hhi / kCtu) - dlo + 1);
             prev_lo = ilo;
             prev_hi = ihi;
             prev_slot = (int)p->items.size();

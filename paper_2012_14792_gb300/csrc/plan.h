@@ -16,6 +16,7 @@ struct HostPlan {
     std::vector<int32_t> slot_of;
     std::vector<int16_t> band_x0, band_x1;
     std::vector<int32_t> band_items;  // [nb+1] prefix of items per band
+    int max_nd = 0;  // most full-CTU slice heights an item admits (sizes the row DP's staging)
 };
 
 struct SearchScratch {

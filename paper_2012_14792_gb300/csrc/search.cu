@@ -33,6 +33,8 @@
 //                       decoded into trs_partition.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "trs_internal.cuh"
 
 namespace trs {
@@ -891,7 +893,8 @@ int prepare_search_kernels() {
 }
 
 int launch_search(const LaunchArgs &a, int total_bands, int total_windows, int maxC, int maxR, int maxN,
-                  uint64_t *scal, size_t nscal, void *stream, cudaEvent_t *ev, const SearchTune *tune, int steps) {
+                  uint64_t *scal, size_t nscal, void *stream, cudaEvent_t *ev, const SearchTune *tune, int steps,
+                  int max_nd) {
     const SearchTune t = tune ? *tune : SearchTune{};
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
@@ -901,7 +904,9 @@ int launch_search(const LaunchArgs &a, int total_bands, int total_windows, int m
     const int bw = t.band_warps, cw = t.col_warps;
     const int stage_words = maxR * 32;  // rebuild's staging (stride 32)
     const int S = maxR <= 17 && maxN <= 16 ? 17 : 32;
-    const int band_stage = maxR * S, band_itm = maxR * 32;
+    // the per-item staging holds the admitted full-height values (at most
+    // max_nd heights) in the paired path, up to R heights in the other
+    const int band_stage = maxR * S, band_itm = (S == 17 && max_nd > 0 ? std::min(max_nd, maxR) : maxR) * 32;
     const size_t band_smem = (size_t)bw * (band_stage + band_itm + kBandTail) * sizeof(uint64_t);
     const int h_words = (maxC + 1) * (maxN + 1);
     const size_t col_smem = (size_t)h_words * sizeof(uint64_t) + (size_t)num_bands(maxC) * sizeof(int32_t);

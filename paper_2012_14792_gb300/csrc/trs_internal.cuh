@@ -246,10 +246,11 @@ struct SearchTune {  // defaults: what trs_autotune picks for 2160p frames on GB
 
 // scal: the T_min / Q* words of every frame of the launch (reset to +inf first).
 // ev (optional, 6 events): recorded after each of the six search kernels.
-// maxC / maxR / maxN: largest C, R and n over the frames of the launch (shared-memory sizing).
+// maxC / maxR / maxN: largest C, R and n over the frames of the launch (shared-memory sizing);
+// max_nd: largest HostPlan::max_nd over them (0: size for maxR heights).
 int launch_search(const LaunchArgs &a, int total_bands, int total_windows, int maxC, int maxR, int maxN,
                   uint64_t *scal, size_t nscal, void *stream, cudaEvent_t *ev = nullptr,
-                  const SearchTune *tune = nullptr, int steps = 3);
+                  const SearchTune *tune = nullptr, int steps = 3, int max_nd = 0);
 // steps: 1 = step 1 only (resets scal first), 2 = step 2, rebuild and decode
 // only (scal[0] must already hold T_min and scal[1] +infinity), 3 = both.
 
