@@ -37,6 +37,7 @@ METRIC = "TRS partition decisions/sec at 2160p (batched vs plain); p50/p99 laten
 UNIT = "decisions/s"
 NFRAMES = 64
 PARTS = 2  # chunks a captured batch is pipelined in (trs_set_batch_parts)
+IN_FLIGHT = 2  # batches in flight in the timed stream of steps
 N_REGIONS = 16
 LAMBDA = 0.1
 WORKLOAD = "3840x2160p10 moving-blob sequence, 64 frames, n=16, lambda=0.1, k=3"
@@ -347,6 +348,8 @@ def main():
     ap.add_argument("--no-light", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default launch shapes (short profiling runs)")
+    ap.add_argument("--in-flight", type=int, default=IN_FLIGHT, choices=[1, 2, 3],
+                    help="batches in flight (contexts on separate streams)")
     ap.add_argument("--parts", type=int, default=PARTS, choices=[1, 2, 3, 4],
                     help="chunks a captured batch is pipelined in")
     ap.add_argument("--frames", type=int, default=NFRAMES,
@@ -399,27 +402,60 @@ def main():
         if dist:
             dist.barrier()
 
-    # --- batched, timed --------------------------------------------------
+    # --- batched, timed: a stream of batches, IN_FLIGHT of them in flight ----
+    # Each step decides the whole 64-frame batch through trs_batch_decide.
+    # Consecutive steps alternate between IN_FLIGHT contexts, each on its own
+    # CUDA stream (double-buffered submission, as a serving pipeline runs),
+    # so one batch's HBM-bound texture map overlaps another's ALU-bound search.
     tune = None if args.no_tune else dec.autotune(ins)  # launch shapes picked on this workload
     trs.trs_set_batch_parts(dec.ctx, args.parts)
-    for _ in range(args.warmup):
-        dec.batch_decide(ins, out)
-    sync_all()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    launches = trs.trs_batch_kernels(dec.ctx) * args.steps  # the same graph every step
-    with ClockSampler(local) as clk:
+    decs = [dec] + [runtime.Decider(max_width=3840, max_height=2160, max_regions=N_REGIONS, max_batch=nfr,
+                                    device=local) for _ in range(args.in_flight - 1)]
+    outs = [out] + [torch.zeros_like(out) for _ in range(args.in_flight - 1)]
+    streams = [torch.cuda.Stream(dev) for _ in range(args.in_flight)]
+    for d in decs[1:]:
+        if tune is not None:
+            trs.trs_set_tune(d.ctx, tune["band_warps"], tune["col_warps"], tune["col_batch"])
+        trs.trs_set_batch_parts(d.ctx, args.parts)
+
+    def run_steps(count: int, flight: int):
+        for s in range(count):
+            i = s % flight
+            with torch.cuda.stream(streams[i]):
+                decs[i].batch_decide(ins, outs[i])
+
+    def timed(count: int, flight: int) -> float:
+        """Device time of `count` steps: every stream starts after ev0, ev1 after all of them."""
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        for _ in range(args.steps):
-            dec.batch_decide(ins, out)
+        for st in streams[:flight]:
+            st.wait_event(ev0)
+        run_steps(count, flight)
+        for st in streams[:flight]:
+            e = torch.cuda.Event()
+            e.record(st)
+            stream.wait_event(e)
         ev1.record(stream)
         sync_all()
-    ms = ev0.elapsed_time(ev1)
-    stage_overlap = trs.trs_batch_stage_ms(dec.ctx)  # CUDA events inside the graph, last timed step
-    overlap_frames = trs.trs_batch_stage_frames(dec.ctx)  # the first half of the batch
+        return ev0.elapsed_time(ev1)
+
+    run_steps(max(args.warmup, args.in_flight), args.in_flight)
+    sync_all()
+    launches = trs.trs_batch_kernels(dec.ctx) * args.steps  # the same graph every step
+    with ClockSampler(local) as clk:
+        ms = timed(args.steps, args.in_flight)
+    stage_overlap = trs.trs_batch_stage_ms(dec.ctx)  # CUDA events inside the graph (this context's last step)
+    overlap_frames = trs.trs_batch_stage_frames(dec.ctx)  # the first chunk of the batch
     ms = max_over_ranks(ms, dist, dev)
     value = job_throughput(nfr * args.steps, world, ms / 1e3)
     parts = dec.partitions(out, nfr)
     assert all(p.status == 0 for p in parts), [p.status for p in parts]
+    for o in outs[1:]:
+        assert bytes(o.cpu().numpy()) == bytes(out.cpu().numpy())  # every context decides the same bytes
+    # the same steps one batch at a time on one stream
+    one_ms = max_over_ranks(timed(max(3, args.steps // 2), 1), dist, dev)
+    one_batch = {"value": job_throughput(nfr * max(3, args.steps // 2), world, one_ms / 1e3), "unit": UNIT,
+                 "ms_per_step": one_ms / max(3, args.steps // 2), "form": "one batch in flight, one stream"}
 
     # --- kernels alone: the batch as one launch chain, no second half running
     # beside it; the per-kernel durations of the roofline, averaged over steps
@@ -548,8 +584,11 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
                 "config": {"workload": WORKLOAD if nfr == NFRAMES else f"{WORKLOAD} (first {nfr} frames)",
-                           "frames_per_step": nfr, "form": f"batched, CUDA graph, {args.parts} pipelined chunks",
+                           "frames_per_step": nfr,
+                           "form": f"batched, CUDA graph, {args.parts} pipelined chunks, "
+                                   f"{args.in_flight} batches in flight (contexts on separate streams)",
                            "l2": f"inputs {nfr * 16588800 / 1e9:.2f} GB per step > L2, no flush"},
+                "one_batch_in_flight": one_batch,
                 "plain": {"value": plain_value, "unit": UNIT, "form": "one frame per launch chain"},
                 "stage_ms": stage, "stage_frames": stage_frames,
                 "stage_ms_overlapped": stage_overlap, "stage_frames_overlapped": overlap_frames,
@@ -559,7 +598,8 @@ def main():
                 "gpu_launches": launches, "roofline": roof, "roofline_texture": tex_roof,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
-    dec.close()
+    for d in decs:
+        d.close()
     if dist:
         dist.destroy_process_group()
 
