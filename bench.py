@@ -586,6 +586,16 @@ def main():
                 "frac": tex_gbs / hbm, "traffic": ncu_traffic("texture", stage_frames), "algorithmic_bytes": tex_bytes,
                 "peak_source": src}
 
+    # the candidate space the exact search covers (distinct partitions of S(n), one tile row)
+    space = trs.trs_count_partitions(3840, 2160, N_REGIONS)
+    search_ms = sum(stage.get(k, 0.0) for k in ("step1_rows", "step1_columns", "step2_rows", "step2_columns",
+                                                "rebuild", "decode"))
+    search_space = {"partitions": space,
+                    "effective_candidates_per_s": space * value,
+                    "effective_candidates_per_s_search_only": space * nfr / (search_ms / 1e3) if search_ms else None,
+                    "note": "|S(n)| at 3840x2160, n = 16, k = 3 (exact count, one tile row: tile rows add codes, "
+                            "not partitions) x decisions/s; search only: over the search kernels' one-chunk time"}
+
     serving = None
     if not args.no_serving:
         serving = run_serving(trs, local)
@@ -614,6 +624,7 @@ def main():
                 "serving": serving,
                 "clocks": clk.summary(), "e2e": e2e,
                 "gpu_launches": launches, "roofline": roof, "roofline_texture": tex_roof,
+                "search_space": search_space,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     for d in decs:

@@ -178,6 +178,14 @@ int trs_plan_stats(int width, int height, int n_regions, int k_area, int *n_wind
  * minimum.  Pure host arithmetic. */
 int trs_plan_work(int width, int height, int n_regions, int k_area, double *row_relax, double *col_relax);
 
+/* Host only: the number of distinct partitions the search chooses among,
+ * i.e. of S(n) (exactly n slices, slices of whole CTU rows inside tile
+ * columns, k*A_min > A_max in luma samples, Sec. 2.3) with one tile row --
+ * tile rows add codes but no new partition.  Exact (128-bit counting DPs,
+ * each partition counted once at its smallest slice area), returned as a
+ * double.  For reporting candidates per second; TRS_EINVAL on bad shapes. */
+int trs_count_partitions(int width, int height, int n_regions, int k_area, double *count);
+
 /* Measured INT32 throughput of the device (32-bit add / min / max chains
  * over every SM, CUDA-event timed, best of three), in operations per
  * second: the peak the search kernels' arithmetic is compared with. */

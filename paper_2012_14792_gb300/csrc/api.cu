@@ -159,6 +159,14 @@ int trs_plan_work(int width, int height, int n, int k, double *row_relax, double
     return TRS_OK;
 }
 
+int trs_count_partitions(int width, int height, int n, int k, double *count) {
+    if (!count) return TRS_EINVAL;
+    long double c = 0.0L;
+    TRS_TRY(count_partitions(width, height, n, k, &c));
+    *count = (double)c;
+    return TRS_OK;
+}
+
 int trs_plan_stats(int width, int height, int n, int k, int *n_windows, int *n_items) {
     if (!n_windows || !n_items) return TRS_EINVAL;
     HostPlan p;

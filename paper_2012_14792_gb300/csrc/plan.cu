@@ -105,6 +105,56 @@ int build_plan(int W, int H, int n, int k, HostPlan *p, int window_step) {
     return TRS_OK;
 }
 
+// Partitions with exactly n slices, one tile row, all slice areas in
+// [lo, hi]: a counting row DP per tile column, then a counting column DP.
+static unsigned __int128 count_in_range(int W, int H, int C, int R, int n, uint64_t lo, uint64_t hi) {
+    std::vector<unsigned __int128> g((size_t)num_bands(C) * (n + 1), 0), F((size_t)(C + 1) * (n + 1), 0);
+    std::vector<unsigned __int128> cnt((size_t)(R + 1) * (n + 1));
+    for (int x0 = 0; x0 < C; ++x0)
+        for (int x1 = x0 + 1; x1 <= C; ++x1) {
+            const uint64_t w = line_px(x1, W) - line_px(x0, W);
+            std::fill(cnt.begin(), cnt.end(), 0);
+            cnt[0] = 1;  // rows [0, 0) in 0 slices
+            for (int y = 1; y <= R; ++y)
+                for (int yp = 0; yp < y; ++yp) {
+                    const uint64_t a = w * (line_px(y, H) - line_px(yp, H));
+                    if (a < lo || a > hi) continue;
+                    for (int k = 1; k <= n; ++k) cnt[(size_t)y * (n + 1) + k] += cnt[(size_t)yp * (n + 1) + k - 1];
+                }
+            for (int k = 0; k <= n; ++k) g[(size_t)band_index(C, x0, x1) * (n + 1) + k] = cnt[(size_t)R * (n + 1) + k];
+        }
+    F[0] = 1;  // columns [0, 0) in 0 slices
+    for (int x = 1; x <= C; ++x)
+        for (int xp = 0; xp < x; ++xp) {
+            const unsigned __int128 *gb = &g[(size_t)band_index(C, xp, x) * (n + 1)];
+            for (int m = 1; m <= n; ++m)
+                for (int k = 1; k <= m; ++k) F[(size_t)x * (n + 1) + m] += gb[k] * F[(size_t)xp * (n + 1) + m - k];
+        }
+    return F[(size_t)C * (n + 1) + n];
+}
+
+int count_partitions(int W, int H, int n, int k, long double *out) {
+    if (W <= 0 || H <= 0 || n < 1 || n > kMaxN || k < 1 || !out) return TRS_EINVAL;
+    const int C = (W + kCtu - 1) / kCtu, R = (H + kCtu - 1) / kCtu;
+    if (C > kMaxC || R > kMaxR) return TRS_EINVAL;
+    // every slice area, ascending
+    std::set<uint64_t> areas;
+    for (uint32_t w : extents(C, W))
+        for (uint32_t h : extents(R, H)) areas.insert((uint64_t)w * h);
+    const std::vector<uint64_t> a(areas.begin(), areas.end());
+    // each partition counted once, at its smallest slice area m: all areas in
+    // [m, k*m - 1] minus those with all areas in (m, k*m - 1]
+    unsigned __int128 total = 0;
+    for (size_t i = 0; i < a.size(); ++i) {
+        const uint64_t m = a[i], hi = (uint64_t)k * m - 1;
+        if (m * (uint64_t)n > (uint64_t)W * H || hi * (uint64_t)n < (uint64_t)W * H) continue;
+        total += count_in_range(W, H, C, R, n, m, hi);
+        if (i + 1 < a.size() && a[i + 1] <= hi) total -= count_in_range(W, H, C, R, n, a[i + 1], hi);
+    }
+    *out = (long double)total;
+    return TRS_OK;
+}
+
 size_t plan_blob_bytes(const HostPlan &p) {
     size_t s = align256(sizeof(DevPlan));
     s += align256(p.win_a.size() * sizeof(uint64_t) + 8);

@@ -26,6 +26,8 @@ struct SearchScratch {
 // window_step > 1 keeps every window_step-th area window only, counted from
 // the largest (the lightweight search); 1 is the exact search.
 int build_plan(int W, int H, int n, int k, HostPlan *p, int window_step = 1);
+// Exact number of partitions in S(n) with one tile row (see trs_count_partitions).
+int count_partitions(int W, int H, int n, int k, long double *out);
 size_t plan_blob_bytes(const HostPlan &p);
 // Lays the plan out as a device blob whose pointers assume it will be copied to dev_base.
 void plan_serialize(const HostPlan &p, uint8_t *dev_base, std::vector<uint8_t> &blob);

@@ -119,6 +119,7 @@ def _load():
         "trs_sizeof": ([ct.c_char_p], sz),
         "trs_plan_stats": ([i, i, i, i, ct.POINTER(i), ct.POINTER(i)], i),
         "trs_plan_work": ([i, i, i, i, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)], i),
+        "trs_count_partitions": ([i, i, i, i, ct.POINTER(ct.c_double)], i),
         "trs_alu_peak": ([i, ct.POINTER(ct.c_double)], i),
         "trs_create": ([ct.POINTER(vp), ct.POINTER(trs_opts)], i),
         "trs_destroy": ([vp], i),
@@ -206,6 +207,12 @@ def trs_plan_stats(width: int, height: int, n_regions: int, k_area: int = 3) -> 
     nw, ni = ct.c_int(0), ct.c_int(0)
     _check(_lib.trs_plan_stats(width, height, n_regions, k_area, ct.byref(nw), ct.byref(ni)), "trs_plan_stats")
     return nw.value, ni.value
+
+
+def trs_count_partitions(width: int, height: int, n_regions: int, k_area: int = 3) -> float:
+    c = ct.c_double()
+    _check(_lib.trs_count_partitions(width, height, n_regions, k_area, ct.byref(c)), "trs_count_partitions")
+    return c.value
 
 
 def trs_plan_work(width: int, height: int, n_regions: int, k_area: int = 3) -> tuple[float, float]:

@@ -72,3 +72,32 @@ def test_plan_rejects_oversize(trs):
         trs.trs_plan_stats(100, 4097, 4)
     with pytest.raises(trs.TrsError):
         trs.trs_plan_stats(100, 100, 33)
+
+
+def _brute_partitions(W, H, n, k):
+    """Distinct slice sets of S(n) (the rule applied to luma-sample areas),
+    by enumerating every code with bruteforce.configurations."""
+    import bruteforce
+    C, R, cw, ch = bruteforce.geometry(W, H)
+    seen = set()
+    for _, regions, _ in bruteforce.configurations(W, H, n):
+        areas = [sum(cw[r[0]:r[1]]) * sum(ch[r[2]:r[3]]) for r in regions]
+        if k * min(areas) > max(areas):
+            seen.add(frozenset(regions))
+    return len(seen)
+
+
+@pytest.mark.parametrize("W,H,n", [(384, 384, 3), (512, 256, 4), (500, 300, 4), (640, 384, 5), (300, 520, 3),
+                                   (129, 640, 4), (640, 129, 2), (256, 256, 1)])
+def test_count_partitions_matches_brute_force(trs, W, H, n):
+    assert trs.trs_count_partitions(W, H, n) == _brute_partitions(W, H, n, 3)
+
+
+@pytest.mark.parametrize("C,R,n", [(7, 4, 4), (15, 9, 8), (30, 17, 16), (5, 5, 1)])
+def test_count_partitions_without_the_rule_is_the_closed_form(trs, C, R, n):
+    """With k beyond every area ratio the rule admits all: choose c tile
+    columns, then n - c of the c(R-1) in-column cut lines."""
+    from math import comb
+    expect = sum(comb(C - 1, c - 1) * comb(c * (R - 1), n - c) for c in range(1, min(C, n) + 1))
+    got = trs.trs_count_partitions(C * 128, R * 128, n, 1 << 20)
+    assert got == pytest.approx(float(expect), rel=1e-15)

@@ -332,6 +332,28 @@ def test_batch_chunks_equal_alone(dec, nf):
             trs.trs_set_batch_parts(dec.ctx, bad)
 
 
+def test_two_contexts_in_flight_on_two_streams(dec):
+    """Batches of two contexts running at once on two streams (a stream of
+    steps with two in flight) decide the same bytes as one context alone."""
+    from paper_2012_14792_gb300 import runtime
+    items = synth.mixed_batch(256, seed=8)[:24]
+    ins, keep = _batch_inputs(items)
+    ref = bytes(dec.batch_decide(ins).cpu().numpy())
+    other = runtime.Decider(max_width=3840, max_height=2160, max_regions=32, max_batch=24)
+    try:
+        ctxs = [dec, other]
+        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        outs = [torch.zeros(24 * 840, dtype=torch.uint8, device="cuda") for _ in range(2)]
+        for step in range(6):
+            i = step % 2
+            with torch.cuda.stream(streams[i]):
+                ctxs[i].batch_decide(ins, outs[i])
+        torch.cuda.synchronize()
+        assert bytes(outs[0].cpu().numpy()) == ref and bytes(outs[1].cpu().numpy()) == ref
+    finally:
+        other.close()
+
+
 def test_batch_replay_after_descriptor_growth(dec):
     """A multi-lambda search that needs a larger descriptor buffer drops the
     captured batches that pointed at the old one; replays stay correct."""
