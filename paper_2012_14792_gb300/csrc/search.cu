@@ -356,8 +356,8 @@ __device__ void items_paired(const DevFrame &fr, const DevPlan &pl, int i0, int 
 // time through item_rows for taller frames or n > 16).  V[k] = G_k[0] is
 // collected in lane k and stored with one coalesced write per item.
 // per warp after the two staging areas: G tables (288 words), item list
-// (64), step-2 window mask (16)
-constexpr int kBandTail = 368;
+// (kListMax 16-bit entries: 32 words), step-2 window mask (16)
+constexpr int kBandTail = 336;
 template <int STEP, int S>
 __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, int total, int stage_words,
                                                                int itm_words) {
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, i
     uint64_t *itm = stage + stage_words;
     uint64_t *gbuf = itm + itm_words;
     int16_t *list = reinterpret_cast<int16_t *>(gbuf + 288);
-    uint32_t *wmask = reinterpret_cast<uint32_t *>(gbuf + 352);
+    uint32_t *wmask = reinterpret_cast<uint32_t *>(gbuf + 320);
     uint32_t tok = 0;  // step 2: bit d-1 set if the slice [lane, lane+d) meets the Eq. 4 bound
 #pragma unroll 8
     for (int d = 1; d <= R; ++d) {

@@ -229,6 +229,30 @@ def test_2160p_sequence_matches_oracle(dec, oracle):
             assert_valid_partition(oracle, p, st, Tq, n)
 
 
+def test_bench_launch_matches_oracle_on_all_64_frames(dec, oracle):
+    """The benchmark's launch: the 64-frame UHD sequence in one captured batch
+    (2 pipelined chunks, default launch shapes), replayed, every frame equal
+    to the oracle."""
+    from paper_2012_14792_gb300 import trs
+    frames = list(synth.sequence_2160p_blob(64))
+    ins, keep = [], []
+    for plane, times in frames:
+        luma, ptr, pitch = _dev(plane)
+        tt = torch.from_numpy(times).cuda()
+        keep += [luma, tt]
+        ins.append((ptr, pitch, 3840, 2160, 10, tt, 16, 0.1))
+    trs.trs_set_tune(dec.ctx, 2, 2, 4)
+    try:
+        dec.batch_decide(ins)  # capture
+        ps = dec.partitions(dec.batch_decide(ins), 64)  # replay
+        assert trs.trs_batch_kernels(dec.ctx) == 16
+    finally:
+        trs.trs_set_tune(dec.ctx, 4, 4, 8)
+    for (plane, times), p in zip(frames, ps):
+        d, _, _ = oracle.decide(plane, times, 10, 16, 0.1)
+        assert_partition_equal(p, d, 17)
+
+
 def test_single_slice_and_infeasible(dec, oracle):
     plane, times = synth.small_frame(700, 300, 10, 3)
     p = _decide(dec, plane, times, 10, 1, 0.0)
