@@ -62,12 +62,14 @@ def make_inputs(nframes: int, mixed: bool = False):
     return seq, mix
 
 
-def run_mixed(runtime, trs, items, device: int, steps: int, warmup: int, n_parts: int):
+def run_mixed(runtime, trs, items, device: int, steps: int, warmup: int, n_parts: int, in_flight: int):
     """The 256-frame mixed batch (146 x 480p8, 73 x 1080p10, 37 x 2160p10,
-    n from {4, 8, 16}, lambda 0.1) in one graph launch per step."""
+    n from {4, 8, 16}, lambda 0.1), one graph launch per step, the steps
+    spread over `in_flight` contexts on their own streams."""
     import torch
     dev = torch.device("cuda", device)
-    dec = runtime.Decider(max_width=3840, max_height=2160, max_regions=16, max_batch=len(items), device=device)
+    decs = [runtime.Decider(max_width=3840, max_height=2160, max_regions=16, max_batch=len(items), device=device)
+            for _ in range(in_flight)]
     ins, keep = [], []
     for it in items:
         raw = np.ascontiguousarray(it.plane).view(np.uint8)
@@ -75,31 +77,46 @@ def run_mixed(runtime, trs, items, device: int, steps: int, warmup: int, n_parts
         t = torch.from_numpy(it.times).to(dev)
         keep += [l, t]
         ins.append((l, raw.strides[0], it.spec.width, it.spec.height, it.spec.bit_depth, t, it.n_regions, it.lam))
-    tune = dec.autotune(ins)
-    trs.trs_set_batch_parts(dec.ctx, n_parts)
-    out = torch.zeros(len(items) * trs.PARTITION_BYTES, dtype=torch.uint8, device=dev)
-    for _ in range(warmup):
-        dec.batch_decide(ins, out)
+    tune = decs[0].autotune(ins)
+    for d in decs:
+        trs.trs_set_tune(d.ctx, tune["band_warps"], tune["col_warps"], tune["col_batch"])
+        trs.trs_set_batch_parts(d.ctx, n_parts)
+    outs = [torch.zeros(len(items) * trs.PARTITION_BYTES, dtype=torch.uint8, device=dev) for _ in decs]
+    streams = [torch.cuda.Stream(dev) for _ in decs]
+    cur = torch.cuda.current_stream(dev)
+
+    def run(count):
+        for s in range(count):
+            i = s % in_flight
+            with torch.cuda.stream(streams[i]):
+                decs[i].batch_decide(ins, outs[i])
+
+    run(max(warmup, in_flight))
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s = torch.cuda.current_stream(dev)
-    e0.record(s)
-    for _ in range(steps):
-        dec.batch_decide(ins, out)
-    e1.record(s)
+    e0.record(cur)
+    for st in streams:
+        st.wait_event(e0)
+    run(steps)
+    for st in streams:
+        e = torch.cuda.Event()
+        e.record(st)
+        cur.wait_event(e)
+    e1.record(cur)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1)
-    parts = dec.partitions(out, len(items))
+    parts = decs[0].partitions(outs[0], len(items))
     assert all(p.status == 0 for p in parts)
-    stage = trs.trs_batch_stage_ms(dec.ctx)
-    sf = trs.trs_batch_stage_frames(dec.ctx)
-    dec.close()
+    stage = trs.trs_batch_stage_ms(decs[0].ctx)
+    sf = trs.trs_batch_stage_frames(decs[0].ctx)
+    for d in decs:
+        d.close()
     luma_bytes = sum(it.spec.frame_bytes for it in items)
     half_bytes = sum(it.spec.frame_bytes for it in items[:sf])
     return {"value": len(items) * steps / (ms / 1e3), "unit": UNIT, "frames_per_step": len(items),
-            "ms_per_step": ms / steps, "luma_gb_per_step": luma_bytes / 1e9, "stage_ms": stage,
-            "parts": n_parts, "stage_frames": sf, "texture_gbs": half_bytes / (stage["texture"] / 1e3) / 1e9, "autotune": tune}
-
+            "ms_per_step": ms / steps, "luma_gb_per_step": luma_bytes / 1e9, "in_flight": in_flight,
+            "stage_ms": stage, "parts": n_parts, "stage_frames": sf,
+            "texture_gbs": half_bytes / (stage["texture"] / 1e3) / 1e9, "autotune": tune}
 
 def max_over_ranks(x: float, dist, device=None) -> float:
     """The slowest rank's time (every rank calls this with its own)."""
@@ -531,22 +548,19 @@ def main():
     # --- lightweight search: every 4th area window --------------------------
     light = None
     if not args.no_light:
-        trs.trs_set_window_step(dec.ctx, 4)
-        for _ in range(args.warmup):
-            dec.batch_decide(ins, out)
-        torch.cuda.synchronize(dev)
+        for d in decs:
+            trs.trs_set_window_step(d.ctx, 4)
+        run_steps(max(args.warmup, args.in_flight), args.in_flight)
+        sync_all()
         l_steps = max(3, args.steps // 4)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(l_steps):
-            dec.batch_decide(ins, out)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
+        l_ms = timed(l_steps, args.in_flight)  # the same stream of steps as `value`
         lp = dec.partitions(out, nfr)
-        trs.trs_set_window_step(dec.ctx, 1)
+        for d in decs:
+            trs.trs_set_window_step(d.ctx, 1)
         tr = np.array([a.t_q / b.t_q for a, b in zip(lp, parts)])
         qr = np.array([a.q / max(1, b.q) for a, b in zip(lp, parts)])
-        light = {"window_step": 4, "value": nfr * l_steps / (e0.elapsed_time(e1) / 1e3), "unit": UNIT,
+        light = {"window_step": 4, "value": nfr * l_steps / (l_ms / 1e3), "unit": UNIT,
+                 "in_flight": args.in_flight,
                  "identical_frac": float(np.mean([a.x_edges() == b.x_edges() and a.band_cuts() == b.band_cuts()
                                                   for a, b in zip(lp, parts)])),
                  "t_ratio_mean": float(tr.mean()), "t_ratio_max": float(tr.max()),
@@ -650,7 +664,8 @@ def main():
         serving = run_serving(trs, local)
     mixed_res = None
     if mixed is not None:
-        mixed_res = run_mixed(runtime, trs, mixed, local, max(3, args.steps // 20), args.warmup, args.parts)
+        mixed_res = run_mixed(runtime, trs, mixed, local, max(3, args.steps // 20), args.warmup, args.parts,
+                              args.in_flight)
 
     cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
