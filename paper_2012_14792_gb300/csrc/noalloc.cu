@@ -44,7 +44,7 @@ constexpr int kMaxDevices = 64;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 // static host storage (no heap): the plan is laid out here, then copied
-unsigned char g_host_plan[kNoAllocBytes];
+alignas(256) unsigned char g_host_plan[kNoAllocBytes];
 uint64_t g_areas[4 * kMaxC * kMaxR];
 std::mutex g_mu;
 
@@ -131,6 +131,7 @@ int layout_plan(int W, int H, int n, int k, unsigned char *dev_base, DeviceSlot 
                 it.hlo = hs[ilo];
                 it.hhi = hs[ihi];
                 it.kmax = std::min(std::min(n, R), (int)(H / it.hlo));
+                it.kmin = 1;
                 prev_lo = ilo;
                 prev_hi = ihi;
                 prev_slot = nitems++;

@@ -8,7 +8,12 @@
 // partition meets the rule iff all its slice areas fit one such window.
 //
 // Items: for tile column b of pixel width w and window [a, k*a-1], a slice of
-// pixel height h is admissible iff a <= w*h <= k*a-1.  Slice heights come
+// pixel height h is admissible iff a <= w*h <= k*a-1.  The columns left and
+// right of the band, of areas AL and AR, hold the other slices, so the band
+// takes between n - floor(AL/a) - floor(AR/a) and
+// n - ceil(AL/(k*a-1)) - ceil(AR/(k*a-1)) of them (necessary conditions);
+// a band with no such count is left out of the window, and each item keeps
+// the widest range over its windows (kmin, kmax).  Slice heights come
 // from a short sorted list, so the admissible heights are a range [hlo, hhi]
 // of that list.  Consecutive windows often give a column the same range;
 // each distinct (column, range) becomes one item, shared by those windows.
@@ -72,7 +77,10 @@ int build_plan(int W, int H, int n, int k, HostPlan *p, int window_step) {
     for (int b = 0; b < p->nb; ++b) {
         p->band_items[b] = (int32_t)p->items.size();
         const uint64_t wb = line_px(p->band_x1[b], W) - line_px(p->band_x0[b], W);
-        int prev_lo = -1, prev_hi = -1, prev_slot = -1;
+        // the columns left and right of the band hold the other slices
+        const uint64_t AL = (uint64_t)line_px(p->band_x0[b], W) * H;
+        const uint64_t AR = (uint64_t)(W - line_px(p->band_x1[b], W)) * H;
+        int prev_lo = -1, prev_hi = -1, prev_slot = -1, kmax_w_max = 0;
         for (int wi = 0; wi < nwin; ++wi) {
             const uint64_t lo = p->win_a[wi], hi = (uint64_t)k * lo - 1;
             // admissible heights: lo <= wb*h <= hi
@@ -81,9 +89,22 @@ int build_plan(int W, int H, int n, int k, HostPlan *p, int window_step) {
             int ihi = (int)hs.size() - 1;
             while (ihi >= 0 && wb * hs[ihi] > hi) --ihi;
             if (ilo > ihi) continue;
+            // slice counts the band can take in this window: a part of area
+            // A made of slices with areas in [lo, hi] has between ceil(A/hi)
+            // and floor(A/lo) of them, and the n slices add up
+            const int64_t kmax_w = (int64_t)n - (int64_t)((AL + hi - 1) / hi) - (int64_t)((AR + hi - 1) / hi);
+            const int64_t kmin_w = std::max<int64_t>(1, (int64_t)n - (int64_t)(AL / lo) - (int64_t)(AR / lo));
+            if (kmax_w < kmin_w) {  // no partition of this window uses the band
+                prev_lo = prev_hi = -1;  // an item's windows stay consecutive (exact step-2 liveness)
+                continue;
+            }
             if (ilo == prev_lo && ihi == prev_hi) {
+                PlanItem &it = p->items[prev_slot];
                 p->slot_of[(size_t)wi * p->nb + b] = prev_slot;
-                p->items[prev_slot].w_last = wi;
+                it.w_last = wi;
+                it.kmin = std::min<int32_t>(it.kmin, (int32_t)kmin_w);
+                kmax_w_max = std::max<int>(kmax_w_max, (int)kmax_w);
+                it.kmax = std::min(std::min(std::min(n, R), (int)(H / it.hlo)), kmax_w_max);
                 continue;
             }
             PlanItem it;
@@ -91,7 +112,9 @@ int build_plan(int W, int H, int n, int k, HostPlan *p, int window_step) {
             it.w_first = it.w_last = wi;
             it.hlo = hs[ilo];
             it.hhi = hs[ihi];
-            it.kmax = std::min(std::min(n, R), (int)(H / it.hlo));
+            kmax_w_max = (int)kmax_w;
+            it.kmax = std::min(std::min(std::min(n, R), (int)(H / it.hlo)), kmax_w_max);
+            it.kmin = (int32_t)kmin_w;
             const int dlo = std::max(1, (int)((it.hlo + kCtu - 1) / kCtu));
             p->max_nd = std::max(p->max_nd, (int)(it.hhi / kCtu) - dlo + 1);
             prev_lo = ilo;

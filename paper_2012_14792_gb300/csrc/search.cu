@@ -283,7 +283,8 @@ __device__ void item_pair(const DevFrame &fr, const DevPlan &pl, int mi, const P
     if (have) {
         uint64_t *V = Vall + (size_t)mi * (n + 1);
         if (l == 0) V[0] = kInf;
-        if (l < n) V[l + 1] = vreg;
+        const int kmin = pl.items[mi].kmin;  // read here: nothing extra stays live through the k loop
+        if (l < n) V[l + 1] = l + 1 >= kmin ? vreg : kInf;  // counts below kmin complete no partition
     }
 }
 
@@ -336,7 +337,7 @@ __device__ void items_paired(const DevFrame &fr, const DevPlan &pl, int i0, int 
         __syncwarp();
     }
     auto item_at = [&](int j) { return j < cnt ? i0 + (STEP == 1 ? j : (int)list[j]) : -1; };
-    PlanItem nxt{0, 0, 1u, 0u, 0, -1};
+    PlanItem nxt{0, 0, 1u, 0u, 0, -1, 1, 0};
     int mnext = item_at(h);
     if (mnext >= 0) nxt = pl.items[mnext];
     for (int p = 0; p < cnt; p += 2) {
@@ -456,9 +457,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, i
         }
         if (lane == 0) {
             V[0] = kInf;
-            if (n == 32) V[32] = vreg;
+            if (n == 32) V[32] = 32 >= it.kmin ? vreg : kInf;
         } else if (lane <= n) {
-            V[lane] = vreg;
+            V[lane] = lane >= it.kmin ? vreg : kInf;  // counts below kmin complete no partition
         }
     }
 }

@@ -113,11 +113,16 @@ __device__ inline uint64_t eq4_threshold(uint64_t t_min, uint32_t lambda_q) {
 // One unit of row-DP work of the search: tile column b whose slices must
 // have a pixel height in [hlo, hhi] (the slice heights that land in the area
 // window of every window mapped to this unit).  kmax bounds the slice count.
-struct PlanItem {
+struct alignas(16) PlanItem {  // 32 bytes: two 16-byte loads
     int32_t b;
     int32_t kmax;
     uint32_t hlo, hhi;
     int32_t w_first, w_last;  // the windows mapped to this item are [w_first, w_last]
+    // slice counts below kmin cannot complete a partition in any of those
+    // windows: the rest of the frame could not hold the other slices (see
+    // build_plan); their V entries are stored as +infinity
+    int32_t kmin;
+    int32_t reserved;
 };
 
 // Search plan of one frame shape (W, H, n, k), built on the host once per
