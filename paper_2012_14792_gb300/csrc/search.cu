@@ -12,17 +12,20 @@
 //       sum separate over bands and, inside a band, over slices.
 // For each window the search is a DP over bands of a DP over slice rows.
 // Windows that give a band the same admissible slice heights share one row
-// DP ("item" of the shape's plan).
+// DP ("item" of the shape's plan); the plan also bounds each item's slice
+// count by what the rest of the frame can hold (necessary conditions).
 //
-//  band_kernel<STEP>    one warp per (frame, tile column), running all of
-//                       the column's items: lanes are the start row y of
-//                       the remaining rows [y, R); for k = 1..kmax it
-//                       relaxes every admissible slice height d, reading
-//                       G_{k-1}[y+d] from the warp's shared-memory table.  Step 1
-//                       combines with max (Eq. 1), step 2 with + (Eq. 2) and
-//                       drops slices whose time exceeds the Eq. 4 bound.
-//  column_kernel<STEP>  one warp per (frame, window): DP over tile-column
-//                       right edges with lanes over the slice count m.
+//  band_kernel<STEP,S>  one warp per (frame, tile column), running all of
+//                       the column's items (two at a time for frames of at
+//                       most 17 CTU rows): lanes are the start row y of the
+//                       remaining rows [y, R); for k = 1..kmax it relaxes
+//                       every admissible slice height d, reading
+//                       G_{k-1}[y+d] from shared memory.  Step 1 combines
+//                       with max (Eq. 1), step 2 with + (Eq. 2) and drops
+//                       slices whose time exceeds the Eq. 4 bound.
+//  column_kernel<STEP>  one block per (frame, window): DP over tile-column
+//                       right edges with lanes over the slice count m, the
+//                       block's warps splitting the candidate edges.
 //                       Step 1's window minima reduce into T_min (Eq. 3),
 //                       step 2's into Q*.
 //  rebuild_kernel       one warp per (frame, window): in a window that
