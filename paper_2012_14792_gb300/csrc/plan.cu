@@ -11,9 +11,11 @@
 // pixel height h is admissible iff a <= w*h <= k*a-1.  The columns left and
 // right of the band, of areas AL and AR, hold the other slices, so the band
 // takes between n - floor(AL/a) - floor(AR/a) and
-// n - ceil(AL/(k*a-1)) - ceil(AR/(k*a-1)) of them (necessary conditions);
-// a band with no such count is left out of the window, and each item keeps
-// the widest range over its windows (kmin, kmax).  Slice heights come
+// n - ceil(AL/(k*a-1)) - ceil(AR/(k*a-1)) of them, and at least
+// ceil(H/hmax), at most floor(H/hmin) slices of its admissible heights cover
+// its H pixel rows (necessary conditions); a band with no count meeting all
+// of them is left out of the window, and each item keeps the widest range
+// over its windows (kmin, kmax).  Slice heights come
 // from a short sorted list, so the admissible heights are a range [hlo, hhi]
 // of that list.  Consecutive windows often give a column the same range;
 // each distinct (column, range) becomes one item, shared by those windows.
@@ -94,7 +96,9 @@ int build_plan(int W, int H, int n, int k, HostPlan *p, int window_step) {
             // and floor(A/lo) of them, and the n slices add up
             const int64_t kmax_w = (int64_t)n - (int64_t)((AL + hi - 1) / hi) - (int64_t)((AR + hi - 1) / hi);
             const int64_t kmin_w = std::max<int64_t>(1, (int64_t)n - (int64_t)(AL / lo) - (int64_t)(AR / lo));
-            if (kmax_w < kmin_w) {  // no partition of this window uses the band
+            // and k slices of heights in [hs[ilo], hs[ihi]] cover the band's H rows of pixels
+            const int64_t kgeo_lo = ((int64_t)H + hs[ihi] - 1) / hs[ihi], kgeo_hi = (int64_t)H / hs[ilo];
+            if (std::max(kmin_w, kgeo_lo) > std::min(kmax_w, kgeo_hi)) {  // no partition of this window uses the band
                 prev_lo = prev_hi = -1;  // an item's windows stay consecutive (exact step-2 liveness)
                 continue;
             }
