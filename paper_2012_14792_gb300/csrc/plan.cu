@@ -36,6 +36,115 @@ static std::vector<uint32_t> extents(int cells, int total) {
     return std::vector<uint32_t>(s.begin(), s.end());
 }
 
+// Exact pruning of a plan: in each window keep only the (tile column, slice
+// count) options that take part in some complete partition of the window
+// with n slices -- a column's count k must leave the columns to its left a
+// count they can reach and the columns to its right the rest (forward and
+// backward reachability over slice counts, bit sets).  Column options come
+// from the slice counts that tile the column's H pixel rows with its
+// admissible heights, within the area bounds of build_plan.  Columns left
+// without an option leave the window; items keep the union of their
+// columns' options (kmin, kmax) and the windows that still use them.  Drops
+// only options no partition of the window uses.
+static void prune_by_reachability(HostPlan *p) {
+    const int W = p->W, H = p->H, C = p->C, R = p->R, n = p->n, nb = p->nb, k = p->k;
+    const int nwin = (int)p->win_a.size(), ni = (int)p->items.size();
+    if (ni == 0 || n > 62) return;
+    const uint64_t full = (2ull << n) - 1;  // slice counts 0..n
+    // slice counts that tile the H pixel rows with each item's heights
+    std::vector<uint64_t> kset(ni, 0), reach(R + 1);
+    for (int i = 0; i < ni; ++i) {
+        const PlanItem &it = p->items[i];
+        std::fill(reach.begin(), reach.end(), 0);
+        reach[0] = 1;
+        for (int y = 1; y <= R; ++y)
+            for (int yp = 0; yp < y; ++yp) {
+                const uint32_t h = line_px(y, H) - line_px(yp, H);
+                if (h >= it.hlo && h <= it.hhi) reach[y] |= (reach[yp] << 1) & full;
+            }
+        const int kmax = std::min(it.kmax, n);
+        kset[i] = reach[R] & ~1ull & ((2ull << kmax) - 1);
+    }
+    std::vector<uint64_t> use(ni, 0), opt(nb), fw(C + 1), bw(C + 1);
+    std::vector<int> wfirst(ni, nwin), wlast(ni, -1);
+    auto spread = [&](uint64_t m, uint64_t ks) {  // OR of m << k over k in ks
+        uint64_t r = 0;
+        for (; ks; ks &= ks - 1) r |= m << __builtin_ctzll(ks);
+        return r & full;
+    };
+    for (int wi = 0; wi < nwin; ++wi) {
+        const uint64_t lo = p->win_a[wi], hi = (uint64_t)k * lo - 1;
+        int32_t *srow = &p->slot_of[(size_t)wi * nb];
+        for (int b = 0; b < nb; ++b) {
+            opt[b] = 0;
+            if (srow[b] < 0) continue;
+            const uint64_t AL = (uint64_t)line_px(p->band_x0[b], W) * H;
+            const uint64_t AR = (uint64_t)(W - line_px(p->band_x1[b], W)) * H;
+            const int64_t kmax_w = (int64_t)n - (int64_t)((AL + hi - 1) / hi) - (int64_t)((AR + hi - 1) / hi);
+            const int64_t kmin_w = std::max<int64_t>(1, (int64_t)n - (int64_t)(AL / lo) - (int64_t)(AR / lo));
+            if (kmax_w < kmin_w) continue;
+            const uint64_t win = ((2ull << kmax_w) - 1) & ~((1ull << kmin_w) - 1);
+            opt[b] = kset[srow[b]] & win;
+        }
+        std::fill(fw.begin(), fw.end(), 0);
+        std::fill(bw.begin(), bw.end(), 0);
+        fw[0] = 1;
+        for (int x0 = 0; x0 < C; ++x0)
+            if (fw[x0])
+                for (int x1 = x0 + 1; x1 <= C; ++x1) fw[x1] |= spread(fw[x0], opt[band_index(C, x0, x1)]);
+        bw[C] = 1;
+        for (int x1 = C; x1 > 0; --x1)
+            if (bw[x1])
+                for (int x0 = x1 - 1; x0 >= 0; --x0) bw[x0] |= spread(bw[x1], opt[band_index(C, x0, x1)]);
+        for (int b = 0; b < nb; ++b) {
+            uint64_t useful = 0;
+            const uint64_t L = fw[p->band_x0[b]], Rr = bw[p->band_x1[b]];
+            for (uint64_t ks = opt[b]; ks; ks &= ks - 1) {
+                const int kk = __builtin_ctzll(ks);
+                bool ok = false;
+                for (uint64_t l = L; l && !ok; l &= l - 1) {
+                    const int rest = n - kk - __builtin_ctzll(l);
+                    ok = rest >= 0 && ((Rr >> rest) & 1ull);
+                }
+                if (ok) useful |= 1ull << kk;
+            }
+            if (!useful) {
+                srow[b] = -1;
+                continue;
+            }
+            const int it = srow[b];
+            use[it] |= useful;
+            wfirst[it] = std::min(wfirst[it], wi);
+            wlast[it] = std::max(wlast[it], wi);
+        }
+    }
+    // keep the used items, in order, with their option ranges
+    std::vector<int32_t> remap(ni, -1);
+    std::vector<PlanItem> kept;
+    std::vector<int32_t> band_items(nb + 1, 0);
+    p->max_nd = 0;
+    for (int b = 0, i = 0; b < nb; ++b) {
+        band_items[b] = (int32_t)kept.size();
+        for (; i < p->band_items[b + 1]; ++i) {
+            if (!use[i]) continue;
+            PlanItem it = p->items[i];
+            it.kmin = __builtin_ctzll(use[i]);
+            it.kmax = 63 - __builtin_clzll(use[i]);
+            it.w_first = wfirst[i];
+            it.w_last = wlast[i];
+            const int dlo = std::max(1, (int)((it.hlo + kCtu - 1) / kCtu));
+            p->max_nd = std::max(p->max_nd, (int)(it.hhi / kCtu) - dlo + 1);
+            remap[i] = (int32_t)kept.size();
+            kept.push_back(it);
+        }
+    }
+    band_items[nb] = (int32_t)kept.size();
+    for (int32_t &sl : p->slot_of)
+        if (sl >= 0) sl = remap[sl];
+    p->items.swap(kept);
+    p->band_items.swap(band_items);
+}
+
 int build_plan(int W, int H, int n, int k, HostPlan *p, int window_step) {
     if (W <= 0 || H <= 0 || n < 1 || n > kMaxN || k < 1 || window_step < 1) return TRS_EINVAL;
     const int C = (W + kCtu - 1) / kCtu, R = (H + kCtu - 1) / kCtu;
@@ -129,6 +238,7 @@ int build_plan(int W, int H, int n, int k, HostPlan *p, int window_step) {
         }
     }
     p->band_items[p->nb] = (int32_t)p->items.size();
+    prune_by_reachability(p);
     return TRS_OK;
 }
 
