@@ -48,6 +48,20 @@ class _Result(ct.Structure):
     ]
 
 
+class _MtResult(ct.Structure):
+    _fields_ = [
+        ("status", ct.c_int),
+        ("n", ct.c_int),
+        ("t_min", ct.c_uint64),
+        ("thr", ct.c_uint64),
+        ("t", ct.c_uint64),
+        ("q", ct.c_uint64),
+        ("n_sets", ct.c_uint64),
+        ("region", (ct.c_int16 * 4) * 64),
+        ("sse_real", ct.c_double),
+    ]
+
+
 @dataclass
 class Decision:
     status: int
@@ -118,6 +132,11 @@ def lib():
                                      ct.c_int, u64p, u64p]
         _lib.oracle_result_size.restype = ct.c_size_t
         assert _lib.oracle_result_size() == ct.sizeof(_Result)
+        _lib.oracle_mt_search.argtypes = [ct.c_int, ct.c_int, u64p, u64p, u64p, u32p, ct.c_int, ct.c_int,
+                                          ct.c_uint32, ct.POINTER(_MtResult)]
+        _lib.oracle_mt_count.argtypes = [ct.c_int, ct.c_int, ct.c_int, ct.c_int, u64p]
+        _lib.oracle_mt_result_size.restype = ct.c_size_t
+        assert _lib.oracle_mt_result_size() == ct.sizeof(_MtResult)
     return _lib
 
 
@@ -277,3 +296,25 @@ def decide(plane: np.ndarray, times: np.ndarray, bit_depth: int, n: int, lam: fl
     if s != OK:
         return Decision(status=s), st, Tq
     return search_dp(st, Tq, n, lam, k_area), st, Tq
+
+
+# --- multi-tile rectangular slices (enumerated; small frames only) ---
+
+def mt_count(width: int, height: int, n: int, k_area: int = 3) -> int:
+    """Distinct slice sets of the multi-tile space that pass the area rule."""
+    out = np.zeros(1, np.uint64)
+    st = lib().oracle_mt_count(width, height, n, k_area, _p64(out))
+    if st != OK:
+        raise ValueError(f"oracle_mt_count status {st}")
+    return int(out[0])
+
+
+def mt_search(st: Stats, Tq: np.ndarray, n: int, lam: float = 0.0, k_area: int = 3) -> dict:
+    """The multi-tile search: T_min (Eq. 3), then the smallest (Q, raster-ordered
+    slice list) under Eq. 4.  Regions are (x0, y0, x1, y1) in CTUs."""
+    S1, S2, N, T = _search_args(st, Tq)
+    r = _MtResult()
+    lib().oracle_mt_search(st.width, st.height, _p64(S1), _p64(S2), _p64(N), _p32(T), n, k_area,
+                           lambda_q(lam), ct.byref(r))
+    regions = [tuple(int(v) for v in r.region[i]) for i in range(n)] if r.status == OK else []
+    return dict(status=r.status, t_min=r.t_min, thr=r.thr, t=r.t, q=r.q, regions=regions, sse=r.sse_real)

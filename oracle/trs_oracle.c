@@ -18,6 +18,8 @@
  *                       Eq. 4, both under k*A_min > A_max (Sec. 2.3)
  *   oracle_search_dp    O2: exact dynamic programme over the same space;
  *                       equal to O1 by construction (checked by the tests)
+ *   oracle_mt_search    the multi-tile slice space (slices of one tile or
+ *                       rectangles of whole tiles), enumerated (Sec. 1, Fig. 1b)
  *
  * Readings of the paper used here (the paper is silent on these points):
  *   - CTUs are 128x128 luma samples; edge CTUs are clipped to the frame.
@@ -852,6 +854,327 @@ static int search_dp_windows(int W, int H, const uint64_t *S1, const uint64_t *S
     res->status = OR_OK;
     return OR_OK;
 }
+
+/* ------------------------------------------------------------------ */
+/* Multi-tile rectangular slices                                       */
+/*
+ * A wider reading of the slice shapes of Sec. 1 (Fig. 1b): a slice is either
+ * a run of complete CTU rows inside one tile (as above) or a rectangle of
+ * two or more complete tiles.  A configuration is a tile grid (column lines
+ * X, row lines Y) whose tiles are grouped into rectangles of tiles; a group
+ * of one tile holds k >= 1 in-tile slices, a larger group is one slice.
+ * Exactly n slices, the area rule and the objective are as above.  Different
+ * configurations can give the same slices; the search is over slice sets,
+ * and ties on Q go to the smallest slice list in raster order (slices sorted
+ * by top row, then left column, compared as (y0, x0, y1, x1)).
+ *
+ * Enumeration: row-line masks, then column-line masks, in increasing order;
+ * the tiles grouped from the first ungrouped tile in raster order (width,
+ * then height, increasing); a single tile's in-tile cuts as increasing masks.
+ */
+typedef struct {
+    int status;
+    int n;
+    uint64_t t_min, thr, t, q;
+    uint64_t n_sets;         /* distinct slice sets passing the area rule (count mode) */
+    int16_t region[OR_MAX_N][4];   /* x0, y0, x1, y1 in CTUs, raster order */
+    double sse_real;
+} oracle_mt_result;
+
+typedef struct {
+    const frame_t *f;
+    memo_t *m;
+    int n, k_area, C, R;
+    int xs[OR_MAX_C + 1], ys[OR_MAX_R + 1], c, r;
+    int grp[OR_MAX_R][OR_MAX_C];     /* tile grouped? */
+    int rect[OR_MAX_N][4];           /* x0, x1, y0, y1 of the slices so far */
+    int ns;
+    int mode;                        /* 0: step 1, 1: step 2, 2: collect keys */
+    uint64_t t_min, thr;
+    int have;
+    uint64_t best_q, best_t;
+    int best_key[OR_MAX_N][4];       /* y0, x0, y1, x1 in raster order */
+    int16_t *keys;                   /* count mode: n*4 entries per slice set */
+    size_t nkeys, capkeys;
+    int oom;
+} mt_t;
+
+static int key_cmp4(const int *a, const int *b) {
+    for (int j = 0; j < 4; ++j)
+        if (a[j] != b[j]) return a[j] < b[j] ? -1 : 1;
+    return 0;
+}
+
+static void mt_evaluate(mt_t *e) {
+    const frame_t *f = e->f;
+    /* the slice list in raster order, as (y0, x0, y1, x1) */
+    int key[OR_MAX_N][4];
+    for (int i = 0; i < e->n; ++i) {
+        key[i][0] = e->rect[i][2];
+        key[i][1] = e->rect[i][0];
+        key[i][2] = e->rect[i][3];
+        key[i][3] = e->rect[i][1];
+    }
+    for (int i = 1; i < e->n; ++i)  /* insertion sort */
+        for (int j = i; j > 0 && key_cmp4(key[j], key[j - 1]) < 0; --j)
+            for (int q = 0; q < 4; ++q) {
+                int t = key[j][q];
+                key[j][q] = key[j - 1][q];
+                key[j - 1][q] = t;
+            }
+    uint64_t amin = OR_INF, amax = 0, tmax = 0, qsum = 0;
+    for (int i = 0; i < e->n; ++i) {
+        rsum_t s = memo_get(e->m, key[i][1], key[i][3], key[i][0], key[i][2]);
+        amin = s.N < amin ? s.N : amin;
+        amax = s.N > amax ? s.N : amax;
+        tmax = s.T > tmax ? s.T : tmax;
+        qsum += sse_floor(s.S1, s.S2, s.N);
+    }
+    if (!((uint64_t)e->k_area * amin > amax)) return;
+    if (e->mode == 2) {
+        if (e->nkeys == e->capkeys) {
+            size_t cap = e->capkeys ? 2 * e->capkeys : 1024;
+            int16_t *k2 = (int16_t *)realloc(e->keys, cap * (size_t)e->n * 4 * sizeof(int16_t));
+            if (!k2) {
+                e->oom = 1;
+                return;
+            }
+            e->keys = k2;
+            e->capkeys = cap;
+        }
+        int16_t *dst = e->keys + e->nkeys * (size_t)e->n * 4;
+        for (int i = 0; i < e->n; ++i)
+            for (int q = 0; q < 4; ++q) dst[i * 4 + q] = (int16_t)key[i][q];
+        e->nkeys++;
+        return;
+    }
+    if (e->mode == 0) {
+        if (tmax < e->t_min) e->t_min = tmax;
+        return;
+    }
+    if (tmax > e->thr) return;
+    int better = !e->have || qsum < e->best_q;
+    if (!better && qsum == e->best_q)
+        for (int i = 0; i < e->n; ++i) {
+            int c = key_cmp4(key[i], e->best_key[i]);
+            if (c) {
+                better = c < 0;
+                break;
+            }
+        }
+    if (!better) return;
+    e->have = 1;
+    e->best_q = qsum;
+    e->best_t = tmax;
+    for (int i = 0; i < e->n; ++i)
+        for (int q = 0; q < 4; ++q) e->best_key[i][q] = key[i][q];
+    (void)f;
+}
+
+static void mt_group(mt_t *e);
+
+/* in-tile cuts of a single tile [x0,x1) x [ty0,ty1): rows ty0+1 .. ty1-1 */
+static void mt_split(mt_t *e, int x0, int x1, int ty0, int ty1) {
+    const int h = ty1 - ty0;
+    for (uint64_t cm = 0; cm < (1ull << (h - 1)); ++cm) {
+        const int k = __builtin_popcountll(cm) + 1;
+        if (e->ns + k > e->n) continue;
+        int y0 = ty0;
+        for (int y = ty0 + 1; y <= ty1; ++y) {
+            if (y < ty1 && !((cm >> (y - ty0 - 1)) & 1ull)) continue;
+            e->rect[e->ns][0] = x0;
+            e->rect[e->ns][1] = x1;
+            e->rect[e->ns][2] = y0;
+            e->rect[e->ns][3] = y;
+            e->ns++;
+            y0 = y;
+        }
+        mt_group(e);
+        e->ns -= k;
+    }
+}
+
+static void mt_group(mt_t *e) {
+    if (e->oom) return;
+    int tx = -1, ty = -1;
+    for (int j = 0; j < e->r && tx < 0; ++j)
+        for (int i = 0; i < e->c; ++i)
+            if (!e->grp[j][i]) {
+                tx = i;
+                ty = j;
+                break;
+            }
+    if (tx < 0) {
+        if (e->ns == e->n) mt_evaluate(e);
+        return;
+    }
+    if (e->ns >= e->n) return;  /* an ungrouped tile still needs a slice */
+    for (int w = 1; tx + w <= e->c && !e->grp[ty][tx + w - 1]; ++w)
+        for (int h = 1; ty + h <= e->r; ++h) {
+            int freecells = 1;
+            for (int i = tx; i < tx + w && freecells; ++i)
+                if (e->grp[ty + h - 1][i]) freecells = 0;
+            if (!freecells) break;
+            for (int j = ty; j < ty + h; ++j)
+                for (int i = tx; i < tx + w; ++i) e->grp[j][i] = 1;
+            if (w == 1 && h == 1) {
+                mt_split(e, e->xs[tx], e->xs[tx + 1], e->ys[ty], e->ys[ty + 1]);
+            } else {
+                e->rect[e->ns][0] = e->xs[tx];
+                e->rect[e->ns][1] = e->xs[tx + w];
+                e->rect[e->ns][2] = e->ys[ty];
+                e->rect[e->ns][3] = e->ys[ty + h];
+                e->ns++;
+                mt_group(e);
+                e->ns--;
+            }
+            for (int j = ty; j < ty + h; ++j)
+                for (int i = tx; i < tx + w; ++i) e->grp[j][i] = 0;
+        }
+}
+
+static void mt_all(mt_t *e) {
+    const int C = e->C, R = e->R;
+    for (uint64_t ym = 0; ym < (1ull << (R - 1)); ++ym) {
+        e->r = 0;
+        e->ys[0] = 0;
+        for (int y = 1; y < R; ++y)
+            if ((ym >> (y - 1)) & 1ull) e->ys[++e->r] = y;
+        e->ys[++e->r] = R;
+        for (uint64_t xm = 0; xm < (1ull << (C - 1)); ++xm) {
+            e->c = 0;
+            e->xs[0] = 0;
+            for (int x = 1; x < C; ++x)
+                if ((xm >> (x - 1)) & 1ull) e->xs[++e->c] = x;
+            e->xs[++e->c] = C;
+            memset(e->grp, 0, sizeof(e->grp));
+            e->ns = 0;
+            mt_group(e);
+        }
+    }
+}
+
+static int cmp_keys_n;
+static int cmp_keys(const void *a, const void *b) {
+    const int16_t *x = (const int16_t *)a, *y = (const int16_t *)b;
+    for (int i = 0; i < cmp_keys_n * 4; ++i)
+        if (x[i] != y[i]) return x[i] < y[i] ? -1 : 1;
+    return 0;
+}
+
+/* Shapes with up to 16 column and 16 row lines only: the enumeration is exponential in both. */
+static int mt_setup(mt_t *e, frame_t *f, memo_t *m, int W, int H, int n, int k_area) {
+    int st = check_inputs(W, H, n, k_area);
+    if (st) return st;
+    memset(e, 0, sizeof(*e));
+    e->f = f;
+    e->m = m;
+    e->n = n;
+    e->k_area = k_area;
+    e->C = f->C;
+    e->R = f->R;
+    if (f->C > 17 || f->R > 17) return OR_EINVAL;
+    return OR_OK;
+}
+
+int oracle_mt_count(int W, int H, int n, int k_area, uint64_t *count) {
+    if (!count) return OR_EINVAL;
+    const int C = (W + OR_CTU - 1) / OR_CTU, R = (H + OR_CTU - 1) / OR_CTU;
+    size_t cells = (size_t)(C > 0 ? C : 1) * (R > 0 ? R : 1);
+    uint64_t *ones = (uint64_t *)calloc(cells, sizeof(uint64_t));
+    uint32_t *zeros = (uint32_t *)calloc(cells, sizeof(uint32_t));
+    if (!ones || !zeros) {
+        free(ones);
+        free(zeros);
+        return OR_ENOMEM;
+    }
+    frame_t f = {W, H, C, R, ones, ones, NULL, zeros};
+    uint64_t *N = (uint64_t *)calloc(cells, sizeof(uint64_t));
+    if (!N) {
+        free(ones);
+        free(zeros);
+        return OR_ENOMEM;
+    }
+    for (int y = 0; y < R; ++y)
+        for (int x = 0; x < C; ++x) N[y * C + x] = (uint64_t)ctu_w(&f, x) * ctu_h(&f, y);
+    f.N = N;
+    memo_t m;
+    mt_t e;
+    int st = OR_ENOMEM;
+    if (!memo_init(&m, &f)) {
+        st = mt_setup(&e, &f, &m, W, H, n, k_area);
+        if (st == OR_OK) {
+            e.mode = 2;
+            mt_all(&e);
+            if (e.oom) {
+                st = OR_ENOMEM;
+            } else {
+                cmp_keys_n = n;
+                qsort(e.keys, e.nkeys, (size_t)n * 4 * sizeof(int16_t), cmp_keys);
+                uint64_t distinct = 0;
+                for (size_t i = 0; i < e.nkeys; ++i)
+                    if (i == 0 || cmp_keys(e.keys + (i - 1) * (size_t)n * 4, e.keys + i * (size_t)n * 4)) distinct++;
+                *count = distinct;
+            }
+            free(e.keys);
+        }
+    }
+    memo_free(&m);
+    free(ones);
+    free(zeros);
+    free(N);
+    return st;
+}
+
+int oracle_mt_search(int W, int H, const uint64_t *S1, const uint64_t *S2, const uint64_t *N, const uint32_t *Tq,
+                     int n, int k_area, uint32_t lambda_q, oracle_mt_result *res) {
+    memset(res, 0, sizeof(*res));
+    frame_t f = {W, H, (W + OR_CTU - 1) / OR_CTU, (H + OR_CTU - 1) / OR_CTU, S1, S2, N, Tq};
+    memo_t m;
+    if (memo_init(&m, &f)) {
+        memo_free(&m);
+        res->status = OR_ENOMEM;
+        return OR_ENOMEM;
+    }
+    mt_t e;
+    int st = mt_setup(&e, &f, &m, W, H, n, k_area);
+    if (st) {
+        memo_free(&m);
+        res->status = st;
+        return st;
+    }
+    e.mode = 0;
+    e.t_min = OR_INF;
+    mt_all(&e);
+    res->n = n;
+    if (e.t_min == OR_INF) {
+        memo_free(&m);
+        res->status = OR_EINFEASIBLE;
+        return OR_EINFEASIBLE;
+    }
+    e.thr = eq4_thr(e.t_min, lambda_q);
+    e.mode = 1;
+    mt_all(&e);
+    res->t_min = e.t_min;
+    res->thr = e.thr;
+    res->t = e.best_t;
+    res->q = e.best_q;
+    long double sse = 0.0L;
+    for (int i = 0; i < n; ++i) {
+        res->region[i][0] = (int16_t)e.best_key[i][1];
+        res->region[i][1] = (int16_t)e.best_key[i][0];
+        res->region[i][2] = (int16_t)e.best_key[i][3];
+        res->region[i][3] = (int16_t)e.best_key[i][2];
+        rsum_t s = memo_get(&m, e.best_key[i][1], e.best_key[i][3], e.best_key[i][0], e.best_key[i][2]);
+        sse += sse_exact(s.S1, s.S2, s.N);
+    }
+    res->sse_real = (double)sse;
+    memo_free(&m);
+    res->status = OR_OK;
+    return OR_OK;
+}
+
+size_t oracle_mt_result_size(void) { return sizeof(oracle_mt_result); }
 
 /* Objective of a given partition by direct sums (used to check any result). */
 int oracle_evaluate(int W, int H, const uint64_t *S1, const uint64_t *S2, const uint64_t *N,

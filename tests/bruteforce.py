@@ -129,3 +129,108 @@ def search_in_windows(W, H, S1, S2, Tq, n, lam_q, window_step, k=3):
     feas = [c for c in cands if c[2] * 65536 <= t_min * (65536 + lam_q)]
     best = min(feas, key=lambda c: (c[3], c[0]))
     return dict(t_min=t_min, t=best[2], q=best[3], regions=best[1], n_windows=len(kept))
+
+
+# --- multi-tile rectangular slices (slices of one tile, or unions of whole tiles) ---
+
+def _ctu_rect_partitions(C, R, n):
+    """Every partition of the C x R CTU grid into exactly n rectangles
+    (x0, x1, y0, y1), built cell by cell from the first free CTU."""
+    free = [[True] * C for _ in range(R)]
+    out = []
+
+    def rec(acc):
+        if len(acc) > n:
+            return
+        for y in range(R):
+            for x in range(C):
+                if free[y][x]:
+                    for x1 in range(x + 1, C + 1):
+                        if not free[y][x1 - 1]:
+                            break
+                        for y1 in range(y + 1, R + 1):
+                            if not all(free[yy][xx] for yy in range(y, y1) for xx in range(x, x1)):
+                                break
+                            for yy in range(y, y1):
+                                for xx in range(x, x1):
+                                    free[yy][xx] = False
+                            acc.append((x, x1, y, y1))
+                            rec(acc)
+                            acc.pop()
+                            for yy in range(y, y1):
+                                for xx in range(x, x1):
+                                    free[yy][xx] = True
+                    return
+        if len(acc) == n:
+            out.append(list(acc))
+
+    rec([])
+    return out
+
+
+def _mt_valid(rects, C, R):
+    """True if some tile grid makes every rectangle either a run of whole CTU
+    rows spanning one tile's width, or a union of whole tiles."""
+    for Y in _subsets(range(1, R)):
+        ys = [0] + sorted(Y) + [R]
+        for X in _subsets(range(1, C)):
+            xs = [0] + sorted(X) + [C]
+            ok = True
+            for i in range(len(xs) - 1):
+                for j in range(len(ys) - 1):
+                    tx0, tx1, ty0, ty1 = xs[i], xs[i + 1], ys[j], ys[j + 1]
+                    inside = [r for r in rects if r[0] < tx1 and r[1] > tx0 and r[2] < ty1 and r[3] > ty0]
+                    whole = [r for r in inside if r[0] <= tx0 and r[1] >= tx1 and r[2] <= ty0 and r[3] >= ty1]
+                    if whole and (whole[0][1] - whole[0][0], whole[0][3] - whole[0][2]) != (tx1 - tx0, ty1 - ty0):
+                        # a union of tiles: its edges on tile lines
+                        r = whole[0]
+                        if len(inside) != 1 or r[0] not in xs or r[1] not in xs or r[2] not in ys or r[3] not in ys:
+                            ok = False
+                    elif not all(r[0] == tx0 and r[1] == tx1 and r[2] >= ty0 and r[3] <= ty1 for r in inside):
+                        ok = False
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            if ok:
+                return True
+    return False
+
+
+def mt_partitions(W, H, n, k=3):
+    """Distinct slice sets of the multi-tile space with the area rule, as
+    raster-sorted tuples of (x0, x1, y0, y1) in CTUs."""
+    C, R, cw, ch = geometry(W, H)
+    found = []
+    for rects in _ctu_rect_partitions(C, R, n):
+        areas = [sum(cw[r[0]:r[1]]) * sum(ch[r[2]:r[3]]) for r in rects]
+        if not (k * min(areas) > max(areas)):
+            continue
+        if _mt_valid(rects, C, R):
+            found.append(tuple(sorted(rects, key=lambda r: (r[2], r[0]))))
+    return found
+
+
+def mt_search(W, H, S1, S2, Tq, n, lam_q, k=3):
+    """The multi-tile search by brute force: T_min, then the smallest
+    (Q, raster-sorted slice list) among slice sets meeting Eq. 4."""
+    C, R, cw, ch = geometry(W, H)
+
+    def rsum(a, r):
+        return sum(a[y][x] for y in range(r[2], r[3]) for x in range(r[0], r[1]))
+
+    cands = []
+    for key in mt_partitions(W, H, n, k):
+        t = max(rsum(Tq, r) for r in key)
+        q = 0
+        for r in key:
+            a = sum(cw[r[0]:r[1]]) * sum(ch[r[2]:r[3]])
+            s1 = rsum(S1, r)
+            q += rsum(S2, r) - (-(-s1 * s1 // a))
+        cands.append((key, t, q))
+    if not cands:
+        return None
+    t_min = min(c[1] for c in cands)
+    feas = [c for c in cands if c[1] * 65536 <= t_min * (65536 + lam_q)]
+    key, t, q = min(feas, key=lambda c: (c[2], [(r[2], r[0], r[3], r[1]) for r in c[0]]))
+    return dict(t_min=t_min, t=t, q=q, regions=list(key), count=len(cands))

@@ -1,0 +1,65 @@
+"""Pins of the oracle's multi-tile slice search (slices of one tile, or
+rectangles of two or more whole tiles; Sec. 1, Fig. 1b).
+
+The oracle enumerates tile grids and groups their tiles into rectangles; the
+pure-Python brute force instead cuts the CTU grid into every set of n
+rectangles and asks whether some tile grid realises it.  The two methods
+share nothing but the definition, so equal counts and equal decisions on
+tiny frames pin the enumeration.  The single-tile-row space S(n) is a subset:
+T_min can only fall, and the space can only grow.
+"""
+
+import numpy as np
+import pytest
+
+import bruteforce
+from test_oracle_search import random_instance, stats_from
+
+
+@pytest.mark.parametrize("W,H,n", [(256, 256, 2), (384, 256, 3), (384, 384, 3), (512, 256, 4), (300, 200, 3),
+                                   (512, 384, 4), (384, 384, 4), (640, 256, 3), (128, 384, 2), (256, 128, 1)])
+def test_count_matches_bruteforce(oracle, W, H, n):
+    assert oracle.mt_count(W, H, n) == len(bruteforce.mt_partitions(W, H, n))
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_search_matches_bruteforce(oracle, seed):
+    rng = np.random.default_rng(900 + seed)
+    W, H = [(384, 384), (512, 256), (300, 200), (512, 384), (640, 256), (384, 300)][seed % 6]
+    n = [2, 3, 4][seed % 3]
+    mode = ["random", "flat", "uniform"][seed % 3]
+    lam = [0.0, 0.1, 0.3][(seed // 3) % 3]
+    S1, S2, N, Tq = random_instance(rng, W, H, mode)
+    st = stats_from(oracle, W, H, S1, S2, N)
+    got = oracle.mt_search(st, Tq, n, lam)
+    ref = bruteforce.mt_search(W, H, S1.tolist(), S2.tolist(), Tq.astype(np.int64).tolist(), n,
+                               oracle.lambda_q(lam))
+    if ref is None:
+        assert got["status"] == oracle.EINFEASIBLE
+        return
+    assert got["status"] == oracle.OK
+    assert (got["t_min"], got["t"], got["q"]) == (ref["t_min"], ref["t"], ref["q"])
+    # regions: (x0, y0, x1, y1) in raster order vs the brute force's (x0, x1, y0, y1)
+    assert got["regions"] == [(r[0], r[2], r[1], r[3]) for r in ref["regions"]]
+
+
+@pytest.mark.parametrize("W,H,n", [(832, 480, 4), (384, 384, 3), (512, 384, 4)])
+def test_single_tile_row_space_is_a_subset(oracle, W, H, n):
+    from paper_2012_14792_gb300 import trs
+    assert oracle.mt_count(W, H, n) >= trs.trs_count_partitions(W, H, n)
+    rng = np.random.default_rng(W + n)
+    S1, S2, N, Tq = random_instance(rng, W, H, "random")
+    st = stats_from(oracle, W, H, S1, S2, N)
+    mt = oracle.mt_search(st, Tq, n, 0.1)
+    one = oracle.search_dp(st, Tq, n, 0.1)
+    assert mt["t_min"] <= one.t_min
+
+
+def test_single_slice_and_invalid(oracle):
+    rng = np.random.default_rng(5)
+    S1, S2, N, Tq = random_instance(rng, 384, 384, "random")
+    st = stats_from(oracle, 384, 384, S1, S2, N)
+    got = oracle.mt_search(st, Tq, 1, 0.0)
+    assert got["status"] == oracle.OK and got["regions"] == [(0, 0, 3, 3)]
+    assert got["t_min"] == int(Tq.astype(np.int64).sum())
+    assert oracle.mt_search(st, Tq, 10, 0.0)["status"] == oracle.EINFEASIBLE  # 9 CTUs
