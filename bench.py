@@ -371,6 +371,58 @@ def run_serving(trs, device: int, duration_s: float = 7.0, saturate_s: float = 1
         trs.trs_server_destroy(srv)
 
 
+def run_multi_tile(runtime, trs, device: int, reps: int = 50):
+    """Multi-tile rectangular slices (trs_search_mt) on one 1920x1080 frame:
+    the slice-set list is built on the host once per shape (timed apart), then
+    the device search (three passes over the list, one decode warp) is timed
+    alone with CUDA events on its stream."""
+    import torch
+    import synth
+    spec = synth.SPEC_1080P10
+    W, H = spec.width, spec.height
+    plane, times = synth.make_frame(spec, seed=7)
+    dev = f"cuda:{device}"
+    dec = runtime.Decider(max_width=W, max_height=H, max_regions=8, max_batch=1, device=device)
+    res = []
+    try:
+        luma, pitch = runtime.luma_to_device(plane, dev)
+        st = dec.stats_buffers(W, H)
+        dec.texture_map(luma, W, H, pitch, spec.bit_depth, st)
+        tab = dec.tables_buffer(W, H)
+        dec.region_tables(st, torch.from_numpy(times).to(dev), W, H, tab)
+        out = torch.zeros(trs.MT_PARTITION_BYTES, dtype=torch.uint8, device=dev)
+        s = torch.cuda.current_stream(device)
+        for n in (6, 7):
+            t0 = time.perf_counter()
+            trs.trs_search_mt(dec.ctx, tab, W, H, n, 0.1, out)
+            torch.cuda.synchronize(device)
+            build_s = time.perf_counter() - t0
+            for _ in range(3):
+                trs.trs_search_mt(dec.ctx, tab, W, H, n, 0.1, out)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(device)
+            e0.record(s)
+            for _ in range(reps):
+                trs.trs_search_mt(dec.ctx, tab, W, H, n, 0.1, out)
+            e1.record(s)
+            torch.cuda.synchronize(device)
+            ms = e0.elapsed_time(e1) / reps
+            rec = trs.trs_mt_partition.from_buffer_copy(out.cpu().numpy().tobytes())
+            one = dec.partitions(dec.search(tab, W, H, n, 0.1))[0]
+            list_bytes = rec.candidates * n * 4
+            res.append({"frame": "1920x1080", "n": n, "lambda": 0.1, "status": rec.status,
+                        "slice_sets": rec.candidates, "list_build_s": round(build_s, 3),
+                        "ms_per_search": ms, "searches_per_s": 1e3 / ms,
+                        "slice_sets_per_s": rec.candidates / (ms / 1e3),
+                        "list_read_gbs": 3 * list_bytes / (ms / 1e3) / 1e9,
+                        "launches_per_search": 4, "t_min_multi_tile": rec.t_min,
+                        "t_min_single_tile_row": one.t_min, "q_multi_tile": rec.q, "q_single_tile_row": one.q})
+    finally:
+        dec.close()
+    return {"searches": res, "note": "list read three times per search (L2-resident at these sizes); "
+                                     "memset + 3 passes + decode per search"}
+
+
 def run_reference(args, rank, world):
     """Reference arm: the oracle timed on this host's cores, same metric."""
     if rank != 0:
@@ -412,6 +464,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-light", action="store_true")
+    ap.add_argument("--no-mt", action="store_true", help="skip the multi-tile slice search timing")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default launch shapes (short profiling runs)")
     ap.add_argument("--in-flight", type=int, default=IN_FLIGHT, choices=[1, 2, 3],
@@ -667,6 +720,10 @@ def main():
         mixed_res = run_mixed(runtime, trs, mixed, local, max(3, args.steps // 20), args.warmup, args.parts,
                               args.in_flight)
 
+    multi_tile = None
+    if not args.no_mt:
+        multi_tile = run_multi_tile(runtime, trs, local)
+
     cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(frames)
@@ -686,7 +743,7 @@ def main():
                 "stage_ms": stage, "stage_frames": stage_frames,
                 "stage_ms_overlapped": stage_overlap, "stage_frames_overlapped": overlap_frames,
                 "no_overlap": no_overlap, "autotune": tune, "mixed_256": mixed_res, "lightweight": light,
-                "serving": serving,
+                "serving": serving, "multi_tile": multi_tile,
                 "clocks": clk.summary(), "e2e": e2e,
                 "gpu_launches": launches, "roofline": roof, "roofline_texture": tex_roof,
                 "search_space": search_space,

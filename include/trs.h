@@ -235,6 +235,48 @@ int trs_region_tables(trs_ctx *ctx, const trs_ctu_stats *stats, const float *ctu
 int trs_search(trs_ctx *ctx, const void *tables_dev, int width, int height, int n_regions, float lambda,
                trs_partition *out_dev, void *stream);
 
+/* Multi-tile rectangular slices (Sec. 1, Fig. 1b: a rectangular slice may
+ * also be a rectangle of several complete tiles).  The space: every tile
+ * grid, its tiles grouped into rectangles of tiles; a one-tile group holds
+ * k >= 1 in-tile slices (runs of whole CTU rows), a larger group is one
+ * slice; exactly n slices; the k*A_min > A_max rule in luma samples.  A grid
+ * with a line at every slice edge realises any partition of the CTU grid
+ * into rectangles, so the space is exactly those partitions; it contains the
+ * single-tile-row space of trs_search.  The search is an enumeration: the
+ * host lists the slice sets of a frame shape once, in increasing order of
+ * their slice lists (raster order, (y0, x0, y1, x1) per slice), one GPU
+ * thread evaluates each from the region tables; ties on Q go to the first
+ * set of that order.  The tile grid of the winner: column and row lines at
+ * its slices' edges.  Shapes are limited by the size of the list. */
+typedef struct trs_mt_partition {
+    int32_t status;          /* TRS_OK, TRS_ERANGE or TRS_EINFEASIBLE */
+    int32_t n_regions;
+    int64_t candidates;      /* slice sets searched */
+    int64_t winner;          /* index of the winner in the list, -1 if none */
+    uint64_t t_min_q;        /* Eq. 3 over this space, Q16 */
+    uint64_t thr_q;          /* largest time Eq. 4 admits */
+    uint64_t t_q, q;         /* T(P*) and Q(P*) */
+    double t_min, t, sse;    /* T_min, T(P*) in time units; exact SSE of P* */
+    int16_t region[TRS_MAX_REGIONS][4];  /* x0, y0, x1, y1 in CTUs, raster order */
+} trs_mt_partition;
+
+/* Host only: the number of slice sets of the multi-tile space for a frame
+ * shape (k_area as in trs_opts).  TRS_EINVAL for a shape beyond
+ * TRS_MAX_COLS x TRS_MAX_ROWS CTUs, n outside 1..TRS_MAX_REGIONS, or a list
+ * beyond the enumerated form (more than 2^22 slice sets, 256 MiB, or 2^28
+ * partial partitions visited; 1920x1080 holds up to n = 8, 3840x2160 up to
+ * n = 5).  A shape with no valid set counts 0. */
+int trs_mt_count(int width, int height, int n_regions, int k_area, int64_t *count);
+
+/* Searches the multi-tile space of the frame whose region tables are in
+ * tables_dev (trs_region_tables): T_min (Eq. 3), then the smallest Q (Eq. 2)
+ * among slice sets within Eq. 4's bound.  Writes one trs_mt_partition to
+ * out_dev (device memory).  The first call for a shape enumerates it on the
+ * host and keeps the list on the device.  Errors as trs_mt_count, plus
+ * TRS_EINVAL for bad arguments. */
+int trs_search_mt(trs_ctx *ctx, const void *tables_dev, int width, int height, int n_regions, float lambda,
+                  trs_mt_partition *out_dev, void *stream);
+
 /* Both search steps for several trade-offs at once: the paper tries
  * lambda in {0, 0.1, 0.3} and keeps the best per resolution and thread
  * count (Sec. 3.2).  Step 1 (T_min, Eq. 3) does not depend on lambda and

@@ -21,7 +21,7 @@ INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
-SOURCES = ["texture.cu", "tables.cu", "search.cu", "plan.cu", "api.cu", "noalloc.cu", "server.cu", "alu.cu"]
+SOURCES = ["texture.cu", "tables.cu", "search.cu", "plan.cu", "api.cu", "noalloc.cu", "server.cu", "alu.cu", "mt.cu"]
 
 
 def _nvcc() -> str:

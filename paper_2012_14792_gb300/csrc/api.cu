@@ -136,6 +136,7 @@ size_t trs_sizeof(const char *name) {
     if (!std::strcmp(name, "trs_decision")) return sizeof(trs_decision);
     if (!std::strcmp(name, "trs_server_stats")) return sizeof(trs_server_stats);
     if (!std::strcmp(name, "trs_tune_report")) return sizeof(trs_tune_report);
+    if (!std::strcmp(name, "trs_mt_partition")) return sizeof(trs_mt_partition);
     return 0;
 }
 
@@ -226,6 +227,11 @@ int trs_destroy(trs_ctx *c) {
         dev_free(p.second->blob);
         delete p.second;
     }
+    for (auto &m : c->mt) {
+        dev_free(m.second->cands);
+        delete m.second;
+    }
+    dev_free(c->mt_scal);
     DevBuf *bufs[] = {&c->s1, &c->s2, &c->cnt, &c->vmax, &c->flags, &c->tables, &c->scratch, &c->scal,
                       &c->part, &c->luma_stage, &c->time_stage, &c->arena, &c->desc,
                       &c->hb_luma, &c->hb_time, &c->hb_out};

@@ -50,6 +50,14 @@ constexpr int kChunkMin = 4;         // fewest frames in a chunk
 
 }  // namespace trs
 
+namespace trs {
+// The multi-tile candidate list of one frame shape, on the device.
+struct MtEntry {
+    DevBuf cands;        // count * n * 4 bytes: (y0, x0, y1, x1) per slice, raster order
+    int64_t count = 0;
+};
+}  // namespace trs
+
 struct trs_ctx {
     trs_opts o{};
     size_t total = 0;
@@ -76,6 +84,9 @@ struct trs_ctx {
     trs::DevBuf hb_luma, hb_time, hb_out;
     trs::SearchTune tune;  // launch shapes of the search kernels (trs_autotune)
     std::map<std::vector<int64_t>, trs::BatchGraph> graphs;
+    // multi-tile search: candidate lists by (W, H, n), and its three result words
+    std::map<std::tuple<int, int, int>, trs::MtEntry *> mt;
+    trs::DevBuf mt_scal;
 };
 
 namespace trs {

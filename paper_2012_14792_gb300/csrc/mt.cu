@@ -1,0 +1,344 @@
+// Multi-tile rectangular slices: the search over the wider slice shapes of
+// Sec. 1 / Fig. 1b, where a rectangular slice is either a run of whole CTU
+// rows inside one tile or a rectangle of whole tiles.
+//
+// With the tile grid free, this space is exactly the partitions of the CTU
+// grid into n rectangles: a valid slice set is such a partition, and any such
+// partition is realised by the tile grid whose column and row lines are all
+// of the slices' edges (every slice is then a rectangle of whole tiles).
+// No decomposition like the single-tile-row search holds, so the space is
+// enumerated:
+//
+//  * host, once per frame shape: the first free CTU in raster order is the
+//    top-left corner of the next slice; its height, then its width, grow in
+//    turn.  Every partition is made once, its slices come in raster order and
+//    the partitions in increasing (y0, x0, y1, x1, ...) order, which is the
+//    tie order.  The k*A_min > A_max rule (luma samples) prunes: a new slice
+//    must keep the rule among the slices so far, and the free area must fit
+//    the slices left.  Each set is stored as (y0, x0, y1, x1) bytes per slice.
+//  * device: one thread per slice set reads each slice's time and quality
+//    term from the region tables (any rectangle of CTUs is a tile-column
+//    slice there), and three grid-wide minima give T_min (Eq. 3), Q* (Eq. 2
+//    under Eq. 4) and the first slice set reaching Q*; one warp decodes it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "ctx.h"
+#include "trs_internal.cuh"
+
+namespace trs {
+
+namespace {
+
+constexpr int64_t kMtMaxSets = 1 << 22;        // slice sets kept
+constexpr size_t kMtMaxBytes = size_t(1) << 28;  // bytes of the kept list
+constexpr int64_t kMtMaxVisits = 1ll << 28;    // partial partitions visited
+
+struct MtEnum {
+    int W, H, C, R, n, k;
+    uint64_t freem[kMaxR];   // per CTU row: free CTUs, bit x
+    uint64_t free_area;      // luma samples not yet in a slice
+    uint8_t cur[kMaxN][4];   // slices so far: y0, x0, y1, x1
+    int ns;
+    int64_t visits, sets;
+    bool over;
+    std::vector<uint8_t> *keys;
+
+    // consecutive free CTUs of row y from column x
+    int run(int y, int x) const {
+        const uint64_t v = ~(freem[y] >> x);
+        return v ? __builtin_ctzll(v) : 64 - x;
+    }
+
+    void emit() {
+        if (++sets > kMtMaxSets || keys->size() + (size_t)n * 4 > kMtMaxBytes) {
+            over = true;
+            return;
+        }
+        keys->insert(keys->end(), &cur[0][0], &cur[0][0] + (size_t)n * 4);
+    }
+
+    // amin / amax: smallest and largest slice area so far (none: ~0, 0)
+    void rec(int ry, uint64_t amin, uint64_t amax) {
+        if (over) return;
+        if (++visits > kMtMaxVisits) {
+            over = true;
+            return;
+        }
+        while (ry < R && freem[ry] == 0) ++ry;
+        if (ry == R) {
+            if (ns == n) emit();
+            return;
+        }
+        if (ns == n) return;
+        const int x = __builtin_ctzll(freem[ry]);
+        const uint64_t m = (uint64_t)(n - ns - 1);  // slices after this one
+        const uint64_t px0 = line_px(x, W), py0 = line_px(ry, H);
+        int maxw = C - x;
+        for (int h = 1; ry + h <= R; ++h) {
+            maxw = std::min(maxw, run(ry + h - 1, x));
+            if (maxw == 0) break;
+            const uint64_t ph = line_px(ry + h, H) - py0;
+            for (int w = 1; w <= maxw; ++w) {
+                const uint64_t a = (line_px(x + w, W) - px0) * ph;
+                const uint64_t na = std::min(amin, a), xa = std::max(amax, a);
+                if ((uint64_t)k * na <= xa) {
+                    if (a >= amin) break;  // only larger areas follow in this row
+                    continue;
+                }
+                const uint64_t f = free_area - a;
+                if (m == 0 ? f != 0 : (f == 0 || (uint64_t)k * f <= m * xa || f >= m * (uint64_t)k * na))
+                    continue;
+                const uint64_t bits = ((w == 64 ? ~0ull : ((1ull << w) - 1)) << x);
+                for (int y = ry; y < ry + h; ++y) freem[y] &= ~bits;
+                cur[ns][0] = (uint8_t)ry;
+                cur[ns][1] = (uint8_t)x;
+                cur[ns][2] = (uint8_t)(ry + h);
+                cur[ns][3] = (uint8_t)(x + w);
+                ++ns;
+                free_area = f;
+                rec(ry, na, xa);
+                free_area += a;
+                --ns;
+                for (int y = ry; y < ry + h; ++y) freem[y] |= bits;
+                if (over) return;
+            }
+        }
+    }
+};
+
+}  // namespace
+
+// The slice-set list of a frame shape in tie order (n * 4 bytes each).
+int mt_enumerate(int W, int H, int n, int k, std::vector<uint8_t> *keys, int64_t *count) {
+    if (W <= 0 || H <= 0 || n < 1 || n > kMaxN || k < 1) return TRS_EINVAL;
+    const int C = (W + kCtu - 1) / kCtu, R = (H + kCtu - 1) / kCtu;
+    if (C > kMaxC || R > kMaxR) return TRS_EINVAL;
+    keys->clear();
+    MtEnum e;
+    e.W = W;
+    e.H = H;
+    e.C = C;
+    e.R = R;
+    e.n = n;
+    e.k = k;
+    for (int y = 0; y < R; ++y) e.freem[y] = C == 64 ? ~0ull : (1ull << C) - 1;
+    e.free_area = (uint64_t)W * H;
+    e.ns = 0;
+    e.visits = 0;
+    e.sets = 0;
+    e.over = false;
+    e.keys = keys;
+    e.rec(0, ~0ull, 0);
+    if (e.over) {
+        keys->clear();
+        return TRS_EINVAL;
+    }
+    *count = e.sets;
+    return TRS_OK;
+}
+
+namespace {
+
+struct MtArgs {
+    const uint8_t *cands;  // count * n * 4 bytes: (y0, x0, y1, x1) per slice
+    int64_t count;
+    int n, C, R, W, H;
+    const uint8_t *tables;
+    uint64_t *scal;        // [0] T_min, [1] Q*, [2] first slice set reaching Q*
+    uint32_t lambda_q;
+    trs_mt_partition *out;
+};
+
+__device__ __forceinline__ uint64_t warp_min64(uint64_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = u < v ? u : v;
+    }
+    return v;
+}
+
+// Time (max over slices, Eq. 1) and quality term (sum, Eq. 2) of slice set c.
+__device__ __forceinline__ void mt_eval(const MtArgs &a, const uint64_t *RT, const uint64_t *RQ, int64_t c,
+                                        uint64_t *tmax, uint64_t *qsum) {
+    const uint8_t *s = a.cands + (size_t)c * a.n * 4;
+    uint64_t t = 0, q = 0;
+    for (int i = 0; i < a.n; ++i) {
+        const int y0 = s[4 * i], x0 = s[4 * i + 1], y1 = s[4 * i + 2], x1 = s[4 * i + 3];
+        const size_t e = ((size_t)band_index(a.C, x0, x1) * a.R + (y1 - y0 - 1)) * a.R + y0;
+        const uint64_t tv = RT[e];
+        t = tv > t ? tv : t;
+        q += RQ[e];
+    }
+    *tmax = t;
+    *qsum = q;
+}
+
+// PASS 0: T_min; PASS 1: Q* among sets within Eq. 4's bound; PASS 2: the
+// first set (list order) within the bound reaching Q*.  Grid-stride loop,
+// per-thread minima, one warp reduction and one atomic per warp.
+template <int PASS>
+__global__ void __launch_bounds__(256) mt_pass_kernel(MtArgs a) {
+    const TablesOffsets off = tables_offsets(a.C, a.R);
+    if (reinterpret_cast<const int32_t *>(a.tables + off.status)[0] != TRS_OK) return;
+    const uint64_t *RT = reinterpret_cast<const uint64_t *>(a.tables + off.rect_t);
+    const uint64_t *RQ = reinterpret_cast<const uint64_t *>(a.tables + off.rect_q);
+    const uint64_t thr = PASS == 0 ? kInf : eq4_threshold(a.scal[0], a.lambda_q);
+    const uint64_t qstar = PASS == 2 ? a.scal[1] : kInf;
+    uint64_t best = kInf;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < a.count; c += stride) {
+        uint64_t t, q;
+        mt_eval(a, RT, RQ, c, &t, &q);
+        if (PASS == 0) {
+            best = t < best ? t : best;
+        } else if (t <= thr) {
+            if (PASS == 1) best = q < best ? q : best;
+            else if (q == qstar && (uint64_t)c < best) best = (uint64_t)c;
+        }
+    }
+    best = warp_min64(best);
+    if ((threadIdx.x & 31) == 0 && best != kInf)
+        atomicMin(reinterpret_cast<unsigned long long *>(&a.scal[PASS]), (unsigned long long)best);
+}
+
+// One warp: lane i decodes slice i of the winner.
+__global__ void __launch_bounds__(32) mt_finish_kernel(MtArgs a) {
+    const int lane = threadIdx.x;
+    trs_mt_partition *out = a.out;
+    uint64_t *words = reinterpret_cast<uint64_t *>(out);
+    for (int i = lane; i < (int)(sizeof(trs_mt_partition) / 8); i += 32) words[i] = 0;
+    __syncwarp();
+    const TablesOffsets off = tables_offsets(a.C, a.R);
+    int32_t status = reinterpret_cast<const int32_t *>(a.tables + off.status)[0];
+    const uint64_t t_min = a.scal[0], win = a.scal[2];
+    if (status == TRS_OK && (t_min == kInf || win >= (uint64_t)a.count)) status = TRS_EINFEASIBLE;
+    if (status != TRS_OK) {
+        if (lane == 0) {
+            out->status = status;
+            out->n_regions = a.n;
+            out->candidates = a.count;
+            out->winner = -1;
+        }
+        return;
+    }
+    const uint64_t *RT = reinterpret_cast<const uint64_t *>(a.tables + off.rect_t);
+    const uint64_t *RQ = reinterpret_cast<const uint64_t *>(a.tables + off.rect_q);
+    const uint64_t *sat1 = reinterpret_cast<const uint64_t *>(a.tables + off.sat_s1);
+    uint64_t t = 0, q = 0;
+    double sse = 0.0;
+    if (lane < a.n) {
+        const uint8_t *s = a.cands + ((size_t)win * a.n + lane) * 4;
+        const int y0 = s[0], x0 = s[1], y1 = s[2], x1 = s[3];
+        const size_t e = ((size_t)band_index(a.C, x0, x1) * a.R + (y1 - y0 - 1)) * a.R + y0;
+        t = RT[e];
+        q = RQ[e];
+        const int C1 = a.C + 1;
+        const uint64_t s1 = sat1[y1 * C1 + x1] - sat1[y0 * C1 + x1] - sat1[y1 * C1 + x0] + sat1[y0 * C1 + x0];
+        const uint32_t np = (line_px(x1, a.W) - line_px(x0, a.W)) * (line_px(y1, a.H) - line_px(y0, a.H));
+        uint32_t rem;
+        (void)ceil_square_div(s1, np, &rem);
+        sse = (double)q + (rem ? (double)(np - rem) / (double)np : 0.0);  // exact SSE = floor + fraction
+        out->region[lane][0] = (int16_t)x0;
+        out->region[lane][1] = (int16_t)y0;
+        out->region[lane][2] = (int16_t)x1;
+        out->region[lane][3] = (int16_t)y1;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t tu = __shfl_xor_sync(0xffffffffu, t, o);
+        t = tu > t ? tu : t;
+        q += __shfl_xor_sync(0xffffffffu, q, o);
+        sse += __shfl_xor_sync(0xffffffffu, sse, o);
+    }
+    if (lane == 0) {
+        out->n_regions = a.n;
+        out->candidates = a.count;
+        out->winner = (int64_t)win;
+        out->t_min_q = t_min;
+        out->thr_q = eq4_threshold(t_min, a.lambda_q);
+        out->t_q = t;
+        out->q = q;
+        out->t_min = (double)t_min / 65536.0;
+        out->t = (double)t / 65536.0;
+        out->sse = sse;
+        // consistency guard: the winner's sums must reproduce the reduced minima
+        out->status = (q != a.scal[1] || t > out->thr_q) ? TRS_EINFEASIBLE : TRS_OK;
+    }
+}
+
+}  // namespace
+
+}  // namespace trs
+
+using namespace trs;
+
+extern "C" {
+
+int trs_mt_count(int width, int height, int n, int k, int64_t *count) {
+    if (!count) return TRS_EINVAL;
+    std::vector<uint8_t> keys;
+    return mt_enumerate(width, height, n, k, &keys, count);
+}
+
+int trs_search_mt(trs_ctx *ctx, const void *tables, int W, int H, int n, float lambda, trs_mt_partition *out,
+                  void *stream) {
+    if (!ctx || !tables || !out || (uintptr_t)tables % 256) return TRS_EINVAL;
+    TRS_TRY(check_frame(ctx, W, H));
+    if (n < 1 || n > ctx->o.max_regions) return TRS_EINVAL;
+    if (!std::isfinite(lambda) || lambda < 0.0f || lambda > 1000.0f) return TRS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const auto key = std::make_tuple(W, H, n);
+    MtEntry *me;
+    auto it = ctx->mt.find(key);
+    if (it != ctx->mt.end()) {
+        me = it->second;
+    } else {
+        std::vector<uint8_t> keys;
+        int64_t count = 0;
+        TRS_TRY(mt_enumerate(W, H, n, ctx->o.k_area, &keys, &count));
+        me = new MtEntry;
+        me->count = count;
+        int st = dev_alloc(me->cands, keys.size(), &ctx->total);
+        if (st == TRS_OK && !keys.empty() && cudaMemcpy(me->cands.p, keys.data(), keys.size(),
+                                                         cudaMemcpyHostToDevice) != cudaSuccess)
+            st = TRS_ECUDA;
+        if (st != TRS_OK) {
+            dev_free(me->cands);
+            delete me;
+            return st;
+        }
+        ctx->mt[key] = me;
+    }
+    TRS_TRY(dev_alloc(ctx->mt_scal, 4 * sizeof(uint64_t), &ctx->total));
+    MtArgs a;
+    a.cands = (const uint8_t *)me->cands.p;
+    a.count = me->count;
+    a.n = n;
+    a.C = (W + kCtu - 1) / kCtu;
+    a.R = (H + kCtu - 1) / kCtu;
+    a.W = W;
+    a.H = H;
+    a.tables = (const uint8_t *)tables;
+    a.scal = (uint64_t *)ctx->mt_scal.p;
+    a.lambda_q = lambda_to_q(lambda);
+    a.out = out;
+    TRS_CK(cudaMemsetAsync(a.scal, 0xff, 3 * sizeof(uint64_t), s));
+    if (a.count > 0) {
+        const int64_t want = (a.count + 255) / 256;
+        const int blocks = (int)std::min<int64_t>(want, 152 * 8);
+        mt_pass_kernel<0><<<blocks, 256, 0, s>>>(a);
+        mt_pass_kernel<1><<<blocks, 256, 0, s>>>(a);
+        mt_pass_kernel<2><<<blocks, 256, 0, s>>>(a);
+    }
+    mt_finish_kernel<<<1, 32, 0, s>>>(a);
+    TRS_CK(cudaGetLastError());
+    return TRS_OK;
+}
+
+}  // extern "C"

@@ -68,6 +68,12 @@ class Decider:
         trs.trs_search(self.ctx, tables, width, height, n, lam, out)
         return out
 
+    def search_mt(self, tables: torch.Tensor, width: int, height: int, n: int, lam: float):
+        """Multi-tile rectangular slices (trs_search_mt); the record read back."""
+        out = torch.zeros(trs.MT_PARTITION_BYTES, dtype=torch.uint8, device=self.device)
+        trs.trs_search_mt(self.ctx, tables, width, height, n, lam, out)
+        return trs.trs_mt_partition.from_buffer_copy(out.cpu().numpy().tobytes())
+
     def search_lambdas(self, tables: torch.Tensor, width: int, height: int, n: int, lams: list) -> torch.Tensor:
         out = torch.zeros(len(lams) * trs.PARTITION_BYTES, dtype=torch.uint8, device=self.device)
         trs.trs_search_lambdas(self.ctx, tables, width, height, n, list(lams), out)

@@ -105,6 +105,20 @@ class trs_tune_report(ct.Structure):
 PARTITION_BYTES = ct.sizeof(trs_partition)
 
 
+class trs_mt_partition(ct.Structure):
+    _fields_ = [("status", ct.c_int32), ("n_regions", ct.c_int32), ("candidates", ct.c_int64),
+                ("winner", ct.c_int64), ("t_min_q", ct.c_uint64), ("thr_q", ct.c_uint64), ("t_q", ct.c_uint64),
+                ("q", ct.c_uint64), ("t_min", ct.c_double), ("t", ct.c_double), ("sse", ct.c_double),
+                ("region", (ct.c_int16 * 4) * MAX_REGIONS)]
+
+    def regions(self) -> list[tuple[int, int, int, int]]:
+        """Slices as (x0, y0, x1, y1) in CTUs, raster order."""
+        return [tuple(int(v) for v in self.region[i]) for i in range(self.n_regions)]
+
+
+MT_PARTITION_BYTES = ct.sizeof(trs_mt_partition)
+
+
 def _load():
     path = _build.LIB
     if not os.path.exists(path):
@@ -120,6 +134,7 @@ def _load():
         "trs_plan_stats": ([i, i, i, i, ct.POINTER(i), ct.POINTER(i)], i),
         "trs_plan_work": ([i, i, i, i, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)], i),
         "trs_count_partitions": ([i, i, i, i, ct.POINTER(ct.c_double)], i),
+        "trs_mt_count": ([i, i, i, i, ct.POINTER(ct.c_int64)], i),
         "trs_alu_peak": ([i, ct.POINTER(ct.c_double)], i),
         "trs_create": ([ct.POINTER(vp), ct.POINTER(trs_opts)], i),
         "trs_destroy": ([vp], i),
@@ -129,6 +144,7 @@ def _load():
         "trs_region_tables": ([vp, ct.POINTER(trs_ctu_stats), vp, i, i, vp, sz, vp], i),
         "trs_search": ([vp, vp, i, i, i, f, vp, vp], i),
         "trs_search_noalloc": ([vp, i, i, i, i, f, vp, vp], i),
+        "trs_search_mt": ([vp, vp, i, i, i, f, vp, vp], i),
         "trs_search_lambdas": ([vp, vp, i, i, i, ct.POINTER(ct.c_float), i, vp, vp], i),
         "trs_decide": ([vp, vp, i, i, sz, i, vp, i, f, vp, vp], i),
         "trs_decide_host": ([vp, vp, i, i, sz, i, vp, i, f, ct.POINTER(trs_partition), vp], i),
@@ -273,6 +289,17 @@ def trs_search_lambdas(ctx, tables, width, height, n_regions, lambdas, out, stre
     arr = (ct.c_float * len(lambdas))(*lambdas)
     _check(_lib.trs_search_lambdas(ctx, _ptr(tables), width, height, n_regions, arr, len(lambdas), _ptr(out),
                                    _stream(stream)), "trs_search_lambdas")
+
+
+def trs_mt_count(width: int, height: int, n_regions: int, k_area: int = 3) -> int:
+    c = ct.c_int64()
+    _check(_lib.trs_mt_count(width, height, n_regions, k_area, ct.byref(c)), "trs_mt_count")
+    return c.value
+
+
+def trs_search_mt(ctx, tables, width, height, n_regions, lam, out, stream=None) -> None:
+    _check(_lib.trs_search_mt(ctx, _ptr(tables), width, height, n_regions, lam, _ptr(out), _stream(stream)),
+           "trs_search_mt")
 
 
 def trs_search_noalloc(tables, width, height, n_regions, k_area, lam, out, stream=None) -> None:

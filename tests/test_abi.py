@@ -38,7 +38,7 @@ def test_every_declared_symbol_is_exported(trs):
 
 @pytest.mark.parametrize("name", ["trs_opts", "trs_ctu_stats", "trs_tables_layout", "trs_partition",
                                   "trs_frame_desc", "trs_server_opts", "trs_decision", "trs_server_stats",
-                                  "trs_tune_report"])
+                                  "trs_tune_report", "trs_mt_partition"])
 def test_struct_sizes_match_binding(trs, name):
     import ctypes
     assert trs.trs_sizeof(name) == ctypes.sizeof(getattr(trs, name))
@@ -101,3 +101,20 @@ def test_count_partitions_without_the_rule_is_the_closed_form(trs, C, R, n):
     expect = sum(comb(C - 1, c - 1) * comb(c * (R - 1), n - c) for c in range(1, min(C, n) + 1))
     got = trs.trs_count_partitions(C * 128, R * 128, n, 1 << 20)
     assert got == pytest.approx(float(expect), rel=1e-15)
+
+
+@pytest.mark.parametrize("W,H,n", [(256, 256, 2), (384, 256, 3), (384, 384, 3), (300, 200, 3), (512, 384, 4),
+                                   (640, 256, 3), (256, 128, 1), (832, 480, 4), (1024, 512, 3), (640, 640, 5)])
+def test_mt_count_matches_oracle(trs, oracle, W, H, n):
+    """The library's host enumeration of the multi-tile space (slices of one
+    tile, or rectangles of whole tiles) finds the oracle's set count."""
+    assert trs.trs_mt_count(W, H, n) == oracle.mt_count(W, H, n)
+
+
+def test_mt_count_limits(trs):
+    assert trs.trs_mt_count(128, 128, 1) == 1
+    assert trs.trs_mt_count(128, 128, 2) == 0          # one CTU cannot hold two slices
+    for bad in [(0, 128, 1), (128, 128, 0), (64 * 128 + 1, 128, 1), (128, 128, trs.MAX_REGIONS + 1)]:
+        with pytest.raises(trs.TrsError) as e:
+            trs.trs_mt_count(*bad)
+        assert e.value.status == trs.EINVAL
