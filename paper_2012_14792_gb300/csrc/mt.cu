@@ -15,7 +15,9 @@
 //    the partitions in increasing (y0, x0, y1, x1, ...) order, which is the
 //    tie order.  The k*A_min > A_max rule (luma samples) prunes: a new slice
 //    must keep the rule among the slices so far, and the free area must fit
-//    the slices left.  Each set is stored as (y0, x0, y1, x1) bytes per slice.
+//    the slices left; so does the corner count of the free region, which
+//    bounds the slices it needs from below.  Each set is stored as
+//    (y0, x0, y1, x1) bytes per slice.
 //  * device: one thread per slice set reads each slice's time and quality
 //    term from the region tables (any rectangle of CTUs is a tile-column
 //    slice there), and three grid-wide minima give T_min (Eq. 3), Q* (Eq. 2
@@ -54,6 +56,27 @@ struct MtEnum {
         return v ? __builtin_ctzll(v) : 64 - x;
     }
 
+    // A lower bound on the slices the free region needs: a grid point with an
+    // odd number of free cells around it is one corner of the region, one
+    // with two diagonal free cells is two, and each is a corner of some slice
+    // in any partition of the region (m rectangles have 4m corners).  Rows
+    // above ry are covered.
+    int corner_bound(int ry) const {
+        typedef unsigned __int128 u128;
+        int corners = 0;
+        u128 up = 0;
+        for (int y = ry; y <= R; ++y) {
+            const u128 dn = y < R ? (u128)freem[y] : 0;
+            const u128 a = up << 1, b = up, c = dn << 1, d = dn;  // the 2x2 cells at each grid point
+            const u128 odd = a ^ b ^ c ^ d;
+            const u128 diag = (a & d & ~b & ~c) | (b & c & ~a & ~d);
+            corners += __builtin_popcountll((uint64_t)odd) + __builtin_popcountll((uint64_t)(odd >> 64)) +
+                       2 * (__builtin_popcountll((uint64_t)diag) + __builtin_popcountll((uint64_t)(diag >> 64)));
+            up = dn;
+        }
+        return (corners + 3) / 4;
+    }
+
     void emit() {
         if (++sets > kMtMaxSets || keys->size() + (size_t)n * 4 > kMtMaxBytes) {
             over = true;
@@ -74,7 +97,7 @@ struct MtEnum {
             if (ns == n) emit();
             return;
         }
-        if (ns == n) return;
+        if (ns == n || corner_bound(ry) > n - ns) return;
         const int x = __builtin_ctzll(freem[ry]);
         const uint64_t m = (uint64_t)(n - ns - 1);  // slices after this one
         const uint64_t px0 = line_px(x, W), py0 = line_px(ry, H);

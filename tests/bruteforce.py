@@ -211,6 +211,55 @@ def mt_partitions(W, H, n, k=3):
     return found
 
 
+
+def guillotine_partitions(W, H, n, k=3):
+    """Partitions of the CTU grid into n rectangles (x0, x1, y0, y1) made by
+    full cuts (a cut runs across the whole rectangle being split, and each
+    side is split again the same way), with the area rule, as raster-sorted
+    tuples.  A partition of a rectangle into at most four rectangles always
+    has such a cut (the smallest one without, the pinwheel, has five pieces),
+    so for n <= 4 this is the whole multi-tile space, at any frame size.
+    Every slice area a meets A/(n k) < a < k A/n (A the frame's area), which
+    bounds the rectangles each sub-problem may hold."""
+    from functools import lru_cache
+    assert 1 <= n <= 4
+    C, R, cw, ch = geometry(W, H)
+    px, py = [0], [0]
+    for w in cw:
+        px.append(px[-1] + w)
+    for h in ch:
+        py.append(py[-1] + h)
+    A = W * H
+
+    def area(x0, x1, y0, y1):
+        return (px[x1] - px[x0]) * (py[y1] - py[y0])
+
+    @lru_cache(maxsize=None)
+    def parts(x0, x1, y0, y1, j):
+        a = area(x0, x1, y0, y1)
+        if not (a * n * k > j * A and a * n < j * k * A):
+            return frozenset()
+        if j == 1:
+            return frozenset([((x0, x1, y0, y1),)])
+        out = set()
+        for j1 in range(1, j):
+            for x in range(x0 + 1, x1):
+                for left in parts(x0, x, y0, y1, j1):
+                    for right in parts(x, x1, y0, y1, j - j1):
+                        out.add(tuple(sorted(left + right)))
+            for y in range(y0 + 1, y1):
+                for top in parts(x0, x1, y0, y, j1):
+                    for bottom in parts(x0, x1, y, y1, j - j1):
+                        out.add(tuple(sorted(top + bottom)))
+        return frozenset(out)
+
+    found = []
+    for p in parts(0, C, 0, R, n):
+        areas = [area(*r) for r in p]
+        if k * min(areas) > max(areas):
+            found.append(tuple(sorted(p, key=lambda r: (r[2], r[0]))))
+    return found
+
 def mt_search(W, H, S1, S2, Tq, n, lam_q, k=3):
     """The multi-tile search by brute force: T_min, then the smallest
     (Q, raster-sorted slice list) among slice sets meeting Eq. 4."""

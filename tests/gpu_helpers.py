@@ -38,3 +38,30 @@ def assert_valid_partition(oracle, p, st, Tq, n, k=3):
     assert ev["t"] == p.t_q and ev["q"] == p.q
     assert p.t_q <= p.thr_q
     assert p.t_min_q <= p.t_q
+
+
+def mt_best(oracle, st, Tq, sets, lam):
+    """The multi-tile decision over an explicit list of slice sets (each a
+    raster-sorted tuple of (x0, x1, y0, y1) CTU rectangles): T_min (Eq. 3),
+    the Q16 bound of Eq. 4, then the smallest (Q, slice list as (y0, x0, y1,
+    x1) per slice) within it, each slice's time and floored SSE from the
+    oracle's direct rectangle sums.  Regions come back as (x0, y0, x1, y1)."""
+    cache = {}
+
+    def rect(r):
+        if r not in cache:
+            cache[r] = oracle.rect(st, Tq, *r)
+        return cache[r]
+
+    cands = []
+    for s in sets:
+        tq = [rect(r) for r in s]
+        key = [(r[2], r[0], r[3], r[1]) for r in s]
+        cands.append((max(t for t, _ in tq), sum(q for _, q in tq), key, s))
+    if not cands:
+        return dict(status=oracle.EINFEASIBLE, count=0)
+    t_min = min(c[0] for c in cands)
+    thr = t_min * (65536 + oracle.lambda_q(lam)) // 65536
+    t, q, _, s = min((c for c in cands if c[0] <= thr), key=lambda c: (c[1], c[2]))
+    return dict(status=oracle.OK, count=len(cands), t_min=t_min, thr=thr, t=t, q=q,
+                regions=[(r[0], r[2], r[1], r[3]) for r in s])

@@ -5,14 +5,15 @@ Small frames: the whole record (T_min, the Eq. 4 bound, T, Q, the slices and
 the list size) equals the oracle's, which enumerates tile grids and groups
 their tiles; the library lists partitions of the CTU grid directly.  Full
 frames: with two slices the space is every straight cut across the frame,
-so T_min and the winner follow from the oracle's rectangle sums over those
-cuts alone."""
+and up to four slices it is every partition made by recursive full cuts, so
+T_min and the winner follow from the oracle's rectangle sums over those
+sets alone."""
 
 import numpy as np
 import pytest
 
 import synth
-from gpu_helpers import SSE_ABS, SSE_REL
+from gpu_helpers import SSE_ABS, SSE_REL, mt_best
 
 pytestmark = pytest.mark.gpu
 
@@ -115,6 +116,27 @@ def test_mt_two_slices_full_frame(dec, oracle, spec_name):
         assert p.status == 0 and p.candidates == len(cands)
         assert (p.t_min_q, p.thr_q, p.t_q, p.q) == (t_min, thr, best[1], best[2])
         assert p.regions() == sorted(best[3], key=lambda r: (r[1], r[0]))
+
+
+@pytest.mark.parametrize("spec_name,n", [("SPEC_1080P10", 3), ("SPEC_1080P10", 4), ("SPEC_2160P10", 3),
+                                         ("SPEC_2160P10", 4)])
+def test_mt_full_frames_up_to_four_slices(dec, oracle, spec_name, n):
+    """Up to four slices every partition has a full cut, so the recursive
+    full-cut enumeration lists the whole space at full frame sizes."""
+    import bruteforce
+    spec = getattr(synth, spec_name)
+    W, H = spec.width, spec.height
+    plane, times = synth.make_frame(spec, seed=35)
+    tab = _tables(dec, plane, times, spec.bit_depth)
+    st = oracle.texture(plane, spec.bit_depth)
+    Tq, _ = oracle.time_q(times)
+    sets = bruteforce.guillotine_partitions(W, H, n)
+    for lam in (0.0, 0.1):
+        ref = mt_best(oracle, st, Tq, sets, lam)
+        p = dec.search_mt(tab, W, H, n, lam)
+        assert p.status == ref["status"] == 0 and p.candidates == ref["count"]
+        assert (p.t_min_q, p.thr_q, p.t_q, p.q) == (ref["t_min"], ref["thr"], ref["t"], ref["q"])
+        assert p.regions() == ref["regions"]
 
 
 def test_mt_no_valid_set_and_out_of_range(dec, oracle):

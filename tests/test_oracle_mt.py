@@ -63,3 +63,28 @@ def test_single_slice_and_invalid(oracle):
     assert got["status"] == oracle.OK and got["regions"] == [(0, 0, 3, 3)]
     assert got["t_min"] == int(Tq.astype(np.int64).sum())
     assert oracle.mt_search(st, Tq, 10, 0.0)["status"] == oracle.EINFEASIBLE  # 9 CTUs
+
+
+@pytest.mark.parametrize("W,H,n", [(384, 384, 3), (512, 384, 4), (384, 384, 4), (640, 256, 3), (300, 200, 3),
+                                   (512, 512, 4), (256, 128, 1), (128, 384, 2)])
+def test_guillotine_cuts_give_the_same_space(W, H, n):
+    """Up to four slices, recursive full cuts reach every partition the
+    brute force finds (and no other), so they can stand in for it on frames
+    far too large for the brute force."""
+    assert sorted(bruteforce.guillotine_partitions(W, H, n)) == sorted(bruteforce.mt_partitions(W, H, n))
+
+
+@pytest.mark.parametrize("W,H,n,lam,seed", [(832, 480, 4, 0.1, 1), (640, 640, 4, 0.0, 2), (1024, 512, 3, 0.3, 3),
+                                            (768, 768, 4, 0.1, 4)])
+def test_decision_over_guillotine_sets_equals_oracle(oracle, W, H, n, lam, seed):
+    from gpu_helpers import mt_best
+    import synth
+    plane, times = synth.small_frame(W, H, 10, seed)
+    st = oracle.texture(plane, 10)
+    Tq, _ = oracle.time_q(times)
+    got = mt_best(oracle, st, Tq, bruteforce.guillotine_partitions(W, H, n), lam)
+    ref = oracle.mt_search(st, Tq, n, lam)
+    assert got["status"] == ref["status"] == oracle.OK
+    assert got["count"] == oracle.mt_count(W, H, n)
+    assert (got["t_min"], got["thr"], got["t"], got["q"], got["regions"]) == \
+        (ref["t_min"], ref["thr"], ref["t"], ref["q"], ref["regions"])
