@@ -218,11 +218,13 @@ def guillotine_partitions(W, H, n, k=3):
     side is split again the same way), with the area rule, as raster-sorted
     tuples.  A partition of a rectangle into at most four rectangles always
     has such a cut (the smallest one without, the pinwheel, has five pieces),
-    so for n <= 4 this is the whole multi-tile space, at any frame size.
+    so for n <= 4 this is the whole multi-tile space, at any frame size;
+    with five, the sides of the first cut hold at most four pieces each, so
+    only the pinwheels are missing (`cut_partitions` adds them).
     Every slice area a meets A/(n k) < a < k A/n (A the frame's area), which
     bounds the rectangles each sub-problem may hold."""
     from functools import lru_cache
-    assert 1 <= n <= 4
+    assert 1 <= n <= 5
     C, R, cw, ch = geometry(W, H)
     px, py = [0], [0]
     for w in cw:
@@ -259,6 +261,38 @@ def guillotine_partitions(W, H, n, k=3):
         if k * min(areas) > max(areas):
             found.append(tuple(sorted(p, key=lambda r: (r[2], r[0]))))
     return found
+
+
+def pinwheels(W, H, k=3):
+    """The five-rectangle partitions without a full cut: a centre rectangle
+    [a, b) x [c, d) strictly inside the grid and four arms turning around it,
+    clockwise or anticlockwise, with the area rule."""
+    C, R, cw, ch = geometry(W, H)
+    px, py = [0], [0]
+    for w in cw:
+        px.append(px[-1] + w)
+    for h in ch:
+        py.append(py[-1] + h)
+    found = []
+    for a in range(1, C):
+        for b in range(a + 1, C):
+            for c in range(1, R):
+                for d in range(c + 1, R):
+                    centre = (a, b, c, d)
+                    turn_cw = [(0, b, 0, c), (b, C, 0, d), (a, C, d, R), (0, a, c, R), centre]
+                    turn_ccw = [(0, a, 0, d), (a, C, 0, c), (b, C, c, R), (0, b, d, R), centre]
+                    for p in (turn_cw, turn_ccw):
+                        areas = [(px[r[1]] - px[r[0]]) * (py[r[3]] - py[r[2]]) for r in p]
+                        if k * min(areas) > max(areas):
+                            found.append(tuple(sorted(p, key=lambda r: (r[2], r[0]))))
+    return found
+
+
+def cut_partitions(W, H, n, k=3):
+    """The whole multi-tile space for n <= 5 at any frame size: full-cut
+    partitions, plus the pinwheels when n = 5."""
+    found = guillotine_partitions(W, H, n, k)
+    return found + pinwheels(W, H, k) if n == 5 else found
 
 def mt_search(W, H, S1, S2, Tq, n, lam_q, k=3):
     """The multi-tile search by brute force: T_min, then the smallest

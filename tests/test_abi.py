@@ -120,12 +120,12 @@ def test_mt_count_limits(trs):
         assert e.value.status == trs.EINVAL
 
 
-@pytest.mark.parametrize("W,H,n", [(1920, 1080, 2), (1920, 1080, 3), (1920, 1080, 4), (3840, 2160, 2),
-                                   (3840, 2160, 3), (3840, 2160, 4), (8192, 4096, 3), (8000, 300, 4),
-                                   (300, 4000, 3)])
-def test_mt_count_full_frames_matches_guillotine_cuts(trs, W, H, n):
+@pytest.mark.parametrize("W,H,n", [(1920, 1080, 2), (1920, 1080, 3), (1920, 1080, 4), (1920, 1080, 5),
+                                   (3840, 2160, 2), (3840, 2160, 3), (3840, 2160, 4), (3840, 2160, 5),
+                                   (8192, 4096, 3), (8000, 300, 4), (300, 4000, 3)])
+def test_mt_count_full_frames_matches_cut_partitions(trs, W, H, n):
     """At full frame sizes (and the largest, 64 x 32 CTUs) the library's
-    count equals the recursive full-cut enumeration, which is the whole
-    space up to four slices."""
+    count equals the recursive full-cut enumeration plus the pinwheels,
+    which is the whole space up to five slices."""
     import bruteforce
-    assert trs.trs_mt_count(W, H, n) == len(bruteforce.guillotine_partitions(W, H, n))
+    assert trs.trs_mt_count(W, H, n) == len(bruteforce.cut_partitions(W, H, n))

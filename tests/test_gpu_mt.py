@@ -5,9 +5,9 @@ Small frames: the whole record (T_min, the Eq. 4 bound, T, Q, the slices and
 the list size) equals the oracle's, which enumerates tile grids and groups
 their tiles; the library lists partitions of the CTU grid directly.  Full
 frames: with two slices the space is every straight cut across the frame,
-and up to four slices it is every partition made by recursive full cuts, so
-T_min and the winner follow from the oracle's rectangle sums over those
-sets alone."""
+and up to five slices it is every partition made by recursive full cuts plus
+the pinwheels, so T_min and the winner follow from the oracle's rectangle
+sums over those sets alone."""
 
 import numpy as np
 import pytest
@@ -118,11 +118,11 @@ def test_mt_two_slices_full_frame(dec, oracle, spec_name):
         assert p.regions() == sorted(best[3], key=lambda r: (r[1], r[0]))
 
 
-@pytest.mark.parametrize("spec_name,n", [("SPEC_1080P10", 3), ("SPEC_1080P10", 4), ("SPEC_2160P10", 3),
-                                         ("SPEC_2160P10", 4)])
-def test_mt_full_frames_up_to_four_slices(dec, oracle, spec_name, n):
-    """Up to four slices every partition has a full cut, so the recursive
-    full-cut enumeration lists the whole space at full frame sizes."""
+@pytest.mark.parametrize("spec_name,n", [("SPEC_1080P10", 3), ("SPEC_1080P10", 4), ("SPEC_1080P10", 5),
+                                         ("SPEC_2160P10", 3), ("SPEC_2160P10", 4), ("SPEC_2160P10", 5)])
+def test_mt_full_frames_up_to_five_slices(dec, oracle, spec_name, n):
+    """Up to five slices every partition has a full cut or is a pinwheel, so
+    those two lists are the whole space at full frame sizes."""
     import bruteforce
     spec = getattr(synth, spec_name)
     W, H = spec.width, spec.height
@@ -130,7 +130,7 @@ def test_mt_full_frames_up_to_four_slices(dec, oracle, spec_name, n):
     tab = _tables(dec, plane, times, spec.bit_depth)
     st = oracle.texture(plane, spec.bit_depth)
     Tq, _ = oracle.time_q(times)
-    sets = bruteforce.guillotine_partitions(W, H, n)
+    sets = bruteforce.cut_partitions(W, H, n)
     for lam in (0.0, 0.1):
         ref = mt_best(oracle, st, Tq, sets, lam)
         p = dec.search_mt(tab, W, H, n, lam)

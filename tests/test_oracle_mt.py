@@ -66,23 +66,28 @@ def test_single_slice_and_invalid(oracle):
 
 
 @pytest.mark.parametrize("W,H,n", [(384, 384, 3), (512, 384, 4), (384, 384, 4), (640, 256, 3), (300, 200, 3),
-                                   (512, 512, 4), (256, 128, 1), (128, 384, 2)])
-def test_guillotine_cuts_give_the_same_space(W, H, n):
-    """Up to four slices, recursive full cuts reach every partition the
-    brute force finds (and no other), so they can stand in for it on frames
-    far too large for the brute force."""
-    assert sorted(bruteforce.guillotine_partitions(W, H, n)) == sorted(bruteforce.mt_partitions(W, H, n))
+                                   (512, 512, 4), (256, 128, 1), (128, 384, 2), (384, 384, 5), (512, 384, 5),
+                                   (640, 384, 5), (512, 512, 5), (640, 640, 5)])
+def test_cut_partitions_give_the_same_space(W, H, n):
+    """Up to five slices, recursive full cuts (and the pinwheels at five)
+    reach every partition the brute force finds and no other, so they can
+    stand in for it on frames far too large for the brute force."""
+    got = bruteforce.cut_partitions(W, H, n)
+    assert len(got) == len(set(got))
+    assert sorted(got) == sorted(bruteforce.mt_partitions(W, H, n))
+    if n == 5:
+        assert bruteforce.pinwheels(W, H)          # the pinwheels do occur at these sizes
 
 
 @pytest.mark.parametrize("W,H,n,lam,seed", [(832, 480, 4, 0.1, 1), (640, 640, 4, 0.0, 2), (1024, 512, 3, 0.3, 3),
-                                            (768, 768, 4, 0.1, 4)])
+                                            (768, 768, 4, 0.1, 4), (832, 480, 5, 0.1, 5), (640, 640, 5, 0.0, 6)])
 def test_decision_over_guillotine_sets_equals_oracle(oracle, W, H, n, lam, seed):
     from gpu_helpers import mt_best
     import synth
     plane, times = synth.small_frame(W, H, 10, seed)
     st = oracle.texture(plane, 10)
     Tq, _ = oracle.time_q(times)
-    got = mt_best(oracle, st, Tq, bruteforce.guillotine_partitions(W, H, n), lam)
+    got = mt_best(oracle, st, Tq, bruteforce.cut_partitions(W, H, n), lam)
     ref = oracle.mt_search(st, Tq, n, lam)
     assert got["status"] == ref["status"] == oracle.OK
     assert got["count"] == oracle.mt_count(W, H, n)
