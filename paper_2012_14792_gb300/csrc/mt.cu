@@ -17,7 +17,9 @@
 //    must keep the rule among the slices so far, and the free area must fit
 //    the slices left; so does the corner count of the free region, which
 //    bounds the slices it needs from below.  Each set is stored as
-//    (y0, x0, y1, x1) bytes per slice.
+//    (y0, x0, y1, x1) bytes per slice.  The partitions under each choice of
+//    the first two slices are enumerated on a pool of host threads and the
+//    pieces joined in that order.
 //  * device: one thread per slice set reads each slice's time and quality
 //    term from the region tables (any rectangle of CTUs is a tile-column
 //    slice there), and three grid-wide minima give T_min (Eq. 3), Q* (Eq. 2
@@ -25,8 +27,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <new>
+#include <system_error>
+#include <thread>
 #include <vector>
 
 #include "ctx.h"
@@ -39,6 +45,24 @@ namespace {
 constexpr int64_t kMtMaxSets = 1 << 22;        // slice sets kept
 constexpr size_t kMtMaxBytes = size_t(1) << 28;  // bytes of the kept list
 constexpr int64_t kMtMaxVisits = 1ll << 28;    // partial partitions visited
+constexpr int kMtPrefix = 2;                   // slices fixed per host task
+constexpr int kMtMaxThreads = 64;
+constexpr int64_t kMtFlush = 1 << 14;          // local counts added to the shared ones this often
+
+// Counts shared by the host threads of one enumeration: exact totals are
+// summed at the end; these (lower bounds of them) only stop the threads early.
+struct MtShared {
+    std::atomic<int64_t> visits{0}, sets{0};
+    std::atomic<bool> over{false};
+    int64_t max_sets = kMtMaxSets;
+};
+
+// A partial partition with kMtPrefix slices placed: the state rec() resumes.
+struct MtTask {
+    uint8_t cur[kMtPrefix][4];
+    uint64_t amin, amax;
+    int ry;
+};
 
 struct MtEnum {
     int W, H, C, R, n, k;
@@ -46,9 +70,44 @@ struct MtEnum {
     uint64_t free_area;      // luma samples not yet in a slice
     uint8_t cur[kMaxN][4];   // slices so far: y0, x0, y1, x1
     int ns;
-    int64_t visits, sets;
-    bool over;
-    std::vector<uint8_t> *keys;
+    int64_t visits = 0, sets = 0;              // this enumerator's exact counts
+    int64_t vflushed = 0, sflushed = 0;        // parts of them added to shared
+    MtShared *shared = nullptr;
+    std::vector<uint8_t> *keys = nullptr;
+    std::vector<MtTask> *tasks = nullptr;      // set: stop at kMtPrefix slices and record
+
+    void reset(int W_, int H_, int n_, int k_) {
+        W = W_;
+        H = H_;
+        C = (W + kCtu - 1) / kCtu;
+        R = (H + kCtu - 1) / kCtu;
+        n = n_;
+        k = k_;
+        for (int y = 0; y < R; ++y) freem[y] = C == 64 ? ~0ull : (1ull << C) - 1;
+        free_area = (uint64_t)W * H;
+        ns = 0;
+    }
+
+    void place(int y0, int x0, int y1, int x1) {
+        const uint64_t bits = ((x1 - x0 == 64 ? ~0ull : ((1ull << (x1 - x0)) - 1)) << x0);
+        for (int y = y0; y < y1; ++y) freem[y] &= ~bits;
+        free_area -= (uint64_t)(line_px(x1, W) - line_px(x0, W)) * (line_px(y1, H) - line_px(y0, H));
+        cur[ns][0] = (uint8_t)y0;
+        cur[ns][1] = (uint8_t)x0;
+        cur[ns][2] = (uint8_t)y1;
+        cur[ns][3] = (uint8_t)x1;
+        ++ns;
+    }
+
+    bool stopped() const { return shared->over.load(std::memory_order_relaxed); }
+
+    void flush() {
+        const int64_t v = shared->visits.fetch_add(visits - vflushed, std::memory_order_relaxed) + visits - vflushed;
+        const int64_t s = shared->sets.fetch_add(sets - sflushed, std::memory_order_relaxed) + sets - sflushed;
+        vflushed = visits;
+        sflushed = sets;
+        if (v > kMtMaxVisits || s > shared->max_sets) shared->over.store(true, std::memory_order_relaxed);
+    }
 
     // consecutive free CTUs of row y from column x
     int run(int y, int x) const {
@@ -78,26 +137,31 @@ struct MtEnum {
     }
 
     void emit() {
-        if (++sets > kMtMaxSets || keys->size() + (size_t)n * 4 > kMtMaxBytes) {
-            over = true;
-            return;
-        }
+        ++sets;
+        if (sets - sflushed >= kMtFlush) flush();
+        if (stopped()) return;
         keys->insert(keys->end(), &cur[0][0], &cur[0][0] + (size_t)n * 4);
     }
 
     // amin / amax: smallest and largest slice area so far (none: ~0, 0)
     void rec(int ry, uint64_t amin, uint64_t amax) {
-        if (over) return;
-        if (++visits > kMtMaxVisits) {
-            over = true;
-            return;
-        }
+        if (++visits - vflushed >= kMtFlush) flush();
+        if (stopped()) return;
         while (ry < R && freem[ry] == 0) ++ry;
         if (ry == R) {
             if (ns == n) emit();
             return;
         }
         if (ns == n || corner_bound(ry) > n - ns) return;
+        if (tasks && ns == kMtPrefix) {
+            MtTask t;
+            std::memcpy(t.cur, cur, sizeof(t.cur));
+            t.amin = amin;
+            t.amax = amax;
+            t.ry = ry;
+            tasks->push_back(t);
+            return;
+        }
         const int x = __builtin_ctzll(freem[ry]);
         const uint64_t m = (uint64_t)(n - ns - 1);  // slices after this one
         const uint64_t px0 = line_px(x, W), py0 = line_px(ry, H);
@@ -128,7 +192,7 @@ struct MtEnum {
                 free_area += a;
                 --ns;
                 for (int y = ry; y < ry + h; ++y) freem[y] |= bits;
-                if (over) return;
+                if (stopped()) return;
             }
         }
     }
@@ -136,32 +200,105 @@ struct MtEnum {
 
 }  // namespace
 
-// The slice-set list of a frame shape in tie order (n * 4 bytes each).
+// The slice-set list of a frame shape in tie order (n * 4 bytes each).  The
+// calling thread enumerates the first kMtPrefix slices of every partition in
+// order; a pool of host threads enumerates the partitions under each such
+// prefix, and the pieces are joined in prefix order, which is tie order.
 int mt_enumerate(int W, int H, int n, int k, std::vector<uint8_t> *keys, int64_t *count) {
     if (W <= 0 || H <= 0 || n < 1 || n > kMaxN || k < 1) return TRS_EINVAL;
     const int C = (W + kCtu - 1) / kCtu, R = (H + kCtu - 1) / kCtu;
     if (C > kMaxC || R > kMaxR) return TRS_EINVAL;
+    const int64_t max_sets = std::min<int64_t>(kMtMaxSets, (int64_t)(kMtMaxBytes / ((size_t)n * 4)));
     keys->clear();
-    MtEnum e;
-    e.W = W;
-    e.H = H;
-    e.C = C;
-    e.R = R;
-    e.n = n;
-    e.k = k;
-    for (int y = 0; y < R; ++y) e.freem[y] = C == 64 ? ~0ull : (1ull << C) - 1;
-    e.free_area = (uint64_t)W * H;
-    e.ns = 0;
-    e.visits = 0;
-    e.sets = 0;
-    e.over = false;
-    e.keys = keys;
-    e.rec(0, ~0ull, 0);
-    if (e.over) {
+    MtShared shared;
+    shared.max_sets = max_sets;
+    std::vector<MtTask> tasks;
+    int64_t visits = 0, sets = 0;
+    std::atomic<bool> nomem{false};
+    try {
+        MtEnum root;
+        root.reset(W, H, n, k);
+        root.shared = &shared;
+        root.keys = keys;
+        if (n > kMtPrefix) root.tasks = &tasks;
+        root.rec(0, ~0ull, 0);
+        root.flush();
+        visits = root.visits;
+        sets = root.sets;
+    } catch (const std::bad_alloc &) {
         keys->clear();
+        return TRS_ENOMEM;
+    }
+    if (!tasks.empty() && !shared.over.load()) {
+        std::atomic<size_t> next{0};
+        const int hw = (int)std::thread::hardware_concurrency();
+        const int nt = (int)std::min<size_t>(tasks.size(), (size_t)std::max(1, std::min(hw, kMtMaxThreads)));
+        std::vector<std::vector<uint8_t>> parts;
+        std::vector<int64_t> wv, ws;
+        std::vector<std::thread> pool;
+        try {  // everything allocated before the first thread starts
+            parts.resize(tasks.size());
+            wv.assign(nt, 0);
+            ws.assign(nt, 0);
+            pool.reserve(nt);
+        } catch (const std::bad_alloc &) {
+            return TRS_ENOMEM;
+        }
+        auto work = [&](int t) {
+            MtEnum e;
+            e.shared = &shared;
+            try {
+                for (;;) {
+                    const size_t i = next.fetch_add(1);
+                    if (i >= tasks.size() || e.stopped()) break;
+                    e.reset(W, H, n, k);
+                    for (int j = 0; j < kMtPrefix; ++j)
+                        e.place(tasks[i].cur[j][0], tasks[i].cur[j][1], tasks[i].cur[j][2], tasks[i].cur[j][3]);
+                    e.keys = &parts[i];
+                    e.rec(tasks[i].ry, tasks[i].amin, tasks[i].amax);
+                }
+            } catch (const std::bad_alloc &) {
+                nomem.store(true);
+                shared.over.store(true);
+            }
+            e.flush();
+            wv[t] = e.visits;
+            ws[t] = e.sets;
+        };
+        for (int t = 1; t < nt; ++t) {
+            try {
+                pool.emplace_back(work, t);
+            } catch (const std::system_error &) {
+                break;  // fewer threads: the running ones take the remaining tasks
+            }
+        }
+        work(0);
+        for (auto &th : pool) th.join();
+        for (int t = 0; t < nt; ++t) {
+            visits += wv[t];
+            sets += ws[t];
+        }
+        if (!shared.over.load() && visits <= kMtMaxVisits && sets <= max_sets) {
+            try {
+                keys->reserve((size_t)sets * n * 4);
+                for (auto &p : parts) {
+                    keys->insert(keys->end(), p.begin(), p.end());
+                    std::vector<uint8_t>().swap(p);
+                }
+            } catch (const std::bad_alloc &) {
+                nomem.store(true);
+            }
+        }
+    }
+    if (nomem.load()) {
+        std::vector<uint8_t>().swap(*keys);
+        return TRS_ENOMEM;
+    }
+    if (shared.over.load() || visits > kMtMaxVisits || sets > max_sets) {
+        std::vector<uint8_t>().swap(*keys);
         return TRS_EINVAL;
     }
-    *count = e.sets;
+    *count = sets;
     return TRS_OK;
 }
 
