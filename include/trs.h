@@ -271,6 +271,16 @@ typedef struct trs_mt_partition {
  * counts 0. */
 int trs_mt_count(int width, int height, int n_regions, int k_area, int64_t *count);
 
+/* Host only: the slice-set list trs_search_mt searches for a frame shape,
+ * in its tie order (increasing lexicographic order of the records): *count
+ * sets of n_regions slices, 4 bytes per slice (y0, x0, y1, x1 in CTUs),
+ * slices in raster order of (y0, x0).  With list == NULL only *count is
+ * written; otherwise list must hold capacity >= *count * n_regions * 4 bytes
+ * (TRS_EINVAL if it does not; *count is still written).  Errors as
+ * trs_mt_count. */
+int trs_mt_list(int width, int height, int n_regions, int k_area, uint8_t *list, size_t capacity,
+                int64_t *count);
+
 /* Searches the multi-tile space of the frame whose region tables are in
  * tables_dev (trs_region_tables): T_min (Eq. 3), then the smallest Q (Eq. 2)
  * among slice sets within Eq. 4's bound.  Writes one trs_mt_partition to

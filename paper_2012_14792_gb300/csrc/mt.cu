@@ -446,6 +446,18 @@ int trs_mt_count(int width, int height, int n, int k, int64_t *count) {
     return mt_enumerate(width, height, n, k, &keys, count);
 }
 
+int trs_mt_list(int width, int height, int n, int k, uint8_t *list, size_t capacity, int64_t *count) {
+    if (!count) return TRS_EINVAL;
+    std::vector<uint8_t> keys;
+    int64_t c = 0;
+    TRS_TRY(mt_enumerate(width, height, n, k, &keys, &c));
+    *count = c;
+    if (!list) return TRS_OK;
+    if (capacity < keys.size()) return TRS_EINVAL;
+    if (!keys.empty()) std::memcpy(list, keys.data(), keys.size());
+    return TRS_OK;
+}
+
 int trs_search_mt(trs_ctx *ctx, const void *tables, int W, int H, int n, float lambda, trs_mt_partition *out,
                   void *stream) {
     if (!ctx || !tables || !out || (uintptr_t)tables % 256) return TRS_EINVAL;

@@ -135,6 +135,7 @@ def _load():
         "trs_plan_work": ([i, i, i, i, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)], i),
         "trs_count_partitions": ([i, i, i, i, ct.POINTER(ct.c_double)], i),
         "trs_mt_count": ([i, i, i, i, ct.POINTER(ct.c_int64)], i),
+        "trs_mt_list": ([i, i, i, i, vp, sz, ct.POINTER(ct.c_int64)], i),
         "trs_alu_peak": ([i, ct.POINTER(ct.c_double)], i),
         "trs_create": ([ct.POINTER(vp), ct.POINTER(trs_opts)], i),
         "trs_destroy": ([vp], i),
@@ -295,6 +296,18 @@ def trs_mt_count(width: int, height: int, n_regions: int, k_area: int = 3) -> in
     c = ct.c_int64()
     _check(_lib.trs_mt_count(width, height, n_regions, k_area, ct.byref(c)), "trs_mt_count")
     return c.value
+
+
+def trs_mt_list(width: int, height: int, n_regions: int, k_area: int = 3):
+    """The slice-set list of the multi-tile space as a uint8 array of shape
+    [count, n_regions, 4] (y0, x0, y1, x1 per slice), in tie order."""
+    import numpy as np
+    c = ct.c_int64()
+    _check(_lib.trs_mt_list(width, height, n_regions, k_area, None, 0, ct.byref(c)), "trs_mt_list")
+    out = np.zeros((c.value, n_regions, 4), np.uint8)
+    _check(_lib.trs_mt_list(width, height, n_regions, k_area, out.ctypes.data, out.nbytes, ct.byref(c)),
+           "trs_mt_list")
+    return out
 
 
 def trs_search_mt(ctx, tables, width, height, n_regions, lam, out, stream=None) -> None:

@@ -129,3 +129,68 @@ def test_mt_count_full_frames_matches_cut_partitions(trs, W, H, n):
     which is the whole space up to five slices."""
     import bruteforce
     assert trs.trs_mt_count(W, H, n) == len(bruteforce.cut_partitions(W, H, n))
+
+
+def _mt_sets(arr):
+    """trs_mt_list records as a set of tuples of (y0, x0, y1, x1) slices."""
+    return {tuple(tuple(int(v) for v in sl) for sl in rec) for rec in arr}
+
+
+def _cut_sets(parts):
+    """Brute-force partitions ((x0, x1, y0, y1) raster-sorted) as the same tuples."""
+    return {tuple((r[2], r[0], r[3], r[1]) for r in p) for p in parts}
+
+
+@pytest.mark.parametrize("W,H,n", [(832, 480, 4), (832, 480, 6), (640, 640, 8), (1280, 720, 6), (300, 200, 3),
+                                   (8000, 300, 4), (1920, 1080, 5)])
+def test_mt_list_order_and_validity(trs, W, H, n):
+    """Records strictly increase (the tie order, no repeats), slices come in
+    raster order, every set covers each CTU once, and the area rule holds."""
+    import numpy as np
+    arr = trs.trs_mt_list(W, H, n)
+    assert len(arr) == trs.trs_mt_count(W, H, n)
+    flat = arr.reshape(len(arr), -1).astype(np.int16)
+    d = flat[1:] - flat[:-1]
+    first = np.argmax(d != 0, axis=1)
+    assert (d[np.arange(len(d)), first] > 0).all()
+    C, R = -(-W // 128), -(-H // 128)
+    px = lambda v, ext: min(v * 128, ext)
+    for rec in arr:
+        cover = np.zeros((R, C), np.int8)
+        areas = []
+        for y0, x0, y1, x1 in rec.tolist():
+            assert 0 <= y0 < y1 <= R and 0 <= x0 < x1 <= C
+            cover[y0:y1, x0:x1] += 1
+            areas.append((px(x1, W) - px(x0, W)) * (px(y1, H) - px(y0, H)))
+        assert (cover == 1).all()
+        assert 3 * min(areas) > max(areas)
+        starts = [(int(s[0]), int(s[1])) for s in rec]
+        assert starts == sorted(starts) and len(set(starts)) == n
+
+
+@pytest.mark.parametrize("W,H,n", [(384, 384, 3), (512, 384, 4), (640, 384, 5), (512, 512, 5), (512, 384, 6),
+                                   (300, 200, 3), (128, 384, 2)])
+def test_mt_list_equals_bruteforce(trs, W, H, n):
+    import bruteforce
+    assert _mt_sets(trs.trs_mt_list(W, H, n)) == _cut_sets(bruteforce.mt_partitions(W, H, n))
+
+
+@pytest.mark.parametrize("W,H,n", [(1920, 1080, 3), (1920, 1080, 4), (1920, 1080, 5), (3840, 2160, 4),
+                                   (3840, 2160, 5), (8192, 4096, 3)])
+def test_mt_list_full_frames_equals_cut_partitions(trs, W, H, n):
+    """Full frame sizes: the very same slice sets as full cuts plus pinwheels."""
+    import bruteforce
+    assert _mt_sets(trs.trs_mt_list(W, H, n)) == _cut_sets(bruteforce.cut_partitions(W, H, n))
+
+
+def test_mt_list_capacity(trs):
+    import ctypes
+    import numpy as np
+    lib = trs.lib()
+    c = ctypes.c_int64(-1)
+    assert lib.trs_mt_list(832, 480, 4, 3, None, 0, ctypes.byref(c)) == trs.OK and c.value == 106
+    buf = np.zeros(106 * 16 - 1, np.uint8)
+    c = ctypes.c_int64(-1)
+    assert lib.trs_mt_list(832, 480, 4, 3, buf.ctypes.data, buf.nbytes, ctypes.byref(c)) == trs.EINVAL
+    assert c.value == 106 and not buf.any()
+    assert lib.trs_mt_list(832, 480, 4, 3, None, 0, None) == trs.EINVAL
