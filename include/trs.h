@@ -186,6 +186,19 @@ int trs_plan_work(int width, int height, int n_regions, int k_area, double *row_
  * double.  For reporting candidates per second; TRS_EINVAL on bad shapes. */
 int trs_count_partitions(int width, int height, int n_regions, int k_area, double *count);
 
+/* Host only: checks that the search plan of a frame shape loses no
+ * partition.  The plan prunes, per area window [a, k*a - 1], the tile
+ * columns and slice counts that no partition of the window with n slices
+ * can use; for every window this counts the one-tile-row partitions whose
+ * slice areas all fit the window twice -- all of them, and those the plan's
+ * row-DP units can form (each tile column through its unit in that window,
+ * with the unit's heights and slice-count range) -- with 128-bit counting
+ * DPs.  *short_windows = windows where the second count is smaller (0 for
+ * a sound plan), *windows = windows checked.  window_step as in
+ * trs_set_window_step.  TRS_EINVAL for bad shapes. */
+int trs_plan_coverage(int width, int height, int n_regions, int k_area, int window_step, int *windows,
+                      int *short_windows);
+
 /* Measured INT32 throughput of the device (32-bit add / min / max chains
  * over every SM, CUDA-event timed, best of three), in operations per
  * second: the peak the search kernels' arithmetic is compared with. */

@@ -242,24 +242,11 @@ int build_plan(int W, int H, int n, int k, HostPlan *p, int window_step) {
     return TRS_OK;
 }
 
-// Partitions with exactly n slices, one tile row, all slice areas in
-// [lo, hi]: a counting row DP per tile column, then a counting column DP.
-static unsigned __int128 count_in_range(int W, int H, int C, int R, int n, uint64_t lo, uint64_t hi) {
-    std::vector<unsigned __int128> g((size_t)num_bands(C) * (n + 1), 0), F((size_t)(C + 1) * (n + 1), 0);
-    std::vector<unsigned __int128> cnt((size_t)(R + 1) * (n + 1));
-    for (int x0 = 0; x0 < C; ++x0)
-        for (int x1 = x0 + 1; x1 <= C; ++x1) {
-            const uint64_t w = line_px(x1, W) - line_px(x0, W);
-            std::fill(cnt.begin(), cnt.end(), 0);
-            cnt[0] = 1;  // rows [0, 0) in 0 slices
-            for (int y = 1; y <= R; ++y)
-                for (int yp = 0; yp < y; ++yp) {
-                    const uint64_t a = w * (line_px(y, H) - line_px(yp, H));
-                    if (a < lo || a > hi) continue;
-                    for (int k = 1; k <= n; ++k) cnt[(size_t)y * (n + 1) + k] += cnt[(size_t)yp * (n + 1) + k - 1];
-                }
-            for (int k = 0; k <= n; ++k) g[(size_t)band_index(C, x0, x1) * (n + 1) + k] = cnt[(size_t)R * (n + 1) + k];
-        }
+// Counting column DP: partitions of the C CTU columns into tile columns whose
+// slice counts add up to n, g[b * (n + 1) + k] ways for tile column b with k
+// slices.
+static unsigned __int128 combine_columns(int C, int n, const std::vector<unsigned __int128> &g) {
+    std::vector<unsigned __int128> F((size_t)(C + 1) * (n + 1), 0);
     F[0] = 1;  // columns [0, 0) in 0 slices
     for (int x = 1; x <= C; ++x)
         for (int xp = 0; xp < x; ++xp) {
@@ -268,6 +255,64 @@ static unsigned __int128 count_in_range(int W, int H, int C, int R, int n, uint6
                 for (int k = 1; k <= m; ++k) F[(size_t)x * (n + 1) + m] += gb[k] * F[(size_t)xp * (n + 1) + m - k];
         }
     return F[(size_t)C * (n + 1) + n];
+}
+
+// Counting row DP of one tile column: cnt[k] = ways to cut its R CTU rows
+// into k slices whose pixel heights h pass keep(h).
+template <class Keep>
+static void count_rows(int H, int R, int n, Keep keep, std::vector<unsigned __int128> &cnt) {
+    cnt.assign((size_t)(R + 1) * (n + 1), 0);
+    cnt[0] = 1;  // rows [0, 0) in 0 slices
+    for (int y = 1; y <= R; ++y)
+        for (int yp = 0; yp < y; ++yp) {
+            if (!keep(line_px(y, H) - line_px(yp, H))) continue;
+            for (int k = 1; k <= n; ++k) cnt[(size_t)y * (n + 1) + k] += cnt[(size_t)yp * (n + 1) + k - 1];
+        }
+}
+
+// Partitions with exactly n slices, one tile row, all slice areas in
+// [lo, hi]: a counting row DP per tile column, then a counting column DP.
+static unsigned __int128 count_in_range(int W, int H, int C, int R, int n, uint64_t lo, uint64_t hi) {
+    std::vector<unsigned __int128> g((size_t)num_bands(C) * (n + 1), 0), cnt;
+    for (int x0 = 0; x0 < C; ++x0)
+        for (int x1 = x0 + 1; x1 <= C; ++x1) {
+            const uint64_t w = line_px(x1, W) - line_px(x0, W);
+            count_rows(H, R, n, [&](uint32_t h) { return w * h >= lo && w * h <= hi; }, cnt);
+            for (int k = 0; k <= n; ++k) g[(size_t)band_index(C, x0, x1) * (n + 1) + k] = cnt[(size_t)R * (n + 1) + k];
+        }
+    return combine_columns(C, n, g);
+}
+
+// The same count for window wi of a plan, through the plan only: a tile
+// column counts through its item in that window (none: it is left out),
+// with the item's heights and its slice counts kmin..kmax.
+static unsigned __int128 count_planned(const HostPlan &p, int wi) {
+    const int n = p.n;
+    std::vector<unsigned __int128> g((size_t)p.nb * (n + 1), 0), cnt;
+    for (int b = 0; b < p.nb; ++b) {
+        const int slot = p.slot_of[(size_t)wi * p.nb + b];
+        if (slot < 0) continue;
+        const PlanItem &it = p.items[slot];
+        count_rows(p.H, p.R, n, [&](uint32_t h) { return h >= it.hlo && h <= it.hhi; }, cnt);
+        for (int k = std::max(1, (int)it.kmin); k <= std::min(n, (int)it.kmax); ++k)
+            g[(size_t)b * (n + 1) + k] = cnt[(size_t)p.R * (n + 1) + k];
+    }
+    return combine_columns(p.C, n, g);
+}
+
+int plan_coverage(int W, int H, int n, int k, int window_step, int *windows, int *short_windows) {
+    if (!windows || !short_windows) return TRS_EINVAL;
+    HostPlan p;
+    const int st = build_plan(W, H, n, k, &p, window_step);
+    if (st != TRS_OK) return st;
+    int bad = 0;
+    for (int wi = 0; wi < (int)p.win_a.size(); ++wi) {
+        const uint64_t lo = p.win_a[wi], hi = (uint64_t)k * lo - 1;
+        if (count_planned(p, wi) != count_in_range(W, H, p.C, p.R, n, lo, hi)) ++bad;
+    }
+    *windows = (int)p.win_a.size();
+    *short_windows = bad;
+    return TRS_OK;
 }
 
 int count_partitions(int W, int H, int n, int k, long double *out) {

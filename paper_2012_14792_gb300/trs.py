@@ -134,6 +134,7 @@ def _load():
         "trs_plan_stats": ([i, i, i, i, ct.POINTER(i), ct.POINTER(i)], i),
         "trs_plan_work": ([i, i, i, i, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)], i),
         "trs_count_partitions": ([i, i, i, i, ct.POINTER(ct.c_double)], i),
+        "trs_plan_coverage": ([i, i, i, i, i, ct.POINTER(i), ct.POINTER(i)], i),
         "trs_mt_count": ([i, i, i, i, ct.POINTER(ct.c_int64)], i),
         "trs_mt_list": ([i, i, i, i, vp, sz, ct.POINTER(ct.c_int64)], i),
         "trs_alu_peak": ([i, ct.POINTER(ct.c_double)], i),
@@ -230,6 +231,15 @@ def trs_count_partitions(width: int, height: int, n_regions: int, k_area: int = 
     c = ct.c_double()
     _check(_lib.trs_count_partitions(width, height, n_regions, k_area, ct.byref(c)), "trs_count_partitions")
     return c.value
+
+
+def trs_plan_coverage(width: int, height: int, n_regions: int, k_area: int = 3,
+                      window_step: int = 1) -> tuple[int, int]:
+    """(windows checked, windows whose plan misses a partition of the window)."""
+    nw, bad = ct.c_int(0), ct.c_int(0)
+    _check(_lib.trs_plan_coverage(width, height, n_regions, k_area, window_step, ct.byref(nw), ct.byref(bad)),
+           "trs_plan_coverage")
+    return nw.value, bad.value
 
 
 def trs_plan_work(width: int, height: int, n_regions: int, k_area: int = 3) -> tuple[float, float]:

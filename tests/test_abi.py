@@ -194,3 +194,28 @@ def test_mt_list_capacity(trs):
     assert lib.trs_mt_list(832, 480, 4, 3, buf.ctypes.data, buf.nbytes, ctypes.byref(c)) == trs.EINVAL
     assert c.value == 106 and not buf.any()
     assert lib.trs_mt_list(832, 480, 4, 3, None, 0, None) == trs.EINVAL
+
+
+@pytest.mark.parametrize("W,H,n,k,step", [(832, 480, 4, 3, 1), (1920, 1080, 8, 3, 1), (3840, 2160, 16, 3, 1),
+                                          (3840, 2160, 16, 3, 4), (3840, 2160, 16, 3, 8), (8192, 4096, 32, 3, 1),
+                                          (1920, 1080, 8, 2, 1), (1920, 1080, 12, 4, 1), (3840, 2160, 4, 3, 1),
+                                          (129, 257, 2, 3, 1), (128, 128, 1, 3, 1)])
+def test_plan_loses_no_partition(trs, W, H, n, k, step):
+    """Every one-tile-row partition whose slice areas fit a window of the
+    plan can be formed from the plan's units in that window (the pruning by
+    area bounds, tiling bounds and slice-count reachability drops only
+    options no partition uses)."""
+    windows, short = trs.trs_plan_coverage(W, H, n, k, step)
+    assert short == 0
+    assert windows == (trs.trs_plan_stats(W, H, n, k)[0] if step == 1 else windows)
+
+
+def test_plan_loses_no_partition_random_shapes(trs):
+    import numpy as np
+    rng = np.random.default_rng(2012)
+    for _ in range(60):
+        W, H = int(rng.integers(1, 8193)), int(rng.integers(1, 4097))
+        C, R = -(-W // 128), -(-H // 128)
+        n = int(rng.integers(1, min(32, C * R) + 1))
+        windows, short = trs.trs_plan_coverage(W, H, n, int(rng.integers(2, 5)), int(rng.integers(1, 5)))
+        assert short == 0, (W, H, n)
