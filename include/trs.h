@@ -158,7 +158,8 @@ typedef struct trs_frame_desc {
 
 /* Size in bytes of the ABI structure called `name` ("trs_opts",
  * "trs_ctu_stats", "trs_tables_layout", "trs_partition", "trs_frame_desc",
- * "trs_server_opts", "trs_decision", "trs_server_stats", "trs_tune_report"),
+ * "trs_server_opts", "trs_decision", "trs_server_stats", "trs_tune_report",
+ * "trs_mt_partition"),
  * 0 for an unknown name; lets bindings check their copies of the layouts. */
 size_t trs_sizeof(const char *name);
 

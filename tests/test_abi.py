@@ -219,3 +219,63 @@ def test_plan_loses_no_partition_random_shapes(trs):
         n = int(rng.integers(1, min(32, C * R) + 1))
         windows, short = trs.trs_plan_coverage(W, H, n, int(rng.integers(2, 5)), int(rng.integers(1, 5)))
         assert short == 0, (W, H, n)
+
+
+C_CLIENT = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "trs.h"
+
+#define CHECK_SIZE(T) do { if (trs_sizeof(#T) != sizeof(T)) { \
+    printf("size mismatch %s: C %zu, library %zu\n", #T, sizeof(T), trs_sizeof(#T)); return 1; } } while (0)
+
+int main(void) {
+    double parts = 0.0;
+    int64_t sets = -1;
+    int nw = 0, ni = 0;
+    CHECK_SIZE(trs_opts);
+    CHECK_SIZE(trs_ctu_stats);
+    CHECK_SIZE(trs_tables_layout);
+    CHECK_SIZE(trs_partition);
+    CHECK_SIZE(trs_frame_desc);
+    CHECK_SIZE(trs_mt_partition);
+    CHECK_SIZE(trs_tune_report);
+    CHECK_SIZE(trs_server_opts);
+    CHECK_SIZE(trs_decision);
+    CHECK_SIZE(trs_server_stats);
+    if (trs_version() != 1) return 2;
+    if (trs_count_partitions(832, 480, 4, 3, &parts) != TRS_OK) return 3;
+    if (trs_mt_count(832, 480, 4, 3, &sets) != TRS_OK) return 4;
+    if (trs_plan_stats(3840, 2160, 16, 3, &nw, &ni) != TRS_OK) return 5;
+    if (trs_create(NULL, NULL) != TRS_EINVAL) return 6;
+    printf("%.0f %lld %d %d %s\n", parts, (long long)sets, nw, ni, trs_strerror(TRS_EINFEASIBLE));
+    return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_links(trs, tmp_path):
+    """include/trs.h compiles as strict C99, links against the library, and
+    the C compiler lays out every structure as the library does."""
+    import os
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_2012_14792_gb300 import build
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(build.LIB)
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(root, "include"),
+                        str(src), "-o", str(exe), "-L", libdir, "-ltrs", "-Wl,-rpath," + libdir],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    parts, sets, nw, ni = r.stdout.split()[:4]
+    assert float(parts) == trs.trs_count_partitions(832, 480, 4)
+    assert int(sets) == trs.trs_mt_count(832, 480, 4)
+    assert (int(nw), int(ni)) == trs.trs_plan_stats(3840, 2160, 16)
