@@ -730,7 +730,10 @@ def main():
 
     multi_tile = None
     if not args.no_mt:
-        multi_tile = run_multi_tile(runtime, trs, local)
+        try:
+            multi_tile = run_multi_tile(runtime, trs, local)
+        except Exception as e:  # a secondary figure: report it, keep the headline line
+            multi_tile = {"error": f"{type(e).__name__}: {e}"}
 
     cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
