@@ -474,18 +474,28 @@ int trs_search_mt(trs_ctx *ctx, const void *tables, int W, int H, int n, float l
         std::vector<uint8_t> keys;
         int64_t count = 0;
         TRS_TRY(mt_enumerate(W, H, n, ctx->o.k_area, &keys, &count));
-        me = new MtEntry;
-        me->count = count;
-        int st = dev_alloc(me->cands, keys.size(), &ctx->total);
-        if (st == TRS_OK && !keys.empty() && cudaMemcpy(me->cands.p, keys.data(), keys.size(),
-                                                         cudaMemcpyHostToDevice) != cudaSuccess)
-            st = TRS_ECUDA;
+        MtEntry *ne = new (std::nothrow) MtEntry;
+        if (!ne) return TRS_ENOMEM;
+        ne->count = count;
+        int st = dev_alloc(ne->cands, keys.size(), &ctx->total);
+        if (st == TRS_OK && !keys.empty()) {
+            const cudaError_t e = cudaMemcpy(ne->cands.p, keys.data(), keys.size(), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpy (slice-set list)");
+        }
+        if (st == TRS_OK) {
+            try {
+                ctx->mt[key] = ne;
+            } catch (const std::bad_alloc &) {
+                st = TRS_ENOMEM;
+            }
+        }
         if (st != TRS_OK) {
-            dev_free(me->cands);
-            delete me;
+            ctx->total -= ne->cands.n;
+            dev_free(ne->cands);
+            delete ne;
             return st;
         }
-        ctx->mt[key] = me;
+        me = ne;
     }
     TRS_TRY(dev_alloc(ctx->mt_scal, 4 * sizeof(uint64_t), &ctx->total));
     MtArgs a;
