@@ -60,6 +60,7 @@ int check_frame(const trs_ctx *ctx, int W, int H) {
 }
 
 int get_plan(trs_ctx *ctx, int W, int H, int n, PlanEntry **out) {
+    TRS_GUARD_BEGIN
     auto key = std::make_tuple(W, H, n, ctx->window_step);
     auto it = ctx->plans.find(key);
     if (it != ctx->plans.end()) {
@@ -91,6 +92,7 @@ int get_plan(trs_ctx *ctx, int W, int H, int n, PlanEntry **out) {
     ctx->plans[key] = e;
     *out = e;
     return TRS_OK;
+    TRS_GUARD_END
 }
 
 size_t stats_bytes(int C, int R) {
@@ -182,6 +184,7 @@ int trs_plan_coverage(int width, int height, int n, int k, int window_step, int 
 }
 
 int trs_create(trs_ctx **out, const trs_opts *o) {
+    TRS_GUARD_BEGIN
     if (!out || !o) return TRS_EINVAL;
     *out = nullptr;
     if (o->max_width < 1 || o->max_width > kCtu * kMaxC || o->max_height < 1 || o->max_height > kCtu * kMaxR ||
@@ -221,6 +224,7 @@ int trs_create(trs_ctx **out, const trs_opts *o) {
     }
     *out = c;
     return TRS_OK;
+    TRS_GUARD_END
 }
 
 int trs_destroy(trs_ctx *c) {
@@ -363,6 +367,7 @@ static int search_one(trs_ctx *ctx, const void *tables, int W, int H, int n, flo
 
 int trs_search_lambdas(trs_ctx *ctx, const void *tables, int W, int H, int n, const float *lambdas, int nl,
                        trs_partition *out, void *stream) {
+    TRS_GUARD_BEGIN
     if (!ctx || !tables || !out || !lambdas || (uintptr_t)tables % 256) return TRS_EINVAL;
     if (nl < 1 || nl > TRS_MAX_LAMBDAS) return TRS_EINVAL;
     TRS_TRY(check_frame(ctx, W, H));
@@ -432,6 +437,7 @@ int trs_search_lambdas(trs_ctx *ctx, const void *tables, int W, int H, int n, co
     TRS_CK((cudaError_t)launch_search(all, bl.bands, bl.windows, pe->host.C, pe->host.R, n, scal, (size_t)nl * 4, s,
                                       nullptr, &ctx->tune, 2, pe->host.max_nd));
     return TRS_OK;
+    TRS_GUARD_END
 }
 
 int trs_search(trs_ctx *ctx, const void *tables, int W, int H, int n, float lambda, trs_partition *out,
@@ -478,6 +484,7 @@ namespace trs {
 
 int batch_run(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partition *out, cudaStream_t stream,
               bool use_graph) {
+    TRS_GUARD_BEGIN
     if (!ctx || !fd || !out || nf < 1 || nf > ctx->o.max_batch) return TRS_EINVAL;
     std::vector<PlanEntry *> pe(nf);
     std::vector<int64_t> key;
@@ -634,6 +641,7 @@ int batch_run(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partition *out
     ctx->stage_frames = first[1];
     ctx->last_kernels = parts * kKernelsPerBatch;
     return TRS_OK;
+    TRS_GUARD_END
 }
 
 size_t batch_blob_bytes(int nf) {
@@ -749,6 +757,7 @@ int trs_batch_decide(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partiti
 }
 
 int trs_autotune(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_tune_report *rep, void *stream) {
+    TRS_GUARD_BEGIN
     if (!ctx || !fd || !rep || nf < 1 || nf > ctx->o.max_batch) return TRS_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     TRS_TRY(dev_alloc(ctx->hb_out, (size_t)ctx->o.max_batch * sizeof(trs_partition), &ctx->total));
@@ -803,6 +812,7 @@ int trs_autotune(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_tune_report
         rep->cols_ms[j] = cols[j];
     }
     return TRS_OK;
+    TRS_GUARD_END
 }
 
 int trs_set_window_step(trs_ctx *ctx, int step) {
@@ -847,6 +857,7 @@ int trs_batch_stage_ms(trs_ctx *ctx, float *ms, int max_stages) {
 }
 
 int trs_batch_decide_host(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partition *out_host, void *stream) {
+    TRS_GUARD_BEGIN
     if (!ctx || !fd || !out_host || nf < 1 || nf > ctx->o.max_batch) return TRS_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<size_t> lo(nf), to(nf), dp(nf);
@@ -885,6 +896,7 @@ int trs_batch_decide_host(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_pa
     TRS_CK(cudaMemcpyAsync(out_host, ctx->hb_out.p, (size_t)nf * sizeof(trs_partition), cudaMemcpyDeviceToHost, s));
     TRS_CK(cudaStreamSynchronize(s));
     return TRS_OK;
+    TRS_GUARD_END
 }
 
 }  // extern "C"

@@ -10,6 +10,9 @@
 #include <tuple>
 #include <vector>
 
+#include <new>
+#include <system_error>
+
 #include "plan.h"
 #include "trs_internal.cuh"
 
@@ -18,6 +21,14 @@
         cudaError_t e_ = (call);                                      \
         if (e_ != cudaSuccess) return ::trs::cuda_fail(e_, #call);    \
     } while (0)
+
+// Host allocation or thread start-up failures end an entry point with
+// TRS_ENOMEM instead of unwinding into its C caller.
+#define TRS_GUARD_BEGIN try {
+#define TRS_GUARD_END                                       \
+    }                                                       \
+    catch (const std::bad_alloc &) { return TRS_ENOMEM; }   \
+    catch (const std::system_error &) { return TRS_ENOMEM; }
 
 #define TRS_TRY(expr)                \
     do {                             \

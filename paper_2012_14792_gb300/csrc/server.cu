@@ -118,6 +118,7 @@ size_t slot_bytes(const Stream &st) {
 
 // Launches one batch on slot b (called by the worker without the lock).
 int launch_batch(trs_server *srv, Batch &b) {
+    TRS_GUARD_BEGIN
     const int nf = (int)b.reqs.size();
     std::vector<PlanEntry *> pe(nf);
     DevFrame *hf = (DevFrame *)b.hb;
@@ -155,6 +156,7 @@ int launch_batch(trs_server *srv, Batch &b) {
     TRS_CK(cudaMemcpyAsync(b.out_host, b.out_dev, (size_t)nf * sizeof(trs_partition), cudaMemcpyDeviceToHost, b.s));
     TRS_CK(cudaEventRecord(b.done, b.s));
     return TRS_OK;
+    TRS_GUARD_END
 }
 
 void worker_main(trs_server *srv) {
@@ -180,7 +182,11 @@ void worker_main(trs_server *srv) {
                 d.status = b.failed != TRS_OK ? b.failed : (q == cudaSuccess ? b.out_host[i].status : TRS_ECUDA);
                 d.latency_us = t - r.t_submit;
                 d.partition = b.out_host[i];
-                srv->done.push_back(d);
+                try {
+                    srv->done.push_back(d);
+                } catch (const std::bad_alloc &) {
+                    srv->worker_status = TRS_ENOMEM;  // the decision is lost; callers see the status
+                }
                 Stream &st = srv->streams[r.stream];
                 st.slot[r.slot].busy = false;
                 st.inflight--;
@@ -242,11 +248,21 @@ int trs_server_create(trs_server **out, const trs_server_opts *o) {
     trs_opts co{o->max_width, o->max_height, o->max_regions, o->max_batch, o->k_area, o->device};
     trs_ctx *ctx = nullptr;
     TRS_TRY(trs_create(&ctx, &co));
-    trs_server *srv = new trs_server();
+    trs_server *srv = new (std::nothrow) trs_server();
+    if (!srv) {
+        trs_destroy(ctx);
+        return TRS_ENOMEM;
+    }
     srv->o = *o;
     srv->ctx = ctx;
-    srv->streams.resize(o->max_streams);
-    srv->batches.resize(o->max_inflight);
+    try {
+        srv->streams.resize(o->max_streams);
+        srv->batches.resize(o->max_inflight);
+        for (Batch &b : srv->batches) b.reqs.reserve(o->max_batch);  // the worker never grows them
+    } catch (const std::bad_alloc &) {
+        trs_server_destroy(srv);
+        return TRS_ENOMEM;
+    }
     const size_t blob = batch_blob_bytes(o->max_batch);
     const size_t fl = align256((size_t)o->max_batch * 4), sc = align256((size_t)o->max_batch * 32);
     const size_t pb = align256((size_t)o->max_batch * sizeof(trs_partition));
@@ -273,7 +289,12 @@ int trs_server_create(trs_server **out, const trs_server_opts *o) {
         trs_server_destroy(srv);
         return rc;
     }
-    srv->worker = std::thread(worker_main, srv);
+    try {
+        srv->worker = std::thread(worker_main, srv);
+    } catch (const std::system_error &) {
+        trs_server_destroy(srv);
+        return TRS_ENOMEM;
+    }
     *out = srv;
     return TRS_OK;
 }
@@ -310,6 +331,7 @@ int trs_server_open_stream(trs_server *srv, int width, int height, int bit_depth
 
 int trs_server_open_stream_layers(trs_server *srv, int width, int height, int bit_depth, int n_regions,
                                   float lambda, int n_layers, int *stream_id) {
+    TRS_GUARD_BEGIN
     if (!srv || !stream_id || n_layers < 1 || n_layers > kMaxLayers) return TRS_EINVAL;
     TRS_TRY(check_frame(srv->ctx, width, height));
     if (bit_depth < 8 || bit_depth > 12 || n_regions < 1 || n_regions > srv->o.max_regions) return TRS_EINVAL;
@@ -359,6 +381,7 @@ int trs_server_open_stream_layers(trs_server *srv, int width, int height, int bi
     srv->streams[id] = st;
     *stream_id = id;
     return TRS_OK;
+    TRS_GUARD_END
 }
 
 // Waits (bounded) until no request of the stream is on the device.
@@ -405,6 +428,7 @@ int trs_server_submit(trs_server *srv, int id, const void *luma_host, size_t pit
 
 int trs_server_submit_layer(trs_server *srv, int id, int layer, const void *luma_host, size_t pitch_bytes,
                             uint64_t tag, uint64_t *ticket) {
+    TRS_GUARD_BEGIN
     if (!srv || !luma_host) return TRS_EINVAL;
     std::lock_guard<std::mutex> lk(srv->mu);
     if (id < 0 || id >= (int)srv->streams.size() || !srv->streams[id].open) return TRS_EINVAL;
@@ -436,6 +460,7 @@ int trs_server_submit_layer(trs_server *srv, int id, int layer, const void *luma
     if (ticket) *ticket = r.ticket;
     srv->cv_work.notify_one();
     return TRS_OK;
+    TRS_GUARD_END
 }
 
 int trs_server_poll(trs_server *srv, trs_decision *out, int max_out, int timeout_us, int *n_out) {
