@@ -274,3 +274,23 @@ def test_windowed_search_step_one_is_exact_and_never_better(oracle):
         assert h.n_windows == -(-exact.n_windows // step)
         ev = oracle.evaluate(st, Tq, h.x_edges, h.band_cuts)
         assert ev["n"] == 8 and 3 * ev["amin"] > ev["amax"] and ev["t"] == h.t and ev["q"] == h.q
+
+
+@pytest.mark.parametrize("H,expect_rows", [(511, 1), (512, 2)])
+def test_largest_admissible_area_ratio(oracle, H, expect_rows):
+    """The area rule admits A_max = k*A_min - 1 and no more (Sec. 2.3, strict
+    '>').  A 1-pixel-wide frame of 4 CTU rows split into two slices: with
+    H = 511 the top row (128 px) over the rest (383 = 3*128 - 1 px) is valid
+    and, with the slow top CTU, the time-optimal split; with H = 512 the rest
+    is 384 = 3*128 px, the split is invalid and two rows over two wins."""
+    W, n = 1, 2
+    N = pixel_counts(W, H)
+    S1, S2 = 5 * N, 25 * N
+    Tq = (np.array([[10], [1], [1], [1]]) * 65536).astype(np.uint32)
+    st = stats_from(oracle, W, H, S1, S2, N)
+    ref = bruteforce.search(W, H, S1.tolist(), S2.tolist(), Tq.astype(np.int64).tolist(), n, 0)
+    assert ref["t_min"] == (10 if expect_rows == 1 else 11) * 65536
+    for d in (oracle.search_enum(st, Tq, n, 0.0), oracle.search_dp(st, Tq, n, 0.0)):
+        assert d.status == oracle.OK
+        assert (d.t_min, d.t, d.q) == (ref["t_min"], ref["t"], ref["q"])
+        assert d.band_cuts[0] == 1 << (expect_rows - 1)
