@@ -69,6 +69,24 @@ MUTANTS = [
      "if (!((uint64_t)e->k_area * amin > amax)) return;", "if (!((uint64_t)e->k_area * amin >= amax)) return;"),
     ("mt_eq4_exclusive", "Eq. 4 (multi-tile)",
      "if (tmax > e->thr) return;", "if (tmax >= e->thr) return;"),
+    ("time_round_half_away", "Sec. 2.1 times in Q16 (half-even)",
+     "Tq[i] = (uint32_t)rint(v * 65536.0);", "Tq[i] = (uint32_t)round(v * 65536.0);"),
+    ("light_windows_from_smallest", "Sec. 4 lighter search",
+     "if ((nw - 1 - i) % window_step == 0) win[kept++] = win[i];", "if (i % window_step == 0) win[kept++] = win[i];"),
+    ("enum_tile_rows_bound", "exactly n slices",
+     "if (used + e->r > e->n) return;", "if (used + e->r >= e->n) return;"),
+    ("sse_exact_sign", "Eq. 2 (reported SSE)",
+     "return (long double)S2 - ((long double)S1 * (long double)S1) / (long double)N;",
+     "return (long double)S2 + ((long double)S1 * (long double)S1) / (long double)N;"),
+    ("dp_lambda_ignored", "Eq. 4",
+     "d.thr = eq4_thr(t_min, lambda_q);", "d.thr = eq4_thr(t_min, 0);"),
+    ("dp_step2_bound_exclusive", "Eq. 4",
+     "if (step == 2 && s.T > d->thr) return 0;", "if (step == 2 && s.T >= d->thr) return 0;"),
+    ("mt_split_all_cuts_dropped", "in-tile slices (multi-tile)",
+     "for (uint64_t cm = 0; cm < (1ull << (h - 1)); ++cm) {",
+     "for (uint64_t cm = 0; cm + 1 < (1ull << (h - 1)); ++cm) {"),
+    ("mt_groups_one_row", "rectangles of whole tiles (multi-tile)",
+     "for (int h = 1; ty + h <= e->r; ++h) {", "for (int h = 1; ty + h <= e->r && h < 2; ++h) {"),
 ]
 
 _DRIVER = r'''

@@ -294,3 +294,44 @@ def test_largest_admissible_area_ratio(oracle, H, expect_rows):
         assert d.status == oracle.OK
         assert (d.t_min, d.t, d.q) == (ref["t_min"], ref["t"], ref["q"])
         assert d.band_cuts[0] == 1 << (expect_rows - 1)
+
+
+def _exact_sse(plane, W, H, rects):
+    """Per slice S2 - S1^2/N as exact rationals, from the samples themselves
+    (rects as (x0, x1, y0, y1) in CTUs)."""
+    from fractions import Fraction
+    out = []
+    for x0, x1, y0, y1 in rects:
+        blk = plane[y0 * 128:min(y1 * 128, H), x0 * 128:min(x1 * 128, W)].astype(np.int64)
+        s1, s2 = int(blk.sum()), int((blk * blk).sum())
+        out.append(Fraction(s2) - Fraction(s1 * s1, blk.size))
+    return out
+
+
+@pytest.mark.parametrize("W,H,n,seed", [(300, 200, 3, 1), (832, 480, 4, 2), (640, 384, 5, 3)])
+def test_reported_sse_is_exact_sum_of_squared_deviations(oracle, W, H, n, seed):
+    """Eq. 2: the reported SSE of the chosen partition is the exact sum over
+    its slices of sum (p - mean)^2, and Q is the sum of their floors."""
+    import math
+    import synth
+    plane, times = synth.small_frame(W, H, 10, seed)
+    d, _, _ = oracle.decide(plane, times, 10, n, 0.1)
+    assert d.status == oracle.OK
+    C, R = oracle.grid(W, H)
+    parts = _exact_sse(plane, W, H, d.regions(R))
+    assert d.q == sum(math.floor(p) for p in parts)
+    assert abs(d.sse_real - float(sum(parts))) <= 1e-9 * float(sum(parts))
+
+
+@pytest.mark.parametrize("W,H,n,seed", [(832, 480, 4, 4), (640, 640, 5, 5)])
+def test_multi_tile_reported_sse_is_exact(oracle, W, H, n, seed):
+    import math
+    import synth
+    plane, times = synth.small_frame(W, H, 10, seed)
+    st = oracle.texture(plane, 10)
+    Tq, _ = oracle.time_q(times)
+    r = oracle.mt_search(st, Tq, n, 0.1)
+    assert r["status"] == oracle.OK
+    parts = _exact_sse(plane, W, H, [(x0, x1, y0, y1) for (x0, y0, x1, y1) in r["regions"]])
+    assert r["q"] == sum(math.floor(p) for p in parts)
+    assert abs(r["sse"] - float(sum(parts))) <= 1e-9 * float(sum(parts))
