@@ -87,6 +87,23 @@ MUTANTS = [
      "for (uint64_t cm = 0; cm + 1 < (1ull << (h - 1)); ++cm) {"),
     ("mt_groups_one_row", "rectangles of whole tiles (multi-tile)",
      "for (int h = 1; ty + h <= e->r; ++h) {", "for (int h = 1; ty + h <= e->r && h < 2; ++h) {"),
+    ("texture_vmax_min", "sample range check",
+     "if (p > vmax[i]) vmax[i] = p;", "if (p < vmax[i]) vmax[i] = p;"),
+    ("texture_pitch_ignored", "sample layout",
+     "const uint8_t *row = base + (size_t)y * pitch;",
+     "const uint8_t *row = base + (size_t)y * (size_t)W * (size_t)bps;"),
+    ("time_nan_accepted", "Sec. 2.1 times in Q16",
+     "if (!(v >= 0.0) || !(v < 65536.0)) {", "if (v < 0.0 || v >= 65536.0) {"),
+    ("dp_tmin_first_window_only", "Eq. 3",
+     "if (t < t_min) t_min = t;", "if (t < t_min && t_min == OR_INF) t_min = t;"),
+    ("evaluate_time_summed", "Eq. 1 (checker)",
+     "                if (s.T > t) t = s.T;\n                q += sse_floor(s.S1, s.S2, s.N);",
+     "                t += s.T;\n                q += sse_floor(s.S1, s.S2, s.N);"),
+    ("evaluate_amin_wrong", "Sec. 2.3 area rule (checker)",
+     "                if (s.N < amin) amin = s.N;\n                if (s.N > amax) amax = s.N;\n                nreg++;",
+     "                if (s.N > amin) amin = s.N;\n                if (s.N > amax) amax = s.N;\n                nreg++;"),
+    ("rect_q_is_time", "Eq. 2 (checker)",
+     "    *q_out = sse_floor(s.S1, s.S2, s.N);\n    return OR_OK;\n}", "    *q_out = s.T;\n    return OR_OK;\n}"),
 ]
 
 _DRIVER = r'''

@@ -335,3 +335,37 @@ def test_multi_tile_reported_sse_is_exact(oracle, W, H, n, seed):
     parts = _exact_sse(plane, W, H, [(x0, x1, y0, y1) for (x0, y0, x1, y1) in r["regions"]])
     assert r["q"] == sum(math.floor(p) for p in parts)
     assert abs(r["sse"] - float(sum(parts))) <= 1e-9 * float(sum(parts))
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_evaluate_and_rect_match_direct_sums(oracle, seed):
+    """The checkers the GPU tests lean on (oracle_evaluate for a whole
+    partition, oracle_rect for one rectangle) against sums written out here
+    over random tile columns and slice cuts of random tiny frames: Eq. 1's
+    slowest slice, Eq. 2's floored SSE sum, the smallest and largest area."""
+    rng = np.random.default_rng(500 + seed)
+    C, R = int(rng.integers(1, 6)), int(rng.integers(1, 6))
+    W = (C - 1) * 128 + int(rng.integers(1, 129))
+    H = (R - 1) * 128 + int(rng.integers(1, 129))
+    S1, S2, N, Tq = random_instance(rng, W, H, "random")
+    st = stats_from(oracle, W, H, S1, S2, N)
+    inner = [x for x in range(1, C) if rng.random() < 0.5]
+    x_edges = [0] + inner + [C]
+    band_cuts = [int(rng.integers(0, 1 << (R - 1))) if R > 1 else 0 for _ in range(len(x_edges) - 1)]
+    slices = []
+    for b in range(len(x_edges) - 1):
+        y0 = 0
+        for y in range(1, R + 1):
+            if y == R or (band_cuts[b] >> (y - 1)) & 1:
+                slices.append((x_edges[b], x_edges[b + 1], y0, y))
+                y0 = y
+    terms = []
+    for x0, x1, y0, y1 in slices:
+        t = int(Tq[y0:y1, x0:x1].astype(np.int64).sum())
+        s1, s2, a = (int(v[y0:y1, x0:x1].astype(object).sum()) for v in (S1, S2, N))
+        q = s2 - (-(-s1 * s1 // a))
+        terms.append((t, q, a))
+        assert oracle.rect(st, Tq, x0, x1, y0, y1) == (t, q)
+    ev = oracle.evaluate(st, Tq, x_edges, band_cuts)
+    assert ev == dict(t=max(t for t, _, _ in terms), q=sum(q for _, q, _ in terms),
+                      amin=min(a for _, _, a in terms), amax=max(a for _, _, a in terms), n=len(terms))
