@@ -195,10 +195,13 @@ int trs_count_partitions(int width, int height, int n_regions, int k_area, doubl
  * row-DP units can form (each tile column through its unit in that window,
  * with the unit's heights and slice-count range) -- with 128-bit counting
  * DPs.  *short_windows = windows where the second count is smaller (0 for
- * a sound plan), *windows = windows checked.  window_step as in
- * trs_set_window_step.  TRS_EINVAL for bad shapes. */
+ * a sound plan), *windows = windows checked.  *in_windows = partitions of
+ * S(n) (one tile row) whose smallest slice area is one of the plan's
+ * windows: with window_step 1 it equals trs_count_partitions when no
+ * window is missing.  window_step as in trs_set_window_step.  TRS_EINVAL
+ * for bad shapes. */
 int trs_plan_coverage(int width, int height, int n_regions, int k_area, int window_step, int *windows,
-                      int *short_windows);
+                      int *short_windows, double *in_windows);
 
 /* Measured INT32 throughput of the device (32-bit add / min / max chains
  * over every SM, CUDA-event timed, best of three), in operations per

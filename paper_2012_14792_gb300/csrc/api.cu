@@ -179,8 +179,9 @@ int trs_plan_stats(int width, int height, int n, int k, int *n_windows, int *n_i
     return TRS_OK;
 }
 
-int trs_plan_coverage(int width, int height, int n, int k, int window_step, int *windows, int *short_windows) {
-    return plan_coverage(width, height, n, k, window_step, windows, short_windows);
+int trs_plan_coverage(int width, int height, int n, int k, int window_step, int *windows, int *short_windows,
+                      double *in_windows) {
+    return plan_coverage(width, height, n, k, window_step, windows, short_windows, in_windows);
 }
 
 int trs_create(trs_ctx **out, const trs_opts *o) {

@@ -300,18 +300,30 @@ static unsigned __int128 count_planned(const HostPlan &p, int wi) {
     return combine_columns(p.C, n, g);
 }
 
-int plan_coverage(int W, int H, int n, int k, int window_step, int *windows, int *short_windows) {
-    if (!windows || !short_windows) return TRS_EINVAL;
+int plan_coverage(int W, int H, int n, int k, int window_step, int *windows, int *short_windows,
+                  double *in_windows) {
+    if (!windows || !short_windows || !in_windows) return TRS_EINVAL;
     HostPlan p;
     const int st = build_plan(W, H, n, k, &p, window_step);
     if (st != TRS_OK) return st;
+    // every slice area, ascending: the area just above a window's own
+    std::set<uint64_t> all;
+    for (uint32_t w : extents(p.C, W))
+        for (uint32_t h : extents(p.R, H)) all.insert((uint64_t)w * h);
     int bad = 0;
+    unsigned __int128 total = 0;
     for (int wi = 0; wi < (int)p.win_a.size(); ++wi) {
         const uint64_t lo = p.win_a[wi], hi = (uint64_t)k * lo - 1;
-        if (count_planned(p, wi) != count_in_range(W, H, p.C, p.R, n, lo, hi)) ++bad;
+        const unsigned __int128 full = count_in_range(W, H, p.C, p.R, n, lo, hi);
+        if (count_planned(p, wi) != full) ++bad;
+        // partitions whose smallest slice area is this window's
+        total += full;
+        const auto next = all.upper_bound(lo);
+        if (next != all.end() && *next <= hi) total -= count_in_range(W, H, p.C, p.R, n, *next, hi);
     }
     *windows = (int)p.win_a.size();
     *short_windows = bad;
+    *in_windows = (double)(long double)total;
     return TRS_OK;
 }
 

@@ -29,7 +29,8 @@ int build_plan(int W, int H, int n, int k, HostPlan *p, int window_step = 1);
 // Soundness of a plan: for each of its windows, whether it represents every
 // one-tile-row partition whose slice areas all fit the window (see
 // trs_plan_coverage).
-int plan_coverage(int W, int H, int n, int k, int window_step, int *windows, int *short_windows);
+int plan_coverage(int W, int H, int n, int k, int window_step, int *windows, int *short_windows,
+                  double *in_windows);
 // Exact number of partitions in S(n) with one tile row (see trs_count_partitions).
 int count_partitions(int W, int H, int n, int k, long double *out);
 size_t plan_blob_bytes(const HostPlan &p);

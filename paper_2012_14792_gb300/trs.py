@@ -134,7 +134,7 @@ def _load():
         "trs_plan_stats": ([i, i, i, i, ct.POINTER(i), ct.POINTER(i)], i),
         "trs_plan_work": ([i, i, i, i, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)], i),
         "trs_count_partitions": ([i, i, i, i, ct.POINTER(ct.c_double)], i),
-        "trs_plan_coverage": ([i, i, i, i, i, ct.POINTER(i), ct.POINTER(i)], i),
+        "trs_plan_coverage": ([i, i, i, i, i, ct.POINTER(i), ct.POINTER(i), ct.POINTER(ct.c_double)], i),
         "trs_mt_count": ([i, i, i, i, ct.POINTER(ct.c_int64)], i),
         "trs_mt_list": ([i, i, i, i, vp, sz, ct.POINTER(ct.c_int64)], i),
         "trs_alu_peak": ([i, ct.POINTER(ct.c_double)], i),
@@ -234,12 +234,13 @@ def trs_count_partitions(width: int, height: int, n_regions: int, k_area: int = 
 
 
 def trs_plan_coverage(width: int, height: int, n_regions: int, k_area: int = 3,
-                      window_step: int = 1) -> tuple[int, int]:
-    """(windows checked, windows whose plan misses a partition of the window)."""
-    nw, bad = ct.c_int(0), ct.c_int(0)
-    _check(_lib.trs_plan_coverage(width, height, n_regions, k_area, window_step, ct.byref(nw), ct.byref(bad)),
-           "trs_plan_coverage")
-    return nw.value, bad.value
+                      window_step: int = 1) -> tuple[int, int, float]:
+    """(windows checked, windows whose plan misses a partition of the window,
+    partitions whose smallest slice area is a window of the plan)."""
+    nw, bad, inw = ct.c_int(0), ct.c_int(0), ct.c_double(0)
+    _check(_lib.trs_plan_coverage(width, height, n_regions, k_area, window_step, ct.byref(nw), ct.byref(bad),
+                                  ct.byref(inw)), "trs_plan_coverage")
+    return nw.value, bad.value, inw.value
 
 
 def trs_plan_work(width: int, height: int, n_regions: int, k_area: int = 3) -> tuple[float, float]:

@@ -205,9 +205,11 @@ def test_plan_loses_no_partition(trs, W, H, n, k, step):
     plan can be formed from the plan's units in that window (the pruning by
     area bounds, tiling bounds and slice-count reachability drops only
     options no partition uses)."""
-    windows, short = trs.trs_plan_coverage(W, H, n, k, step)
+    windows, short, in_windows = trs.trs_plan_coverage(W, H, n, k, step)
     assert short == 0
-    assert windows == (trs.trs_plan_stats(W, H, n, k)[0] if step == 1 else windows)
+    if step == 1:  # and no window is missing: every partition's smallest area is one
+        assert windows == trs.trs_plan_stats(W, H, n, k)[0]
+        assert in_windows == trs.trs_count_partitions(W, H, n, k)
 
 
 def test_plan_loses_no_partition_random_shapes(trs):
@@ -217,8 +219,11 @@ def test_plan_loses_no_partition_random_shapes(trs):
         W, H = int(rng.integers(1, 8193)), int(rng.integers(1, 4097))
         C, R = -(-W // 128), -(-H // 128)
         n = int(rng.integers(1, min(32, C * R) + 1))
-        windows, short = trs.trs_plan_coverage(W, H, n, int(rng.integers(2, 5)), int(rng.integers(1, 5)))
+        k, step = int(rng.integers(2, 5)), int(rng.integers(1, 5))
+        windows, short, in_windows = trs.trs_plan_coverage(W, H, n, k, step)
         assert short == 0, (W, H, n)
+        if step == 1:
+            assert in_windows == trs.trs_count_partitions(W, H, n, k), (W, H, n, k)
 
 
 C_CLIENT = r"""
