@@ -284,3 +284,17 @@ def test_header_is_plain_c_and_links(trs, tmp_path):
     assert float(parts) == trs.trs_count_partitions(832, 480, 4)
     assert int(sets) == trs.trs_mt_count(832, 480, 4)
     assert (int(nw), int(ni)) == trs.trs_plan_stats(3840, 2160, 16)
+
+
+@pytest.mark.parametrize("W,H,n,k", [(1, 511, 2, 3), (1, 512, 2, 3), (1, 255, 1, 2), (255, 1, 1, 2),
+                                     (1, 383, 1, 3), (129, 511, 3, 3)])
+def test_area_rule_boundary_shapes(trs, W, H, n, k):
+    """Shapes with a slice area of exactly k*A_min - 1, the largest the rule
+    admits (Sec. 2.3): 1x511 splits into 128 over 383 = 3*128 - 1 rows of
+    pixels; at k = 2 the 1x255 frame is one slice of 255 = 2*128 - 1 samples,
+    the area just above 128.  Counts equal the brute force's, the plan forms
+    every partition of each window, and no window is missing."""
+    expect = _brute_partitions(W, H, n, k)
+    assert trs.trs_count_partitions(W, H, n, k) == expect
+    _, short, in_windows = trs.trs_plan_coverage(W, H, n, k, 1)
+    assert short == 0 and in_windows == expect
