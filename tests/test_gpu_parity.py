@@ -473,3 +473,29 @@ def test_windowed_search_matches_oracle(dec, oracle, spec_name, n, step):
             assert_partition_equal(p, d, spec.ctu_rows)
     finally:
         trs.trs_set_window_step(dec.ctx, 1)
+
+
+@pytest.mark.parametrize("W,H,n,k", [(1, 511, 2, 3), (1, 512, 2, 3), (129, 511, 3, 3), (1, 255, 1, 2),
+                                     (255, 1, 1, 2)])
+def test_area_rule_edge_frames(oracle, W, H, n, k):
+    """Frames where a slice area can equal k*A_min - 1, the largest the rule
+    admits (Sec. 2.3): with a slow top CTU row the 1x511 frame's best split is
+    128 over 383 = 3*128 - 1 rows of pixels, and 1x512's is 256 over 256; at
+    k = 2 the 1x255 frame's one slice of 255 = 2*128 - 1 samples lies in the
+    window of area 128.  The GPU partition equals the oracle's."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2012_14792_gb300 import runtime
+    d = runtime.Decider(max_width=512, max_height=512, max_regions=4, max_batch=1, k_area=k)
+    try:
+        rng = np.random.default_rng(W + H + k)
+        plane = rng.integers(0, 1024, size=(H, W)).astype(np.uint16)
+        C, R = oracle.grid(W, H)
+        times = np.ones((R, C), np.float32)
+        times[0, :] = 10.0
+        p = _decide(d, plane, times, 10, n, 0.0)
+        ref, _, _ = oracle.decide(plane, times, 10, n, 0.0, k_area=k)
+        assert ref.status == oracle.OK
+        assert_partition_equal(p, ref, R)
+    finally:
+        d.close()
