@@ -30,7 +30,10 @@
  *     Errors that depend on the data (a sample >= 2^bit_depth, a time that
  *     is not finite or outside [0, 65536), no partition satisfying the area
  *     rule) are reported in trs_partition.status, written on the device.
- *   - A context serves one host thread at a time.
+ *   - A context serves one host thread at a time.  Its device scratch is
+ *     reused by every call, so calls on one context must be ordered on the
+ *     device: issue them on one stream, or order the streams with events.
+ *     For work in flight on several streams at once, use a context each.
  *
  * Readings of the paper fixed by this library (the paper is silent on them):
  *   CTUs are 128x128 luma samples, edge CTUs clipped.  A partition has
