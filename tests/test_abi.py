@@ -298,3 +298,33 @@ def test_area_rule_boundary_shapes(trs, W, H, n, k):
     assert trs.trs_count_partitions(W, H, n, k) == expect
     _, short, in_windows = trs.trs_plan_coverage(W, H, n, k, 1)
     assert short == 0 and in_windows == expect
+
+
+@pytest.mark.parametrize("W,H", [(1, 1), (128, 128), (129, 257), (832, 480), (1920, 1080), (3840, 2160),
+                                 (8192, 4096), (8192, 1), (1, 4096)])
+def test_tables_layout_holds_every_documented_array(trs, W, H):
+    """Each array of the region tables starts on a 256-byte boundary, in the
+    documented order, with room for its documented element count, and the
+    total covers the last one; the band index formula enumerates every band
+    [x0, x1) once."""
+    lay = trs.trs_tables_layout_get(W, H)
+    C, R = -(-W // 128), -(-H // 128)
+    assert (lay.width, lay.height, lay.cols, lay.rows, lay.bands) == (W, H, C, R, C * (C + 1) // 2)
+    arrays = [("off_tq", R * C * 4), ("off_sat_s1", (R + 1) * (C + 1) * 8), ("off_sat_s2", (R + 1) * (C + 1) * 8),
+              ("off_sat_t", (R + 1) * (C + 1) * 8), ("off_rect_t", lay.bands * R * R * 8),
+              ("off_rect_q", lay.bands * R * R * 8), ("off_status", 16)]
+    end = 0
+    for name, size in arrays:
+        off = getattr(lay, name)
+        assert off % 256 == 0 and off >= end, name
+        end = off + size
+    assert lay.bytes >= end and lay.bytes % 256 == 0
+    bands = sorted(x0 * (2 * C - x0 + 1) // 2 + (x1 - x0 - 1) for x0 in range(C) for x1 in range(x0 + 1, C + 1))
+    assert bands == list(range(lay.bands))
+
+
+def test_tables_layout_rejects_bad_shapes(trs):
+    for W, H in [(0, 10), (10, 0), (8193, 10), (10, 4097)]:
+        with pytest.raises(trs.TrsError) as e:
+            trs.trs_tables_layout_get(W, H)
+        assert e.value.status == trs.EINVAL
