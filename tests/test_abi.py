@@ -328,3 +328,44 @@ def test_tables_layout_rejects_bad_shapes(trs):
         with pytest.raises(trs.TrsError) as e:
             trs.trs_tables_layout_get(W, H)
         assert e.value.status == trs.EINVAL
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without libtrs.so the binding (and the runtime helper above it)
+    refuses to import: there is no CPU fallback."""
+    import subprocess
+    import sys
+    code = (f"import sys; sys.path.insert(0, {ROOT!r})\n"
+            "import paper_2012_14792_gb300.build as B\n"
+            f"B.LIB = {str(tmp_path / 'absent' / 'libtrs.so')!r}\n"
+            "import importlib\n"
+            "for mod in ('paper_2012_14792_gb300.trs', 'paper_2012_14792_gb300.runtime'):\n"
+            "    try:\n"
+            "        importlib.import_module(mod)\n"
+            "    except ImportError as e:\n"
+            "        assert 'not built' in str(e), e\n"
+            "    else:\n"
+            "        raise SystemExit(mod + ' imported without the library')\n")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+
+
+def test_package_never_reaches_the_oracle():
+    """No module of the package imports the oracle or names its library."""
+    import ast
+    pkg = os.path.join(ROOT, "paper_2012_14792_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            path = os.path.join(dirpath, f)
+            if f.endswith(".py"):
+                tree = ast.parse(open(path).read())
+                for node in ast.walk(tree):
+                    names = []
+                    if isinstance(node, ast.Import):
+                        names = [a.name for a in node.names]
+                    elif isinstance(node, ast.ImportFrom):
+                        names = [node.module or ""]
+                    assert not any(n == "oracle" or n.startswith("oracle.") for n in names), (path, names)
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(path).read()
+                assert "liboracle" not in text and "trs_oracle" not in text, path
