@@ -369,3 +369,21 @@ def test_package_never_reaches_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(path).read()
                 assert "liboracle" not in text and "trs_oracle" not in text, path
+
+
+def test_oracle_never_reaches_the_package():
+    """The oracle shares no code with the CUDA path: its modules import
+    nothing of the package and its C source includes none of the library's
+    headers."""
+    import ast
+    odir = os.path.join(ROOT, "oracle")
+    for f in os.listdir(odir):
+        path = os.path.join(odir, f)
+        if f.endswith(".py"):
+            for node in ast.walk(ast.parse(open(path).read())):
+                if isinstance(node, (ast.Import, ast.ImportFrom)):
+                    names = [a.name for a in node.names] if isinstance(node, ast.Import) else [node.module or ""]
+                    assert not any(n.startswith("paper_2012_14792_gb300") for n in names), (path, names)
+        if f.endswith((".c", ".h")):
+            includes = re.findall(r'#include\s*[<"]([^>"]+)[>"]', open(path).read())
+            assert not any(i.startswith("trs") or "csrc" in i or i.endswith(".cuh") for i in includes), (path, includes)
