@@ -112,8 +112,9 @@ class trs_mt_partition(ct.Structure):
                 ("region", (ct.c_int16 * 4) * MAX_REGIONS)]
 
     def regions(self) -> list[tuple[int, int, int, int]]:
-        """Slices as (x0, y0, x1, y1) in CTUs, raster order."""
-        return [tuple(int(v) for v in self.region[i]) for i in range(self.n_regions)]
+        """Slices as (x0, x1, y0, y1) in CTUs, as trs_partition.regions(), in
+        raster order of their top-left corners."""
+        return [(int(r[0]), int(r[2]), int(r[1]), int(r[3])) for r in self.region[: self.n_regions]]
 
 
 MT_PARTITION_BYTES = ct.sizeof(trs_mt_partition)

@@ -44,6 +44,11 @@ def _tables(dec, plane, times, bd):
     return tab
 
 
+def _x0x1y0y1(regions):
+    """(x0, y0, x1, y1) slices, as the oracle reports them, in the binding's (x0, x1, y0, y1) order."""
+    return [(x0, x1, y0, y1) for (x0, y0, x1, y1) in regions]
+
+
 def _assert_equal(p, ref, count):
     assert p.status == ref["status"], (p.status, ref["status"])
     assert p.candidates == count
@@ -51,7 +56,7 @@ def _assert_equal(p, ref, count):
         assert p.winner == -1
         return
     assert (p.t_min_q, p.thr_q, p.t_q, p.q) == (ref["t_min"], ref["thr"], ref["t"], ref["q"])
-    assert p.regions() == ref["regions"]
+    assert p.regions() == _x0x1y0y1(ref["regions"])
     assert abs(p.sse - ref["sse"]) <= max(SSE_REL * abs(ref["sse"]), SSE_ABS)
     assert p.t_min == p.t_min_q / 65536.0 and p.t == p.t_q / 65536.0
 
@@ -115,7 +120,7 @@ def test_mt_two_slices_full_frame(dec, oracle, spec_name):
         p = dec.search_mt(tab, W, H, 2, lam)
         assert p.status == 0 and p.candidates == len(cands)
         assert (p.t_min_q, p.thr_q, p.t_q, p.q) == (t_min, thr, best[1], best[2])
-        assert p.regions() == sorted(best[3], key=lambda r: (r[1], r[0]))
+        assert p.regions() == _x0x1y0y1(sorted(best[3], key=lambda r: (r[1], r[0])))
 
 
 @pytest.mark.parametrize("spec_name,n", [("SPEC_1080P10", 3), ("SPEC_1080P10", 4), ("SPEC_1080P10", 5),
@@ -136,7 +141,7 @@ def test_mt_full_frames_up_to_five_slices(dec, oracle, spec_name, n):
         p = dec.search_mt(tab, W, H, n, lam)
         assert p.status == ref["status"] == 0 and p.candidates == ref["count"]
         assert (p.t_min_q, p.thr_q, p.t_q, p.q) == (ref["t_min"], ref["thr"], ref["t"], ref["q"])
-        assert p.regions() == ref["regions"]
+        assert p.regions() == _x0x1y0y1(ref["regions"])
 
 
 def test_mt_no_valid_set_and_out_of_range(dec, oracle):
