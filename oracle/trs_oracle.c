@@ -18,8 +18,21 @@
  *                       Eq. 4, both under k*A_min > A_max (Sec. 2.3)
  *   oracle_search_dp    O2: exact dynamic programme over the same space;
  *                       equal to O1 by construction (checked by the tests)
+ *   oracle_search_dp_windows  O2 over every s-th area window only (the
+ *                       lighter search the paper leaves to future work, Sec. 4)
  *   oracle_mt_search    the multi-tile slice space (slices of one tile or
- *                       rectangles of whole tiles), enumerated (Sec. 1, Fig. 1b)
+ *                       rectangles of whole tiles), enumerated (Sec. 1, Fig. 1b):
+ *                       every tile grid, its tiles grouped into rectangles
+ *   oracle_mt_count     the number of distinct slice sets of that space
+ *   oracle_evaluate,    T, Q and the area extremes of a given partition or
+ *   oracle_rect         rectangle by direct sums (checkers for the tests)
+ *
+ * Every function is pinned by the tests against what the paper and the
+ * mathematics fix, not against itself: brute force over all line subsets or
+ * all rectangle partitions on tiny frames, closed-form counts, constant and
+ * ramp planes, hand-worked cases, exact rational SSE from the samples.
+ * tests/test_oracle_mutants.py plants slips in a copy of this file and
+ * checks that each one fails a pin.
  *
  * Readings of the paper used here (the paper is silent on these points):
  *   - CTUs are 128x128 luma samples; edge CTUs are clipped to the frame.
@@ -36,7 +49,9 @@
  *   - Ties on Q are broken by the smallest canonical code: the tile-row cut
  *     bits top to bottom, then per tile column left to right its right edge
  *     followed by the in-tile slice cut bits of its tiles top to bottom
- *     ('0' < '1').
+ *     ('0' < '1').  In the multi-tile space, by the smallest list of slices in
+ *     raster order of their top-left corners, each compared as
+ *     (y0, x0, y1, x1).
  */
 #include <math.h>
 #include <stdint.h>
