@@ -387,3 +387,16 @@ def test_oracle_never_reaches_the_package():
         if f.endswith((".c", ".h")):
             includes = re.findall(r'#include\s*[<"]([^>"]+)[>"]', open(path).read())
             assert not any(i.startswith("trs") or "csrc" in i or i.endswith(".cuh") for i in includes), (path, includes)
+
+
+def test_every_exported_entry_point_is_declared(trs):
+    """No undocumented C entry point: each exported trs_* symbol of the
+    library is declared in include/trs.h."""
+    import shutil
+    import subprocess
+    if shutil.which("nm") is None:
+        pytest.skip("no nm")
+    from paper_2012_14792_gb300 import build
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB], capture_output=True, text=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if ln.split() and ln.split()[-1].startswith("trs_")}
+    assert exported and exported <= set(declared_functions()), sorted(exported - set(declared_functions()))
