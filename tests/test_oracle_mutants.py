@@ -47,15 +47,15 @@ MUTANTS = [
     ("eq4_bound_rounded_up", "Eq. 4",
      "u128 q = v / 65536u;", "u128 q = (v + 65535u) / 65536u;"),
     ("enum_area_rule_not_strict", "Sec. 2.3 area rule",
-     "if (e->area_rule && !((u128)e->k_area * amin > (u128)amax)) return;",
-     "if (e->area_rule && !((u128)e->k_area * amin >= (u128)amax)) return;"),
+     "return !e->area_rule || (u128)e->k_area * p->amin > (u128)p->amax;",
+     "return !e->area_rule || (u128)e->k_area * p->amin >= (u128)p->amax;"),
     ("enum_eq4_exclusive", "Eq. 4",
-     "if ((u128)tmax * 65536u > (u128)e->t_min * (65536u + (u128)e->lambda_q)) return;",
-     "if ((u128)tmax * 65536u >= (u128)e->t_min * (65536u + (u128)e->lambda_q)) return;"),
+     "(u128)p->tmax * 65536u <= (u128)e->t_min * (65536u + (u128)e->lambda_q);",
+     "(u128)p->tmax * 65536u < (u128)e->t_min * (65536u + (u128)e->lambda_q);"),
     ("enum_time_summed", "Eq. 1 (slowest slice)",
-     "if (s.T > tmax) tmax = s.T;", "tmax += s.T;"),
+     "if (s.T > p.tmax) p.tmax = s.T;", "p.tmax += s.T;"),
     ("enum_tie_to_last", "tie order",
-     "if (!e->have_best || q < e->best_q) {", "if (!e->have_best || q <= e->best_q) {"),
+     "if (!e->have_best || p->q < e->best_q) {", "if (!e->have_best || p->q <= e->best_q) {"),
     ("dp_row_times_summed", "Eq. 1, Eq. 3",
      "uint64_t v = G[yp][k - 1] > s.T ? G[yp][k - 1] : s.T;", "uint64_t v = G[yp][k - 1] + s.T;"),
     ("dp_columns_min_not_max", "Eq. 1, Eq. 3",
@@ -73,6 +73,13 @@ MUTANTS = [
      "Tq[i] = (uint32_t)rint(v * 65536.0);", "Tq[i] = (uint32_t)round(v * 65536.0);"),
     ("light_windows_from_smallest", "Sec. 4 lighter search",
      "if ((nw - 1 - i) % window_step == 0) win[kept++] = win[i];", "if (i % window_step == 0) win[kept++] = win[i];"),
+    ("enum_rest_unclipped", "Sec. 2.3 area rule (the rest of the frame, clipped edge CTUs)",
+     "int wpx = (x1 * OR_CTU < f->W ? x1 * OR_CTU : f->W);", "int wpx = x1 * OR_CTU;"),
+    ("enum_rest_count_off_by_one", "exactly n slices (slices still to come)",
+     "u128 left = (u128)(uint64_t)(e->n - used);", "u128 left = (u128)(uint64_t)(e->n - used + 1);"),
+    ("enum_line_skipped", "in-tile slice cuts",
+     "enum_lines(e, x, x1, y + 1, y, cuts | (1ull << (y - 1)), tile_row ? k : k + 1, used, c);",
+     "enum_lines(e, x, x1, y + 2 > f->R ? f->R : y + 2, y, cuts | (1ull << (y - 1)), tile_row ? k : k + 1, used, c);"),
     ("enum_tile_rows_bound", "exactly n slices",
      "if (used + e->r > e->n) return;", "if (used + e->r >= e->n) return;"),
     ("sse_exact_sign", "Eq. 2 (reported SSE)",
