@@ -331,22 +331,27 @@ int trs_decide_host(trs_ctx *ctx, const void *luma_host, int width, int height, 
                     int bit_depth, const float *ctu_time_host, int n_regions, float lambda,
                     trs_partition *out_host, void *stream);
 
-/* trs_search for callers that cannot allocate memory (code running while
- * other work is captured into a CUDA graph, real-time loops that cannot
- * absorb the device synchronisation of cudaMalloc/cudaFree, hosts whose own
- * pool allocator owns all device memory).  The paper has no counterpart: it
- * is a deployment variant of the search call above, with the same result.
- * No context: the search plan and scratch live in one file-scope device
- * array of 8 MiB that every GPU loading the library keeps until exit.  A
- * frame shape whose plan and scratch exceed it returns TRS_ENOMEM (a
- * 3840x2160 frame with n = 16 needs about 2.5 MB).  No cudaMalloc, cudaFree
- * or allocating library call is made.  All calls on a device share the
- * array, which keeps the last call's contents; calls whose work overlaps on
- * the GPU race on it, so serialise them.  The first call on a device looks
- * up the array's address (cudaGetSymbolAddress, with that device current)
- * and should come before any stream capture; a call with a new shape copies
- * its plan with cudaMemcpyAsync after the stream drains.  Arguments as for
- * trs_search, plus k_area (the area-rule factor, 3 in the paper). */
+/* trs_search for callers that cannot allocate memory (real-time loops that
+ * cannot absorb the device synchronisation of cudaMalloc/cudaFree, hosts
+ * whose own pool allocator owns all device memory, code running while
+ * another thread captures a CUDA graph in global mode, where cudaMalloc is
+ * not permitted).  The paper has no counterpart: it is a deployment variant
+ * of the search call above, with the same result.  No context: the search
+ * plan and scratch live in one file-scope device array of 8 MiB that every
+ * GPU loading the library keeps until exit.  A frame shape whose plan and
+ * scratch exceed it returns TRS_ENOMEM (a 3840x2160 frame with n = 16 needs
+ * about 2.5 MB).  No cudaMalloc, cudaFree or allocating library call is
+ * made.  All calls on a device share the array, which keeps the last call's
+ * contents; calls whose work overlaps on the GPU race on it, so serialise
+ * them.  The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress, with that device current) and should come before
+ * any stream capture.  A call whose shape (width, height, n, k_area)
+ * differs from the previous one's writes its plan over the old one with a
+ * cudaMemcpyAsync from pageable host memory on `stream`, ordered only after
+ * earlier work on that stream: the work of earlier calls must have finished
+ * by then, and such calls (the first one included) belong outside any
+ * stream capture in the process.  Arguments as for trs_search, plus k_area
+ * (the area-rule factor, 3 in the paper). */
 int trs_search_noalloc(const void *tables_dev, int width, int height, int n_regions, int k_area, float lambda,
                        trs_partition *out_dev, void *stream);
 

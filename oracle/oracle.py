@@ -130,6 +130,7 @@ def lib():
                                          ct.POINTER(ct.c_int)]
         _lib.oracle_rect.argtypes = [ct.c_int, ct.c_int, u64p, u64p, u64p, u32p, ct.c_int, ct.c_int, ct.c_int,
                                      ct.c_int, u64p, u64p]
+        _lib.oracle_rect_all.argtypes = [ct.c_int, ct.c_int, u64p, u64p, u64p, u32p, u64p, u64p]
         _lib.oracle_result_size.restype = ct.c_size_t
         assert _lib.oracle_result_size() == ct.sizeof(_Result)
         _lib.oracle_mt_search.argtypes = [ct.c_int, ct.c_int, u64p, u64p, u64p, u32p, ct.c_int, ct.c_int,
@@ -284,6 +285,19 @@ def rect(st: Stats, Tq: np.ndarray, x0: int, x1: int, y0: int, y1: int) -> tuple
     if s != OK:
         raise ValueError(f"oracle_rect status {s}")
     return int(t[0]), int(q[0])
+
+
+def rect_all(st: Stats, Tq: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """(time, floor SSE) of every CTU rectangle by direct sums, as two uint64
+    arrays indexed [x0, x1, y0, y1] (zero where x0 >= x1 or y0 >= y1)."""
+    S1, S2, N, T = _search_args(st, Tq)
+    R, C = st.S1.shape
+    t = np.zeros((C + 1, C + 1, R + 1, R + 1), np.uint64)
+    q = np.zeros_like(t)
+    s = lib().oracle_rect_all(st.width, st.height, _p64(S1), _p64(S2), _p64(N), _p32(T), _p64(t), _p64(q))
+    if s != OK:
+        raise ValueError(f"oracle_rect_all status {s}")
+    return t, q
 
 
 def decide(plane: np.ndarray, times: np.ndarray, bit_depth: int, n: int, lam: float,

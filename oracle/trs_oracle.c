@@ -29,7 +29,8 @@
  *                       every tile grid, its tiles grouped into rectangles
  *   oracle_mt_count     the number of distinct slice sets of that space
  *   oracle_evaluate,    T, Q and the area extremes of a given partition or
- *   oracle_rect         rectangle by direct sums (checkers for the tests)
+ *   oracle_rect,        rectangle, or of every CTU rectangle, by direct sums
+ *   oracle_rect_all     (checkers for the tests)
  *
  * Every function is pinned by the tests against what the paper and the
  * mathematics fix, not against itself: brute force over all line subsets or
@@ -1278,6 +1279,29 @@ int oracle_rect(int W, int H, const uint64_t *S1, const uint64_t *S2, const uint
     rsum_t s = rect_direct(&f, x0, x1, y0, y1);
     *t_out = s.T;
     *q_out = sse_floor(s.S1, s.S2, s.N);
+    return OR_OK;
+}
+
+/* Time and floor SSE of every CTU rectangle, each by direct sums like
+   oracle_rect: entry ((x0*(C+1) + x1)*(R+1) + y0)*(R+1) + y1 for x0 < x1,
+   y0 < y1; the other entries are set to zero. */
+int oracle_rect_all(int W, int H, const uint64_t *S1, const uint64_t *S2, const uint64_t *N, const uint32_t *Tq,
+                    uint64_t *t_out, uint64_t *q_out) {
+    if (W <= 0 || H <= 0) return OR_EINVAL;
+    frame_t f = {W, H, (W + OR_CTU - 1) / OR_CTU, (H + OR_CTU - 1) / OR_CTU, S1, S2, N, Tq};
+    if (f.C > OR_MAX_C || f.R > OR_MAX_R) return OR_EINVAL;
+    size_t cells = (size_t)(f.C + 1) * (f.C + 1) * (f.R + 1) * (f.R + 1);
+    memset(t_out, 0, cells * sizeof(uint64_t));
+    memset(q_out, 0, cells * sizeof(uint64_t));
+    for (int x0 = 0; x0 < f.C; ++x0)
+        for (int x1 = x0 + 1; x1 <= f.C; ++x1)
+            for (int y0 = 0; y0 < f.R; ++y0)
+                for (int y1 = y0 + 1; y1 <= f.R; ++y1) {
+                    size_t i = (((size_t)x0 * (f.C + 1) + x1) * (f.R + 1) + y0) * (f.R + 1) + y1;
+                    rsum_t r = rect_direct(&f, x0, x1, y0, y1);
+                    t_out[i] = r.T;
+                    q_out[i] = sse_floor(r.S1, r.S2, r.N);
+                }
     return OR_OK;
 }
 

@@ -1,13 +1,14 @@
 // trs_search_noalloc: trs_search for callers that must not allocate memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while other work is
-// being captured into a CUDA graph, real-time loops where the implicit
+// Some callers cannot call cudaMalloc: real-time loops where the implicit
 // device synchronisation of cudaMalloc/cudaFree would stall the pipeline,
-// and hosts that hand all device memory to their own pool allocator and
-// forbid stray allocations.  This entry point needs no context: its search
-// plan and scratch live in one file-scope device array of fixed size, and it
-// makes no cudaMalloc / cudaFree call and no call of an allocating library
-// routine (host-side it uses static storage only).
+// hosts that hand all device memory to their own pool allocator and forbid
+// stray allocations, and code that runs while another thread of the process
+// captures a CUDA graph in global mode, where cudaMalloc is not permitted.
+// This entry point needs no context: its search plan and scratch live in
+// one file-scope device array of fixed size, and it makes no cudaMalloc /
+// cudaFree call and no call of an allocating library routine (host-side it
+// uses static storage only).
 //
 // Limits and sharing:
 //  * kNoAllocBytes (8 MiB) holds the plan and scratch of one frame; a frame
@@ -22,9 +23,16 @@
 //    race on the array: serialise them.
 //  * The first call on a device looks up the array's device address with
 //    cudaGetSymbolAddress (with that device current); make that first call
-//    before any stream capture.  A call whose shape differs from the previous
-//    one on that device copies the new plan from static host storage with
-//    cudaMemcpyAsync, which waits for the stream to drain first.
+//    before any stream capture.
+//  * A call whose shape (W, H, n, k) differs from the one the array holds
+//    writes the new plan over the old one: a cudaMemcpyAsync on the call's
+//    stream from static, pageable host storage.  The copy is ordered after
+//    earlier work on that stream only, not on other streams, so the kernels
+//    of every earlier call with another shape must have finished first.
+//    The first call and every call that changes the shape make this copy,
+//    so make them outside any stream capture in the process.  Until the
+//    copy is enqueued the device keeps no shape: a failed copy leaves the
+//    next call to copy its plan again.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -66,8 +74,12 @@ int extents(int cells, int total, uint32_t *out) {
 }
 
 // Lays the plan of (W, H, n, k) out in g_host_plan, addressed for a copy at
-// dev_base, with the same windows, items and slot map as the context path.
-// Returns TRS_ENOMEM if plan + scratch exceed kNoAllocBytes.
+// dev_base.  It is the unpruned form of the context path's plan: the same
+// area windows, but every tile column a window admits (no slice-count,
+// tiling or reachability pruning), slice counts 1..min(n, R, H / hlo) for
+// every item and no per-item staging bound.  The search then relaxes
+// options no partition uses, at a cost in time, and returns the same
+// result.  Returns TRS_ENOMEM if plan + scratch exceed kNoAllocBytes.
 int layout_plan(int W, int H, int n, int k, unsigned char *dev_base, DeviceSlot *s) {
     const int C = (W + kCtu - 1) / kCtu, R = (H + kCtu - 1) / kCtu;
     static uint32_t ws[kMaxC * (kMaxC + 1) / 2], hs[kMaxR * (kMaxR + 1) / 2];
@@ -199,6 +211,9 @@ extern "C" int trs_search_noalloc(const void *tables, int W, int H, int n, int k
         DeviceSlot t = s;
         const int rc = layout_plan(W, H, n, k_area, s.base, &t);
         if (rc != TRS_OK) return rc;
+        // the old plan is overwritten from here on: the slot holds no shape
+        // until the new plan's copy is enqueued
+        s.W = s.H = s.n = s.k = -1;
         if (cudaMemcpyAsync(s.base, g_host_plan, t.plan_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
             return TRS_ECUDA;
         t.W = W;

@@ -77,6 +77,20 @@ def test_texture_flags_out_of_range_sample(dec, oracle):
     assert oracle.texture(plane, 10).status == oracle.ERANGE
 
 
+def _check_every_band(oracle, got, ref, Tq):
+    """Every slice of every tile column in the GPU's rectangle table (time and
+    floor SSE) against the oracle's direct sums of the same rectangle."""
+    R, C = Tq.shape
+    t_all, q_all = oracle.rect_all(ref, Tq)
+    for x0 in range(C):
+        for x1 in range(x0 + 1, C + 1):
+            b = x0 * (2 * C - x0 + 1) // 2 + (x1 - x0 - 1)
+            for d in range(1, R + 1):
+                y = np.arange(R - d + 1)
+                assert (got["rect_t"][b, d - 1, : R - d + 1] == t_all[x0, x1, y, y + d]).all(), (x0, x1, d)
+                assert (got["rect_q"][b, d - 1, : R - d + 1] == q_all[x0, x1, y, y + d]).all(), (x0, x1, d)
+
+
 @pytest.mark.parametrize("W,H,seed", [(832, 480, 1), (1920, 1080, 2), (3840, 2160, 3), (200, 520, 4)])
 def test_tables_bit_exact(dec, oracle, W, H, seed):
     plane, times = synth.small_frame(W, H, 10, seed)
@@ -93,25 +107,15 @@ def test_tables_bit_exact(dec, oracle, W, H, seed):
     assert (got["sat_s1"] == oracle.sat(ref.S1)).all()
     assert (got["sat_s2"] == oracle.sat(ref.S2)).all()
     assert (got["sat_t"] == oracle.sat(Tq.astype(np.uint64))).all()
-    R, C = Tq.shape
-    rng = np.random.default_rng(seed)
-    bands = [(x0, x1) for x0 in range(C) for x1 in range(x0 + 1, C + 1)]
-    sample = bands if len(bands) <= 120 else [bands[i] for i in rng.choice(len(bands), 120, replace=False)]
-    for (x0, x1) in sample:
-        b = x0 * (2 * C - x0 + 1) // 2 + (x1 - x0 - 1)
-        for y in range(R):
-            for d in range(1, R - y + 1):
-                t, q = oracle.rect(ref, Tq, x0, x1, y, y + d)
-                assert int(got["rect_t"][b, d - 1, y]) == t
-                assert int(got["rect_q"][b, d - 1, y]) == q
+    _check_every_band(oracle, got, ref, Tq)
 
 
 @pytest.mark.parametrize("W,H,pattern", [(8192, 4096, "max"), (8191, 4095, "checker"), (4000, 2200, "coin"),
                                           (129, 131, "checker"), (1, 1, "max")])
 def test_tables_extreme_sums_bit_exact(dec, oracle, W, H, pattern):
     """12-bit planes at the sum extremes: S1 up to 4095 * 2^25 and the
-    largest slice SSE, on clipped edges too; every sampled Q is the exact
-    S2 - ceil(S1^2 / N)."""
+    largest slice SSE, on clipped edges too; every Q of every tile column is
+    the exact S2 - ceil(S1^2 / N)."""
     rng = np.random.default_rng(W + H)
     if pattern == "max":
         plane = np.full((H, W), 4095, np.uint16)
@@ -128,16 +132,7 @@ def test_tables_extreme_sums_bit_exact(dec, oracle, W, H, pattern):
     got = dec.read_tables(tab, W, H)
     ref = oracle.texture(plane, 12)
     Tq, _ = oracle.time_q(times)
-    bands = [(x0, x1) for x0 in range(C) for x1 in range(x0 + 1, C + 1)]
-    sample = bands if len(bands) <= 24 else [bands[i] for i in rng.choice(len(bands), 24, replace=False)]
-    sample += [(0, C), (C - 1, C)]
-    for (x0, x1) in sample:
-        b = x0 * (2 * C - x0 + 1) // 2 + (x1 - x0 - 1)
-        for y in range(R):
-            for d in range(1, R - y + 1):
-                t, q = oracle.rect(ref, Tq, x0, x1, y, y + d)
-                assert int(got["rect_t"][b, d - 1, y]) == t
-                assert int(got["rect_q"][b, d - 1, y]) == q
+    _check_every_band(oracle, got, ref, Tq)
 
 
 @pytest.mark.parametrize("bad", [np.nan, -0.5, 65536.0, np.inf])

@@ -1,6 +1,7 @@
 """Continuous-batching server: every decision taken in the mix of concurrent
-streams equals the same frame decided alone (bit for bit), admission is
-bounded by memory, waits are bounded, and time-map updates take effect."""
+streams equals the same frame decided alone (bit for bit) and the oracle's
+decision for that frame and its co-located time map (Sec. 2.1), admission
+is bounded by memory, waits are bounded, and time-map updates take effect."""
 
 import time
 
@@ -8,6 +9,7 @@ import numpy as np
 import pytest
 
 import synth
+from gpu_helpers import assert_partition_equal
 
 pytestmark = pytest.mark.gpu
 
@@ -32,7 +34,7 @@ def _alone(dec, plane, times, bd, n, lam):
     return dec.partitions(out)[0]
 
 
-def test_mix_equals_alone(lib):
+def test_mix_equals_alone(lib, oracle):
     trs, runtime = lib
     srv = trs.trs_server_create(3840, 2160, max_regions=16, max_streams=8, max_batch=8, max_inflight=2)
     dec = runtime.Decider(max_width=3840, max_height=2160, max_regions=16)
@@ -75,6 +77,8 @@ def test_mix_equals_alone(lib):
                 assert d.status == 0 and d.latency_us > 0
                 ref = _alone(dec, frames[(sid, f)], times, spec.bit_depth, n, 0.1)
                 assert bytes(d.partition) == bytes(ref)
+                want, _, _ = oracle.decide(frames[(sid, f)], times, spec.bit_depth, n, 0.1)
+                assert_partition_equal(d.partition, want, spec.ctu_rows)
     finally:
         trs.trs_server_destroy(srv)
         dec.close()
@@ -123,7 +127,7 @@ def test_bounded_waits_and_argument_errors(lib):
         trs.trs_server_destroy(srv)
 
 
-def test_time_map_update_takes_effect(lib):
+def test_time_map_update_takes_effect(lib, oracle):
     trs, runtime = lib
     srv = trs.trs_server_create(1920, 1080, max_regions=8, max_streams=1, max_batch=2, max_inflight=2)
     dec = runtime.Decider(max_width=1920, max_height=1080, max_regions=8)
@@ -141,12 +145,14 @@ def test_time_map_update_takes_effect(lib):
                 ds = trs.trs_server_poll(srv, 4, 10_000)
             assert len(ds) == 1 and ds[0].status == 0
             assert bytes(ds[0].partition) == bytes(_alone(dec, plane, np.ascontiguousarray(times), 10, 8, 0.0))
+            want, _, _ = oracle.decide(plane, np.ascontiguousarray(times), 10, 8, 0.0)
+            assert_partition_equal(ds[0].partition, want, 9)
     finally:
         trs.trs_server_destroy(srv)
         dec.close()
 
 
-def test_temporal_layer_maps_follow_the_co_tl_frame(lib):
+def test_temporal_layer_maps_follow_the_co_tl_frame(lib, oracle):
     """One random-access GOP of 16 in coding order: each frame is decided
     with the CTU times of the previous frame of its temporal layer (the co-TL
     frame of Sec. 2.1), or the most recent map before its layer has one."""
@@ -171,6 +177,9 @@ def test_temporal_layer_maps_follow_the_co_tl_frame(lib):
                 ds = trs.trs_server_poll(srv, 4, 10_000)
             assert len(ds) == 1 and ds[0].status == 0 and ds[0].tag == poc
             assert bytes(ds[0].partition) == bytes(_alone(dec, plane, np.ascontiguousarray(expect), 10, 8, 0.1))
+            # the oracle, given the co-TL frame's CTU times, takes the same decision
+            want, _, _ = oracle.decide(plane, np.ascontiguousarray(expect), 10, 8, 0.1)
+            assert_partition_equal(ds[0].partition, want, 9)
             # the frame is encoded: its CTU times become its layer's co-TL map
             trs.trs_server_update_times_layer(srv, sid, L, np.ascontiguousarray(encoded_times))
             layer_map[L] = encoded_times

@@ -45,3 +45,34 @@ def test_sat_matches_cumsum_and_rect_sums(oracle, R, C):
                 for x1 in range(x0 + 1, C + 1):
                     rect = int(s[y1, x1]) - int(s[y0, x1]) - int(s[y1, x0]) + int(s[y0, x0])
                     assert rect == int(v[y0:y1, x0:x1].sum())
+
+
+@pytest.mark.parametrize("W,H", [(300, 520), (128, 128), (1, 700)])
+def test_rect_all_matches_written_out_sums(oracle, W, H):
+    """Every CTU rectangle's time (Eq. 1) and floor SSE (Eq. 2), against sums
+    and an integer ceiling written out here; the unused entries are zero."""
+    rng = np.random.default_rng(W + 7 * H)
+    C, R = -(-W // 128), -(-H // 128)
+    cw = [min(128 * (x + 1), W) - 128 * x for x in range(C)]
+    ch = [min(128 * (y + 1), H) - 128 * y for y in range(R)]
+    N = np.array([[w * h for w in cw] for h in ch], np.uint64)
+    mu = rng.integers(0, 1024, size=(R, C)).astype(np.uint64)
+    S1 = mu * N + rng.integers(0, 100, size=(R, C)).astype(np.uint64)
+    S2 = mu * mu * N + rng.integers(10 ** 5, 10 ** 7, size=(R, C)).astype(np.uint64)
+    Tq = rng.integers(0, 5 * 65536, size=(R, C)).astype(np.uint32)
+    st = oracle.Stats(W, H, S1, S2, N, np.zeros((R, C), np.uint32), 0)
+    t, q = oracle.rect_all(st, Tq)
+    for x0 in range(C + 1):
+        for x1 in range(C + 1):
+            for y0 in range(R + 1):
+                for y1 in range(R + 1):
+                    if x0 >= x1 or y0 >= y1:
+                        assert t[x0, x1, y0, y1] == 0 and q[x0, x1, y0, y1] == 0
+                        continue
+                    s1 = sum(int(S1[y, x]) for y in range(y0, y1) for x in range(x0, x1))
+                    s2 = sum(int(S2[y, x]) for y in range(y0, y1) for x in range(x0, x1))
+                    nn = sum(int(N[y, x]) for y in range(y0, y1) for x in range(x0, x1))
+                    tt = sum(int(Tq[y, x]) for y in range(y0, y1) for x in range(x0, x1))
+                    assert int(t[x0, x1, y0, y1]) == tt
+                    assert int(q[x0, x1, y0, y1]) == s2 - (-(-s1 * s1 // nn))
+                    assert (int(t[x0, x1, y0, y1]), int(q[x0, x1, y0, y1])) == oracle.rect(st, Tq, x0, x1, y0, y1)

@@ -1,15 +1,19 @@
 """trs_search_noalloc, the search entry point for callers that cannot
-allocate device memory (graph-capture regions, real-time loops, hosts with
-their own pool allocator), must return exactly what trs_search returns.
-Two calls in a row on different frames check that the shared scratch array
-carries nothing over; a third call with another shape checks the plan swap.
-Collected last, so a stop at the first failure has run every other test."""
+allocate device memory (real-time loops that cannot absorb cudaMalloc's
+device synchronisation, hosts whose own pool allocator owns all device
+memory, code running while another thread captures a CUDA graph in global
+mode), must return exactly what trs_search returns, and the oracle's
+decision.  Calls in a row on one shape check that the shared scratch array
+carries nothing over; later calls swap shapes, go back to an earlier one,
+and cover 832x480, a flat frame whose ties only the canonical code decides,
+n = 32 (TRS_MAX_REGIONS) and an area-rule factor k = 2.  Collected last, so
+a stop at the first failure has run every other test."""
 
 import numpy as np
 import pytest
 
 import synth
-from gpu_helpers import SSE_ABS, SSE_REL
+from gpu_helpers import SSE_ABS, SSE_REL, assert_partition_equal
 
 pytestmark = pytest.mark.gpu
 
@@ -23,7 +27,7 @@ def _tables(dec, plane, times, bd):
     st = dec.stats_buffers(W, H)
     dec.texture_map(luma, W, H, raw.strides[0], bd, st)
     tab = dec.tables_buffer(W, H)
-    dec.region_tables(st, torch.from_numpy(times).cuda(), W, H, tab)
+    dec.region_tables(st, torch.from_numpy(np.ascontiguousarray(times)).cuda(), W, H, tab)
     return tab, (luma, st)
 
 
@@ -37,26 +41,54 @@ def _same(a, b):
     assert a.t == b.t and a.t_min == b.t_min
 
 
-def test_noalloc_matches_trs_search():
+def _frame(kind, seed):
+    if kind == "flat1080":
+        # one sample value everywhere and equal CTU times: Q = 0 and T ties
+        return np.full((1080, 1920), 300, np.uint16), np.ones((9, 15), np.float32), 10
+    spec = {"480": synth.SPEC_480P8, "1080": synth.SPEC_1080P10, "2160": synth.SPEC_2160P10}[kind]
+    plane, times = synth.make_frame(spec, seed)
+    return plane, times, spec.bit_depth
+
+
+# (frame kind, seed, n, k, lambda), in call order
+CALLS = [
+    ("2160", 0, 16, 3, 0.1), ("2160", 1, 16, 3, 0.1),  # two calls in a row on one shape
+    ("1080", 2, 8, 3, 0.1),                             # a swap
+    ("2160", 3, 16, 3, 0.1),                            # back to the earlier shape
+    ("480", 0, 4, 3, 0.3),
+    ("flat1080", 0, 8, 3, 0.0),
+    ("1080", 4, 32, 3, 0.1),                            # n = TRS_MAX_REGIONS
+    ("480", 1, 6, 2, 0.1), ("1080", 5, 8, 2, 0.0),      # k = 2
+    ("1080", 6, 8, 3, 0.1),                             # k back to 3 on a shape seen with k = 2
+    ("2160", 7, 16, 3, 0.0),
+]
+
+
+def test_noalloc_matches_trs_search_and_oracle(oracle):
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     import __graft_entry__
     __graft_entry__.build()
     from paper_2012_14792_gb300 import runtime, trs
-    dec = runtime.Decider(max_width=3840, max_height=2160, max_regions=16)
-    cases = [(synth.SPEC_2160P10, 0, 16), (synth.SPEC_2160P10, 1, 16), (synth.SPEC_1080P10, 2, 8)]
-    for spec, seed, n in cases:
-        plane, times = synth.make_frame(spec, seed)
-        tab, keep = _tables(dec, plane, times, spec.bit_depth)
-        W, H = spec.width, spec.height
-        ref = dec.search(tab, W, H, n, 0.1)
-        got = torch.full((trs.PARTITION_BYTES,), 0xAB, dtype=torch.uint8, device="cuda")
-        trs.trs_search_noalloc(tab, W, H, n, 3, 0.1, got)
-        torch.cuda.synchronize()
-        a, b = dec.partitions(got)[0], dec.partitions(ref)[0]
-        assert b.status == 0
-        _same(a, b)
-    dec.close()
+    decs = {k: runtime.Decider(max_width=3840, max_height=2160, max_regions=32, k_area=k) for k in (2, 3)}
+    try:
+        for kind, seed, n, k, lam in CALLS:
+            plane, times, bd = _frame(kind, seed)
+            H, W = plane.shape
+            dec = decs[k]
+            tab, keep = _tables(dec, plane, times, bd)
+            ref = dec.search(tab, W, H, n, lam)
+            got = torch.full((trs.PARTITION_BYTES,), 0xAB, dtype=torch.uint8, device="cuda")
+            trs.trs_search_noalloc(tab, W, H, n, k, lam, got)
+            torch.cuda.synchronize()
+            a, b = dec.partitions(got)[0], dec.partitions(ref)[0]
+            assert b.status == 0, (kind, n, k)
+            _same(a, b)
+            want, _, _ = oracle.decide(plane, times, bd, n, lam, k_area=k)
+            assert_partition_equal(a, want, -(-H // 128))
+    finally:
+        for d in decs.values():
+            d.close()
 
 
 def test_noalloc_rejects_oversize_shape():
