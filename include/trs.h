@@ -177,9 +177,10 @@ int trs_plan_stats(int width, int height, int n_regions, int k_area, int *n_wind
  * counts x the unit's slice heights x R start rows (a transition G_k[y] <-
  * G_{k-1}[y+d] combined with the slice value, inadmissible ones included,
  * as the DP evaluates them); col_relax = for every window and tile column
- * with slices there, kmax x n transitions H[x][m] <- V[k], H[x1][m-k].
- * Each transition is one combine (max for Eq. 1, + for Eq. 2) and one
- * minimum.  Pure host arithmetic. */
+ * with slices there, the transitions H[x][m] <- V[k], H[x1][m-k] with k in
+ * the unit's slice-count range [kmin, kmax] and k <= m <= n.  Each
+ * transition is one combine (max for Eq. 1, + for Eq. 2) and one minimum.
+ * Pure host arithmetic. */
 int trs_plan_work(int width, int height, int n_regions, int k_area, double *row_relax, double *col_relax);
 
 /* Host only: the number of distinct partitions the search chooses among,

@@ -155,7 +155,9 @@ int trs_plan_work(int width, int height, int n, int k, double *row_relax, double
     for (size_t w = 0; w < p.win_a.size(); ++w)
         for (int b = 0; b < p.nb; ++b) {
             const int32_t slot = p.slot_of[w * p.nb + b];
-            if (slot >= 0) cols += (double)p.items[slot].kmax * p.n;
+            if (slot < 0) continue;
+            const int klo = std::max(1, (int)p.items[slot].kmin), khi = std::min((int)p.items[slot].kmax, p.n);
+            for (int k = klo; k <= khi; ++k) cols += (double)(p.n - k + 1);  // m = k..n
         }
     *row_relax = rows;
     *col_relax = cols;
@@ -361,8 +363,9 @@ static int search_one(trs_ctx *ctx, const void *tables, int W, int H, int n, flo
     a.single_items = nitems;
     a.single_windows = nwin;
     a.single_bands = pe->host.nb;
-    TRS_CK((cudaError_t)launch_search(a, pe->host.nb, nwin, f.C, f.R, n, f.scal, 4, stream, nullptr, &ctx->tune, 3,
-                                      pe->host.max_nd));
+    const ColGeom cg = col_uniform(a, pe->host, 1, ctx->tune);
+    TRS_CK((cudaError_t)launch_search(a, pe->host.nb, nwin, f.C, f.R, n, f.scal, 4, stream, cg, nullptr, &ctx->tune,
+                                      3, pe->host.max_nd));
     return TRS_OK;
 }
 
@@ -415,7 +418,7 @@ int trs_search_lambdas(trs_ctx *ctx, const void *tables, int W, int H, int n, co
     }
     std::vector<PlanEntry *> pes(nl, pe);
     BatchLaunch bl;
-    batch_describe(bl, hb, (uint8_t *)ctx->desc.p, nl, pes.data(), nullptr, scal);
+    batch_describe(bl, hb, (uint8_t *)ctx->desc.p, nl, pes.data(), nullptr, scal, ctx->tune);
     TRS_CK(cudaMemcpyAsync(bl.db, hb, bl.blob, cudaMemcpyHostToDevice, s));
     TRS_CK(cudaEventRecord(ctx->copied, s));
     TRS_CK(cudaMemsetAsync(scal, 0xff, (size_t)nl * 4 * sizeof(uint64_t), s));
@@ -425,8 +428,9 @@ int trs_search_lambdas(trs_ctx *ctx, const void *tables, int W, int H, int n, co
     one.single_items = (int)pe->host.items.size();
     one.single_windows = (int)pe->host.win_a.size();
     one.single_bands = pe->host.nb;
+    const ColGeom cg1 = col_uniform(one, pe->host, 1, ctx->tune);
     TRS_CK((cudaError_t)launch_search(one, pe->host.nb, one.single_windows, pe->host.C, pe->host.R, n, scal, 4, s,
-                                      nullptr, &ctx->tune, 1, pe->host.max_nd));
+                                      cg1, nullptr, &ctx->tune, 1, pe->host.max_nd));
     for (int i = 1; i < nl; ++i)  // T_min of step 1 for every lambda
         TRS_CK(cudaMemcpyAsync(scal + 4 * i, scal, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
     LaunchArgs all{};
@@ -435,8 +439,9 @@ int trs_search_lambdas(trs_ctx *ctx, const void *tables, int W, int H, int n, co
     all.pre.items = (const int32_t *)(bl.db + bl.fr_bytes + 2 * bl.pre_bytes);
     all.pre.windows = (const int32_t *)(bl.db + bl.fr_bytes + 3 * bl.pre_bytes);
     all.pre.bands = (const int32_t *)(bl.db + bl.fr_bytes + 4 * bl.pre_bytes);
+    const ColGeom cg2 = col_uniform(all, pe->host, nl, ctx->tune);
     TRS_CK((cudaError_t)launch_search(all, bl.bands, bl.windows, pe->host.C, pe->host.R, n, scal, (size_t)nl * 4, s,
-                                      nullptr, &ctx->tune, 2, pe->host.max_nd));
+                                      cg2, nullptr, &ctx->tune, 2, pe->host.max_nd));
     return TRS_OK;
     TRS_GUARD_END
 }
@@ -540,12 +545,30 @@ int batch_run(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partition *out
         TRS_CK(cudaMallocHost(&ctx->staging, blob * 2));
         ctx->staging_n = blob * 2;
     }
+    // Graph batches run as P chunks of at least kChunkMin frames each (see
+    // below).  Inside each chunk the frames are ordered by shape so that
+    // frames sharing a plan are adjacent (the column DP packs them into one
+    // warp); every frame keeps its own output slot.
+    const int parts = use_graph ? std::max(1, std::min(ctx->parts, nf / kChunkMin)) : 1;
+    int first[kMaxParts + 1];
+    first[0] = 0;
+    for (int c = 0; c < parts; ++c) first[c + 1] = (int)((int64_t)nf * (c + 1) / parts);
+    std::vector<int> order(nf);
+    for (int i = 0; i < nf; ++i) order[i] = i;
+    for (int c = 0; c < parts; ++c)
+        std::stable_sort(order.begin() + first[c], order.begin() + first[c + 1], [&](int x, int y) {
+            return std::make_tuple(fd[x].width, fd[x].height, fd[x].n_regions) <
+                   std::make_tuple(fd[y].width, fd[y].height, fd[y].n_regions);
+        });
+    std::vector<PlanEntry *> pes(nf);
+    for (int j = 0; j < nf; ++j) pes[j] = pe[order[j]];
     // the previous replay must have read the staging blob before it is rewritten
     TRS_CK(cudaEventSynchronize(ctx->copied));
     uint8_t *hb = (uint8_t *)ctx->staging;
     DevFrame *hf = (DevFrame *)hb;
     uint8_t *ab = (uint8_t *)ctx->arena.p;
-    for (int i = 0; i < nf; ++i) {
+    for (int j = 0; j < nf; ++j) {
+        const int i = order[j];
         const trs_frame_desc &d = fd[i];
         const HostPlan &hp = pe[i]->host;
         DevFrame f{};
@@ -563,19 +586,19 @@ int batch_run(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partition *out
         f.vmax = (uint32_t *)(p + 2 * align256((size_t)cells * 4));
         f.s2 = (uint64_t *)(p + 3 * align256((size_t)cells * 4));
         p += stats_bytes(C, R);
-        f.flags = (uint32_t *)(ab + flags_off) + i;
+        f.flags = (uint32_t *)(ab + flags_off) + j;
         f.tables = p;
         p += tables_offsets(C, R).bytes;
         set_search_scratch(f, *pe[i], p, d.n_regions, d.lambda);
-        f.scal = (uint64_t *)(ab + scal_off) + 4 * i;
+        f.scal = (uint64_t *)(ab + scal_off) + 4 * j;
         f.out = out + i;
-        hf[i] = f;
+        hf[j] = f;
     }
     uint32_t *flags = (uint32_t *)(ab + flags_off);
     uint64_t *scal = (uint64_t *)(ab + scal_off);
     if (!use_graph) {
         BatchLaunch bl;
-        batch_describe(bl, hb, (uint8_t *)ctx->desc.p, nf, pe.data(), flags, scal);
+        batch_describe(bl, hb, (uint8_t *)ctx->desc.p, nf, pes.data(), flags, scal, ctx->tune);
         bl.tune = ctx->tune;
         cudaError_t e = batch_enqueue(bl, stream, ctx->copied, ctx->stage);
         if (e != cudaSuccess) return cuda_fail(e, "batch launch");
@@ -584,22 +607,15 @@ int batch_run(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partition *out
         ctx->last_kernels = kKernelsPerBatch;
         return TRS_OK;
     }
-    // Graph batches run as P chunks of at least kChunkMin frames each, software
-    // pipelined on two streams (chunk c on stream c % 2): chunk c's texture
-    // kernel (bound by HBM) starts once chunk c-1's has finished and runs
-    // beside chunk c-1's tables and search (bound by the ALUs).  Stage events
-    // time chunk 0.
-    const int parts = std::max(1, std::min(ctx->parts, nf / kChunkMin));
+    // Graph batches run as P chunks, software pipelined on two streams
+    // (chunk c on stream c % 2): chunk c's texture kernel (bound by HBM)
+    // starts once chunk c-1's has finished and runs beside chunk c-1's tables
+    // and search (bound by the ALUs).  Stage events time chunk 0.
     key.push_back(parts);
     BatchLaunch bl[kMaxParts];
-    int first[kMaxParts + 1];
     size_t off_c[kMaxParts + 1];
-    first[0] = 0;
     off_c[0] = 0;
-    for (int c = 0; c < parts; ++c) {
-        first[c + 1] = (int)((int64_t)nf * (c + 1) / parts);
-        off_c[c + 1] = off_c[c] + batch_blob_bytes(first[c + 1] - first[c]);
-    }
+    for (int c = 0; c < parts; ++c) off_c[c + 1] = off_c[c] + batch_blob_bytes(first[c + 1] - first[c]);
     // each chunk's descriptors at the start of its own blob; the last chunk
     // first, so that no move overwrites descriptors not yet moved
     for (int c = parts - 1; c > 0; --c)
@@ -607,7 +623,7 @@ int batch_run(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partition *out
                      (size_t)(first[c + 1] - first[c]) * sizeof(DevFrame));
     for (int c = 0; c < parts; ++c) {
         batch_describe(bl[c], hb + off_c[c], (uint8_t *)ctx->desc.p + off_c[c], first[c + 1] - first[c],
-                       pe.data() + first[c], flags + first[c], scal + 4 * first[c]);
+                       pes.data() + first[c], flags + first[c], scal + 4 * first[c], ctx->tune);
         bl[c].tune = ctx->tune;
     }
     BatchGraph &g = ctx->graphs[key];
@@ -646,7 +662,19 @@ int batch_run(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partition *out
 }
 
 size_t batch_blob_bytes(int nf) {
-    return align256((size_t)nf * sizeof(DevFrame)) + 5 * align256((size_t)(nf + 1) * 4);
+    return align256((size_t)nf * sizeof(DevFrame)) + 5 * align256((size_t)(nf + 1) * 4) +
+           align256((size_t)nf * sizeof(ColChunk));
+}
+
+ColGeom col_uniform(LaunchArgs &a, const HostPlan &hp, int nf, const SearchTune &t) {
+    const int fpw = nf == 1 ? 1 : col_fpw(hp.n, t);
+    a.cchunks = nullptr;
+    a.col_fpw = fpw;
+    a.col_nchunks = (nf + fpw - 1) / fpw;
+    ColGeom g;
+    g.units = (int)hp.win_a.size() * a.col_nchunks;
+    g.add(hp.C, hp.n, hp.max_edge_vals, fpw);
+    return g;
 }
 
 void set_search_scratch(DevFrame &f, const PlanEntry &pe, uint8_t *p, int n, float lambda) {
@@ -664,7 +692,7 @@ void set_search_scratch(DevFrame &f, const PlanEntry &pe, uint8_t *p, int n, flo
 }
 
 void batch_describe(BatchLaunch &bl, uint8_t *hb, uint8_t *db, int nf, PlanEntry *const *pe, uint32_t *flags_dev,
-                    uint64_t *scal_dev) {
+                    uint64_t *scal_dev, const SearchTune &tune) {
     bl.hb = hb;
     bl.db = db;
     bl.nf = nf;
@@ -705,6 +733,36 @@ void batch_describe(BatchLaunch &bl, uint8_t *hb, uint8_t *db, int nf, PlanEntry
         bl.u_windows = pw[1];
         bl.u_bands = pb[1];
     }
+    // column DP: runs of consecutive frames with one plan, cut into chunks
+    // of as many frames as one warp takes
+    bl.col = ColGeom{};
+    bl.col_chunks_dev = nullptr;
+    if (nf > 0 && bl.uniform) {
+        LaunchArgs a{};
+        a.nframes = nf;
+        bl.col = col_uniform(a, pe[0]->host, nf, tune);
+        bl.col_nchunks = a.col_nchunks;
+        bl.col_fpw = a.col_fpw;
+        return;
+    }
+    const size_t ch_off = bl.fr_bytes + 5 * bl.pre_bytes;
+    ColChunk *ch = (ColChunk *)(hb + ch_off);
+    int nch = 0, unit = 0;
+    for (int i = 0; i < nf;) {
+        const HostPlan &hp = pe[i]->host;
+        const int fpw = col_fpw(hp.n, tune);
+        int cnt = 1;
+        while (cnt < fpw && i + cnt < nf && pe[i + cnt] == pe[i]) ++cnt;
+        ch[nch] = ColChunk{i, cnt, fpw, unit};
+        unit += (int)hp.win_a.size();
+        bl.col.add(hp.C, hp.n, hp.max_edge_vals, fpw);
+        ++nch;
+        i += cnt;
+    }
+    bl.col.units = unit;
+    bl.col_nchunks = nch;
+    bl.col_fpw = 0;
+    bl.col_chunks_dev = (const ColChunk *)(db + ch_off);
 }
 
 cudaError_t batch_enqueue_work(const BatchLaunch &bl, cudaStream_t cs, cudaEvent_t *stage, cudaEvent_t after_texture) {
@@ -724,6 +782,9 @@ cudaError_t batch_enqueue_work(const BatchLaunch &bl, cudaStream_t cs, cudaEvent
         a.single_windows = bl.u_windows;
         a.single_bands = bl.u_bands;
     }
+    a.cchunks = bl.col_chunks_dev;
+    a.col_nchunks = bl.col_nchunks;
+    a.col_fpw = bl.col_fpw;
     const bool events = stage != nullptr;
     auto mark = [&](int i, cudaError_t e) {
         if (events && e == cudaSuccess) e = record_event(stage[i], cs);
@@ -738,7 +799,8 @@ cudaError_t batch_enqueue_work(const BatchLaunch &bl, cudaStream_t cs, cudaEvent
     e = mark(2, e);
     if (e == cudaSuccess)
         e = (cudaError_t)launch_search(a, bl.bands, bl.windows, bl.maxC, bl.maxR, bl.maxN, bl.scal_dev,
-                                       (size_t)bl.nf * 4, cs, events ? stage + 3 : nullptr, &bl.tune, 3, bl.maxND);
+                                       (size_t)bl.nf * 4, cs, bl.col, events ? stage + 3 : nullptr, &bl.tune, 3,
+                                       bl.maxND);
     return e;
 }
 

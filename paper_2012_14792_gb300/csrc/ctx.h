@@ -124,13 +124,21 @@ struct BatchLaunch {
     uint32_t *flags_dev = nullptr;  // nf words, zeroed by the launch
     uint64_t *scal_dev = nullptr;   // nf * 4 words, reset by the launch
     SearchTune tune;
+    // column DP: chunks of frames that share a plan (device table in the blob unless uniform)
+    ColGeom col;
+    int col_nchunks = 0, col_fpw = 1;
+    const ColChunk *col_chunks_dev = nullptr;
 };
 size_t batch_blob_bytes(int nf);
+// Column-DP units of nf frames that all use plan hp (a's col_* fields are set).
+ColGeom col_uniform(LaunchArgs &a, const HostPlan &hp, int nf, const SearchTune &t);
 // Points a frame's search fields at the plan and at the scratch starting at p.
 void set_search_scratch(DevFrame &f, const PlanEntry &pe, uint8_t *p, int n, float lambda);
-// Writes the work prefix sums after the DevFrame array already placed in hb.
+// Writes the work prefix sums and the column-DP chunks after the DevFrame
+// array already placed in hb (frames that share a plan are grouped into
+// chunks when they are consecutive there).
 void batch_describe(BatchLaunch &bl, uint8_t *hb, uint8_t *db, int nf, PlanEntry *const *pe, uint32_t *flags_dev,
-                    uint64_t *scal_dev);
+                    uint64_t *scal_dev, const SearchTune &tune);
 // Enqueues the descriptor copy (then records `copied`), the flag reset and
 // every kernel of the hot path on cs; stage events (9) when stage != nullptr.
 cudaError_t batch_enqueue(const BatchLaunch &bl, cudaStream_t cs, cudaEvent_t copied, cudaEvent_t *stage);

@@ -60,7 +60,7 @@ struct DeviceSlot {
     unsigned char *base = nullptr;  // device address of g_noalloc_scratch on this device
     int W = -1, H = -1, n = -1, k = -1;  // shape whose plan the array holds
     size_t plan_bytes = 0;
-    int nwin = 0, nitems = 0, nb = 0, C = 0, R = 0;
+    int nwin = 0, nitems = 0, nb = 0, C = 0, R = 0, max_edge_vals = 1;
 };
 DeviceSlot g_dev[kMaxDevices];
 
@@ -153,7 +153,27 @@ int layout_plan(int W, int H, int n, int k, unsigned char *dev_base, DeviceSlot 
         }
     }
     bitems[nb] = nitems;
-    const size_t plan_bytes = align256(off_items + (size_t)nitems * sizeof(PlanItem) + 16);
+    // the column DP's step entries of every (window, band), after the items
+    const size_t off_sk = align256(off_items + (size_t)nitems * sizeof(PlanItem) + 16);
+    if (off_sk + (size_t)nwin * nb * 8 + 8 > kNoAllocBytes) return TRS_ENOMEM;
+    uint64_t *sk = reinterpret_cast<uint64_t *>(g_host_plan + off_sk);
+    int max_edge_vals = 1;
+    for (int wi = 0; wi < nwin; ++wi)
+        for (int x = 0; x < C; ++x) {
+            int vals = 0;
+            for (int x1 = x + 1; x1 <= C; ++x1) {
+                const int b = band_index(C, x, x1);
+                const int sl = slot[(size_t)wi * nb + b];
+                uint64_t e = 0;
+                if (sl >= 0 && items[sl].kmax >= 1) {
+                    e = pack_slot_k(sl, 1, items[sl].kmax);
+                    vals += items[sl].kmax;
+                }
+                sk[(size_t)wi * nb + b] = e;
+            }
+            max_edge_vals = std::max(max_edge_vals, vals);
+        }
+    const size_t plan_bytes = align256(off_sk + (size_t)nwin * nb * 8 + 8);
     // scratch of the search after the plan
     const size_t v = (size_t)nitems * (n + 1) * 8;
     const size_t need = plan_bytes + 2 * align256(v + 8) + 2 * align256((size_t)nwin * 8 + 8) +
@@ -178,6 +198,8 @@ int layout_plan(int W, int H, int n, int k, unsigned char *dev_base, DeviceSlot 
     d.band_x0 = reinterpret_cast<const int16_t *>(dev_base + off_x0);
     d.band_x1 = reinterpret_cast<const int16_t *>(dev_base + off_x1);
     d.band_items = reinterpret_cast<const int32_t *>(dev_base + off_bi);
+    d.slot_k = reinterpret_cast<const uint64_t *>(dev_base + off_sk);
+    d.max_edge_vals = max_edge_vals;
     std::memcpy(g_host_plan, &d, sizeof(d));
     s->plan_bytes = plan_bytes;
     s->nwin = nwin;
@@ -185,6 +207,7 @@ int layout_plan(int W, int H, int n, int k, unsigned char *dev_base, DeviceSlot 
     s->nb = nb;
     s->C = C;
     s->R = R;
+    s->max_edge_vals = max_edge_vals;
     return TRS_OK;
 }
 
@@ -248,7 +271,12 @@ extern "C" int trs_search_noalloc(const void *tables, int W, int H, int n, int k
     a.single_items = s.nitems;
     a.single_windows = s.nwin;
     a.single_bands = s.nb;
+    a.col_nchunks = 1;
+    a.col_fpw = 1;
+    ColGeom cg;
+    cg.units = s.nwin;
+    cg.add(s.C, n, s.max_edge_vals, 1);
     // launch_search resets T_min and Q* to +infinity before its kernels
-    if (launch_search(a, s.nb, s.nwin, s.C, s.R, n, f.scal, 4, stream) != (int)cudaSuccess) return TRS_ECUDA;
+    if (launch_search(a, s.nb, s.nwin, s.C, s.R, n, f.scal, 4, stream, cg) != (int)cudaSuccess) return TRS_ECUDA;
     return TRS_OK;
 }

@@ -239,7 +239,29 @@ int build_plan(int W, int H, int n, int k, HostPlan *p, int window_step) {
     }
     p->band_items[p->nb] = (int32_t)p->items.size();
     prune_by_reachability(p);
+    column_program(p);
     return TRS_OK;
+}
+
+void column_program(HostPlan *p) {
+    const int C = p->C, nb = p->nb, nwin = (int)p->win_a.size();
+    p->slot_k.assign((size_t)nwin * nb, 0);
+    p->max_edge_vals = 1;
+    for (int w = 0; w < nwin; ++w)
+        for (int x = 0; x < C; ++x) {
+            int vals = 0;
+            for (int x1 = x + 1; x1 <= C; ++x1) {
+                const int b = band_index(C, x, x1);
+                const int sl = p->slot_of[(size_t)w * nb + b];
+                if (sl < 0) continue;
+                const PlanItem &it = p->items[sl];
+                const int klo = std::max(1, (int)it.kmin), khi = std::min((int)it.kmax, p->n);
+                if (khi < klo) continue;  // no slice count of this item completes a partition
+                p->slot_k[(size_t)w * nb + b] = pack_slot_k(sl, klo, khi);
+                vals += khi - klo + 1;
+            }
+            p->max_edge_vals = std::max(p->max_edge_vals, vals);
+        }
 }
 
 // Counting column DP: partitions of the C CTU columns into tile columns whose
@@ -356,6 +378,7 @@ size_t plan_blob_bytes(const HostPlan &p) {
     s += align256(p.slot_of.size() * sizeof(int32_t) + 4);
     s += 2 * align256(p.band_x0.size() * sizeof(int16_t) + 2);
     s += align256(p.band_items.size() * sizeof(int32_t) + 4);
+    s += align256(p.slot_k.size() * sizeof(uint64_t) + 8);
     return s;
 }
 
@@ -385,6 +408,8 @@ void plan_serialize(const HostPlan &p, uint8_t *dev_base, std::vector<uint8_t> &
     d.band_x0 = (const int16_t *)put(p.band_x0.data(), p.band_x0.size() * sizeof(int16_t), 2);
     d.band_x1 = (const int16_t *)put(p.band_x1.data(), p.band_x1.size() * sizeof(int16_t), 2);
     d.band_items = (const int32_t *)put(p.band_items.data(), p.band_items.size() * sizeof(int32_t), 4);
+    d.slot_k = (const uint64_t *)put(p.slot_k.data(), p.slot_k.size() * sizeof(uint64_t), 8);
+    d.max_edge_vals = p.max_edge_vals;
     std::copy((const uint8_t *)&d, (const uint8_t *)&d + sizeof(d), blob.begin());
 }
 

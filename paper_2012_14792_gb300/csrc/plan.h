@@ -17,7 +17,12 @@ struct HostPlan {
     std::vector<int16_t> band_x0, band_x1;
     std::vector<int32_t> band_items;  // [nb+1] prefix of items per band
     int max_nd = 0;  // most full-CTU slice heights an item admits (sizes the row DP's staging)
+    std::vector<uint64_t> slot_k;  // [nwin * nb]: the column DP's step entries (see DevPlan::slot_k)
+    int max_edge_vals = 0;         // see DevPlan::max_edge_vals
 };
+
+// Fills slot_k and max_edge_vals from slot_of and the items' slice-count ranges.
+void column_program(HostPlan *p);
 
 struct SearchScratch {
     size_t V1, V2, w1, w2, H2, codes, bytes;

@@ -23,9 +23,11 @@
 //                       G_{k-1}[y+d] from shared memory.  Step 1 combines
 //                       with max (Eq. 1), step 2 with + (Eq. 2) and drops
 //                       slices whose time exceeds the Eq. 4 bound.
-//  column_kernel<STEP>  one block per (frame, window): DP over tile-column
-//                       right edges with lanes over the slice count m, the
-//                       block's warps splitting the candidate edges.
+//  column_kernel<STEP>  one warp per (window, frames sharing the plan): DP
+//                       over tile-column right edges with lanes over
+//                       (slice count m, frame); the candidate steps and
+//                       their V values of the next left edge are staged in
+//                       shared memory while the current one relaxes.
 //                       Step 1's window minima reduce into T_min (Eq. 3),
 //                       step 2's into Q*.
 //  rebuild_kernel       one warp per (frame, window): in a window that
@@ -287,7 +289,8 @@ __device__ void item_pair(const DevFrame &fr, const DevPlan &pl, int mi, const P
         uint64_t *V = Vall + (size_t)mi * (n + 1);
         if (l == 0) V[0] = kInf;
         const int kmin = pl.items[mi].kmin;  // read here: nothing extra stays live through the k loop
-        if (l < n) V[l + 1] = l + 1 >= kmin ? vreg : kInf;  // counts below kmin complete no partition
+        // counts below kmin complete no partition; "none" is kSoft in step 2 (the column DP adds it)
+        if (l < n) V[l + 1] = l + 1 >= kmin && vreg != kInf ? vreg : (STEP == 1 ? kInf : kSoft);
     }
 }
 
@@ -379,7 +382,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, i
     uint64_t *Vall = STEP == 1 ? fr.V1 : fr.V2;
     if (frame_status(fr) != TRS_OK) {
         for (int ii = i0; ii < i1; ++ii)
-            for (int k = lane; k <= n; k += 32) Vall[(size_t)ii * (n + 1) + k] = kInf;
+            for (int k = lane; k <= n; k += 32) Vall[(size_t)ii * (n + 1) + k] = STEP == 1 ? kInf : kSoft;
         return;
     }
     const uint64_t thr = STEP == 2 ? eq4_threshold(fr.scal[0], fr.lambda_q) : kInf;
@@ -430,7 +433,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, i
             bool need = false;
             for (int w = it.w_first + lane; w <= it.w_last; w += 32) need |= fr.wres1[w] <= thr;
             if (!__any_sync(kFull, need)) {
-                for (int k = lane; k <= n; k += 32) V[k] = kInf;
+                for (int k = lane; k <= n; k += 32) V[k] = kSoft;
                 continue;
             }
         }
@@ -458,154 +461,245 @@ __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, i
             }
             vreg = item_rows<STEP, uint64_t>(itm, gbuf, nd, dmin, it.kmax, R);
         }
+        // counts below kmin complete no partition; "none" is kSoft in step 2 (the column DP adds it)
+        const uint64_t none = STEP == 1 ? kInf : kSoft;
         if (lane == 0) {
             V[0] = kInf;
-            if (n == 32) V[32] = 32 >= it.kmin ? vreg : kInf;
+            if (n == 32) V[32] = 32 >= it.kmin && vreg != kInf ? vreg : none;
         } else if (lane <= n) {
-            V[lane] = lane >= it.kmin ? vreg : kInf;  // counts below kmin complete no partition
+            V[lane] = lane >= it.kmin && vreg != kInf ? vreg : none;
         }
     }
 }
 
-__device__ __forceinline__ void smem_min(uint32_t *p, uint32_t v) { atomicMin(p, v); }
-__device__ __forceinline__ void smem_min(uint64_t *p, uint64_t v) {
-    atomicMin(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
+// ---- column DP ---------------------------------------------------------
+//
+// For one window w, the suffix DP over tile-column edges
+//   H[x][m] = min over x1 > x and k of  V[item(w, [x, x1))][k] (max | +) H[x1][m - k],
+//   H[C][0] = 0,
+// where k runs over the item's slice counts [klo, khi].  One warp runs one
+// window for F frames that share the plan (the plan fixes which bands and
+// slice counts each step relaxes, so the warp's control flow is the same
+// for all of them): lane (m - 1) * F + f holds H[x][m] of frame f.  The H
+// tables sit in the warp's shared memory, frames interleaved, so a step is
+// two shared loads (V broadcast to the frame's lanes, H[x1][m - k]
+// consecutive over the lanes), a max (Eq. 1) or add (Eq. 2) and a min.
+// The candidate steps of left edge x - 1 and their V values are staged while
+// edge x relaxes: the step list through the plan's per-window entries
+// (loaded one edge further ahead) and the V values by asynchronous
+// global-to-shared copies, double-buffered, so no global load latency sits
+// on the chain of edges.  No block barrier: the warps of a block are
+// independent.
+
+constexpr int kEdgeSteps = 64;  // candidate right edges of one left edge (C <= 64)
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// every committed group but the most recent one is complete
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// One warp's shared memory for the column DP.
+struct ColSmem {
+    const uint64_t **vptr;  // [8]: V array of each frame of the warp
+    uint32_t *sb;           // [2][kEdgeSteps]: step lists of two left edges
+    uint64_t *vb;           // [2][v_words]: their V values, frames interleaved
+    void *hs;               // H tables, frames interleaved
+    int v_words;
+};
+
+// Stages left edge x into buffer bsel: the steps (right edge x1, slice
+// counts [klo, khi], offset of their V values) of every band [x, x1) that
+// has an item in the window, and V[item][klo..khi] of each of the F frames
+// by asynchronous copies.  e0: the entries of the first 32 candidate right
+// edges (lane j: x1 = x + 1 + j), loaded ahead.  Returns the step count.
+__device__ int col_stage(const uint64_t *sk, int C, int x, uint64_t e0, int stride, int F, int lf,
+                         const ColSmem &sm, int bsel) {
+    const int lane = threadIdx.x & 31;
+    uint32_t *sb = sm.sb + bsel * kEdgeSteps;
+    uint64_t *vb = sm.vb + (size_t)bsel * sm.v_words;
+    const int ncand = C - x;
+    const int b0 = band_index(C, x, x + 1);  // bands [x, x+1), [x, x+2), ... are consecutive
+    int nsteps = 0, vtot = 0;
+    for (int j0 = 0; j0 < ncand; j0 += 32) {
+        const int j = j0 + lane;
+        const uint64_t e = j0 == 0 ? e0 : (j < ncand ? __ldg(sk + b0 + j) : 0ull);
+        const int item = (int)(uint32_t)e - 1;
+        const int klo = (int)(e >> 32) & 0xff, khi = (int)(e >> 40) & 0xff;
+        const int len = item >= 0 ? khi - klo + 1 : 0;
+        const unsigned mk = __ballot_sync(kFull, len > 0);
+        int incl = len;  // inclusive prefix sum of len over the lanes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (len > 0) {
+            const int vofs = vtot + incl - len;
+            sb[nsteps + __popc(mk & ((1u << lane) - 1u))] =
+                (uint32_t)(x + 1 + j) | (uint32_t)klo << 8 | (uint32_t)khi << 14 | (uint32_t)vofs << 20;
+            for (int ff = 0; ff < F; ++ff) {
+                const uint64_t *src = sm.vptr[ff] + (size_t)item * stride + klo;
+                uint64_t *dst = vb + (size_t)vofs * F + ff;
+                for (int t = 0; t < len; ++t) cp_async8(dst + (size_t)t * F, src + t);
+            }
+        }
+        nsteps += __popc(mk);
+        vtot += __shfl_sync(kFull, incl, 31);
+    }
+    return nsteps;
 }
 
-// The column DP of one window (see column_kernel) on values of type VT, by
-// the P warps of the block, in the block's shared-memory table Hraw
-// ((C+1)*(n+1) words of 8 bytes); slots holds the window's item of every
-// band.  Returns H[0][n] with kInf where no partition exists; for 64-bit
-// values the table keeps every entry (kSoft for none) for the rebuild.
-template <int STEP, typename VT, int kBatch, bool PAIR>
-__device__ uint64_t column_dp(uint64_t *Hraw, const int32_t *slots, const uint64_t *V, int C, int n) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, P = blockDim.x >> 5;
-    const int stride = n + 1;
+// The column DP of window w for the F frames of the warp (lane
+// (m - 1) * F + f, F = 1 << lf), values of type VT; V values are read as
+// stored (the missing ones are kInf for step 1, whose low word exceeds the
+// 32-bit saturating infinity too, and kSoft for step 2).  Leaves the H
+// tables in shared memory; returns H[0][n] of the lane's frame.
+template <int STEP, typename VT>
+__device__ VT col_frames(const DevPlan &pl, int C, int w, int F, int lf, int f, int mi, const ColSmem &sm) {
+    const int lane = threadIdx.x & 31;
+    const int n = pl.n, stride = n + 1;
     constexpr VT soft = Soft<VT>::v;
-    VT *Hs = reinterpret_cast<VT *>(Hraw);
-    // PAIR (n <= 16): lanes 0-15 relax one candidate edge and lanes 16-31
-    // another, each half over m = 1..16; otherwise the whole warp takes one
-    const int half = PAIR ? lane >> 4 : 0;
-    const int kl = PAIR ? lane & 15 : lane;  // lane kl holds V[kl+1] of its half's edge
-    const int m = kl + 1;
-    constexpr int kPer = PAIR ? 2 : 1;       // edges per warp step
-    // warp w takes, at left edge x, the candidate right edges x + 1 + c with
-    // c = (s * P + w) * kPer + half for its steps s = 0, 1, ...
-    auto cand = [&](int s) { return (s * P + w) * kPer + half; };
-    auto load = [&](int x, int s0, uint64_t (&vb)[kBatch]) {
-        const int32_t *srow = slots + band_index(C, x, x + 1);  // edges x+1.. are consecutive bands
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-            const int c = cand(s0 + u);
-            const int sj = (c < C - x && kl < n) ? srow[c] : -1;
-            vb[u] = sj >= 0 ? __ldg(V + (size_t)sj * stride + kl + 1) : kInf;
-        }
+    VT *Hs = reinterpret_cast<VT *>(sm.hs);
+    const int m = mi < n ? mi + 1 : n;  // lanes past n shadow m = n and never store
+    const bool mlive = mi < n;
+    const int total = (C + 1) * stride * F, zero0 = C * stride * F;
+    for (int i = lane; i < total; i += 32) Hs[i] = (i >= zero0 && i < zero0 + F) ? VT(0) : soft;  // H[C][0] = 0
+    const uint64_t *sk = pl.slot_k + (size_t)w * pl.nb;
+    auto entry = [&](int x) -> uint64_t {  // plan entries of the first 32 candidate right edges of left edge x
+        return (x >= 0 && lane < C - x) ? __ldg(sk + band_index(C, x, x + 1) + lane) : 0ull;
     };
-    uint64_t cur[kBatch], nxt[kBatch];
-    load(C - 1, 0, cur);
+    __syncwarp();
+    int ns = col_stage(sk, C, C - 1, entry(C - 1), stride, F, lf, sm, 0);
+    cp_async_commit();
+    uint64_t e_next = entry(C - 2);
     for (int x = C - 1; x >= 0; --x) {
-        const int ncand = C - x;
-        // the next left edge's first V rows are in flight while this one relaxes
-        if (x > 0) load(x - 1, 0, nxt);
+        const int bsel = (C - 1 - x) & 1;
+        int ns_next = 0;
+        if (x > 0) {
+            const uint64_t e_after = entry(x - 2);
+            ns_next = col_stage(sk, C, x - 1, e_next, stride, F, lf, sm, bsel ^ 1);
+            e_next = e_after;
+        }
+        cp_async_commit();
+        cp_async_wait_prev();  // edge x's values have landed
+        __syncwarp();
+        const uint32_t *sb = sm.sb + bsel * kEdgeSteps;
+        const uint64_t *vb = sm.vb + (size_t)bsel * sm.v_words + f;
         VT acc = soft;
-        for (int s0 = 0; (s0 * P + w) * kPer < ncand; s0 += kBatch) {
-            uint64_t vb[kBatch];
-            if (s0 == 0) {
-#pragma unroll
-                for (int u = 0; u < kBatch; ++u) vb[u] = cur[u];
-            } else {
-                load(x, s0, vb);
-            }
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                const unsigned fin = __ballot_sync(kFull, vb[u] != kInf);
-                const unsigned any = PAIR ? ((fin & 0xffffu) | (fin >> 16)) : fin;
-                if (!any) continue;
-                const int c = cand(s0 + u);
-                const VT *Hrow = Hs + (size_t)(x + 1 + (c < ncand ? c : 0)) * stride;
-                // the slice counts between the lowest and highest finite k of
-                // either half; a count this half lacks relaxes its saturating
-                // infinity, which no minimum keeps
-                const VT vv = vb[u] == kInf ? soft : (VT)vb[u];
-                const int khi = 32 - __clz(any);
-                for (int k = __ffs(any); k <= khi; ++k) {
-                    const VT v = __shfl_sync(kFull, vv, (half << 4) + k - 1);
-                    const VT h = (m >= k && m <= n) ? Hrow[m - k] : soft;
-                    const VT cc = STEP == 1 ? (v > h ? v : h) : VT(v + h);
-                    acc = cc < acc ? cc : acc;
-                }
+        for (int st = 0; st < ns; ++st) {
+            const uint32_t d = sb[st];
+            const int x1 = (int)(d & 0xff), klo = (int)(d >> 8) & 63, khi = (int)(d >> 14) & 63;
+            const int vofs = (int)(d >> 20);
+            const VT *hp = Hs + (x1 * stride + m) * F + f;  // H[x1][m - k] at hp[-k * F]
+            const uint64_t *vp = vb + (vofs - klo) * F;      // V[k] at vp[k * F]
+            for (int k = klo; k <= khi; ++k) {
+                const VT v = (VT)vp[k * F];
+                const VT h = k <= m ? hp[-k * F] : soft;
+                const VT c = STEP == 1 ? (v > h ? v : h) : VT(v + h);
+                acc = c < acc ? c : acc;
             }
         }
-        if (PAIR) {
-            const VT o = __shfl_xor_sync(kFull, acc, 16);
-            acc = o < acc ? o : acc;
-        }
-        if (half == 0 && m <= n && acc < soft) smem_min(Hs + (size_t)x * stride + m, acc);
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) cur[u] = nxt[u];
-        __syncthreads();  // row x is complete before any warp reads it
+        if (mlive) Hs[(x * stride + m) * F + f] = acc;
+        __syncwarp();
+        ns = ns_next;
     }
-    const VT r = Hs[n];
-    return r >= soft ? kInf : (uint64_t)r;
+    return Hs[n * F + f];
 }
 
-// Suffix DP over tile-column edges of one window, one block of P warps:
-//   H[x][m] = min over x1 > x, k of  V[item(w, [x,x1))][k] (+|max) H[x1][m-k],
-// H[C][0] = 0.  Lane m-1 owns slice count m.  At each left edge x the
-// block's warps split the candidate right edges x1 between them, relax the
-// slice counts whose V is finite (a ballot per row) and merge their minima
-// into row x with shared-memory atomics; the V rows of the next left edge
-// are loaded while the current one relaxes.
-template <int STEP, int kBatch>
-__global__ void __launch_bounds__(kMaxWarps * 32) column_kernel(LaunchArgs args, int total, int h_words) {
-    extern __shared__ uint64_t csm[];
-    const int w = blockIdx.x;
-    if (w >= total) return;
-    int wl;
-    const int f = locate(args, args.pre.windows, args.single_windows, w, &wl);
-    const DevFrame &fr = frame_at(args, f);
-    const DevPlan &pl = *fr.plan;
-    const int C = fr.C, n = pl.n, nb = pl.nb, stride = n + 1;
-    uint64_t *wres = STEP == 1 ? fr.wres1 : fr.wres2;
-    const uint64_t *V = STEP == 1 ? fr.V1 : fr.V2;
-    if (frame_status(fr) != TRS_OK) {
-        if (threadIdx.x == 0) wres[wl] = kInf;
+// Which frames and window column-DP warp u runs.
+__device__ __forceinline__ void col_unit(const LaunchArgs &a, int u, int *first, int *count, int *F, int *w) {
+    if (!a.cchunks) {
+        const int nch = a.col_nchunks, fpw = a.col_fpw;
+        const int ww = u / nch, c = u - ww * nch;
+        *w = ww;
+        *F = fpw;
+        *first = c * fpw;
+        *count = min(fpw, a.nframes - c * fpw);
         return;
     }
-    if (STEP == 2) {
-        // a window whose best time breaks Eq. 4 holds no step-2 candidate
-        const uint64_t thr = eq4_threshold(fr.scal[0], fr.lambda_q);
-        if (fr.wres1[wl] > thr) {
-            if (threadIdx.x == 0) wres[wl] = kInf;
-            return;
+    int lo = 0, hi = a.col_nchunks - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.cchunks[mid].unit0 <= u) lo = mid; else hi = mid - 1;
+    }
+    const ColChunk ch = a.cchunks[lo];
+    *first = ch.first;
+    *count = ch.count;
+    *F = ch.fpw;
+    *w = u - ch.unit0;
+}
+
+constexpr int kColHead = 64 + 2 * kEdgeSteps * 4;  // vptr table and step lists of a warp's shared memory
+
+// One warp per (window, frames sharing the plan): the column DP of Eq. 1
+// (step 1, reduced into T_min, Eq. 3) or Eq. 2 (step 2, into Q*), see
+// col_frames.  Step 2 runs only for frames whose step-1 window best meets
+// Eq. 4 (every item of such a window was relaxed by step 2's row DP) and
+// stores their H tables for the rebuild.
+template <int STEP>
+__global__ void __launch_bounds__(kMaxWarps * 32) column_kernel(LaunchArgs args, int total, int warp_bytes,
+                                                                 int v_words) {
+    extern __shared__ __align__(16) unsigned char colsm[];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int u = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (u >= total) return;
+    int first, count, F, w;
+    col_unit(args, u, &first, &count, &F, &w);
+    const int lf = __ffs(F) - 1;
+    const int f = lane & (F - 1), mi = lane >> lf;
+    const bool fvalid = f < count;
+    const DevFrame &fr = frame_at(args, first + (fvalid ? f : 0));
+    const DevPlan &pl = *fr.plan;
+    const int C = fr.C, n = pl.n;
+    unsigned char *base = colsm + (size_t)wib * warp_bytes;
+    ColSmem sm;
+    sm.vptr = reinterpret_cast<const uint64_t **>(base);
+    sm.sb = reinterpret_cast<uint32_t *>(base + 64);
+    sm.vb = reinterpret_cast<uint64_t *>(base + kColHead);
+    sm.v_words = v_words;
+    sm.hs = base + kColHead + (size_t)2 * v_words * 8;
+    uint64_t *wres = STEP == 1 ? fr.wres1 : fr.wres2;
+    const bool ok = fvalid && frame_status(fr) == TRS_OK;
+    bool pass = ok;
+    if (STEP == 2) pass = ok && fr.wres1[w] <= eq4_threshold(fr.scal[0], fr.lambda_q);
+    if (!__any_sync(kFull, pass)) {  // no frame of the warp has a candidate here
+        if (fvalid && mi == 0) wres[w] = kInf;
+        return;
+    }
+    if (mi == 0) sm.vptr[f] = STEP == 1 ? fr.V1 : fr.V2;
+    uint64_t res = kInf;
+    if (STEP == 1) {
+        if (__all_sync(kFull, !fvalid || frame_t32(fr))) {
+            const uint32_t r = col_frames<1, uint32_t>(pl, C, w, F, lf, f, mi, sm);
+            res = r >= Soft<uint32_t>::v ? kInf : r;
+        } else {
+            // 64-bit values: the frames one at a time, lanes over the slice count
+            for (int g = 0; g < count; ++g) {
+                ColSmem s1 = sm;
+                s1.vptr = sm.vptr + g;
+                const uint64_t r = col_frames<1, uint64_t>(pl, C, w, 1, 0, 0, lane, s1);
+                if (f == g) res = r >= kSoft ? kInf : r;
+                __syncwarp();
+            }
         }
-    }
-    uint64_t *Hraw = csm;
-    int32_t *slots = reinterpret_cast<int32_t *>(csm + h_words);
-    const int32_t *slot_row = pl.slot_of + (size_t)wl * nb;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) slots[i] = slot_row[i];
-    const bool t32 = STEP == 1 && frame_t32(fr);
-    if (t32) {
-        uint32_t *Hs = reinterpret_cast<uint32_t *>(Hraw);
-        for (int i = threadIdx.x; i < (C + 1) * stride; i += blockDim.x) Hs[i] = i == C * stride ? 0u : Soft<uint32_t>::v;
     } else {
-        for (int i = threadIdx.x; i < (C + 1) * stride; i += blockDim.x) Hraw[i] = i == C * stride ? 0ull : kSoft;
+        const uint64_t r = col_frames<2, uint64_t>(pl, C, w, F, lf, f, mi, sm);
+        res = r >= kSoft ? kInf : r;
     }
-    __syncthreads();
-    uint64_t res;
-    if (t32)
-        res = n <= 16 ? column_dp<1, uint32_t, kBatch, true>(Hraw, slots, V, C, n)
-                      : column_dp<1, uint32_t, kBatch, false>(Hraw, slots, V, C, n);
-    else
-        res = n <= 16 ? column_dp<STEP, uint64_t, kBatch, true>(Hraw, slots, V, C, n)
-                      : column_dp<STEP, uint64_t, kBatch, false>(Hraw, slots, V, C, n);
-    if (threadIdx.x == 0) {
-        wres[wl] = res;
+    if (!pass) res = kInf;
+    if (fvalid && mi == 0) {
+        wres[w] = res;
         if (res != kInf) atomicMin(reinterpret_cast<unsigned long long *>(&fr.scal[STEP == 1 ? 0 : 1]), res);
     }
-    if (STEP == 2) {
-        uint64_t *H2 = fr.H2 + (size_t)wl * (C + 1) * stride;
-        for (int i = threadIdx.x; i < (C + 1) * stride; i += blockDim.x) H2[i] = hard_inf(Hraw[i]);
+    if (STEP == 2 && pass) {
+        // the frame's H table of this window, for the rebuild (lanes of frame f)
+        const uint64_t *Hs = reinterpret_cast<const uint64_t *>(sm.hs);
+        const int words = (C + 1) * (n + 1);
+        uint64_t *H2 = fr.H2 + (size_t)w * words;
+        for (int i = mi; i < words; i += 32 >> lf) H2[i] = hard_inf(Hs[i * F + f]);
     }
 }
 
@@ -698,7 +792,7 @@ __global__ void __launch_bounds__(32) rebuild_kernel(LaunchArgs args, int total,
                 bool ok = false;
                 if (k <= m) {
                     const uint64_t v = fr.V2[(size_t)sj * stride + k], h = H2[xj * stride + m - k];
-                    ok = v != kInf && h != kInf && v + h == target;
+                    ok = v < kSoft && h != kInf && v + h == target;
                 }
                 const unsigned km = __ballot_sync(kFull, ok);
                 if (km) {
@@ -881,24 +975,22 @@ __global__ void __launch_bounds__(32) finish_kernel(LaunchArgs args) {
 // largest shapes need (once per device, before any capture).
 int prepare_search_kernels() {
     const int band_smem = kMaxWarps * (2 * kMaxR * 32 + kBandTail) * (int)sizeof(uint64_t);
-    const int col_smem = (kMaxC + 1) * (kMaxN + 1) * (int)sizeof(uint64_t) + num_bands(kMaxC) * (int)sizeof(int32_t);
+    const int col_smem = 227 * 1024;  // the column DP's per-warp tables scale with the shapes of the launch
     const int rb_smem = ((kMaxN + 1) * 32 + kMaxR * 32) * (int)sizeof(uint64_t);
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
     cudaError_t e = cudaFuncSetAttribute(band_kernel<1, 17>, A, band_smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(band_kernel<1, 32>, A, band_smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(band_kernel<2, 17>, A, band_smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(band_kernel<2, 32>, A, band_smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(column_kernel<1, 4>, A, col_smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(column_kernel<1, 8>, A, col_smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(column_kernel<2, 4>, A, col_smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(column_kernel<2, 8>, A, col_smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(column_kernel<1>, A, col_smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(column_kernel<2>, A, col_smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(rebuild_kernel, A, rb_smem);
     return (int)e;
 }
 
 int launch_search(const LaunchArgs &a, int total_bands, int total_windows, int maxC, int maxR, int maxN,
-                  uint64_t *scal, size_t nscal, void *stream, cudaEvent_t *ev, const SearchTune *tune, int steps,
-                  int max_nd) {
+                  uint64_t *scal, size_t nscal, void *stream, const ColGeom &col, cudaEvent_t *ev,
+                  const SearchTune *tune, int steps, int max_nd) {
     const SearchTune t = tune ? *tune : SearchTune{};
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
@@ -912,22 +1004,20 @@ int launch_search(const LaunchArgs &a, int total_bands, int total_windows, int m
     // max_nd heights) in the paired path, up to R heights in the other
     const int band_stage = maxR * S, band_itm = (S == 17 && max_nd > 0 ? std::min(max_nd, maxR) : maxR) * 32;
     const size_t band_smem = (size_t)bw * (band_stage + band_itm + kBandTail) * sizeof(uint64_t);
-    const int h_words = (maxC + 1) * (maxN + 1);
-    const size_t col_smem = (size_t)h_words * sizeof(uint64_t) + (size_t)num_bands(maxC) * sizeof(int32_t);
     const int bb = (total_bands + bw - 1) / bw;
-    const int cb = total_windows;  // one block of cw warps per window
     auto mark = [&](int i) {
         if (ev && e == cudaSuccess) e = record_event(ev[i], s);
     };
     auto columns = [&](int step) {
-        if (total_windows <= 0) return;
-        if (step == 1) {
-            if (t.col_batch == 4) column_kernel<1, 4><<<cb, cw * 32, col_smem, s>>>(a, total_windows, h_words);
-            else column_kernel<1, 8><<<cb, cw * 32, col_smem, s>>>(a, total_windows, h_words);
-        } else {
-            if (t.col_batch == 4) column_kernel<2, 4><<<cb, cw * 32, col_smem, s>>>(a, total_windows, h_words);
-            else column_kernel<2, 8><<<cb, cw * 32, col_smem, s>>>(a, total_windows, h_words);
-        }
+        if (col.units <= 0) return;
+        // per warp: vptr table, step lists, two V buffers, H tables
+        const size_t hb = step == 1 ? col.h_bytes1 : col.h_bytes2;
+        const size_t wb = ((size_t)kColHead + (size_t)2 * col.v_words * 8 + hb + 15) & ~size_t(15);
+        int P = cw;
+        while (P > 1 && (size_t)P * wb > 227 * 1024) P >>= 1;
+        const int blocks = (col.units + P - 1) / P;
+        if (step == 1) column_kernel<1><<<blocks, P * 32, P * wb, s>>>(a, col.units, (int)wb, col.v_words);
+        else column_kernel<2><<<blocks, P * 32, P * wb, s>>>(a, col.units, (int)wb, col.v_words);
     };
     if (steps & 1) {
         if (total_bands > 0) {

@@ -19,6 +19,7 @@
 // is bounded; no device code waits on anything.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -122,7 +123,16 @@ int launch_batch(trs_server *srv, Batch &b) {
     const int nf = (int)b.reqs.size();
     std::vector<PlanEntry *> pe(nf);
     DevFrame *hf = (DevFrame *)b.hb;
-    for (int i = 0; i < nf; ++i) {
+    // frames ordered by shape, so that those sharing a plan are adjacent (the
+    // column DP packs them into one warp); each keeps its own output slot
+    std::vector<int> order(nf);
+    for (int i = 0; i < nf; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const Stream &a = srv->streams[b.reqs[x].stream], &c = srv->streams[b.reqs[y].stream];
+        return std::make_tuple(a.W, a.H, a.n) < std::make_tuple(c.W, c.H, c.n);
+    });
+    for (int j = 0; j < nf; ++j) {
+        const int i = order[j];
         const Request &r = b.reqs[i];
         Stream &st = srv->streams[r.stream];
         Slot &sl = st.slot[r.slot];
@@ -142,16 +152,16 @@ int launch_batch(trs_server *srv, Batch &b) {
         f.cnt = (uint32_t *)(sl.stats + align256((size_t)cells * 4));
         f.vmax = (uint32_t *)(sl.stats + 2 * align256((size_t)cells * 4));
         f.s2 = (uint64_t *)(sl.stats + 3 * align256((size_t)cells * 4));
-        f.flags = b.flags + i;
+        f.flags = b.flags + j;
         f.tables = sl.tables;
         set_search_scratch(f, *st.pe, sl.scratch, st.n, st.lambda);
-        f.scal = b.scal + 4 * i;
+        f.scal = b.scal + 4 * j;
         f.out = b.out_dev + i;
-        hf[i] = f;
-        pe[i] = st.pe;
+        hf[j] = f;
+        pe[j] = st.pe;
     }
     BatchLaunch bl;
-    batch_describe(bl, b.hb, b.db, nf, pe.data(), b.flags, b.scal);
+    batch_describe(bl, b.hb, b.db, nf, pe.data(), b.flags, b.scal, SearchTune{});
     TRS_CK(batch_enqueue(bl, b.s, b.copied, nullptr));
     TRS_CK(cudaMemcpyAsync(b.out_host, b.out_dev, (size_t)nf * sizeof(trs_partition), cudaMemcpyDeviceToHost, b.s));
     TRS_CK(cudaEventRecord(b.done, b.s));

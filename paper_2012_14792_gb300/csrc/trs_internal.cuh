@@ -136,7 +136,17 @@ struct DevPlan {
     const int16_t *band_x0;     // [nb]
     const int16_t *band_x1;     // [nb]
     const int32_t *band_items;  // [nb+1]: items of band b are [band_items[b], band_items[b+1])
+    // column-DP steps, [nwin * nb]: for band b of window w, 0 if the band has
+    // no item there, else (item + 1) | klo << 32 | khi << 40 with [klo, khi]
+    // the item's slice counts (klo >= 1)
+    const uint64_t *slot_k;
+    int max_edge_vals;  // largest sum of khi - klo + 1 over the bands of one left edge of one window
 };
+
+// Column-DP step entry of band (item, slice counts [klo, khi]).
+__host__ __device__ inline uint64_t pack_slot_k(int item, int klo, int khi) {
+    return (uint64_t)(uint32_t)(item + 1) | (uint64_t)(uint32_t)klo << 32 | (uint64_t)(uint32_t)khi << 40;
+}
 
 // A canonical code: c tile columns with right edges xe[1..c] (xe[0] = 0)
 // and the slice cut bits of each (bit y-1 = cut at CTU line y).  c < 0
@@ -187,6 +197,21 @@ struct WorkPrefix {
 
 constexpr int kBandsPerBlock = 16;
 
+// Column-DP work: frames [first, first + count) of a launch share one plan
+// and each warp runs one window for up to fpw of them; the chunk's units
+// (one per window) are [unit0, unit0 + nwin).
+struct ColChunk {
+    int32_t first, count, fpw, unit0;
+};
+
+// Lanes per frame of a column-DP warp: the slice counts m = 1..n, rounded up
+// to a power of two (at least 4, so a warp holds at most 8 frames).
+__host__ __device__ inline int col_lanes(int n) {
+    int L = 4;
+    while (L < n) L <<= 1;
+    return L;
+}
+
 struct LaunchArgs {
     DevFrame single;            // used when frames == nullptr
     const DevFrame *frames;     // device array of nframes, or nullptr
@@ -196,6 +221,28 @@ struct LaunchArgs {
     // array has the same plan) the units of each frame of the array
     int single_ctus, single_bandgrp, single_items, single_windows, single_bands;
     int uniform;
+    // column DP: with cchunks == nullptr every frame of the launch shares one
+    // plan, col_fpw frames per warp in col_nchunks chunks, unit u = window
+    // (u / col_nchunks) of chunk (u % col_nchunks); otherwise col_nchunks
+    // chunks described by cchunks
+    const ColChunk *cchunks;
+    int col_nchunks, col_fpw;
+};
+
+// Launch geometry of the column DP (host side).
+struct ColGeom {
+    int units = 0;          // warps: one per (chunk, window)
+    size_t h_bytes1 = 0;    // per warp: the H tables of step 1 (32-bit for all frames, or 64-bit one at a time)
+    size_t h_bytes2 = 0;    // per warp: the H tables of step 2 (64-bit)
+    int v_words = 1;        // per warp and buffer: staged V values of one left edge
+    void add(int C, int n, int max_edge_vals, int fpw) {
+        const size_t cells = (size_t)(C + 1) * (n + 1);
+        const size_t h1 = cells * (size_t)(4 * fpw > 8 ? 4 * fpw : 8), h2 = cells * 8 * (size_t)fpw;
+        h_bytes1 = h1 > h_bytes1 ? h1 : h_bytes1;
+        h_bytes2 = h2 > h_bytes2 ? h2 : h_bytes2;
+        const int v = (max_edge_vals > 1 ? max_edge_vals : 1) * fpw;
+        v_words = v > v_words ? v : v_words;
+    }
 };
 
 __device__ inline const DevFrame &frame_at(const LaunchArgs &a, int f) {
@@ -245,16 +292,18 @@ int launch_tables(const LaunchArgs &a, int total_groups, int maxC, int maxR, voi
 // Launch shapes of the search kernels, chosen by trs_autotune.
 struct SearchTune {  // defaults: what trs_autotune picks for 2160p frames on GB300
     int band_warps = 2;  // warps per block of the row-DP kernels (2, 4 or 8)
-    int col_warps = 2;   // warps sharing one window's column DP, one block per window (1, 2, 4 or 8)
-    int col_batch = 4;   // candidate steps whose V rows a column-DP warp loads together (4 or 8)
+    int col_warps = 4;   // warps per block of the column-DP kernels (1, 2, 4 or 8)
+    int col_batch = 4;   // 4: a column-DP warp runs one window for 32 / col_lanes(n) frames; 8: for one frame
 };
+inline int col_fpw(int n, const SearchTune &t) { return t.col_batch == 8 ? 1 : 32 / col_lanes(n); }
 
 // scal: the T_min / Q* words of every frame of the launch (reset to +inf first).
 // ev (optional, 6 events): recorded after each of the six search kernels.
 // maxC / maxR / maxN: largest C, R and n over the frames of the launch (shared-memory sizing);
 // max_nd: largest HostPlan::max_nd over them (0: size for maxR heights).
+// col: the column DP's geometry (see ColGeom; a's col_* fields describe its units).
 int launch_search(const LaunchArgs &a, int total_bands, int total_windows, int maxC, int maxR, int maxN,
-                  uint64_t *scal, size_t nscal, void *stream, cudaEvent_t *ev = nullptr,
+                  uint64_t *scal, size_t nscal, void *stream, const ColGeom &col, cudaEvent_t *ev = nullptr,
                   const SearchTune *tune = nullptr, int steps = 3, int max_nd = 0);
 // steps: 1 = step 1 only (resets scal first), 2 = step 2, rebuild and decode
 // only (scal[0] must already hold T_min and scal[1] +infinity), 3 = both.
