@@ -482,16 +482,15 @@ __global__ void __launch_bounds__(kMaxWarps * 32) band_kernel(LaunchArgs args, i
 // slice counts each step relaxes, so the warp's control flow is the same
 // for all of them): lane (m - 1) * F + f holds H[x][m] of frame f.  The H
 // tables sit in the warp's shared memory, frames interleaved, so a step is
-// two shared loads (V broadcast to the frame's lanes, H[x1][m - k]
-// consecutive over the lanes), a max (Eq. 1) or add (Eq. 2) and a min.
-// The candidate steps of left edge x - 1 and their V values are staged while
-// edge x relaxes: the step list through the plan's per-window entries
-// (loaded one edge further ahead) and the V values by asynchronous
-// global-to-shared copies, double-buffered, so no global load latency sits
-// on the chain of edges.  No block barrier: the warps of a block are
-// independent.
-
-constexpr int kEdgeSteps = 64;  // candidate right edges of one left edge (C <= 64)
+// three shared loads (the value's H offset and V, both broadcast to the
+// frame's lanes, and H[x1][m - k], consecutive over the lanes), a max
+// (Eq. 1) or add (Eq. 2) and a min, in one flat loop over the edge's
+// (band, slice count) values with no per-lane branch.  The values of left
+// edge x - 1 are staged while edge x relaxes: their list from the plan's
+// per-window entries (loaded one edge further ahead) and the V values by
+// asynchronous global-to-shared copies spread evenly over the lanes,
+// double-buffered, so no global load latency sits on the chain of edges.
+// No block barrier: the warps of a block are independent.
 
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -504,52 +503,64 @@ __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wa
 // One warp's shared memory for the column DP.
 struct ColSmem {
     const uint64_t **vptr;  // [8]: V array of each frame of the warp
-    uint32_t *sb;           // [2][kEdgeSteps]: step lists of two left edges
-    uint64_t *vb;           // [2][v_words]: their V values, frames interleaved
+    uint32_t *md;           // [2][v_words]: per staged value, its H offset and slice count (see col_stage)
+    uint64_t *vb;           // [2][v_words]: the staged V values, frames interleaved
     void *hs;               // H tables, frames interleaved
     int v_words;
 };
 
-// Stages left edge x into buffer bsel: the steps (right edge x1, slice
-// counts [klo, khi], offset of their V values) of every band [x, x1) that
-// has an item in the window, and V[item][klo..khi] of each of the F frames
-// by asynchronous copies.  e0: the entries of the first 32 candidate right
-// edges (lane j: x1 = x + 1 + j), loaded ahead.  Returns the step count.
+// Stages left edge x into buffer bsel.  The edge's values are the pairs
+// (band [x, x1) with an item in the window, slice count k in the item's
+// range [klo, khi]), in order of x1 then k; value i gets
+//   md[i] = ((x1 * stride - k) * F) << 6 | k
+// (so H[x1][m - k] of frame f sits at Hs[(md[i] >> 6) + m * F + f]) and its
+// V[item][k] of each of the F frames at vb[i * F + f], copied
+// asynchronously.  The lanes take the (value, frame) pairs in turn, each
+// finding its value's band by a binary search over the candidates' prefix
+// sums, so no lane runs a loop of its own length.  e0: the plan entries of
+// the first 32 candidate right edges (lane j: x1 = x + 1 + j), loaded ahead.
+// Returns the number of values.
 __device__ int col_stage(const uint64_t *sk, int C, int x, uint64_t e0, int stride, int F, int lf,
                          const ColSmem &sm, int bsel) {
     const int lane = threadIdx.x & 31;
-    uint32_t *sb = sm.sb + bsel * kEdgeSteps;
+    uint32_t *md = sm.md + bsel * sm.v_words;
     uint64_t *vb = sm.vb + (size_t)bsel * sm.v_words;
     const int ncand = C - x;
     const int b0 = band_index(C, x, x + 1);  // bands [x, x+1), [x, x+2), ... are consecutive
-    int nsteps = 0, vtot = 0;
+    int vtot = 0;
     for (int j0 = 0; j0 < ncand; j0 += 32) {
         const int j = j0 + lane;
         const uint64_t e = j0 == 0 ? e0 : (j < ncand ? __ldg(sk + b0 + j) : 0ull);
         const int item = (int)(uint32_t)e - 1;
         const int klo = (int)(e >> 32) & 0xff, khi = (int)(e >> 40) & 0xff;
         const int len = item >= 0 ? khi - klo + 1 : 0;
-        const unsigned mk = __ballot_sync(kFull, len > 0);
         int incl = len;  // inclusive prefix sum of len over the lanes
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int t = __shfl_up_sync(kFull, incl, o);
             if (lane >= o) incl += t;
         }
-        if (len > 0) {
-            const int vofs = vtot + incl - len;
-            sb[nsteps + __popc(mk & ((1u << lane) - 1u))] =
-                (uint32_t)(x + 1 + j) | (uint32_t)klo << 8 | (uint32_t)khi << 14 | (uint32_t)vofs << 20;
-            for (int ff = 0; ff < F; ++ff) {
-                const uint64_t *src = sm.vptr[ff] + (size_t)item * stride + klo;
-                uint64_t *dst = vb + (size_t)vofs * F + ff;
-                for (int t = 0; t < len; ++t) cp_async8(dst + (size_t)t * F, src + t);
+        const int excl = incl - len;
+        const int cnt = __shfl_sync(kFull, incl, 31);
+        for (int q0 = 0; q0 < cnt * F; q0 += 32) {
+            const int q = q0 + lane, i = q >> lf, ff = q & (F - 1);
+            // the value's candidate: the last lane whose values start at or before i
+            int o = 0;
+#pragma unroll
+            for (int st = 16; st > 0; st >>= 1) {
+                const int ex = __shfl_sync(kFull, excl, o + st);
+                if (ex <= i) o += st;
+            }
+            const int it_o = __shfl_sync(kFull, item, o);
+            const int k = __shfl_sync(kFull, klo, o) + (i - __shfl_sync(kFull, excl, o));
+            if (q < cnt * F) {
+                cp_async8(vb + (size_t)(vtot + i) * F + ff, sm.vptr[ff] + (size_t)it_o * stride + k);
+                if (ff == 0) md[vtot + i] = (uint32_t)(((x + 1 + j0 + o) * stride - k) * F) << 6 | (uint32_t)k;
             }
         }
-        nsteps += __popc(mk);
-        vtot += __shfl_sync(kFull, incl, 31);
+        vtot += cnt;
     }
-    return nsteps;
+    return vtot;
 }
 
 // The column DP of window w for the F frames of the warp (lane
@@ -565,6 +576,7 @@ __device__ VT col_frames(const DevPlan &pl, int C, int w, int F, int lf, int f, 
     VT *Hs = reinterpret_cast<VT *>(sm.hs);
     const int m = mi < n ? mi + 1 : n;  // lanes past n shadow m = n and never store
     const bool mlive = mi < n;
+    const int mF = m * F + f;
     const int total = (C + 1) * stride * F, zero0 = C * stride * F;
     for (int i = lane; i < total; i += 32) Hs[i] = (i >= zero0 && i < zero0 + F) ? VT(0) : soft;  // H[C][0] = 0
     const uint64_t *sk = pl.slot_k + (size_t)w * pl.nb;
@@ -572,39 +584,49 @@ __device__ VT col_frames(const DevPlan &pl, int C, int w, int F, int lf, int f, 
         return (x >= 0 && lane < C - x) ? __ldg(sk + band_index(C, x, x + 1) + lane) : 0ull;
     };
     __syncwarp();
-    int ns = col_stage(sk, C, C - 1, entry(C - 1), stride, F, lf, sm, 0);
+    int nv = col_stage(sk, C, C - 1, entry(C - 1), stride, F, lf, sm, 0);
     cp_async_commit();
     uint64_t e_next = entry(C - 2);
     for (int x = C - 1; x >= 0; --x) {
         const int bsel = (C - 1 - x) & 1;
-        int ns_next = 0;
+        int nv_next = 0;
         if (x > 0) {
             const uint64_t e_after = entry(x - 2);
-            ns_next = col_stage(sk, C, x - 1, e_next, stride, F, lf, sm, bsel ^ 1);
+            nv_next = col_stage(sk, C, x - 1, e_next, stride, F, lf, sm, bsel ^ 1);
             e_next = e_after;
         }
         cp_async_commit();
         cp_async_wait_prev();  // edge x's values have landed
         __syncwarp();
-        const uint32_t *sb = sm.sb + bsel * kEdgeSteps;
+        const uint32_t *md = sm.md + bsel * sm.v_words;
         const uint64_t *vb = sm.vb + (size_t)bsel * sm.v_words + f;
-        VT acc = soft;
-        for (int st = 0; st < ns; ++st) {
-            const uint32_t d = sb[st];
-            const int x1 = (int)(d & 0xff), klo = (int)(d >> 8) & 63, khi = (int)(d >> 14) & 63;
-            const int vofs = (int)(d >> 20);
-            const VT *hp = Hs + (x1 * stride + m) * F + f;  // H[x1][m - k] at hp[-k * F]
-            const uint64_t *vp = vb + (vofs - klo) * F;      // V[k] at vp[k * F]
-            for (int k = klo; k <= khi; ++k) {
-                const VT v = (VT)vp[k * F];
-                const VT h = k <= m ? hp[-k * F] : soft;
-                const VT c = STEP == 1 ? (v > h ? v : h) : VT(v + h);
-                acc = c < acc ? c : acc;
-            }
+        // two minimum chains; H[x1][m - k] is read for every lane (x1 >= 1
+        // keeps the offset inside the table) and replaced by the saturating
+        // infinity where k > m
+        VT acc0 = soft, acc1 = soft;
+        int i = 0;
+        for (; i + 1 < nv; i += 2) {
+            const uint32_t d0 = md[i], d1 = md[i + 1];
+            const VT v0 = (VT)vb[(size_t)i * F], v1 = (VT)vb[(size_t)(i + 1) * F];
+            const VT g0 = Hs[(d0 >> 6) + mF], g1 = Hs[(d1 >> 6) + mF];
+            const VT h0 = (int)(d0 & 63) <= m ? g0 : soft, h1 = (int)(d1 & 63) <= m ? g1 : soft;
+            const VT c0 = STEP == 1 ? (v0 > h0 ? v0 : h0) : VT(v0 + h0);
+            const VT c1 = STEP == 1 ? (v1 > h1 ? v1 : h1) : VT(v1 + h1);
+            acc0 = c0 < acc0 ? c0 : acc0;
+            acc1 = c1 < acc1 ? c1 : acc1;
         }
+        if (i < nv) {
+            const uint32_t d0 = md[i];
+            const VT v0 = (VT)vb[(size_t)i * F];
+            const VT g0 = Hs[(d0 >> 6) + mF];
+            const VT h0 = (int)(d0 & 63) <= m ? g0 : soft;
+            const VT c0 = STEP == 1 ? (v0 > h0 ? v0 : h0) : VT(v0 + h0);
+            acc0 = c0 < acc0 ? c0 : acc0;
+        }
+        const VT acc = acc0 < acc1 ? acc0 : acc1;
         if (mlive) Hs[(x * stride + m) * F + f] = acc;
         __syncwarp();
-        ns = ns_next;
+        nv = nv_next;
     }
     return Hs[n * F + f];
 }
@@ -632,7 +654,7 @@ __device__ __forceinline__ void col_unit(const LaunchArgs &a, int u, int *first,
     *w = u - ch.unit0;
 }
 
-constexpr int kColHead = 64 + 2 * kEdgeSteps * 4;  // vptr table and step lists of a warp's shared memory
+constexpr int kColHead = 64;  // the vptr table at the start of a warp's shared memory
 
 // One warp per (window, frames sharing the plan): the column DP of Eq. 1
 // (step 1, reduced into T_min, Eq. 3) or Eq. 2 (step 2, into Q*), see
@@ -657,10 +679,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32) column_kernel(LaunchArgs args,
     unsigned char *base = colsm + (size_t)wib * warp_bytes;
     ColSmem sm;
     sm.vptr = reinterpret_cast<const uint64_t **>(base);
-    sm.sb = reinterpret_cast<uint32_t *>(base + 64);
     sm.vb = reinterpret_cast<uint64_t *>(base + kColHead);
+    sm.md = reinterpret_cast<uint32_t *>(base + kColHead + (size_t)2 * v_words * 8);
     sm.v_words = v_words;
-    sm.hs = base + kColHead + (size_t)2 * v_words * 8;
+    sm.hs = base + kColHead + (size_t)2 * v_words * 12;
     uint64_t *wres = STEP == 1 ? fr.wres1 : fr.wres2;
     const bool ok = fvalid && frame_status(fr) == TRS_OK;
     bool pass = ok;
@@ -1010,9 +1032,9 @@ int launch_search(const LaunchArgs &a, int total_bands, int total_windows, int m
     };
     auto columns = [&](int step) {
         if (col.units <= 0) return;
-        // per warp: vptr table, step lists, two V buffers, H tables
+        // per warp: vptr table, two buffers of staged values and their offsets, H tables
         const size_t hb = step == 1 ? col.h_bytes1 : col.h_bytes2;
-        const size_t wb = ((size_t)kColHead + (size_t)2 * col.v_words * 8 + hb + 15) & ~size_t(15);
+        const size_t wb = ((size_t)kColHead + (size_t)2 * col.v_words * 12 + hb + 15) & ~size_t(15);
         int P = cw;
         while (P > 1 && (size_t)P * wb > 227 * 1024) P >>= 1;
         const int blocks = (col.units + P - 1) / P;
