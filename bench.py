@@ -8,8 +8,11 @@ the 126 MB L2, so no flush is needed).  The JSON line also carries:
   plain     the same 64 frames decided one frame per launch chain
   e2e       the same metric through trs_batch_decide_host from pinned host
             buffers, host<->device copies inside the timed region
-  roofline  the dominant kernel against its bound, and the texture kernel
-            against HBM
+  roofline  one fixed kernel (the search family's largest) against its
+            bound; rooflines: every kernel of the step with its share of the
+            one-chunk stage sum; roofline_texture: the texture kernel
+  config_480p8_n4, config_1080p10_n8  the two single-frame configurations,
+            batched and one frame per launch chain, beside the oracle
   cpu_baseline  the oracle on this host, on a bounded sample of frames
 
 --impl reference times the oracle as the reference arm.
@@ -41,6 +44,9 @@ IN_FLIGHT = 2  # batches in flight in the timed stream of steps
 N_REGIONS = 16
 LAMBDA = 0.1
 WORKLOAD = "3840x2160p10 moving-blob sequence, 64 frames, n=16, lambda=0.1, k=3"
+# the kernel the headline roofline reports, fixed by name: the search family's
+# largest share of the one-chunk stage sum in the committed profiles
+ROOFLINE_KERNEL = "band_kernel<1>"
 
 
 def _gen(f):
@@ -53,13 +59,95 @@ def _gen_mixed(i):
     return synth.mixed_batch_frame(i)
 
 
-def make_inputs(nframes: int, mixed: bool = False):
+def _gen_config(a):
+    import synth
+    name, seed = a
+    return synth.make_frame(getattr(synth, name), seed)
+
+
+# the single-frame configurations beside the headline one: (spec, n)
+CONFIGS = {"config_480p8_n4": ("SPEC_480P8", 4), "config_1080p10_n8": ("SPEC_1080P10", 8)}
+CONFIG_FRAMES = 64
+
+
+def make_inputs(nframes: int, mixed: bool = False, configs: bool = False):
     """Draws the workload frames in a spawn pool (before any CUDA call)."""
     ctx = mp.get_context("spawn")
     with ctx.Pool(min(16, os.cpu_count() or 1)) as pool:
         seq = pool.map(_gen, range(nframes))
         mix = pool.map(_gen_mixed, range(256)) if mixed else None
-    return seq, mix
+        cfg = {k: pool.map(_gen_config, [(name, s) for s in range(CONFIG_FRAMES)])
+               for k, (name, _) in CONFIGS.items()} if configs else None
+    return seq, mix, cfg
+
+
+def run_config(runtime, trs, spec, n, frames, device: int, steps: int, warmup: int, in_flight: int):
+    """One single-frame configuration (832x480 8-bit n = 4, 1920x1080 10-bit
+    n = 8) at full rate: its seeded frames decided as one batch per step
+    (graph replays, `in_flight` contexts on their own streams), and one frame
+    per launch chain."""
+    import torch
+    dev = torch.device("cuda", device)
+    nf = len(frames)
+    decs = [runtime.Decider(max_width=spec.width, max_height=spec.height, max_regions=n, max_batch=nf,
+                            device=device) for _ in range(in_flight)]
+    try:
+        ins, keep = [], []
+        for plane, times in frames:
+            raw = np.ascontiguousarray(plane).view(np.uint8)
+            l = torch.from_numpy(raw).to(dev)
+            t = torch.from_numpy(times).to(dev)
+            keep += [l, t]
+            ins.append((l, raw.strides[0], spec.width, spec.height, spec.bit_depth, t, n, LAMBDA))
+        outs = [torch.zeros(nf * trs.PARTITION_BYTES, dtype=torch.uint8, device=dev) for _ in decs]
+        streams = [torch.cuda.Stream(dev) for _ in decs]
+        cur = torch.cuda.current_stream(dev)
+
+        def run(count):
+            for k in range(count):
+                i = k % in_flight
+                with torch.cuda.stream(streams[i]):
+                    decs[i].batch_decide(ins, outs[i])
+
+        run(max(warmup, in_flight))
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        for st in streams:
+            st.wait_event(e0)
+        run(steps)
+        for st in streams:
+            e = torch.cuda.Event()
+            e.record(st)
+            cur.wait_event(e)
+        e1.record(cur)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        ps = decs[0].partitions(outs[0], nf)
+        assert all(p.status == 0 for p in ps)
+        # one frame per launch chain
+        one = torch.zeros(trs.PARTITION_BYTES, dtype=torch.uint8, device=dev)
+        for (l, pitch, W, H, bd, t, nn, lam) in ins[:4]:
+            decs[0].decide(l, pitch, W, H, bd, t, nn, lam, one)
+        torch.cuda.synchronize(dev)
+        reps = max(1, steps // 4)
+        e0.record(cur)
+        for _ in range(reps):
+            for (l, pitch, W, H, bd, t, nn, lam) in ins:
+                decs[0].decide(l, pitch, W, H, bd, t, nn, lam, one)
+        e1.record(cur)
+        torch.cuda.synchronize(dev)
+        plain_ms = e0.elapsed_time(e1)
+        assert bytes(decs[0].partitions(one)[0]) == bytes(ps[-1])  # the same decision alone and in the batch
+    finally:
+        for d in decs:
+            d.close()
+    return {"workload": f"{spec.width}x{spec.height}p{spec.bit_depth}, n={n}, lambda={LAMBDA}, k=3, "
+                        f"{nf} seeded frames",
+            "batched": {"value": nf * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+                        "frames_per_step": nf, "in_flight": in_flight,
+                        "form": "batched, CUDA graph, default launch shapes"},
+            "plain": {"value": nf * reps / (plain_ms / 1e3), "unit": UNIT, "form": "one frame per launch chain"}}
 
 
 def run_mixed(runtime, trs, items, device: int, steps: int, warmup: int, n_parts: int, in_flight: int):
@@ -209,23 +297,24 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(frames, budget_s: float = 12.0):
+def cpu_baseline(frames, budget_s: float = 12.0, bd: int = 10, n: int = N_REGIONS, lam: float = LAMBDA,
+                 what: str = "workload"):
     """The oracle (O2, one core) on a bounded sample of the same frames."""
     from oracle import oracle as O
     O.build()
     t0 = time.perf_counter()
     done = 0
     for plane, times in frames:
-        O.decide(plane, times, 10, N_REGIONS, LAMBDA)
+        O.decide(plane, times, bd, n, lam)
         done += 1
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
     return {"value": done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{done} of the {NFRAMES} workload frames, oracle texture + Q16 + exact DP search, 1 thread"}
+            "sample": f"{done} of the {len(frames)} {what} frames, oracle texture + Q16 + exact DP search, 1 thread"}
 
 
-def _oracle_worker_init(shm_name, shape_p, shape_t):
+def _oracle_worker_init(shm_name, shape_p, shape_t, bd, n, lam):
     global _W
     from multiprocessing import shared_memory
     from oracle import oracle as O
@@ -233,19 +322,20 @@ def _oracle_worker_init(shm_name, shape_p, shape_t):
     n_p = int(np.prod(shape_p)) * 2
     planes = np.ndarray(shape_p, dtype=np.uint16, buffer=shm.buf[:n_p])
     times = np.ndarray(shape_t, dtype=np.float32, buffer=shm.buf[n_p:n_p + int(np.prod(shape_t)) * 4])
-    _W = (shm, planes, times, O)
+    _W = (shm, planes, times, O, bd, n, lam)
 
 
 def _oracle_worker_decide(i: int) -> int:
-    shm, planes, times, O = _W
+    shm, planes, times, O, bd, n, lam = _W
     if i >= 0:
-        O.decide(planes[i], times[i], 10, N_REGIONS, LAMBDA)
+        plane = planes[i] if bd > 8 else planes[i].astype(np.uint8)
+        O.decide(plane, times[i], bd, n, lam)
     return i
 
 
-def cpu_baseline_all_cores(frames):
+def cpu_baseline_all_cores(frames, bd: int = 10, n: int = N_REGIONS, lam: float = LAMBDA, what: str = "workload"):
     """The oracle as it stands, one process per host core (spawned), each
-    deciding whole frames read from shared memory; wall-clock over all 64."""
+    deciding whole frames read from shared memory; wall-clock over all of them."""
     import multiprocessing as mp
     from multiprocessing import shared_memory
     planes = np.stack([np.ascontiguousarray(p) for p, _ in frames]).astype(np.uint16)
@@ -258,7 +348,8 @@ def cpu_baseline_all_cores(frames):
         ctx = mp.get_context("spawn")
         # bounded waits: a worker that cannot start is replaced by the pool
         # over and over, so an unbounded map would never return
-        with ctx.Pool(cores, initializer=_oracle_worker_init, initargs=(shm.name, planes.shape, times.shape)) as pool:
+        with ctx.Pool(cores, initializer=_oracle_worker_init,
+                      initargs=(shm.name, planes.shape, times.shape, bd, n, lam)) as pool:
             try:
                 pool.map_async(_oracle_worker_decide, [-1] * cores).get(timeout=180)  # workers up, oracle loaded
                 t0 = time.perf_counter()
@@ -270,15 +361,18 @@ def cpu_baseline_all_cores(frames):
         shm.close()
         shm.unlink()
     return {"value": len(frames) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"all {len(frames)} workload frames, oracle texture + Q16 + exact DP search, "
+            "sample": f"all {len(frames)} {what} frames, oracle texture + Q16 + exact DP search, "
                       f"{cores} spawned processes"}
 
 
-def run_serving(trs, device: int, duration_s: float = 7.0, saturate_s: float = 1.0):
+def run_serving(trs, device: int, duration_s: float = 7.0, saturate_s: float = 1.0,
+                sweep_fracs=(0.1, 0.5, 0.9), sweep_s: float = 2.0):
     """32 concurrent streams (half 1080p10 n=8, half 2160p10 n=16) with
     Poisson arrivals at U[30, 60] fps each, through the continuous-batching
     server.  Latency = wait before the server accepted the frame (both of the
-    stream's slots busy) + the server's submit-to-ready time."""
+    stream's slots busy) + the server's submit-to-ready time.  Then the
+    saturated rate (every stream keeps both slots busy) and the latency at
+    offered loads of 10, 50 and 90 % of it (all stream rates scaled alike)."""
     import collections
 
     import synth
@@ -314,34 +408,37 @@ def run_serving(trs, device: int, duration_s: float = 7.0, saturate_s: float = 1
         while got < len(sids):
             got += len(trs.trs_server_poll(srv, 64, 100_000))
 
-        # Poisson arrivals
-        lat = []
-        waiting = collections.deque()
-        accepted = {}
-        t0 = time.perf_counter()
-        k = 0
-        while k < len(arrivals) or waiting or accepted:
-            now = time.perf_counter() - t0
-            while k < len(arrivals) and arrivals[k][0] <= now:
-                waiting.append(arrivals[k])
-                k += 1
-            still = collections.deque()
-            for (ta, i, f) in waiting:
-                b, pitch = frame(i, f)
-                try:
-                    tk = trs.trs_server_submit(srv, sids[i], b, pitch)
-                    accepted[tk] = (time.perf_counter() - t0) - ta
-                except trs.TrsError as e:
-                    if e.status != trs.EBUSY:
-                        raise
-                    still.append((ta, i, f))
-            waiting = still
-            nxt = arrivals[k][0] - (time.perf_counter() - t0) if k < len(arrivals) else 0.0
-            for d in trs.trs_server_poll(srv, 64, int(max(50, min(2000, nxt * 1e6)))):
-                assert d.status == 0
-                lat.append(accepted.pop(d.ticket) * 1e3 + d.latency_us / 1e3)
-        elapsed = time.perf_counter() - t0
-        lat = np.array(lat)
+        def poisson_run(arr):
+            """Submits each arrival at its time; latency from arrival to ready (ms)."""
+            lat = []
+            waiting = collections.deque()
+            accepted = {}
+            t0 = time.perf_counter()
+            k = 0
+            while k < len(arr) or waiting or accepted:
+                now = time.perf_counter() - t0
+                while k < len(arr) and arr[k][0] <= now:
+                    waiting.append(arr[k])
+                    k += 1
+                still = collections.deque()
+                for (ta, i, f) in waiting:
+                    b, pitch = frame(i, f)
+                    try:
+                        tk = trs.trs_server_submit(srv, sids[i], b, pitch)
+                        accepted[tk] = (time.perf_counter() - t0) - ta
+                    except trs.TrsError as e:
+                        if e.status != trs.EBUSY:
+                            raise
+                        still.append((ta, i, f))
+                waiting = still
+                nxt = arr[k][0] - (time.perf_counter() - t0) if k < len(arr) else 0.0
+                for d in trs.trs_server_poll(srv, 64, int(max(50, min(2000, nxt * 1e6)))):
+                    assert d.status == 0
+                    lat.append(accepted.pop(d.ticket) * 1e3 + d.latency_us / 1e3)
+            return np.array(lat), time.perf_counter() - t0
+
+        # Poisson arrivals at the workload's rates
+        lat, elapsed = poisson_run(arrivals)
 
         # saturation: every stream keeps both request slots busy
         done = 0
@@ -360,11 +457,25 @@ def run_serving(trs, device: int, duration_s: float = 7.0, saturate_s: float = 1
         while trs.trs_server_info(srv).inflight:
             done += len(trs.trs_server_poll(srv, 64, 10_000))
         sat_dt = time.perf_counter() - t1
+        saturated = done / sat_dt
+        # latency under load: the same streams, every rate scaled so that the
+        # offered load is a fraction of the saturated rate
+        natural = sum(st.fps for st in streams)
+        sweep = []
+        for frac in sweep_fracs:
+            scale = frac * saturated / natural
+            scaled = [synth.StreamSpec(st.stream, st.spec, st.n_regions, st.fps * scale) for st in streams]
+            arr = synth.poisson_arrivals(scaled, sweep_s, seed=60 + int(frac * 100))
+            sl, sdt = poisson_run(arr)
+            sweep.append({"offered_frac_of_saturated": frac, "offered_per_s": len(arr) / sweep_s,
+                          "achieved_per_s": len(sl) / sdt, "decisions": int(len(sl)),
+                          "p50_ms": float(np.percentile(sl, 50)), "p99_ms": float(np.percentile(sl, 99)),
+                          "max_ms": float(sl.max())})
         info = trs.trs_server_info(srv)
         return {"streams": len(sids), "offered_per_s": len(arrivals) / duration_s,
                 "decisions": int(len(lat)), "achieved_per_s": len(lat) / elapsed,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "max_ms": float(lat.max()), "saturated_per_s": done / sat_dt,
+                "max_ms": float(lat.max()), "saturated_per_s": saturated, "load_sweep": sweep,
                 "mean_batch": info.frames / max(1, info.batches), "device_bytes": int(info.mem_used_bytes),
                 "form": "continuous batching, 3 batches in flight on separate CUDA streams"}
     finally:
@@ -374,8 +485,8 @@ def run_serving(trs, device: int, duration_s: float = 7.0, saturate_s: float = 1
 def run_multi_tile(runtime, trs, device: int, reps: int = 50, ns=(6, 7)):
     """Multi-tile rectangular slices (trs_search_mt) on one 1920x1080 frame:
     the slice-set list is built on the host once per shape (timed apart), then
-    the device search (three passes over the list, one decode warp) is timed
-    alone with CUDA events on its stream."""
+    the device search (one graph: two passes over the list, one decode warp)
+    is timed alone with CUDA events on its stream."""
     import torch
     import synth
     spec = synth.SPEC_1080P10
@@ -414,20 +525,21 @@ def run_multi_tile(runtime, trs, device: int, reps: int = 50, ns=(6, 7)):
                         "slice_sets": rec.candidates, "list_build_s": round(build_s, 3),
                         "ms_per_search": ms, "searches_per_s": 1e3 / ms,
                         "slice_sets_per_s": rec.candidates / (ms / 1e3),
-                        "list_read_gbs": 3 * list_bytes / (ms / 1e3) / 1e9,
-                        "launches_per_search": 4, "t_min_multi_tile": rec.t_min,
+                        "list_read_gbs": 2 * list_bytes / (ms / 1e3) / 1e9,
+                        "launches_per_search": 1, "t_min_multi_tile": rec.t_min,
                         "t_min_single_tile_row": one.t_min, "q_multi_tile": rec.q, "q_single_tile_row": one.q})
     finally:
         dec.close()
-    return {"searches": res, "note": "list read three times per search (L2-resident at these sizes); "
-                                     "memset + 3 passes + decode per search"}
+    return {"searches": res,
+            "note": "one graph launch per search: argument copy, T_min reset, two passes over the list "
+                    "(L2-resident at these sizes), decode; list_read_gbs counts two reads of the list"}
 
 
 def run_reference(args, rank, world):
     """Reference arm: the oracle timed on this host's cores, same metric."""
     if rank != 0:
         return
-    frames, _ = make_inputs(min(NFRAMES, 8))
+    frames, _, _ = make_inputs(min(NFRAMES, 8))
     from oracle import oracle as O
     O.build()
     per_step = 2  # frames per step: a bounded sample, ~0.4 s of CPU work
@@ -463,6 +575,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 832x480 n=4 and 1920x1080 n=8 configurations")
     ap.add_argument("--no-light", action="store_true")
     ap.add_argument("--no-mt", action="store_true", help="skip the multi-tile slice search timing")
     ap.add_argument("--mt-only", action="store_true",
@@ -489,11 +603,12 @@ def main():
         import __graft_entry__
         __graft_entry__.build()
         from paper_2012_14792_gb300 import runtime, trs
-        print(json.dumps({"multi_tile": run_multi_tile(runtime, trs, local, reps=5, ns=(7,))}), flush=True)
+        print(json.dumps({"multi_tile": run_multi_tile(runtime, trs, local, reps=50, ns=(6, 7))}), flush=True)
         return
 
     nfr = args.frames
-    frames, mixed = make_inputs(nfr, mixed=not args.no_mixed)  # spawn pool, before any CUDA call
+    # spawn pool, before any CUDA call
+    frames, mixed, cfg_frames = make_inputs(nfr, mixed=not args.no_mixed, configs=not args.no_configs)
 
     import torch
     torch.cuda.set_device(local)
@@ -680,35 +795,56 @@ def main():
            "form": f"trs_batch_decide_host from pinned host buffers, {args.in_flight} host threads with a "
                    "context and stream each"}
 
-    # --- roofline -----------------------------------------------------------
+    # --- rooflines: every kernel of the step, from the one-chunk stage times -
     hbm, sm_max, src = peaks()
     tex_bytes = sum(p.numel() for p in pinned[:stage_frames])  # each luma sample read once
-    tex_ms = stage.get("texture", 0.0)
-    tex_gbs = tex_bytes / (tex_ms / 1e3) / 1e9 if tex_ms > 0 else 0.0
     row_relax, col_relax = trs.trs_plan_work(3840, 2160, N_REGIONS)
-    # each DP transition is one combine (max or +) and one minimum: 2 INT32 operations
-    # (step 1 runs on 32-bit values for these frames); the peak is this GPU's
-    # measured INT32 add/min/max throughput
+    # each DP transition is one combine (max or +) and one minimum: 2 INT32
+    # operations (step 1 runs on 32-bit values for these frames); the peak is
+    # this GPU's measured INT32 add/min/max throughput
     alu_peak = trs.trs_alu_peak(local) / 1e12  # T INT32 ops / s
-    kinds = {"step1_rows": row_relax, "step2_rows": row_relax, "step1_columns": col_relax,
-             "step2_columns": col_relax}
+    lay = trs.trs_tables_layout_get(3840, 2160)
+    # the tables kernel writes every slice's time and floor SSE (2 x 8 bytes), the
+    # Q16 times and three SATs, and reads the statistics and the time map
+    C_, R_ = lay.cols, lay.rows
+    tab_bytes = stage_frames * (lay.bands * R_ * (R_ + 1) // 2 * 16 + C_ * R_ * (4 + 4 + 8 + 4 + 4)
+                                + 3 * (C_ + 1) * (R_ + 1) * 8)
+    stage_sum = sum(stage.values()) if stage else 0.0
     kernels = {"texture": "texture_kernel", "tables": "tables_kernel", "step1_rows": "band_kernel<1>",
                "step1_columns": "column_kernel<1>", "step2_rows": "band_kernel<2>",
                "step2_columns": "column_kernel<2>", "rebuild": "rebuild_kernel", "decode": "finish_kernel"}
-    dominant = max(stage, key=stage.get) if stage else "texture"
-    traffic = ncu_traffic(dominant, stage_frames)
-    if dominant == "texture":
-        roof = {"kernel": kernels[dominant], "bound": "hbm", "achieved": tex_gbs, "peak": hbm, "unit": "GB/s",
-                "frac": tex_gbs / hbm, "traffic": traffic, "algorithmic_bytes": tex_bytes, "peak_source": src}
-    else:
-        ops = 2.0 * kinds.get(dominant, row_relax + col_relax) * stage_frames
-        ach = ops / (stage[dominant] / 1e3) / 1e12
-        roof = {"kernel": kernels[dominant], "bound": "alu", "achieved": ach, "peak": alu_peak,
-                "unit": "T INT32 ops/s", "frac": ach / alu_peak, "traffic": traffic, "algorithmic_ops": ops,
+
+    def hbm_roof(kind, nbytes):
+        gbs = nbytes / (stage[kind] / 1e3) / 1e9
+        return {"kernel": kernels[kind], "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                "frac": gbs / hbm, "traffic": ncu_traffic(kind, stage_frames), "algorithmic_bytes": nbytes,
+                "ms": stage[kind], "share": stage[kind] / stage_sum, "peak_source": src}
+
+    def alu_roof(kind, work, note):
+        ops = 2.0 * work * stage_frames
+        ach = ops / (stage[kind] / 1e3) / 1e12
+        return {"kernel": kernels[kind], "bound": "alu", "achieved": ach, "peak": alu_peak,
+                "unit": "T INT32 ops/s", "frac": ach / alu_peak, "traffic": ncu_traffic(kind, stage_frames),
+                "algorithmic_ops": ops, "work": note, "ms": stage[kind], "share": stage[kind] / stage_sum,
                 "peak_source": "measured: trs_alu_peak (32-bit add/min/max chains on every SM)"}
-    tex_roof = {"kernel": "texture_kernel", "bound": "hbm", "achieved": tex_gbs, "peak": hbm, "unit": "GB/s",
-                "frac": tex_gbs / hbm, "traffic": ncu_traffic("texture", stage_frames), "algorithmic_bytes": tex_bytes,
-                "peak_source": src}
+
+    rooflines = [
+        hbm_roof("texture", tex_bytes),
+        hbm_roof("tables", tab_bytes),
+        alu_roof("step1_rows", row_relax, "trs_plan_work row_relax x 2 ops x frames"),
+        alu_roof("step1_columns", col_relax, "trs_plan_work col_relax x 2 ops x frames"),
+        alu_roof("step2_rows", row_relax, "trs_plan_work row_relax x 2 ops x frames; step 2 skips the items "
+                                          "of windows that break Eq. 4, so this over-counts its work"),
+        alu_roof("step2_columns", col_relax, "trs_plan_work col_relax x 2 ops x frames; over-counts like step-2 "
+                                             "rows"),
+    ] + [{"kernel": kernels[k], "bound": "latency", "ms": stage[k], "share": stage[k] / stage_sum,
+          "note": "one dependent warp chain per frame or tied window: no throughput roofline"}
+         for k in ("rebuild", "decode")]
+    by_name = {r["kernel"]: r for r in rooflines}
+    roof = dict(by_name[ROOFLINE_KERNEL])  # a fixed kernel: the search family's largest, by measurement
+    tex_roof = by_name["texture_kernel"]
+    search_keys = ("step1_rows", "step1_columns", "step2_rows", "step2_columns", "rebuild", "decode")
+    search_share = sum(stage[k] for k in search_keys) / stage_sum if stage_sum else None
 
     # the candidate space the exact search covers (distinct partitions of S(n), one tile row)
     space = trs.trs_count_partitions(3840, 2160, N_REGIONS)
@@ -735,10 +871,26 @@ def main():
         except Exception as e:  # a secondary figure: report it, keep the headline line
             multi_tile = {"error": f"{type(e).__name__}: {e}"}
 
+    configs_res = None
+    if cfg_frames is not None:
+        import synth
+        configs_res = {}
+        for key, (name, n_cfg) in CONFIGS.items():
+            configs_res[key] = run_config(runtime, trs, getattr(synth, name), n_cfg, cfg_frames[key], local,
+                                          max(5, args.steps // 4), args.warmup, args.in_flight)
+
     cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(frames)
         cpu_all = cpu_baseline_all_cores(frames)
+        if configs_res:
+            import synth
+            for key, (name, n_cfg) in CONFIGS.items():
+                bd = getattr(synth, name).bit_depth
+                configs_res[key]["cpu_baseline"] = cpu_baseline(cfg_frames[key], 3.0, bd, n_cfg, LAMBDA,
+                                                                "configuration")
+                configs_res[key]["cpu_baseline_all_cores"] = cpu_baseline_all_cores(cfg_frames[key], bd, n_cfg,
+                                                                                    LAMBDA, "configuration")
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -757,6 +909,9 @@ def main():
                 "serving": serving, "multi_tile": multi_tile,
                 "clocks": clk.summary(), "e2e": e2e,
                 "gpu_launches": launches, "roofline": roof, "roofline_texture": tex_roof,
+                "rooflines": rooflines, "search_share_of_stage_sum": search_share,
+                "config_480p8_n4": configs_res.get("config_480p8_n4") if configs_res else None,
+                "config_1080p10_n8": configs_res.get("config_1080p10_n8") if configs_res else None,
                 "search_space": search_space,
                 "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all}
         print(json.dumps(line), flush=True)

@@ -136,6 +136,7 @@ def lib():
         _lib.oracle_mt_search.argtypes = [ct.c_int, ct.c_int, u64p, u64p, u64p, u32p, ct.c_int, ct.c_int,
                                           ct.c_uint32, ct.POINTER(_MtResult)]
         _lib.oracle_mt_count.argtypes = [ct.c_int, ct.c_int, ct.c_int, ct.c_int, u64p]
+        _lib.oracle_mt_search_rects.argtypes = _lib.oracle_mt_search.argtypes
         _lib.oracle_mt_result_size.restype = ct.c_size_t
         assert _lib.oracle_mt_result_size() == ct.sizeof(_MtResult)
     return _lib
@@ -321,6 +322,19 @@ def mt_count(width: int, height: int, n: int, k_area: int = 3) -> int:
     if st != OK:
         raise ValueError(f"oracle_mt_count status {st}")
     return int(out[0])
+
+
+def mt_search_rects(st: Stats, Tq: np.ndarray, n: int, lam: float = 0.0, k_area: int = 3) -> dict:
+    """The multi-tile search over the partitions of the CTU grid into n
+    rectangles (the same space as mt_search, enumerated directly; full frame
+    sizes for small n).  Adds count = the number of slice sets."""
+    S1, S2, N, T = _search_args(st, Tq)
+    r = _MtResult()
+    lib().oracle_mt_search_rects(st.width, st.height, _p64(S1), _p64(S2), _p64(N), _p32(T), n, k_area,
+                                 lambda_q(lam), ct.byref(r))
+    regions = [tuple(int(v) for v in r.region[i]) for i in range(n)] if r.status == OK else []
+    return dict(status=r.status, t_min=r.t_min, thr=r.thr, t=r.t, q=r.q, regions=regions, sse=r.sse_real,
+                count=int(r.n_sets))
 
 
 def mt_search(st: Stats, Tq: np.ndarray, n: int, lam: float = 0.0, k_area: int = 3) -> dict:

@@ -28,6 +28,9 @@
  *                       rectangles of whole tiles), enumerated (Sec. 1, Fig. 1b):
  *                       every tile grid, its tiles grouped into rectangles
  *   oracle_mt_count     the number of distinct slice sets of that space
+ *   oracle_mt_search_rects  the same search over the partitions of the CTU
+ *                       grid into n rectangles (the same space), reaching
+ *                       full frame sizes for small n
  *   oracle_evaluate,    T, Q and the area extremes of a given partition or
  *   oracle_rect,        rectangle, or of every CTU rectangle, by direct sums
  *   oracle_rect_all     (checkers for the tests)
@@ -960,6 +963,7 @@ typedef struct {
     int16_t *keys;                   /* count mode: n*4 entries per slice set */
     size_t nkeys, capkeys;
     int oom;
+    uint64_t n_sets;                 /* rectangle partitions visited (oracle_mt_search_rects) */
 } mt_t;
 
 static int key_cmp4(const int *a, const int *b) {
@@ -1302,6 +1306,131 @@ int oracle_rect_all(int W, int H, const uint64_t *S1, const uint64_t *S2, const 
                     t_out[i] = r.T;
                     q_out[i] = sse_floor(r.S1, r.S2, r.N);
                 }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* The multi-tile space again, as the partitions of the CTU grid into n
+   rectangles (a grid with a line at every slice edge makes each rectangle a
+   group of whole tiles, so this is the same set of slice sets as
+   oracle_mt_search enumerates through tile grids; the tests check both
+   against each other).  Reaches full frame sizes for small n.
+
+   Every partition is made once: the first free CTU in raster order is the
+   top-left corner of the next rectangle, whose width and then height grow.
+   A partial set is not extended once its areas break k*A_min > A_max, or
+   once the rest of the frame cannot be cut into the remaining rectangles
+   under the rule (each of them needs an area s with k*s > A_max and
+   s < k*A_min of the rectangles so far); no completion of it is valid. */
+
+static uint64_t mtr_px(int i, int cells, int extent) {
+    int e = i * OR_CTU;
+    (void)cells;
+    return (uint64_t)(e < extent ? e : extent);
+}
+
+static void mtr_rec(mt_t *e, uint64_t *freem, uint64_t rest, uint64_t amin, uint64_t amax) {
+    const frame_t *f = e->f;
+    int y = 0;
+    while (y < f->R && freem[y] == 0) ++y;
+    int left = e->n - e->ns;
+    if (y == f->R) {
+        if (left == 0) {
+            if (e->mode == 0) e->n_sets++;
+            mt_evaluate(e);
+        }
+        return;
+    }
+    if (left == 0) return;
+    if (e->ns > 0 && !((u128)e->k_area * rest > (u128)left * amax &&
+                       (u128)rest < (u128)left * (u128)e->k_area * amin))
+        return;
+    int x = 0;
+    while (!((freem[y] >> x) & 1u)) ++x;
+    for (int x1 = x + 1; x1 <= f->C && ((freem[y] >> (x1 - 1)) & 1u); ++x1) {
+        uint64_t bits = (x1 == 64 ? ~0ull : ((1ull << x1) - 1)) & ~((1ull << x) - 1);
+        for (int y1 = y + 1; y1 <= f->R && (freem[y1 - 1] & bits) == bits; ++y1) {
+            uint64_t a = (mtr_px(x1, f->C, f->W) - mtr_px(x, f->C, f->W)) *
+                         (mtr_px(y1, f->R, f->H) - mtr_px(y, f->R, f->H));
+            uint64_t lo = a < amin ? a : amin, hi = a > amax ? a : amax;
+            if (!((u128)e->k_area * lo > (u128)hi)) continue;
+            for (int yy = y; yy < y1; ++yy) freem[yy] ^= bits;
+            e->rect[e->ns][0] = x;
+            e->rect[e->ns][1] = x1;
+            e->rect[e->ns][2] = y;
+            e->rect[e->ns][3] = y1;
+            e->ns++;
+            mtr_rec(e, freem, rest - a, lo, hi);
+            e->ns--;
+            for (int yy = y; yy < y1; ++yy) freem[yy] ^= bits;
+        }
+    }
+}
+
+static void mtr_all(mt_t *e) {
+    const frame_t *f = e->f;
+    uint64_t freem[OR_MAX_R];
+    for (int y = 0; y < f->R; ++y) freem[y] = f->C == 64 ? ~0ull : ((1ull << f->C) - 1);
+    e->ns = 0;
+    mtr_rec(e, freem, (uint64_t)f->W * (uint64_t)f->H, OR_INF, 0);
+}
+
+/* The multi-tile search over the rectangle partitions: T_min (Eq. 3), then
+   the smallest (Q, raster-ordered slice list) under Eq. 4, as
+   oracle_mt_search; res->n_sets is the number of slice sets. */
+int oracle_mt_search_rects(int W, int H, const uint64_t *S1, const uint64_t *S2, const uint64_t *N,
+                           const uint32_t *Tq, int n, int k_area, uint32_t lambda_q, oracle_mt_result *res) {
+    memset(res, 0, sizeof(*res));
+    frame_t f = {W, H, (W + OR_CTU - 1) / OR_CTU, (H + OR_CTU - 1) / OR_CTU, S1, S2, N, Tq};
+    memo_t m;
+    if (memo_init(&m, &f)) {
+        memo_free(&m);
+        res->status = OR_ENOMEM;
+        return OR_ENOMEM;
+    }
+    mt_t e;
+    int st = check_inputs(W, H, n, k_area);
+    if (st) {
+        memo_free(&m);
+        res->status = st;
+        return st;
+    }
+    memset(&e, 0, sizeof(e));
+    e.f = &f;
+    e.m = &m;
+    e.n = n;
+    e.k_area = k_area;
+    e.C = f.C;
+    e.R = f.R;
+    e.mode = 0;
+    e.t_min = OR_INF;
+    mtr_all(&e);
+    res->n = n;
+    res->n_sets = e.n_sets;
+    if (e.t_min == OR_INF) {
+        memo_free(&m);
+        res->status = OR_EINFEASIBLE;
+        return OR_EINFEASIBLE;
+    }
+    e.thr = eq4_thr(e.t_min, lambda_q);
+    e.mode = 1;
+    mtr_all(&e);
+    res->t_min = e.t_min;
+    res->thr = e.thr;
+    res->t = e.best_t;
+    res->q = e.best_q;
+    long double sse = 0.0L;
+    for (int i = 0; i < n; ++i) {
+        res->region[i][0] = (int16_t)e.best_key[i][1];
+        res->region[i][1] = (int16_t)e.best_key[i][0];
+        res->region[i][2] = (int16_t)e.best_key[i][3];
+        res->region[i][3] = (int16_t)e.best_key[i][2];
+        rsum_t s = memo_get(&m, e.best_key[i][1], e.best_key[i][3], e.best_key[i][0], e.best_key[i][2]);
+        sse += sse_exact(s.S1, s.S2, s.N);
+    }
+    res->sse_real = (double)sse;
+    memo_free(&m);
+    res->status = OR_OK;
     return OR_OK;
 }
 

@@ -238,11 +238,8 @@ int trs_destroy(trs_ctx *c) {
         dev_free(p.second->blob);
         delete p.second;
     }
-    for (auto &m : c->mt) {
-        dev_free(m.second->cands);
-        delete m.second;
-    }
-    dev_free(c->mt_scal);
+    for (auto &m : c->mt) mt_free(m.second);
+    if (c->mt_cap) cudaStreamDestroy(c->mt_cap);
     DevBuf *bufs[] = {&c->s1, &c->s2, &c->cnt, &c->vmax, &c->flags, &c->tables, &c->scratch, &c->scal,
                       &c->part, &c->luma_stage, &c->time_stage, &c->arena, &c->desc,
                       &c->hb_luma, &c->hb_time, &c->hb_out};

@@ -62,10 +62,27 @@ constexpr int kChunkMin = 4;         // fewest frames in a chunk
 }  // namespace trs
 
 namespace trs {
-// The multi-tile candidate list of one frame shape, on the device.
+// Per-call arguments of a multi-tile search, read by its kernels from device memory.
+struct MtCall {
+    const uint8_t *tables;
+    trs_mt_partition *out;
+    uint32_t lambda_q;
+    uint32_t reserved;
+};
+
+// The multi-tile candidate list of one frame shape, on the device, and the
+// captured graphs of its search: kMtSlots copies, each copying the per-call
+// arguments from its own pinned block, used in turn so that a call waits
+// only for the call kMtSlots before it to have read its block.
+constexpr int kMtSlots = 4;
 struct MtEntry {
-    DevBuf cands;        // count * n * 4 bytes: (y0, x0, y1, x1) per slice, raster order
+    DevBuf cands;        // count * n words: slice i of set c at i * count + c, its rectangle-table entry
     int64_t count = 0;
+    DevBuf work;         // MtCall, T_min, and the second pass's per-block (Q, set) minima
+    MtCall *call_host = nullptr;  // pinned, kMtSlots blocks
+    cudaGraphExec_t graph[kMtSlots] = {};
+    cudaEvent_t copied[kMtSlots] = {};  // graph s has read call_host[s]
+    int next = 0;
 };
 }  // namespace trs
 
@@ -97,7 +114,7 @@ struct trs_ctx {
     std::map<std::vector<int64_t>, trs::BatchGraph> graphs;
     // multi-tile search: candidate lists by (W, H, n), and its three result words
     std::map<std::tuple<int, int, int>, trs::MtEntry *> mt;
-    trs::DevBuf mt_scal;
+    cudaStream_t mt_cap = nullptr;  // capture stream of the multi-tile graphs
 };
 
 namespace trs {
@@ -146,6 +163,9 @@ cudaError_t batch_enqueue(const BatchLaunch &bl, cudaStream_t cs, cudaEvent_t co
 // once the texture kernel is enqueued.
 cudaError_t batch_enqueue_work(const BatchLaunch &bl, cudaStream_t cs, cudaEvent_t *stage, cudaEvent_t after_texture);
 
+
+// Releases a multi-tile entry (device list, work area, pinned block, graph).
+void mt_free(MtEntry *me);
 
 // Decides nf frames described by device pointers in one launch of each
 // kernel on `stream`, through a cached CUDA graph or by direct launches.

@@ -304,14 +304,16 @@ int mt_enumerate(int W, int H, int n, int k, std::vector<uint8_t> *keys, int64_t
 
 namespace {
 
+constexpr int kMtThreads = 256;
+constexpr int kMtBlocks = 152 * 8;  // at most this many blocks per pass (grid-stride beyond)
+
 struct MtArgs {
-    const uint8_t *cands;  // count * n * 4 bytes: (y0, x0, y1, x1) per slice
+    const uint32_t *ent;  // slice i of set c at ent[i * count + c]: its rectangle-table entry index
     int64_t count;
-    int n, C, R, W, H;
-    const uint8_t *tables;
-    uint64_t *scal;        // [0] T_min, [1] Q*, [2] first slice set reaching Q*
-    uint32_t lambda_q;
-    trs_mt_partition *out;
+    int n, C, R, W, H, nblocks;
+    const MtCall *call;   // tables, output, lambda of this call
+    uint64_t *tmin;       // T_min: +infinity before the first pass (set at creation, reset by each decode)
+    uint64_t *part;       // [nblocks][2]: each block's smallest (Q, set) of the second pass
 };
 
 __device__ __forceinline__ uint64_t warp_min64(uint64_t v) {
@@ -323,60 +325,137 @@ __device__ __forceinline__ uint64_t warp_min64(uint64_t v) {
     return v;
 }
 
-// Time (max over slices, Eq. 1) and quality term (sum, Eq. 2) of slice set c.
+// The smaller of (q, c) and the pair in lane ^ o, Q first, then the list index.
+__device__ __forceinline__ void pair_min_xor(uint64_t &q, uint64_t &c, int o) {
+    const uint64_t q2 = __shfl_xor_sync(0xffffffffu, q, o), c2 = __shfl_xor_sync(0xffffffffu, c, o);
+    if (q2 < q || (q2 == q && c2 < c)) {
+        q = q2;
+        c = c2;
+    }
+}
+
+// Time (max over slices, Eq. 1) and quality term (sum, Eq. 2) of slice set
+// c; the slice-major list makes each of the n loads coalesced over the
+// threads of a warp.
 __device__ __forceinline__ void mt_eval(const MtArgs &a, const uint64_t *RT, const uint64_t *RQ, int64_t c,
-                                        uint64_t *tmax, uint64_t *qsum) {
-    const uint8_t *s = a.cands + (size_t)c * a.n * 4;
+                                        uint64_t *tmax, uint64_t *qsum, bool with_q) {
     uint64_t t = 0, q = 0;
-    for (int i = 0; i < a.n; ++i) {
-        const int y0 = s[4 * i], x0 = s[4 * i + 1], y1 = s[4 * i + 2], x1 = s[4 * i + 3];
-        const size_t e = ((size_t)band_index(a.C, x0, x1) * a.R + (y1 - y0 - 1)) * a.R + y0;
-        const uint64_t tv = RT[e];
-        t = tv > t ? tv : t;
-        q += RQ[e];
+    // eight slices at a time: their index loads, then their table gathers,
+    // each group in flight together
+    for (int i0 = 0; i0 < a.n; i0 += 8) {
+        uint32_t e[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) e[u] = i0 + u < a.n ? __ldg(a.ent + (size_t)(i0 + u) * a.count + c) : 0u;
+        uint64_t tv[8], qv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            tv[u] = i0 + u < a.n ? __ldg(RT + e[u]) : 0ull;
+            qv[u] = with_q && i0 + u < a.n ? __ldg(RQ + e[u]) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            t = tv[u] > t ? tv[u] : t;
+            q += qv[u];
+        }
     }
     *tmax = t;
     *qsum = q;
 }
 
-// PASS 0: T_min; PASS 1: Q* among sets within Eq. 4's bound; PASS 2: the
-// first set (list order) within the bound reaching Q*.  Grid-stride loop,
-// per-thread minima, one warp reduction and one atomic per warp.
-template <int PASS>
-__global__ void __launch_bounds__(256) mt_pass_kernel(MtArgs a) {
+// Pass 1: T_min (Eq. 3).  Grid-stride loop, per-thread minima, one warp
+// reduction and one atomic minimum per warp.
+__global__ void __launch_bounds__(kMtThreads) mt_tmin_kernel(MtArgs a) {
+    const MtCall call = *a.call;
     const TablesOffsets off = tables_offsets(a.C, a.R);
-    if (reinterpret_cast<const int32_t *>(a.tables + off.status)[0] != TRS_OK) return;
-    const uint64_t *RT = reinterpret_cast<const uint64_t *>(a.tables + off.rect_t);
-    const uint64_t *RQ = reinterpret_cast<const uint64_t *>(a.tables + off.rect_q);
-    const uint64_t thr = PASS == 0 ? kInf : eq4_threshold(a.scal[0], a.lambda_q);
-    const uint64_t qstar = PASS == 2 ? a.scal[1] : kInf;
+    if (reinterpret_cast<const int32_t *>(call.tables + off.status)[0] != TRS_OK) return;
+    const uint64_t *RT = reinterpret_cast<const uint64_t *>(call.tables + off.rect_t);
     uint64_t best = kInf;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < a.count; c += stride) {
         uint64_t t, q;
-        mt_eval(a, RT, RQ, c, &t, &q);
-        if (PASS == 0) {
-            best = t < best ? t : best;
-        } else if (t <= thr) {
-            if (PASS == 1) best = q < best ? q : best;
-            else if (q == qstar && (uint64_t)c < best) best = (uint64_t)c;
-        }
+        mt_eval(a, RT, nullptr, c, &t, &q, false);
+        best = t < best ? t : best;
     }
     best = warp_min64(best);
     if ((threadIdx.x & 31) == 0 && best != kInf)
-        atomicMin(reinterpret_cast<unsigned long long *>(&a.scal[PASS]), (unsigned long long)best);
+        atomicMin(reinterpret_cast<unsigned long long *>(a.tmin), (unsigned long long)best);
 }
 
-// One warp: lane i decodes slice i of the winner.
+// Pass 2: among the sets within Eq. 4's bound, the smallest (Q, list
+// index) -- Q* (Eq. 2) and the first set reaching it in one go; each block
+// stores its own minimum, the decode kernel reduces them.
+__global__ void __launch_bounds__(kMtThreads) mt_q_kernel(MtArgs a) {
+    __shared__ uint64_t wq[kMtThreads / 32], wc[kMtThreads / 32];
+    const MtCall call = *a.call;
+    const TablesOffsets off = tables_offsets(a.C, a.R);
+    uint64_t bq = kInf, bc = kInf;
+    if (reinterpret_cast<const int32_t *>(call.tables + off.status)[0] == TRS_OK) {
+        const uint64_t *RT = reinterpret_cast<const uint64_t *>(call.tables + off.rect_t);
+        const uint64_t *RQ = reinterpret_cast<const uint64_t *>(call.tables + off.rect_q);
+        const uint64_t thr = eq4_threshold(*a.tmin, call.lambda_q);
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < a.count; c += stride) {
+            uint64_t t, q;
+            mt_eval(a, RT, RQ, c, &t, &q, true);
+            if (t <= thr && q < bq) {  // c grows, so the first set at a thread's minimum is kept
+                bq = q;
+                bc = (uint64_t)c;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pair_min_xor(bq, bc, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        wq[w] = bq;
+        wc[w] = bc;
+    }
+    __syncthreads();
+    if (w == 0) {
+        bq = lane < (int)(blockDim.x >> 5) ? wq[lane] : kInf;
+        bc = lane < (int)(blockDim.x >> 5) ? wc[lane] : kInf;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pair_min_xor(bq, bc, o);
+        if (lane == 0) {
+            a.part[2 * blockIdx.x] = bq;
+            a.part[2 * blockIdx.x + 1] = bc;
+        }
+    }
+}
+
+// One warp: the smallest (Q, set) over the blocks of pass 2, then lane i
+// decodes slice i of the winner from its rectangle-table entry.
 __global__ void __launch_bounds__(32) mt_finish_kernel(MtArgs a) {
     const int lane = threadIdx.x;
-    trs_mt_partition *out = a.out;
+    const MtCall call = *a.call;
+    trs_mt_partition *out = call.out;
     uint64_t *words = reinterpret_cast<uint64_t *>(out);
     for (int i = lane; i < (int)(sizeof(trs_mt_partition) / 8); i += 32) words[i] = 0;
+    uint64_t qstar = kInf, win = kInf;
+    // eight blocks' pairs per lane in flight at a time
+    for (int b0 = 0; b0 < a.nblocks; b0 += 8 * 32) {
+        uint64_t pq[8], pc[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int b = b0 + u * 32 + lane;
+            pq[u] = b < a.nblocks ? a.part[2 * b] : kInf;
+            pc[u] = b < a.nblocks ? a.part[2 * b + 1] : kInf;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (pq[u] < qstar || (pq[u] == qstar && pc[u] < win)) {
+                qstar = pq[u];
+                win = pc[u];
+            }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pair_min_xor(qstar, win, o);
     __syncwarp();
     const TablesOffsets off = tables_offsets(a.C, a.R);
-    int32_t status = reinterpret_cast<const int32_t *>(a.tables + off.status)[0];
-    const uint64_t t_min = a.scal[0], win = a.scal[2];
+    int32_t status = reinterpret_cast<const int32_t *>(call.tables + off.status)[0];
+    const uint64_t t_min = a.count > 0 ? *a.tmin : kInf;
+    __syncwarp();
+    if (lane == 0) *a.tmin = kInf;  // reset for the next search of this shape (calls are stream-ordered)
     if (status == TRS_OK && (t_min == kInf || win >= (uint64_t)a.count)) status = TRS_EINFEASIBLE;
     if (status != TRS_OK) {
         if (lane == 0) {
@@ -387,18 +466,24 @@ __global__ void __launch_bounds__(32) mt_finish_kernel(MtArgs a) {
         }
         return;
     }
-    const uint64_t *RT = reinterpret_cast<const uint64_t *>(a.tables + off.rect_t);
-    const uint64_t *RQ = reinterpret_cast<const uint64_t *>(a.tables + off.rect_q);
-    const uint64_t *sat1 = reinterpret_cast<const uint64_t *>(a.tables + off.sat_s1);
+    const uint64_t *RT = reinterpret_cast<const uint64_t *>(call.tables + off.rect_t);
+    const uint64_t *RQ = reinterpret_cast<const uint64_t *>(call.tables + off.rect_q);
+    const uint64_t *sat1 = reinterpret_cast<const uint64_t *>(call.tables + off.sat_s1);
     uint64_t t = 0, q = 0;
     double sse = 0.0;
     if (lane < a.n) {
-        const uint8_t *s = a.cands + ((size_t)win * a.n + lane) * 4;
-        const int y0 = s[0], x0 = s[1], y1 = s[2], x1 = s[3];
-        const size_t e = ((size_t)band_index(a.C, x0, x1) * a.R + (y1 - y0 - 1)) * a.R + y0;
+        const uint32_t e = a.ent[(size_t)lane * a.count + win];
+        // e = (band * R + (y1 - y0 - 1)) * R + y0, band = band_index(C, x0, x1)
+        const int R = a.R, C = a.C;
+        const int y0 = (int)(e % (uint32_t)R);
+        const int y1 = y0 + 1 + (int)((e / (uint32_t)R) % (uint32_t)R);
+        const int b = (int)(e / ((uint32_t)R * (uint32_t)R));
+        int x0 = 0;
+        while (x0 + 1 < C && band_index(C, x0 + 1, x0 + 2) <= b) ++x0;
+        const int x1 = x0 + 1 + (b - band_index(C, x0, x0 + 1));
         t = RT[e];
         q = RQ[e];
-        const int C1 = a.C + 1;
+        const int C1 = C + 1;
         const uint64_t s1 = sat1[y1 * C1 + x1] - sat1[y0 * C1 + x1] - sat1[y1 * C1 + x0] + sat1[y0 * C1 + x0];
         const uint32_t np = (line_px(x1, a.W) - line_px(x0, a.W)) * (line_px(y1, a.H) - line_px(y0, a.H));
         uint32_t rem;
@@ -421,18 +506,113 @@ __global__ void __launch_bounds__(32) mt_finish_kernel(MtArgs a) {
         out->candidates = a.count;
         out->winner = (int64_t)win;
         out->t_min_q = t_min;
-        out->thr_q = eq4_threshold(t_min, a.lambda_q);
+        out->thr_q = eq4_threshold(t_min, call.lambda_q);
         out->t_q = t;
         out->q = q;
         out->t_min = (double)t_min / 65536.0;
         out->t = (double)t / 65536.0;
         out->sse = sse;
         // consistency guard: the winner's sums must reproduce the reduced minima
-        out->status = (q != a.scal[1] || t > out->thr_q) ? TRS_EINFEASIBLE : TRS_OK;
+        out->status = (q != qstar || t > out->thr_q) ? TRS_EINFEASIBLE : TRS_OK;
     }
 }
 
 }  // namespace
+
+void mt_free(MtEntry *me) {
+    if (!me) return;
+    for (int k = 0; k < kMtSlots; ++k) {
+        if (me->graph[k]) cudaGraphExecDestroy(me->graph[k]);
+        if (me->copied[k]) cudaEventDestroy(me->copied[k]);
+    }
+    if (me->call_host) cudaFreeHost(me->call_host);
+    dev_free(me->cands);
+    dev_free(me->work);
+    delete me;
+}
+
+// Enumerates shape (W, H, n) on the host, uploads its list slice-major as
+// rectangle-table entries and captures the search (argument copy, T_min
+// reset, two passes, decode) as one graph.  The entry joins ctx->mt.
+static int mt_create(trs_ctx *ctx, int W, int H, int n, MtEntry **out) {
+    std::vector<uint8_t> keys;
+    int64_t count = 0;
+    TRS_TRY(mt_enumerate(W, H, n, ctx->o.k_area, &keys, &count));
+    const int C = (W + kCtu - 1) / kCtu, R = (H + kCtu - 1) / kCtu;
+    std::vector<uint32_t> ent((size_t)count * n);
+    for (int64_t c = 0; c < count; ++c)
+        for (int i = 0; i < n; ++i) {
+            const uint8_t *k = &keys[((size_t)c * n + i) * 4];  // y0, x0, y1, x1
+            ent[(size_t)i * count + c] =
+                (uint32_t)(((size_t)band_index(C, k[1], k[3]) * R + (k[2] - k[0] - 1)) * R + k[0]);
+        }
+    std::vector<uint8_t>().swap(keys);
+    MtEntry *me = new (std::nothrow) MtEntry;
+    if (!me) return TRS_ENOMEM;
+    me->count = count;
+    const int nblocks = (int)std::max<int64_t>(1, std::min<int64_t>((count + kMtThreads - 1) / kMtThreads, kMtBlocks));
+    // work: MtCall (4 words), T_min (4 words), per-block pairs
+    const size_t work_bytes = 8 * sizeof(uint64_t) + (size_t)nblocks * 2 * sizeof(uint64_t);
+    int st = dev_alloc(me->cands, std::max<size_t>(ent.size() * 4, 4), &ctx->total);
+    if (st == TRS_OK) st = dev_alloc(me->work, work_bytes, &ctx->total);
+    auto fail = [&](int code) {
+        ctx->total -= me->cands.n + me->work.n;
+        mt_free(me);
+        return code;
+    };
+    if (st != TRS_OK) return fail(st);
+    cudaError_t e = cudaSuccess;
+    if (!ent.empty()) e = cudaMemcpy(me->cands.p, ent.data(), ent.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&me->call_host, kMtSlots * sizeof(MtCall));
+    for (int k = 0; k < kMtSlots && e == cudaSuccess; ++k)
+        e = cudaEventCreateWithFlags(&me->copied[k], cudaEventDisableTiming);
+    if (e == cudaSuccess && !ctx->mt_cap) e = cudaStreamCreateWithFlags(&ctx->mt_cap, cudaStreamNonBlocking);
+    // T_min starts at +infinity; each search's decode kernel resets it for the next
+    if (e == cudaSuccess) e = cudaMemset((uint8_t *)me->work.p + 4 * sizeof(uint64_t), 0xff, sizeof(uint64_t));
+    if (e != cudaSuccess) return fail(cuda_fail(e, "multi-tile list upload"));
+    MtArgs a;
+    a.ent = (const uint32_t *)me->cands.p;
+    a.count = count;
+    a.n = n;
+    a.C = C;
+    a.R = R;
+    a.W = W;
+    a.H = H;
+    a.nblocks = nblocks;
+    uint64_t *wk = (uint64_t *)me->work.p;
+    a.call = (const MtCall *)wk;
+    a.tmin = wk + 4;
+    a.part = wk + 8;
+    cudaStream_t cs = ctx->mt_cap;
+    for (int k = 0; k < kMtSlots && e == cudaSuccess; ++k) {
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) break;
+        e = cudaMemcpyAsync(wk, me->call_host + k, sizeof(MtCall), cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = record_event(me->copied[k], cs);
+        if (e == cudaSuccess && count > 0) {
+            mt_tmin_kernel<<<nblocks, kMtThreads, 0, cs>>>(a);
+            mt_q_kernel<<<nblocks, kMtThreads, 0, cs>>>(a);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) {
+            mt_finish_kernel<<<1, 32, 0, cs>>>(a);
+            e = cudaGetLastError();
+        }
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&me->graph[k], g, 0);
+        if (g) cudaGraphDestroy(g);
+    }
+    if (e != cudaSuccess) return fail(cuda_fail(e, "multi-tile search capture"));
+    try {
+        ctx->mt[std::make_tuple(W, H, n)] = me;
+    } catch (const std::bad_alloc &) {
+        return fail(TRS_ENOMEM);
+    }
+    *out = me;
+    return TRS_OK;
+}
 
 }  // namespace trs
 
@@ -460,6 +640,7 @@ int trs_mt_list(int width, int height, int n, int k, uint8_t *list, size_t capac
 
 int trs_search_mt(trs_ctx *ctx, const void *tables, int W, int H, int n, float lambda, trs_mt_partition *out,
                   void *stream) {
+    TRS_GUARD_BEGIN
     if (!ctx || !tables || !out || (uintptr_t)tables % 256) return TRS_EINVAL;
     TRS_TRY(check_frame(ctx, W, H));
     if (n < 1 || n > ctx->o.max_regions) return TRS_EINVAL;
@@ -471,56 +652,18 @@ int trs_search_mt(trs_ctx *ctx, const void *tables, int W, int H, int n, float l
     if (it != ctx->mt.end()) {
         me = it->second;
     } else {
-        std::vector<uint8_t> keys;
-        int64_t count = 0;
-        TRS_TRY(mt_enumerate(W, H, n, ctx->o.k_area, &keys, &count));
-        MtEntry *ne = new (std::nothrow) MtEntry;
-        if (!ne) return TRS_ENOMEM;
-        ne->count = count;
-        int st = dev_alloc(ne->cands, keys.size(), &ctx->total);
-        if (st == TRS_OK && !keys.empty()) {
-            const cudaError_t e = cudaMemcpy(ne->cands.p, keys.data(), keys.size(), cudaMemcpyHostToDevice);
-            if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpy (slice-set list)");
-        }
-        if (st == TRS_OK) {
-            try {
-                ctx->mt[key] = ne;
-            } catch (const std::bad_alloc &) {
-                st = TRS_ENOMEM;
-            }
-        }
-        if (st != TRS_OK) {
-            ctx->total -= ne->cands.n;
-            dev_free(ne->cands);
-            delete ne;
-            return st;
-        }
-        me = ne;
+        TRS_TRY(mt_create(ctx, W, H, n, &me));
     }
-    TRS_TRY(dev_alloc(ctx->mt_scal, 4 * sizeof(uint64_t), &ctx->total));
-    MtArgs a;
-    a.cands = (const uint8_t *)me->cands.p;
-    a.count = me->count;
-    a.n = n;
-    a.C = (W + kCtu - 1) / kCtu;
-    a.R = (H + kCtu - 1) / kCtu;
-    a.W = W;
-    a.H = H;
-    a.tables = (const uint8_t *)tables;
-    a.scal = (uint64_t *)ctx->mt_scal.p;
-    a.lambda_q = lambda_to_q(lambda);
-    a.out = out;
-    TRS_CK(cudaMemsetAsync(a.scal, 0xff, 3 * sizeof(uint64_t), s));
-    if (a.count > 0) {
-        const int64_t want = (a.count + 255) / 256;
-        const int blocks = (int)std::min<int64_t>(want, 152 * 8);
-        mt_pass_kernel<0><<<blocks, 256, 0, s>>>(a);
-        mt_pass_kernel<1><<<blocks, 256, 0, s>>>(a);
-        mt_pass_kernel<2><<<blocks, 256, 0, s>>>(a);
-    }
-    mt_finish_kernel<<<1, 32, 0, s>>>(a);
-    TRS_CK(cudaGetLastError());
+    // slot k's graph, kMtSlots calls ago, has copied its arguments
+    const int k = me->next;
+    me->next = (k + 1) % kMtSlots;
+    TRS_CK(cudaEventSynchronize(me->copied[k]));
+    me->call_host[k].tables = (const uint8_t *)tables;
+    me->call_host[k].out = out;
+    me->call_host[k].lambda_q = lambda_to_q(lambda);
+    TRS_CK(cudaGraphLaunch(me->graph[k], s));
     return TRS_OK;
+    TRS_GUARD_END
 }
 
 }  // extern "C"

@@ -144,6 +144,22 @@ def test_mt_full_frames_up_to_five_slices(dec, oracle, spec_name, n):
         assert p.regions() == _x0x1y0y1(ref["regions"])
 
 
+@pytest.mark.parametrize("spec_name,n", [("SPEC_1080P10", 6), ("SPEC_1080P10", 7), ("SPEC_2160P10", 5)])
+def test_mt_full_frames_six_and_seven_slices(dec, oracle, spec_name, n):
+    """The benchmarked 1920x1080 searches (n = 6: 75,106 slice sets, n = 7:
+    535,242) against the oracle's search over every partition of the CTU
+    grid into n rectangles, evaluated by direct sums."""
+    spec = getattr(synth, spec_name)
+    W, H = spec.width, spec.height
+    plane, times = synth.make_frame(spec, seed=7)
+    tab = _tables(dec, plane, times, spec.bit_depth)
+    st = oracle.texture(plane, spec.bit_depth)
+    Tq, _ = oracle.time_q(times)
+    for lam in (0.0, 0.1):
+        ref = oracle.mt_search_rects(st, Tq, n, lam)
+        _assert_equal(dec.search_mt(tab, W, H, n, lam), ref, ref["count"])
+
+
 def test_mt_no_valid_set_and_out_of_range(dec, oracle):
     plane, times = synth.small_frame(256, 256, 10, 1)
     tab = _tables(dec, plane, times, 10)

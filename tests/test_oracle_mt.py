@@ -93,3 +93,42 @@ def test_decision_over_guillotine_sets_equals_oracle(oracle, W, H, n, lam, seed)
     assert got["count"] == oracle.mt_count(W, H, n)
     assert (got["t_min"], got["thr"], got["t"], got["q"], got["regions"]) == \
         (ref["t_min"], ref["thr"], ref["t"], ref["q"], ref["regions"])
+
+
+@pytest.mark.parametrize("seed", range(18))
+def test_rectangle_search_equals_tile_grid_search(oracle, seed):
+    """The same space enumerated two ways: as tile grids whose tiles are
+    grouped (oracle_mt_search) and as partitions of the CTU grid into n
+    rectangles (oracle_mt_search_rects).  Equal records and counts."""
+    rng = np.random.default_rng(4400 + seed)
+    W, H, n = [(832, 480, 5), (640, 640, 4), (1000, 700, 3), (513, 385, 6), (768, 512, 5), (384, 300, 4)][seed % 6]
+    S1, S2, N, Tq = random_instance(rng, W, H, ["random", "flat", "uniform"][(seed // 3) % 3])
+    st = stats_from(oracle, W, H, S1, S2, N)
+    for lam in (0.0, 0.1, 0.3):
+        a = oracle.mt_search(st, Tq, n, lam)
+        b = oracle.mt_search_rects(st, Tq, n, lam)
+        assert a["status"] == b["status"]
+        if a["status"] == oracle.OK:
+            assert (a["t_min"], a["thr"], a["t"], a["q"], a["regions"]) == (b["t_min"], b["thr"], b["t"], b["q"],
+                                                                            b["regions"])
+            assert abs(a["sse"] - b["sse"]) <= 1e-9 * max(1.0, abs(a["sse"]))
+    assert b["count"] == oracle.mt_count(W, H, n)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_rectangle_search_matches_bruteforce(oracle, seed):
+    rng = np.random.default_rng(4600 + seed)
+    W, H = [(384, 384), (512, 256), (300, 200), (512, 384)][seed % 4]
+    n = [2, 3, 4][seed % 3]
+    S1, S2, N, Tq = random_instance(rng, W, H, ["random", "flat", "uniform"][seed % 3])
+    st = stats_from(oracle, W, H, S1, S2, N)
+    lam = [0.0, 0.1, 0.3][(seed // 3) % 3]
+    got = oracle.mt_search_rects(st, Tq, n, lam)
+    ref = bruteforce.mt_search(W, H, S1.tolist(), S2.tolist(), Tq.astype(np.int64).tolist(), n,
+                               oracle.lambda_q(lam))
+    if ref is None:
+        assert got["status"] == oracle.EINFEASIBLE
+        return
+    assert (got["t_min"], got["t"], got["q"]) == (ref["t_min"], ref["t"], ref["q"])
+    assert got["regions"] == [(r[0], r[2], r[1], r[3]) for r in ref["regions"]]
+    assert got["count"] == len(bruteforce.mt_partitions(W, H, n))

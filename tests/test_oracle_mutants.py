@@ -80,6 +80,8 @@ MUTANTS = [
     ("enum_line_skipped", "in-tile slice cuts",
      "enum_lines(e, x, x1, y + 1, y, cuts | (1ull << (y - 1)), tile_row ? k : k + 1, used, c);",
      "enum_lines(e, x, x1, y + 2 > f->R ? f->R : y + 2, y, cuts | (1ull << (y - 1)), tile_row ? k : k + 1, used, c);"),
+    ("mt_rects_slices_left", "exactly n slices (multi-tile, rectangle partitions)",
+     "int left = e->n - e->ns;", "int left = e->n - e->ns - 1;"),
     ("enum_tile_rows_bound", "exactly n slices",
      "if (used + e->r > e->n) return;", "if (used + e->r >= e->n) return;"),
     ("sse_exact_sign", "Eq. 2 (reported SSE)",
