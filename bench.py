@@ -531,7 +531,7 @@ def run_multi_tile(runtime, trs, device: int, reps: int = 50, ns=(6, 7)):
     finally:
         dec.close()
     return {"searches": res,
-            "note": "one graph launch per search: argument copy, T_min reset, two passes over the list "
+            "note": "one graph launch per search: argument copy, two passes over the list "
                     "(L2-resident at these sizes), decode; list_read_gbs counts two reads of the list"}
 
 
@@ -660,19 +660,19 @@ def main():
             trs.trs_set_tune(d.ctx, tune["band_warps"], tune["col_warps"], tune["col_batch"])
         trs.trs_set_batch_parts(d.ctx, args.parts)
 
-    def run_steps(count: int, flight: int):
+    def run_steps(count: int, flight: int, inputs=None):
         for s in range(count):
             i = s % flight
             with torch.cuda.stream(streams[i]):
-                decs[i].batch_decide(ins, outs[i])
+                decs[i].batch_decide(ins if inputs is None else inputs, outs[i])
 
-    def timed(count: int, flight: int) -> float:
+    def timed(count: int, flight: int, inputs=None) -> float:
         """Device time of `count` steps: every stream starts after ev0, ev1 after all of them."""
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         for st in streams[:flight]:
             st.wait_event(ev0)
-        run_steps(count, flight)
+        run_steps(count, flight, inputs)
         for st in streams[:flight]:
             e = torch.cuda.Event()
             e.record(st)
@@ -698,6 +698,24 @@ def main():
     one_ms = max_over_ranks(timed(max(3, args.steps // 2), 1), dist, dev)
     one_batch = {"value": job_throughput(nfr * max(3, args.steps // 2), world, one_ms / 1e3), "unit": UNIT,
                  "ms_per_step": one_ms / max(3, args.steps // 2), "form": "one batch in flight, one stream"}
+
+    # the same stream of steps on device-resident packed planes (TRS_PACKED10)
+    import synth
+    lumas_pk = [torch.from_numpy(synth.pack10(p)).to(dev) for p, _ in frames]
+    ins_pk = [(l, l.shape[1], 3840, 2160, trs.PACKED10, t, N_REGIONS, LAMBDA) for l, t in zip(lumas_pk, tts)]
+    ref_bytes = bytes(out.cpu().numpy())
+    run_steps(max(args.warmup, args.in_flight), args.in_flight, ins_pk)
+    sync_all()
+    pk_steps = max(3, args.steps // 2)
+    pk_ms = max_over_ranks(timed(pk_steps, args.in_flight, ins_pk), dist, dev)
+    for o in outs:
+        assert bytes(o.cpu().numpy()) == ref_bytes  # the same decisions as the two-byte planes
+    packed_res = {"value": job_throughput(nfr * pk_steps, world, pk_ms / 1e3), "unit": UNIT,
+                  "ms_per_step": pk_ms / pk_steps,
+                  "luma_bytes_per_step": int(sum(l.numel() for l in lumas_pk)),
+                  "form": "the same stream of steps, planes in the packed 10-bit format (four samples in five "
+                          "bytes) resident in HBM"}
+    del lumas_pk, ins_pk
 
     # --- kernels alone: the batch as one launch chain, no second half running
     # beside it; the per-kernel durations of the roofline, averaged over steps
@@ -759,41 +777,54 @@ def main():
     plain_value = nfr * reps / (e0.elapsed_time(e1) / 1e3)
 
     # --- end to end through the host-buffer C call ------------------------
+    # Two input forms of the same 10-bit samples: the packed format
+    # (TRS_PACKED10, four samples in five bytes: what a capture pipeline
+    # hands over, 37.5 % fewer bytes on the host link) and two bytes per
+    # sample.  Both decide the same bytes (checked).
+    import synth
     pinned = [torch.from_numpy(np.ascontiguousarray(p).view(np.uint8)).pin_memory() for p, _ in frames]
+    pinned_pk = [torch.from_numpy(synth.pack10(p)).pin_memory() for p, _ in frames]
     pinned_t = [torch.from_numpy(t).pin_memory() for _, t in frames]
-    hdescs = [trs.frame_desc(pinned[i], pinned_t[i], 3840, 2160, 7680, 10, N_REGIONS, LAMBDA)
-              for i in range(nfr)]
-    # the same stream of steps as the timed region: IN_FLIGHT host threads,
-    # each calling the synchronous host-buffer entry point on its own context
-    # and stream, so one batch's copies overlap another's kernels
     import threading
-    for i in range(args.in_flight):
-        for _ in range(2):
-            trs.trs_batch_decide_host(decs[i].ctx, hdescs, streams[i])
-    sync_all()
-    e_steps = max(3, args.steps // 4)
-    e_steps += (-e_steps) % args.in_flight
-    results = [None] * args.in_flight
 
-    def host_worker(i: int):
-        for _ in range(e_steps // args.in_flight):
-            results[i] = trs.trs_batch_decide_host(decs[i].ctx, hdescs, streams[i])
+    def e2e_run(descs, lumas, form):
+        # the same stream of steps as the timed region: IN_FLIGHT host threads,
+        # each calling the synchronous host-buffer entry point on its own
+        # context and stream, so one batch's copies overlap another's kernels
+        for i in range(args.in_flight):
+            for _ in range(2):
+                trs.trs_batch_decide_host(decs[i].ctx, descs, streams[i])
+        sync_all()
+        e_steps = max(3, args.steps // 4)
+        e_steps += (-e_steps) % args.in_flight
+        results = [None] * args.in_flight
 
-    workers = [threading.Thread(target=host_worker, args=(i,)) for i in range(args.in_flight)]
-    t0 = time.perf_counter()
-    for t in workers:
-        t.start()
-    for t in workers:
-        t.join()
-    sync_all()
-    e2e_dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
-    for hp in results:
-        assert bytes(hp[0]) == bytes(parts[0])
-    e2e = {"value": job_throughput(nfr * e_steps, world, e2e_dt), "unit": UNIT,
-           "h2d_bytes_per_step": int(sum(p.numel() for p in pinned) + sum(t.numel() * 4 for t in pinned_t)),
-           "d2h_bytes_per_step": nfr * trs.PARTITION_BYTES,
-           "form": f"trs_batch_decide_host from pinned host buffers, {args.in_flight} host threads with a "
-                   "context and stream each"}
+        def host_worker(i: int):
+            for _ in range(e_steps // args.in_flight):
+                results[i] = trs.trs_batch_decide_host(decs[i].ctx, descs, streams[i])
+
+        workers = [threading.Thread(target=host_worker, args=(i,)) for i in range(args.in_flight)]
+        t0 = time.perf_counter()
+        for t in workers:
+            t.start()
+        for t in workers:
+            t.join()
+        sync_all()
+        dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
+        for hp in results:
+            assert bytes(hp[0]) == bytes(parts[0])
+        return {"value": job_throughput(nfr * e_steps, world, dt), "unit": UNIT,
+                "h2d_bytes_per_step": int(sum(p.numel() for p in lumas) + sum(t.numel() * 4 for t in pinned_t)),
+                "d2h_bytes_per_step": nfr * trs.PARTITION_BYTES,
+                "form": f"trs_batch_decide_host from pinned host buffers ({form}), {args.in_flight} host threads "
+                        "with a context and stream each"}
+
+    pk_bytes = (10 * 3840 + 7) // 8
+    e2e = e2e_run([trs.frame_desc(pinned_pk[i], pinned_t[i], 3840, 2160, pk_bytes, trs.PACKED10, N_REGIONS,
+                                  LAMBDA) for i in range(nfr)], pinned_pk,
+                  "10-bit samples packed four in five bytes, TRS_PACKED10")
+    e2e_two_byte = e2e_run([trs.frame_desc(pinned[i], pinned_t[i], 3840, 2160, 7680, 10, N_REGIONS, LAMBDA)
+                            for i in range(nfr)], pinned, "two bytes per 10-bit sample")
 
     # --- rooflines: every kernel of the step, from the one-chunk stage times -
     hbm, sm_max, src = peaks()
@@ -907,7 +938,7 @@ def main():
                 "stage_ms_overlapped": stage_overlap, "stage_frames_overlapped": overlap_frames,
                 "no_overlap": no_overlap, "autotune": tune, "mixed_256": mixed_res, "lightweight": light,
                 "serving": serving, "multi_tile": multi_tile,
-                "clocks": clk.summary(), "e2e": e2e,
+                "clocks": clk.summary(), "e2e": e2e, "e2e_two_byte": e2e_two_byte, "packed": packed_res,
                 "gpu_launches": launches, "roofline": roof, "roofline_texture": tex_roof,
                 "rooflines": rooflines, "search_share_of_stage_sum": search_share,
                 "config_480p8_n4": configs_res.get("config_480p8_n4") if configs_res else None,

@@ -65,6 +65,17 @@ extern "C" {
 #define TRS_MAX_ROWS 32      /* CTU rows:    height <= 4096 */
 #define TRS_MAX_REGIONS 32   /* n, slices (= threads) per frame */
 
+/* Sample formats, passed where a call takes bit_depth:
+ *   8           one byte per sample;
+ *   9..12       two bytes per sample, little endian, value < 2^bit_depth;
+ *   TRS_PACKED10  10-bit samples packed four in five bytes: each row is a
+ *               little-endian bit string in which sample x occupies bits
+ *               [10x, 10x + 10) (bytes 5j..5j+4 hold samples 4j..4j+3, the
+ *               lowest bits first); a row takes ceil(10 W / 8) bytes.
+ * The statistics of a packed plane equal those of the same samples in the
+ * two-byte form; a packed frame moves 37.5 % fewer bytes. */
+#define TRS_PACKED10 0x10A
+
 enum trs_status {
     TRS_OK = 0,
     TRS_EINVAL = 1,       /* bad argument (null pointer, size out of range, misaligned) */
@@ -147,12 +158,12 @@ typedef struct trs_partition {
 
 /* One frame of a batched call. */
 typedef struct trs_frame_desc {
-    const void *luma_dev;     /* W*H samples, rows pitch_bytes apart; uint8 if bit_depth == 8 else
-                                 little-endian uint16 */
+    const void *luma_dev;     /* W*H samples, rows pitch_bytes apart, in the format bit_depth names
+                                 (uint8, little-endian uint16 or TRS_PACKED10) */
     const float *ctu_time_dev;/* R*C co-located CTU times (Sec. 2.1), row-major */
     int width, height;
     size_t pitch_bytes;
-    int bit_depth;            /* 8..12 */
+    int bit_depth;            /* 8..12 or TRS_PACKED10 */
     int n_regions;            /* n */
     float lambda;             /* Eq. 4, >= 0 */
 } trs_frame_desc;
@@ -231,10 +242,12 @@ size_t trs_ctx_bytes(const trs_ctx *ctx);
 
 /* a1.  Per-CTU luma statistics of one frame (Eq. 2 needs S1, S2, N of every
  * slice; they are sums of these).  luma_dev: W*H samples with rows
- * pitch_bytes apart (pitch >= W * bytes per sample).  Samples >= 2^bit_depth
+ * pitch_bytes apart (pitch >= the bytes of a row in the sample format:
+ * W, 2 W, or ceil(10 W / 8) for TRS_PACKED10).  Samples >= 2^bit_depth
  * set stats->flags bit 0 and are still summed.  Rows and the base address
- * aligned to 16 bytes take the vector path; others a scalar path.
- * TRS_EINVAL: null pointers, W/H beyond the context, bit_depth outside 8..12. */
+ * aligned to 16 bytes take the vector path (for TRS_PACKED10: CTUs 128
+ * samples wide), others a scalar path.  TRS_EINVAL: null pointers, W/H
+ * beyond the context, bit_depth neither 8..12 nor TRS_PACKED10. */
 int trs_texture_map(trs_ctx *ctx, const void *luma_dev, int width, int height, size_t pitch_bytes,
                     int bit_depth, const trs_ctu_stats *stats, void *stream);
 

@@ -23,6 +23,7 @@ _LIB = os.path.join(_BUILD, "liboracle.so")
 
 CTU = 128
 OK, EINVAL, ERANGE, EINFEASIBLE, ENOMEM = 0, 1, 2, 3, 4
+PACKED10 = 0x10A  # 10-bit samples packed four in five bytes (little-endian bit string per row)
 _MAX_C = 64
 
 
@@ -165,9 +166,13 @@ class Stats:
     status: int
 
 
-def texture(plane: np.ndarray, bit_depth: int, pitch: int | None = None) -> Stats:
-    """Per-CTU S1, S2, N and max sample of a luma plane [H, W] (uint8 or uint16)."""
+def texture(plane: np.ndarray, bit_depth: int, pitch: int | None = None, width: int | None = None) -> Stats:
+    """Per-CTU S1, S2, N and max sample of a luma plane [H, W] (uint8 or
+    uint16), or, with bit_depth == PACKED10, of a packed plane given as
+    uint8 rows [H, row bytes] holding `width` samples each."""
     H, W = plane.shape
+    if bit_depth == PACKED10:
+        W = width
     if pitch is None:
         buf = np.ascontiguousarray(plane)
         pitch = buf.strides[0]
@@ -302,9 +307,10 @@ def rect_all(st: Stats, Tq: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
 
 
 def decide(plane: np.ndarray, times: np.ndarray, bit_depth: int, n: int, lam: float,
-           k_area: int = 3) -> tuple[Decision, Stats, np.ndarray]:
-    """Whole path on the CPU: texture, Q16 times, O2 search."""
-    st = texture(plane, bit_depth)
+           k_area: int = 3, width: int | None = None) -> tuple[Decision, Stats, np.ndarray]:
+    """Whole path on the CPU: texture, Q16 times, O2 search (width: the
+    samples per row of a PACKED10 plane)."""
+    st = texture(plane, bit_depth, width=width)
     Tq, s = time_q(times)
     if st.status != OK:
         return Decision(status=st.status), st, Tq

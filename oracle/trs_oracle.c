@@ -9,7 +9,8 @@
  * no code, header, table or constant with the CUDA path.
  *
  * Contents, each following the passage cited beside it:
- *   oracle_texture      per-CTU luma sums S1 = sum p, S2 = sum p^2, N     (Sec. 2.2, Eq. 2)
+ *   oracle_texture      per-CTU luma sums S1 = sum p, S2 = sum p^2, N     (Sec. 2.2, Eq. 2),
+ *                       from 8..12-bit samples or the packed 10-bit format
  *   oracle_time_q       Q16 fixed-point CTU times                          (Sec. 2.1, Eq. 1 input)
  *   oracle_sat          summed-area table by its definition (direct sums)
  *   oracle_search_enum  O1: every TRS configuration enumerated in canonical
@@ -73,6 +74,7 @@ typedef unsigned __int128 u128;
 #define OR_MAX_R 64
 #define OR_MAX_N 64
 #define OR_INF UINT64_MAX
+#define OR_PACKED10 0x10A  /* the packed 10-bit sample format's code in the library's interface */
 
 enum { OR_OK = 0, OR_EINVAL = 1, OR_ERANGE = 2, OR_EINFEASIBLE = 3, OR_ENOMEM = 4 };
 
@@ -173,11 +175,16 @@ static rsum_t memo_get(memo_t *m, int x0, int x1, int y0, int y1) {
 /* ------------------------------------------------------------------ */
 /* a1: per-CTU texture statistics (Eq. 2 needs sum p and sum p^2 per RS) */
 
+/* bd: 8..12, or OR_PACKED10 for 10-bit samples packed four in five bytes,
+   each row a little-endian bit string with sample x in bits [10x, 10x+10). */
 int oracle_texture(const void *luma, int W, int H, size_t pitch, int bd,
                    uint64_t *S1, uint64_t *S2, uint64_t *N, uint32_t *vmax) {
+    int packed = bd == OR_PACKED10;
+    if (packed) bd = 10;
     if (!luma || W <= 0 || H <= 0 || bd < 8 || bd > 12) return OR_EINVAL;
     int bps = (bd == 8) ? 1 : 2;
-    if (pitch < (size_t)W * bps) return OR_EINVAL;
+    size_t row_bytes = packed ? ((size_t)W * 10 + 7) / 8 : (size_t)W * bps;
+    if (pitch < row_bytes) return OR_EINVAL;
     int C = (W + OR_CTU - 1) / OR_CTU, R = (H + OR_CTU - 1) / OR_CTU;
     for (int i = 0; i < C * R; ++i) {
         S1[i] = 0;
@@ -191,7 +198,13 @@ int oracle_texture(const void *luma, int W, int H, size_t pitch, int bd,
         const uint8_t *row = base + (size_t)y * pitch;
         for (int x = 0; x < W; ++x) {
             uint32_t p;
-            if (bps == 1) {
+            if (packed) {
+                p = 0;
+                for (int i = 0; i < 10; ++i) {
+                    size_t bit = (size_t)10 * x + i;
+                    p |= (uint32_t)((row[bit >> 3] >> (bit & 7)) & 1u) << i;
+                }
+            } else if (bps == 1) {
                 p = row[x];
             } else {
                 p = (uint32_t)row[2 * x] | ((uint32_t)row[2 * x + 1] << 8); /* little endian */

@@ -285,16 +285,16 @@ int trs_texture_map(trs_ctx *ctx, const void *luma, int W, int H, size_t pitch, 
                     void *stream) {
     if (!ctx || !luma || !st || !st->s1 || !st->s2 || !st->count || !st->vmax || !st->flags) return TRS_EINVAL;
     TRS_TRY(check_frame(ctx, W, H));
-    if (bd < 8 || bd > 12) return TRS_EINVAL;
-    const int bps = bd == 8 ? 1 : 2;
-    if (pitch < (size_t)W * bps) return TRS_EINVAL;
+    if (!fmt_ok(bd)) return TRS_EINVAL;
+    if (pitch < fmt_row_bytes(W, bd)) return TRS_EINVAL;
     LaunchArgs a{};
     DevFrame &f = a.single;
     f.luma = (const uint8_t *)luma;
     f.pitch = pitch;
     f.W = W;
     f.H = H;
-    f.bd = bd;
+    f.bd = fmt_depth(bd);
+    f.packed = bd == TRS_PACKED10;
     f.vec_ok = ((uintptr_t)luma % 16 == 0) && (pitch % 16 == 0);
     f.C = (W + kCtu - 1) / kCtu;
     f.R = (H + kCtu - 1) / kCtu;
@@ -462,14 +462,13 @@ int trs_decide_host(trs_ctx *ctx, const void *luma_host, int W, int H, size_t pi
                     const float *times_host, int n, float lambda, trs_partition *out_host, void *stream) {
     if (!ctx || !luma_host || !times_host || !out_host) return TRS_EINVAL;
     TRS_TRY(check_frame(ctx, W, H));
-    if (bd < 8 || bd > 12) return TRS_EINVAL;
-    const int bps = bd == 8 ? 1 : 2;
-    if (pitch < (size_t)W * bps) return TRS_EINVAL;
+    if (!fmt_ok(bd)) return TRS_EINVAL;
+    const size_t rowb = fmt_row_bytes(W, bd);
+    if (pitch < rowb) return TRS_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t dpitch = align256((size_t)W * bps);
+    const size_t dpitch = (rowb + 15) & ~size_t(15);  // 16-byte rows: the vector path, and no padding to copy
     const int C = (W + kCtu - 1) / kCtu, R = (H + kCtu - 1) / kCtu;
-    TRS_CK(cudaMemcpy2DAsync(ctx->luma_stage.p, dpitch, luma_host, pitch, (size_t)W * bps, H, cudaMemcpyHostToDevice,
-                             s));
+    TRS_CK(copy_rows_h2d(ctx->luma_stage.p, dpitch, luma_host, pitch, rowb, H, s));
     TRS_CK(cudaMemcpyAsync(ctx->time_stage.p, times_host, (size_t)R * C * sizeof(float), cudaMemcpyHostToDevice, s));
     TRS_TRY(trs_decide(ctx, ctx->luma_stage.p, W, H, dpitch, bd, (const float *)ctx->time_stage.p, n, lambda,
                        (trs_partition *)ctx->part.p, stream));
@@ -497,9 +496,8 @@ int batch_run(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partition *out
         const trs_frame_desc &d = fd[i];
         if (!d.luma_dev || !d.ctu_time_dev) return TRS_EINVAL;
         TRS_TRY(check_frame(ctx, d.width, d.height));
-        if (d.bit_depth < 8 || d.bit_depth > 12) return TRS_EINVAL;
-        const int bps = d.bit_depth == 8 ? 1 : 2;
-        if (d.pitch_bytes < (size_t)d.width * bps) return TRS_EINVAL;
+        if (!fmt_ok(d.bit_depth)) return TRS_EINVAL;
+        if (d.pitch_bytes < fmt_row_bytes(d.width, d.bit_depth)) return TRS_EINVAL;
         if (d.n_regions < 1 || d.n_regions > ctx->o.max_regions) return TRS_EINVAL;
         if (!std::isfinite(d.lambda) || d.lambda < 0.0f || d.lambda > 1000.0f) return TRS_EINVAL;
         TRS_TRY(get_plan(ctx, d.width, d.height, d.n_regions, &pe[i]));
@@ -575,7 +573,8 @@ int batch_run(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_partition *out
         f.pitch = d.pitch_bytes;
         f.W = d.width;
         f.H = d.height;
-        f.bd = d.bit_depth;
+        f.bd = fmt_depth(d.bit_depth);
+        f.packed = d.bit_depth == TRS_PACKED10;
         f.vec_ok = ((uintptr_t)d.luma_dev % 16 == 0) && (d.pitch_bytes % 16 == 0);
         f.times = d.ctu_time_dev;
         f.s1 = (uint32_t *)p;
@@ -926,10 +925,9 @@ int trs_batch_decide_host(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_pa
         const trs_frame_desc &d = fd[i];
         if (!d.luma_dev || !d.ctu_time_dev) return TRS_EINVAL;
         TRS_TRY(check_frame(ctx, d.width, d.height));
-        if (d.bit_depth < 8 || d.bit_depth > 12) return TRS_EINVAL;
-        const int bps = d.bit_depth == 8 ? 1 : 2;
-        if (d.pitch_bytes < (size_t)d.width * bps) return TRS_EINVAL;
-        dp[i] = align256((size_t)d.width * bps);
+        if (!fmt_ok(d.bit_depth)) return TRS_EINVAL;
+        if (d.pitch_bytes < fmt_row_bytes(d.width, d.bit_depth)) return TRS_EINVAL;
+        dp[i] = (fmt_row_bytes(d.width, d.bit_depth) + 15) & ~size_t(15);  // the vector path needs 16-byte rows
         lo[i] = lb;
         lb += dp[i] * d.height;
         to[i] = tb;
@@ -941,12 +939,10 @@ int trs_batch_decide_host(trs_ctx *ctx, const trs_frame_desc *fd, int nf, trs_pa
     std::vector<trs_frame_desc> dd(fd, fd + nf);
     for (int i = 0; i < nf; ++i) {
         const trs_frame_desc &d = fd[i];
-        const int bps = d.bit_depth == 8 ? 1 : 2;
         uint8_t *dl = (uint8_t *)ctx->hb_luma.p + lo[i];
         uint8_t *dt = (uint8_t *)ctx->hb_time.p + to[i];
         const size_t cells = (size_t)((d.width + kCtu - 1) / kCtu) * ((d.height + kCtu - 1) / kCtu);
-        TRS_CK(cudaMemcpy2DAsync(dl, dp[i], d.luma_dev, d.pitch_bytes, (size_t)d.width * bps, d.height,
-                                 cudaMemcpyHostToDevice, s));
+        TRS_CK(copy_rows_h2d(dl, dp[i], d.luma_dev, d.pitch_bytes, fmt_row_bytes(d.width, d.bit_depth), d.height, s));
         TRS_CK(cudaMemcpyAsync(dt, d.ctu_time_dev, cells * 4, cudaMemcpyHostToDevice, s));
         dd[i].luma_dev = dl;
         dd[i].pitch_bytes = dp[i];

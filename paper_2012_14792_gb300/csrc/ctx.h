@@ -164,6 +164,16 @@ cudaError_t batch_enqueue(const BatchLaunch &bl, cudaStream_t cs, cudaEvent_t co
 cudaError_t batch_enqueue_work(const BatchLaunch &bl, cudaStream_t cs, cudaEvent_t *stage, cudaEvent_t after_texture);
 
 
+// Host-to-device copy of `rows` rows of `width` bytes: one linear copy when
+// both pitches equal the width (the driver's 2-D copy of rows that are not
+// a multiple of its transfer size runs at half the link rate), else 2-D.
+inline cudaError_t copy_rows_h2d(void *dst, size_t dpitch, const void *src, size_t spitch, size_t width,
+                                 size_t rows, cudaStream_t s) {
+    if (dpitch == width && spitch == width)
+        return cudaMemcpyAsync(dst, src, width * rows, cudaMemcpyHostToDevice, s);
+    return cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, rows, cudaMemcpyHostToDevice, s);
+}
+
 // Releases a multi-tile entry (device list, work area, pinned block, graph).
 void mt_free(MtEntry *me);
 

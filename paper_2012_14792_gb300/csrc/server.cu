@@ -111,8 +111,7 @@ struct trs_server {
 namespace {
 
 size_t slot_bytes(const Stream &st) {
-    const int bps = st.bd == 8 ? 1 : 2;
-    const size_t dpitch = align256((size_t)st.W * bps);
+    const size_t dpitch = (fmt_row_bytes(st.W, st.bd) + 15) & ~size_t(15);
     const int C = st.pe->host.C, R = st.pe->host.R;
     return align256(dpitch * st.H) + align256(stats_bytes(C, R)) + tables_offsets(C, R).bytes + st.pe->scr.bytes;
 }
@@ -136,16 +135,15 @@ int launch_batch(trs_server *srv, Batch &b) {
         const Request &r = b.reqs[i];
         Stream &st = srv->streams[r.stream];
         Slot &sl = st.slot[r.slot];
-        const int bps = st.bd == 8 ? 1 : 2;
-        TRS_CK(cudaMemcpy2DAsync(sl.luma, sl.dpitch, r.luma, r.pitch, (size_t)st.W * bps, st.H,
-                                 cudaMemcpyHostToDevice, b.s));
+        TRS_CK(copy_rows_h2d(sl.luma, sl.dpitch, r.luma, r.pitch, fmt_row_bytes(st.W, st.bd), st.H, b.s));
         const int C = st.pe->host.C, R = st.pe->host.R, cells = C * R;
         DevFrame f{};
         f.luma = sl.luma;
         f.pitch = sl.dpitch;
         f.W = st.W;
         f.H = st.H;
-        f.bd = st.bd;
+        f.bd = fmt_depth(st.bd);
+        f.packed = st.bd == TRS_PACKED10;
         f.vec_ok = 1;
         f.times = r.times;
         f.s1 = (uint32_t *)sl.stats;
@@ -344,7 +342,7 @@ int trs_server_open_stream_layers(trs_server *srv, int width, int height, int bi
     TRS_GUARD_BEGIN
     if (!srv || !stream_id || n_layers < 1 || n_layers > kMaxLayers) return TRS_EINVAL;
     TRS_TRY(check_frame(srv->ctx, width, height));
-    if (bit_depth < 8 || bit_depth > 12 || n_regions < 1 || n_regions > srv->o.max_regions) return TRS_EINVAL;
+    if (!fmt_ok(bit_depth) || n_regions < 1 || n_regions > srv->o.max_regions) return TRS_EINVAL;
     if (!std::isfinite(lambda) || lambda < 0.0f || lambda > 1000.0f) return TRS_EINVAL;
     std::lock_guard<std::mutex> lk(srv->mu);
     int id = -1;
@@ -368,13 +366,12 @@ int trs_server_open_stream_layers(trs_server *srv, int width, int height, int bi
     if (srv->o.mem_budget_bytes && srv->mem_used + need > srv->o.mem_budget_bytes) return TRS_EBUSY;
     size_t used = 0;
     int rc = dev_alloc(st.times, st.tmap * n_layers, &used);
-    const int bps = bit_depth == 8 ? 1 : 2;
     const int C = st.pe->host.C, R = st.pe->host.R;
     for (Slot &sl : st.slot) {
         if (rc != TRS_OK) break;
         rc = dev_alloc(sl.mem, per_slot, &used);
         if (rc != TRS_OK) break;
-        sl.dpitch = align256((size_t)width * bps);
+        sl.dpitch = (fmt_row_bytes(width, bit_depth) + 15) & ~size_t(15);
         sl.luma = (uint8_t *)sl.mem.p;
         sl.stats = sl.luma + align256(sl.dpitch * height);
         sl.tables = sl.stats + align256(stats_bytes(C, R));
@@ -447,7 +444,7 @@ int trs_server_submit_layer(trs_server *srv, int id, int layer, const void *luma
     if (layer < 0 || layer >= st.layers || st.last < 0) return TRS_EINVAL;
     // the co-TL map; before a layer's first encoded frame, the most recent map of any layer
     const int use = st.have[layer] ? layer : st.last;
-    if (pitch_bytes < (size_t)st.W * (st.bd == 8 ? 1 : 2)) return TRS_EINVAL;
+    if (pitch_bytes < fmt_row_bytes(st.W, st.bd)) return TRS_EINVAL;
     int s = -1;
     for (int i = 0; i < kSlotsPerStream; ++i)
         if (!st.slot[i].busy) {

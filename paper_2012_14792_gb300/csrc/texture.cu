@@ -5,7 +5,9 @@
 // One 256-thread block per CTU.  The frame is read exactly once with 128-bit
 // streaming loads (evict-first, the plane is not reused); a warp covers two
 // full 256-byte CTU rows of a 10-bit plane per request, so every request is
-// a whole number of 32-byte sectors.  Each thread keeps 32-bit partial sums
+// a whole number of 32-byte sectors.  A packed 10-bit plane (TRS_PACKED10,
+// 160 bytes per CTU row) gives each thread 64 consecutive samples, five
+// 16-byte loads unpacked in registers with funnel shifts.  Each thread keeps 32-bit partial sums
 // (at most 64 samples of <= 12 bits per thread: 64 * 4095^2 < 2^32), widens
 // S2 to 64 bits for the warp-shuffle reduction, then one shared-memory step
 // combines the 8 warps.  There is no spatial stencil in the measure, so no
@@ -63,6 +65,35 @@ __device__ __forceinline__ void acc_scalar(Acc &a, uint32_t p) {
     a.vs = a.vs > p ? a.vs : p;
 }
 
+// Sample x of a TRS_PACKED10 row: bits [10x, 10x + 10) of the row's
+// little-endian bit string, which always span two bytes.
+__device__ __forceinline__ uint32_t packed_at(const uint8_t *row, int x) {
+    const int bit = 10 * x, b = bit >> 3;
+    return (((uint32_t)row[b] | ((uint32_t)row[b + 1] << 8)) >> (bit & 7)) & 1023u;
+}
+
+// 64 packed samples from 80 bytes (20 little-endian words): sample j is
+// bits [10j, 10j + 10), read across a word boundary with a funnel shift.
+__device__ __forceinline__ void acc_packed64(Acc &a, const uint4 (&v)[5]) {
+    uint32_t wd[21];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        wd[4 * i] = v[i].x;
+        wd[4 * i + 1] = v[i].y;
+        wd[4 * i + 2] = v[i].z;
+        wd[4 * i + 3] = v[i].w;
+    }
+    wd[20] = 0u;
+#pragma unroll
+    for (int j = 0; j < 64; ++j) {
+        const int k = (10 * j) >> 5, sh = (10 * j) & 31;
+        const uint32_t p = __funnelshift_r(wd[k], wd[k + 1], sh) & 1023u;
+        a.s1 += p;
+        a.s2 += p * p;
+        a.vs = a.vs > p ? a.vs : p;
+    }
+}
+
 __global__ void __launch_bounds__(kTexThreads) texture_kernel(LaunchArgs args) {
     int local;
     const int f = locate(args, args.pre.ctus, args.single_ctus, blockIdx.x, &local);
@@ -72,11 +103,30 @@ __global__ void __launch_bounds__(kTexThreads) texture_kernel(LaunchArgs args) {
     const int x0 = cx * kCtu, y0 = cy * kCtu;
     const int w = min(kCtu, fr.W - x0), h = min(kCtu, fr.H - y0);
     const int bps = fr.bd == 8 ? 1 : 2;
-    const uint8_t *base = fr.luma + (size_t)y0 * fr.pitch + (size_t)x0 * bps;
+    // a packed CTU column starts 10 * 128 / 8 = 160 bytes after the previous one
+    const uint8_t *base = fr.luma + (size_t)y0 * fr.pitch + (fr.packed ? (size_t)cx * 160 : (size_t)x0 * bps);
     const int t = threadIdx.x;
 
     Acc a = {0u, 0u, 0u, 0u};
-    if (fr.vec_ok) {
+    if (fr.packed) {
+        if (fr.vec_ok && w == kCtu) {
+            // thread t: row t / 2, the 64 samples in bytes [80 (t & 1), 80 (t & 1) + 80)
+            // of the row's 160: five 16-byte loads
+            const int r = t >> 1;
+            if (r < h) {
+                const uint8_t *p = base + (size_t)r * fr.pitch + 80 * (t & 1);
+                uint4 v[5];
+#pragma unroll
+                for (int i = 0; i < 5; ++i) v[i] = __ldg(reinterpret_cast<const uint4 *>(p + 16 * i));
+                acc_packed64(a, v);
+            }
+        } else {
+            for (int r = t / kCtu; r < h; r += kTexThreads / kCtu) {
+                const int x = t % kCtu;
+                if (x < w) acc_scalar(a, packed_at(base + (size_t)r * fr.pitch, x));
+            }
+        }
+    } else if (fr.vec_ok) {
         // 16-byte vectors: 16 per 10-bit row, 8 per 8-bit row
         const int vpr = (kCtu * bps) / 16;
         const int spv = 16 / bps;
@@ -125,7 +175,7 @@ __global__ void __launch_bounds__(kTexThreads) texture_kernel(LaunchArgs args) {
             if (x < w) acc_scalar(a, sample_at(row, x, bps));
         }
     }
-    // lane-wise packed maxima -> scalar
+    // lane-wise packed maxima -> scalar (a.vm stays 0 on the packed path)
     uint32_t vmax = bps == 2 ? max(a.vm & 0xffffu, a.vm >> 16)
                              : max(max(a.vm & 0xffu, (a.vm >> 8) & 0xffu), max((a.vm >> 16) & 0xffu, a.vm >> 24));
     vmax = max(vmax, a.vs);

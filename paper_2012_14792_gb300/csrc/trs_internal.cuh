@@ -28,6 +28,13 @@ __host__ __device__ inline int band_index(int C, int x0, int x1) {
     return x0 * (2 * C - x0 + 1) / 2 + (x1 - x0 - 1);
 }
 __host__ __device__ inline int num_bands(int C) { return C * (C + 1) / 2; }
+// Sample formats (see TRS_PACKED10): valid codes, the sample bit depth and
+// the bytes of one row of W samples.
+__host__ __device__ inline bool fmt_ok(int bd) { return (bd >= 8 && bd <= 12) || bd == TRS_PACKED10; }
+__host__ __device__ inline int fmt_depth(int bd) { return bd == TRS_PACKED10 ? 10 : bd; }
+__host__ __device__ inline size_t fmt_row_bytes(int W, int bd) {
+    return bd == TRS_PACKED10 ? ((size_t)W * 10 + 7) / 8 : (size_t)W * (bd == 8 ? 1 : 2);
+}
 // Pixel extent of CTU lines: position of line x (clipped to the frame edge).
 __host__ __device__ inline uint32_t line_px(int x, int extent) {
     uint32_t p = (uint32_t)x * kCtu;
@@ -163,7 +170,8 @@ struct DevFrame {
     // a1 input
     const uint8_t *luma;
     size_t pitch;
-    int W, H, bd, vec_ok;  // vec_ok: base and pitch 16-byte aligned
+    int W, H, bd, vec_ok;  // bd: sample bit depth; vec_ok: base and pitch 16-byte aligned
+    int packed;            // samples in the TRS_PACKED10 format (bd = 10)
     // a2 input
     const float *times;
     // a1 output / a2 input

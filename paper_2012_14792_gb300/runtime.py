@@ -88,10 +88,13 @@ class Decider:
         return out
 
     def decide_host(self, plane: np.ndarray, times: np.ndarray, bit_depth: int, n: int,
-                    lam: float) -> trs.trs_partition:
+                    lam: float, width: int | None = None) -> trs.trs_partition:
+        """width: the samples per row of a TRS_PACKED10 plane (uint8 rows)."""
         p = np.ascontiguousarray(plane)
         t = np.ascontiguousarray(times, dtype=np.float32)
         H, W = p.shape
+        if width is not None:
+            W = width
         return trs.trs_decide_host(self.ctx, p, W, H, p.strides[0], bit_depth, t, n, lam)
 
     # ---- batched ----------------------------------------------------------

@@ -18,6 +18,7 @@ CTU = 128
 MAX_COLS = 64
 MAX_ROWS = 32
 MAX_REGIONS = 32
+PACKED10 = 0x10A  # TRS_PACKED10: 10-bit samples packed four in five bytes
 
 OK, EINVAL, ERANGE, EINFEASIBLE, ENOMEM, EBUSY, ETIMEOUT, ECUDA = range(8)
 

@@ -18,6 +18,7 @@ from .frames import (  # noqa: F401
     mixed_batch,
     mixed_batch_frame,
     mixed_batch_layout,
+    pack10,
     poisson_arrivals,
     ra_coding_order,
     ra_temporal_layer,

@@ -304,3 +304,20 @@ def ra_coding_order(gop: int = 16) -> list[int]:
 
     split(0, gop)
     return order
+
+
+def pack10(plane: np.ndarray) -> np.ndarray:
+    """A [H, W] plane of 10-bit samples in the packed format (four samples in
+    five bytes): each row a little-endian bit string with sample x in bits
+    [10x, 10x + 10); rows of ceil(10 W / 8) bytes, returned as uint8 [H, bytes]."""
+    H, W = plane.shape
+    s = np.asarray(plane, np.uint64) & np.uint64(1023)
+    Wp = -(-W // 4) * 4
+    if Wp != W:
+        s = np.concatenate([s, np.zeros((H, Wp - W), np.uint64)], axis=1)
+    g = s.reshape(H, Wp // 4, 4)
+    v = g[:, :, 0] | (g[:, :, 1] << np.uint64(10)) | (g[:, :, 2] << np.uint64(20)) | (g[:, :, 3] << np.uint64(30))
+    out = np.zeros((H, Wp // 4, 5), np.uint8)
+    for b in range(5):
+        out[:, :, b] = ((v >> np.uint64(8 * b)) & np.uint64(255)).astype(np.uint8)
+    return np.ascontiguousarray(out.reshape(H, Wp // 4 * 5)[:, : (10 * W + 7) // 8])

@@ -80,6 +80,11 @@ MUTANTS = [
     ("enum_line_skipped", "in-tile slice cuts",
      "enum_lines(e, x, x1, y + 1, y, cuts | (1ull << (y - 1)), tile_row ? k : k + 1, used, c);",
      "enum_lines(e, x, x1, y + 2 > f->R ? f->R : y + 2, y, cuts | (1ull << (y - 1)), tile_row ? k : k + 1, used, c);"),
+    ("texture_packed_bit_order", "packed 10-bit sample layout",
+     "p |= (uint32_t)((row[bit >> 3] >> (bit & 7)) & 1u) << i;",
+     "p |= (uint32_t)((row[bit >> 3] >> (bit & 7)) & 1u) << (9 - i);"),
+    ("texture_packed_row_bytes", "packed 10-bit sample layout",
+     "size_t bit = (size_t)10 * x + i;", "size_t bit = (size_t)10 * x + (i ^ 1);"),
     ("mt_rects_slices_left", "exactly n slices (multi-tile, rectangle partitions)",
      "int left = e->n - e->ns;", "int left = e->n - e->ns - 1;"),
     ("enum_tile_rows_bound", "exactly n slices",

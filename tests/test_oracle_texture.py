@@ -82,3 +82,37 @@ def test_little_endian_and_range_check(oracle):
     st = oracle.texture(plane, 10)
     assert st.status == oracle.ERANGE
     assert oracle.texture(np.full((2, 2), 255, np.uint8), 8).status == oracle.OK
+
+
+def test_packed10_worked_bytes(oracle):
+    """Four samples 1, 2, 3, 1023 in five bytes: the 40-bit value
+    1 + 2 * 2^10 + 3 * 2^20 + 1023 * 2^30, little endian, is
+    01 08 30 C0 FF; the oracle reads them back."""
+    import synth
+    plane = np.array([[1, 2, 3, 1023]], np.uint16)
+    packed = synth.pack10(plane)
+    assert packed.tolist() == [[0x01, 0x08, 0x30, 0xC0, 0xFF]]
+    st = oracle.texture(packed, oracle.PACKED10, width=4)
+    assert st.status == oracle.OK
+    assert (int(st.S1[0, 0]), int(st.S2[0, 0]), int(st.N[0, 0]), int(st.vmax[0, 0])) == (
+        1029, 1 + 4 + 9 + 1023 * 1023, 4, 1023)
+
+
+@pytest.mark.parametrize("W,H", [(1, 1), (3, 5), (129, 130), (300, 257), (1920, 1080)])
+def test_packed10_equals_two_byte_samples(oracle, W, H):
+    """The packed plane of a 10-bit frame has the frame's statistics; ragged
+    widths (W not a multiple of 4 or 128) and a padded pitch included."""
+    import synth
+    rng = np.random.default_rng(W * 3 + H)
+    plane = rng.integers(0, 1024, size=(H, W)).astype(np.uint16)
+    ref = oracle.texture(plane, 10)
+    packed = synth.pack10(plane)
+    assert packed.shape == (H, (10 * W + 7) // 8)
+    got = oracle.texture(packed, oracle.PACKED10, width=W)
+    for a, b in ((got.S1, ref.S1), (got.S2, ref.S2), (got.N, ref.N), (got.vmax, ref.vmax)):
+        assert (a == b).all()
+    pitch = -(-packed.shape[1] // 16) * 16 + 16
+    buf = np.zeros((H, pitch), np.uint8)
+    buf[:, : packed.shape[1]] = packed
+    got2 = oracle.texture(buf[:, : packed.shape[1]], oracle.PACKED10, pitch=pitch, width=W)
+    assert (got2.S2 == ref.S2).all() and (got2.S1 == ref.S1).all()
