@@ -351,9 +351,8 @@ int trs_decide_host(trs_ctx *ctx, const void *luma_host, int width, int height, 
 
 /* trs_search for callers that cannot allocate memory (real-time loops that
  * cannot absorb the device synchronisation of cudaMalloc/cudaFree, hosts
- * whose own pool allocator owns all device memory, code running while
- * another thread captures a CUDA graph in global mode, where cudaMalloc is
- * not permitted).  The paper has no counterpart: it is a deployment variant
+ * whose own pool allocator owns all device memory).  The paper has no
+ * counterpart: it is a deployment variant
  * of the search call above, with the same result.  No context: the search
  * plan and scratch live in one file-scope device array of 8 MiB that every
  * GPU loading the library keeps until exit.  A frame shape whose plan and
@@ -362,14 +361,13 @@ int trs_decide_host(trs_ctx *ctx, const void *luma_host, int width, int height, 
  * made.  All calls on a device share the array, which keeps the last call's
  * contents; calls whose work overlaps on the GPU race on it, so serialise
  * them.  The first call on a device looks up the array's address
- * (cudaGetSymbolAddress, with that device current) and should come before
- * any stream capture.  A call whose shape (width, height, n, k_area)
- * differs from the previous one's writes its plan over the old one with a
- * cudaMemcpyAsync from pageable host memory on `stream`, ordered only after
- * earlier work on that stream: the work of earlier calls must have finished
- * by then, and such calls (the first one included) belong outside any
- * stream capture in the process.  Arguments as for trs_search, plus k_area
- * (the area-rule factor, 3 in the paper). */
+ * (cudaGetSymbolAddress, with that device current).  A call whose shape
+ * (width, height, n, k_area) differs from the previous one's (the first
+ * call included) writes its plan over the old one with a cudaMemcpyAsync
+ * from pageable host memory on `stream`, ordered only after earlier work on
+ * that stream: the work of earlier calls on other streams must have
+ * finished by then.  Arguments as for trs_search, plus k_area (the
+ * area-rule factor, 3 in the paper). */
 int trs_search_noalloc(const void *tables_dev, int width, int height, int n_regions, int k_area, float lambda,
                        trs_partition *out_dev, void *stream);
 
@@ -395,8 +393,9 @@ int trs_batch_decide_host(trs_ctx *ctx, const trs_frame_desc *frames_host, int n
  * timings that chose them. */
 typedef struct trs_tune_report {
     int band_warps;      /* warps per block of the row-DP kernels */
-    int col_warps;       /* warps sharing one window's column DP (one block per window) */
-    int col_batch;       /* candidate steps whose V rows a column-DP warp loads together */
+    int col_warps;       /* warps per block of the column-DP kernels (each warp one window) */
+    int col_batch;       /* 4: a column-DP warp runs one window for 32 / L frames that share a plan,
+                            L = the smallest power of two >= max(4, n); 8: for one frame */
     int n_candidates;
     int cand_band_warps[6], cand_col_warps[6], cand_col_batch[6];
     float rows_ms[6];    /* both row-DP stages, fastest of three runs */

@@ -16,14 +16,17 @@
 //    tie order.  The k*A_min > A_max rule (luma samples) prunes: a new slice
 //    must keep the rule among the slices so far, and the free area must fit
 //    the slices left; so does the corner count of the free region, which
-//    bounds the slices it needs from below.  Each set is stored as
-//    (y0, x0, y1, x1) bytes per slice.  The partitions under each choice of
+//    bounds the slices it needs from below.  The enumeration yields
+//    (y0, x0, y1, x1) bytes per slice; the partitions under each choice of
 //    the first two slices are enumerated on a pool of host threads and the
-//    pieces joined in that order.
-//  * device: one thread per slice set reads each slice's time and quality
-//    term from the region tables (any rectangle of CTUs is a tile-column
-//    slice there), and three grid-wide minima give T_min (Eq. 3), Q* (Eq. 2
-//    under Eq. 4) and the first slice set reaching Q*; one warp decodes it.
+//    pieces joined in that order.  The device keeps, slice-major, each
+//    slice's 32-bit index into the region tables' rectangle entries (any
+//    rectangle of CTUs is a tile-column slice there).
+//  * device, one captured graph per call: a grid-stride pass takes T_min
+//    (Eq. 3); a second keeps, per block, the smallest (Q, list index) among
+//    the sets within Eq. 4's bound, so Q* (Eq. 2) and the first set reaching
+//    it come out together; one warp reduces the blocks' pairs and decodes
+//    the winner.
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -2,9 +2,8 @@
 //
 // Some callers cannot call cudaMalloc: real-time loops where the implicit
 // device synchronisation of cudaMalloc/cudaFree would stall the pipeline,
-// hosts that hand all device memory to their own pool allocator and forbid
-// stray allocations, and code that runs while another thread of the process
-// captures a CUDA graph in global mode, where cudaMalloc is not permitted.
+// and hosts that hand all device memory to their own pool allocator and
+// forbid stray allocations.
 // This entry point needs no context: its search plan and scratch live in
 // one file-scope device array of fixed size, and it makes no cudaMalloc /
 // cudaFree call and no call of an allocating library routine (host-side it
@@ -22,17 +21,15 @@
 //    whose work overlaps on the GPU (other streams, or several host threads)
 //    race on the array: serialise them.
 //  * The first call on a device looks up the array's device address with
-//    cudaGetSymbolAddress (with that device current); make that first call
-//    before any stream capture.
+//    cudaGetSymbolAddress (with that device current).
 //  * A call whose shape (W, H, n, k) differs from the one the array holds
-//    writes the new plan over the old one: a cudaMemcpyAsync on the call's
-//    stream from static, pageable host storage.  The copy is ordered after
-//    earlier work on that stream only, not on other streams, so the kernels
-//    of every earlier call with another shape must have finished first.
-//    The first call and every call that changes the shape make this copy,
-//    so make them outside any stream capture in the process.  Until the
-//    copy is enqueued the device keeps no shape: a failed copy leaves the
-//    next call to copy its plan again.
+//    (the first call included) writes the new plan over the old one: a
+//    cudaMemcpyAsync on the call's stream from static, pageable host
+//    storage.  The copy is ordered after earlier work on that stream only,
+//    not on other streams, so the kernels of every earlier call with another
+//    shape must have finished first.  Until the copy is enqueued the device
+//    keeps no shape: a failed copy leaves the next call to copy its plan
+//    again.
 #include <cuda_runtime.h>
 
 #include <algorithm>

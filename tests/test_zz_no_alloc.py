@@ -1,8 +1,7 @@
 """trs_search_noalloc, the search entry point for callers that cannot
 allocate device memory (real-time loops that cannot absorb cudaMalloc's
 device synchronisation, hosts whose own pool allocator owns all device
-memory, code running while another thread captures a CUDA graph in global
-mode), must return exactly what trs_search returns, and the oracle's
+memory), must return exactly what trs_search returns, and the oracle's
 decision.  Calls in a row on one shape check that the shared scratch array
 carries nothing over; later calls swap shapes, go back to an earlier one,
 and cover 832x480, a flat frame whose ties only the canonical code decides,
