@@ -181,6 +181,94 @@ __device__ __forceinline__ uint64_t item_rows(const VT *sv, VT *G, int nd, int d
     return vreg;
 }
 
+// k >= 2 of item_pair for ND admitted heights or fewer in each half (ND a
+// compile-time bound): the half's full-height slice values live in
+// registers and the loop over heights is unrolled, so a relaxation step is
+// one shared load, a max (step 1) or add (step 2) and a min.  Ga holds G_1
+// on entry (G_1[16] included), Gb the saturating infinity at 16 and above.
+// Both halves compute every k up to kmm (a half past its kmax is never
+// read); lane k - 1 keeps G_k[0], returned raw.
+template <int STEP, typename VT, int S, int ND>
+__device__ __forceinline__ VT pair_rows(const uint64_t *stage, int nd, int dlo, int kmm, VT *Ga, VT *Gb, VT g0) {
+    const int lane = threadIdx.x & 31, l = lane & 15, y = l;
+    constexpr VT soft = Soft<VT>::v;
+    VT v[ND];
+#pragma unroll
+    for (int i = 0; i < ND; ++i) v[i] = i < nd ? (VT)stage[(dlo + i - 1) * S + y] : soft;
+    const int goff = y + dlo;
+    auto step = [&](const VT *gp, VT *out, int k) {
+        VT b0 = soft, b1 = soft;  // two independent minimum chains
+#pragma unroll
+        for (int i = 0; i < ND; ++i) {
+            const VT p = gp[i];
+            const VT c = STEP == 1 ? (p > v[i] ? p : v[i]) : VT(p + v[i]);
+            if (i & 1)
+                b1 = c < b1 ? c : b1;
+            else
+                b0 = c < b0 ? c : b0;
+        }
+        const VT best = b0 < b1 ? b0 : b1;
+        // step 1 combines with max, so values never pass the saturating
+        // infinity; step 2's sums can, and are clamped
+        out[y] = STEP == 1 ? best : (best < soft ? best : soft);
+        __syncwarp();
+        if (l == k - 1) g0 = out[0];
+    };
+    if (kmm < 2) return g0;
+    step(Ga + goff, Gb, 2);
+    // G_1's buffer takes G_3 next: its row 16 (G_1[16]) becomes empty
+    if (l == 0) Ga[16] = soft;
+    for (int k = 3; k <= kmm; ++k) {
+        VT *t = Ga;
+        Ga = Gb;
+        Gb = t;
+        step(Ga + goff, Gb, k);
+    }
+    return g0;
+}
+
+// The same for any number of heights: the values come from the per-half
+// table sv (sv[i*32 + lane], filled by the caller).
+template <int STEP, typename VT>
+__device__ __forceinline__ VT pair_rows_any(const VT *sv, int ndm, int dlo, int kmm, VT *Ga, VT *Gb, VT g0) {
+    const int lane = threadIdx.x & 31, l = lane & 15, y = l;
+    constexpr VT soft = Soft<VT>::v;
+    const VT *sp = sv + lane;
+    auto step = [&](const VT *gp, VT *out, int k) {
+        VT b0 = soft, b1 = soft;
+        int i = 0;
+#pragma unroll 2
+        for (; i + 1 < ndm; i += 2) {
+            const VT p0 = gp[i], v0 = sp[i * 32], p1 = gp[i + 1], v1 = sp[(i + 1) * 32];
+            const VT c0 = STEP == 1 ? (p0 > v0 ? p0 : v0) : VT(p0 + v0);
+            const VT c1 = STEP == 1 ? (p1 > v1 ? p1 : v1) : VT(p1 + v1);
+            b0 = c0 < b0 ? c0 : b0;
+            b1 = c1 < b1 ? c1 : b1;
+        }
+        if (i < ndm) {
+            const VT p0 = gp[i], v0 = sp[i * 32];
+            const VT c0 = STEP == 1 ? (p0 > v0 ? p0 : v0) : VT(p0 + v0);
+            b0 = c0 < b0 ? c0 : b0;
+        }
+        const VT best = b0 < b1 ? b0 : b1;
+        out[y] = STEP == 1 ? best : (best < soft ? best : soft);
+        __syncwarp();
+        if (l == k - 1) g0 = out[0];
+    };
+    if (kmm < 2) return g0;
+    step(Ga + y + dlo, Gb, 2);
+    if (l == 0) Ga[16] = soft;
+    for (int k = 3; k <= kmm; ++k) {
+        VT *t = Ga;
+        Ga = Gb;
+        Gb = t;
+        step(Ga + y + dlo, Gb, k);
+    }
+    return g0;
+}
+
+constexpr int kNdRegs = 12;  // most admitted heights the register form of the row DP takes
+
 // Two items of one tile column per warp, for frames of at most 17 CTU rows
 // and n <= 16 (every workload of the paper): half h = lane / 16 runs one
 // item with its lane l on start row y = l.
@@ -214,83 +302,47 @@ __device__ void item_pair(const DevFrame &fr, const DevPlan &pl, int mi, const P
     const int ndm = max(nd, __shfl_xor_sync(kFull, nd, 16));
     const int kmm = max(kmax, __shfl_xor_sync(kFull, kmax, 16));
     __syncwarp();  // every lane is done with the previous pair's tables
-    for (int i = 0; i < ndm; ++i)
-        sv[i * 32 + lane] = i < nd ? (VT)stage[(dlo + i - 1) * S + y] : soft;
+    if (ndm > kNdRegs)
+        for (int i = 0; i < ndm; ++i) sv[i * 32 + lane] = i < nd ? (VT)stage[(dlo + i - 1) * S + y] : soft;
     // G_1: the single slice [y, R), for y = l and for row 16
     auto last_slice = [&](int yy) -> VT {
         const uint32_t hh = (uint32_t)H - line_px(yy, H);
         return have && yy < R && hh >= it.hlo && hh <= it.hhi ? (VT)stage[(R - yy - 1) * S + yy] : soft;
     };
+    // G_1 into Gb (row 16 included); every other word of both tables holds
+    // the saturating infinity (G_0 is never read: k = 1 is closed-form)
     const VT g16 = last_slice(16);
-    Gb[y] = kmax >= 1 ? last_slice(y) : soft;
+    const VT g1 = last_slice(y);
+    Gb[y] = g1;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int e = l + 16 * q;
-        Ga[e] = e == R ? VT(0) : soft;  // G_0: only the empty remainder holds zero slices
+        Ga[e] = soft;
         if (q) Gb[e] = soft;
     }
     if (l == 0) Gb[16] = g16;
     __syncwarp();
-    uint64_t vreg = kInf;
-    if (l == 0 && kmax >= 1) {
-        const VT g0 = Gb[0];
-        vreg = g0 >= soft ? kInf : (uint64_t)g0;
-    }
-    VT *t = Ga;
-    Ga = Gb;
-    Gb = t;
-    const VT *sp = sv + lane;
-    for (int k = 2; k <= kmm; ++k) {
-        const VT *gp = Ga + y + dlo;
-        VT best;
-        if (sizeof(VT) == 4) {
-            VT b0 = soft, b1 = soft;  // 32-bit values: two minima, independent chains
-            int i = 0;
-#pragma unroll 2
-            for (; i + 1 < ndm; i += 2) {
-                const VT p0 = gp[i], v0 = sp[i * 32], p1 = gp[i + 1], v1 = sp[(i + 1) * 32];
-                const VT c0 = STEP == 1 ? (p0 > v0 ? p0 : v0) : VT(p0 + v0);
-                const VT c1 = STEP == 1 ? (p1 > v1 ? p1 : v1) : VT(p1 + v1);
-                b0 = c0 < b0 ? c0 : b0;
-                b1 = c1 < b1 ? c1 : b1;
-            }
-            if (i < ndm) {
-                const VT p0 = gp[i], v0 = sp[i * 32];
-                const VT c0 = STEP == 1 ? (p0 > v0 ? p0 : v0) : VT(p0 + v0);
-                b0 = c0 < b0 ? c0 : b0;
-            }
-            best = b0 < b1 ? b0 : b1;
-        } else {
-            best = soft;
-#pragma unroll 4
-            for (int i = 0; i < ndm; ++i) {
-                const VT prev = gp[i], val = sp[i * 32];
-                const VT c = STEP == 1 ? (prev > val ? prev : val) : VT(prev + val);
-                best = c < best ? c : best;
-            }
+    VT g0 = l == 0 ? g1 : soft;  // lane k - 1 collects G_k[0]
+    // k >= 2 relaxes only full-height slices: with none admitted in either
+    // half G_k is empty for every k >= 2
+    if (ndm >= 1) {
+        switch (ndm) {
+#define TRS_ND_CASE(K) \
+    case K: g0 = pair_rows<STEP, VT, S, K>(stage, nd, dlo, kmm, Gb, Ga, g0); break;
+            TRS_ND_CASE(1) TRS_ND_CASE(2) TRS_ND_CASE(3) TRS_ND_CASE(4) TRS_ND_CASE(5) TRS_ND_CASE(6)
+            TRS_ND_CASE(7) TRS_ND_CASE(8) TRS_ND_CASE(9) TRS_ND_CASE(10) TRS_ND_CASE(11) TRS_ND_CASE(12)
+#undef TRS_ND_CASE
+            default: g0 = pair_rows_any<STEP, VT>(sv, ndm, dlo, kmm, Gb, Ga, g0);
         }
-        if (k <= kmax) {  // a half past its kmax runs on, unread
-            Gb[y] = best < soft ? best : soft;
-            if (l == 0) {
-                Gb[16] = soft;  // G_k[16] of a 17-row frame, k >= 2
-                Gb[17] = soft;  // G_k[R] of a 17-row frame, k >= 1
-            }
-        }
-        __syncwarp();
-        if (l == k - 1 && k <= kmax) {
-            const VT g0 = Gb[0];
-            vreg = g0 >= soft ? kInf : (uint64_t)g0;
-        }
-        t = Ga;
-        Ga = Gb;
-        Gb = t;
     }
     if (have) {
         uint64_t *V = Vall + (size_t)mi * (n + 1);
         if (l == 0) V[0] = kInf;
         const int kmin = pl.items[mi].kmin;  // read here: nothing extra stays live through the k loop
-        // counts below kmin complete no partition; "none" is kSoft in step 2 (the column DP adds it)
-        if (l < n) V[l + 1] = l + 1 >= kmin && vreg != kInf ? vreg : (STEP == 1 ? kInf : kSoft);
+        // counts outside [kmin, kmax] complete no partition; "none" is kSoft
+        // in step 2 (the column DP adds it)
+        const int k = l + 1;
+        if (l < n) V[k] = k >= kmin && k <= kmax && g0 < soft ? (uint64_t)g0 : (STEP == 1 ? kInf : kSoft);
     }
 }
 
@@ -1023,8 +1075,10 @@ int launch_search(const LaunchArgs &a, int total_bands, int total_windows, int m
     const int stage_words = maxR * 32;  // rebuild's staging (stride 32)
     const int S = maxR <= 17 && maxN <= 16 ? 17 : 32;
     // the per-item staging holds the admitted full-height values (at most
-    // max_nd heights) in the paired path, up to R heights in the other
-    const int band_stage = maxR * S, band_itm = (S == 17 && max_nd > 0 ? std::min(max_nd, maxR) : maxR) * 32;
+    // max_nd heights) in the paired path, up to R heights in the other; the
+    // paired path keeps up to kNdRegs heights in registers and needs none
+    const int band_itm = S == 17 && max_nd > 0 ? (max_nd <= kNdRegs ? 0 : std::min(max_nd, maxR) * 32) : maxR * 32;
+    const int band_stage = maxR * S;
     const size_t band_smem = (size_t)bw * (band_stage + band_itm + kBandTail) * sizeof(uint64_t);
     const int bb = (total_bands + bw - 1) / bw;
     auto mark = [&](int i) {
