@@ -657,6 +657,7 @@ __device__ VT col_frames(const DevPlan &pl, int C, int w, int F, int lf, int f, 
         // infinity where k > m
         VT acc0 = soft, acc1 = soft;
         int i = 0;
+#pragma unroll 2
         for (; i + 1 < nv; i += 2) {
             const uint32_t d0 = md[i], d1 = md[i + 1];
             const VT v0 = (VT)vb[(size_t)i * F], v1 = (VT)vb[(size_t)(i + 1) * F];
