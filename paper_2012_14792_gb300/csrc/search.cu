@@ -325,16 +325,25 @@ __device__ void item_pair(const DevFrame &fr, const DevPlan &pl, int mi, const P
     VT g0 = l == 0 ? g1 : soft;  // lane k - 1 collects G_k[0]
     // k >= 2 relaxes only full-height slices: with none admitted in either
     // half G_k is empty for every k >= 2
-    if (ndm >= 1) {
-        switch (ndm) {
 #define TRS_ND_CASE(K) \
     case K: g0 = pair_rows<STEP, VT, S, K>(stage, nd, dlo, kmm, Gb, Ga, g0); break;
-            TRS_ND_CASE(1) TRS_ND_CASE(2) TRS_ND_CASE(3) TRS_ND_CASE(4) TRS_ND_CASE(5) TRS_ND_CASE(6)
-            TRS_ND_CASE(7) TRS_ND_CASE(8) TRS_ND_CASE(9) TRS_ND_CASE(10) TRS_ND_CASE(11) TRS_ND_CASE(12)
-#undef TRS_ND_CASE
-            default: g0 = pair_rows_any<STEP, VT>(sv, ndm, dlo, kmm, Gb, Ga, g0);
+    if (ndm >= 1) {
+        if (sizeof(VT) == 8) {
+            // 64-bit values: even bounds only (an odd count runs one height
+            // of the saturating infinity more), half the code to cache
+            switch ((ndm + 1) & ~1) {
+                TRS_ND_CASE(2) TRS_ND_CASE(4) TRS_ND_CASE(6) TRS_ND_CASE(8) TRS_ND_CASE(10) TRS_ND_CASE(12)
+                default: g0 = pair_rows_any<STEP, VT>(sv, ndm, dlo, kmm, Gb, Ga, g0);
+            }
+        } else {
+            switch (ndm) {
+                TRS_ND_CASE(1) TRS_ND_CASE(2) TRS_ND_CASE(3) TRS_ND_CASE(4) TRS_ND_CASE(5) TRS_ND_CASE(6)
+                TRS_ND_CASE(7) TRS_ND_CASE(8) TRS_ND_CASE(9) TRS_ND_CASE(10) TRS_ND_CASE(11) TRS_ND_CASE(12)
+                default: g0 = pair_rows_any<STEP, VT>(sv, ndm, dlo, kmm, Gb, Ga, g0);
+            }
         }
     }
+#undef TRS_ND_CASE
     if (have) {
         uint64_t *V = Vall + (size_t)mi * (n + 1);
         if (l == 0) V[0] = kInf;
