@@ -482,7 +482,7 @@ def run_serving(trs, device: int, duration_s: float = 7.0, saturate_s: float = 1
         trs.trs_server_destroy(srv)
 
 
-def run_multi_tile(runtime, trs, device: int, reps: int = 50, ns=(6, 7)):
+def run_multi_tile(runtime, trs, device: int, reps: int = 50, ns=(6, 7, 8)):
     """Multi-tile rectangular slices (trs_search_mt) on one 1920x1080 frame:
     the slice-set list is built on the host once per shape (timed apart), then
     the device search (one graph: two passes over the list, one decode warp)
@@ -531,8 +531,8 @@ def run_multi_tile(runtime, trs, device: int, reps: int = 50, ns=(6, 7)):
     finally:
         dec.close()
     return {"searches": res,
-            "note": "one graph launch per search: argument copy, two passes over the list "
-                    "(L2-resident at these sizes), decode; list_read_gbs counts two reads of the list"}
+            "note": "one graph launch per search: argument copy, two passes over the list, decode; "
+                    "list_read_gbs counts two reads of the list (L2-resident at n = 6, 7; 125 MB at n = 8)"}
 
 
 def run_reference(args, rank, world):
@@ -580,7 +580,7 @@ def main():
     ap.add_argument("--no-light", action="store_true")
     ap.add_argument("--no-mt", action="store_true", help="skip the multi-tile slice search timing")
     ap.add_argument("--mt-only", action="store_true",
-                    help="only the multi-tile search at 1920x1080, n = 7, 5 timed calls (profiling runs)")
+                    help="only the multi-tile search at 1920x1080, n = 6, 7 and 8, 50 timed calls each")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default launch shapes (short profiling runs)")
     ap.add_argument("--in-flight", type=int, default=IN_FLIGHT, choices=[1, 2, 3],
@@ -603,7 +603,7 @@ def main():
         import __graft_entry__
         __graft_entry__.build()
         from paper_2012_14792_gb300 import runtime, trs
-        print(json.dumps({"multi_tile": run_multi_tile(runtime, trs, local, reps=50, ns=(6, 7))}), flush=True)
+        print(json.dumps({"multi_tile": run_multi_tile(runtime, trs, local)}), flush=True)
         return
 
     nfr = args.frames

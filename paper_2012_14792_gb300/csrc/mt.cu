@@ -22,11 +22,12 @@
 //    pieces joined in that order.  The device keeps, slice-major, each
 //    slice's 32-bit index into the region tables' rectangle entries (any
 //    rectangle of CTUs is a tile-column slice there).
-//  * device, one captured graph per call: a grid-stride pass takes T_min
-//    (Eq. 3); a second keeps, per block, the smallest (Q, list index) among
-//    the sets within Eq. 4's bound, so Q* (Eq. 2) and the first set reaching
-//    it come out together; one warp reduces the blocks' pairs and decodes
-//    the winner.
+//  * device, one captured graph per call: a pass streams the list through
+//    shared memory (asynchronous copies, the next tile in flight while the
+//    current one is evaluated) and takes T_min (Eq. 3); a second keeps, per
+//    block, the smallest (Q, list index) among the sets within Eq. 4's
+//    bound, so Q* (Eq. 2) and the first set reaching it come out together;
+//    one warp reduces the blocks' pairs and decodes the winner.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -308,12 +309,14 @@ int mt_enumerate(int W, int H, int n, int k, std::vector<uint8_t> *keys, int64_t
 namespace {
 
 constexpr int kMtThreads = 256;
-constexpr int kMtBlocks = 152 * 8;  // at most this many blocks per pass (grid-stride beyond)
+constexpr int kMtStageBytes = 32 * 1024;  // one tile's slice indices (two tiles in flight per block)
 
 struct MtArgs {
-    const uint32_t *ent;  // slice i of set c at ent[i * count + c]: its rectangle-table entry index
-    int64_t count;
+    const uint32_t *ent;  // slice i of set c at ent[i * pitch + c]: its rectangle-table entry index
+    int64_t count;        // slice sets
+    int64_t pitch;        // count rounded up to a multiple of 4 (16-byte rows)
     int n, C, R, W, H, nblocks;
+    int tile;             // sets per tile: a multiple of kMtThreads with n * tile * 4 <= kMtStageBytes
     const MtCall *call;   // tables, output, lambda of this call
     uint64_t *tmin;       // T_min: +infinity before the first pass (set at creation, reset by each decode)
     uint64_t *part;       // [nblocks][2]: each block's smallest (Q, set) of the second pass
@@ -337,91 +340,136 @@ __device__ __forceinline__ void pair_min_xor(uint64_t &q, uint64_t &c, int o) {
     }
 }
 
-// Time (max over slices, Eq. 1) and quality term (sum, Eq. 2) of slice set
-// c; the slice-major list makes each of the n loads coalesced over the
-// threads of a warp.
-__device__ __forceinline__ void mt_eval(const MtArgs &a, const uint64_t *RT, const uint64_t *RQ, int64_t c,
-                                        uint64_t *tmax, uint64_t *qsum, bool with_q) {
-    uint64_t t = 0, q = 0;
-    // eight slices at a time: their index loads, then their table gathers,
-    // each group in flight together
-    for (int i0 = 0; i0 < a.n; i0 += 8) {
-        uint32_t e[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) e[u] = i0 + u < a.n ? __ldg(a.ent + (size_t)(i0 + u) * a.count + c) : 0u;
-        uint64_t tv[8], qv[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            tv[u] = i0 + u < a.n ? __ldg(RT + e[u]) : 0ull;
-            qv[u] = with_q && i0 + u < a.n ? __ldg(RQ + e[u]) : 0ull;
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            t = tv[u] > t ? tv[u] : t;
-            q += qv[u];
-        }
+__device__ __forceinline__ void mt_cp16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void mt_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void mt_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Copies tile t's slice indices (n rows of up to `tile` words, 16 bytes
+// at a time) into stage buffer `buf` with asynchronous copies.
+__device__ __forceinline__ void mt_stage(const MtArgs &a, uint32_t *stage, int64_t t) {
+    const int64_t c0 = t * a.tile;
+    const int64_t rest = a.pitch - c0;
+    const int len = rest < a.tile ? (int)rest : a.tile;  // a multiple of 4
+    const int q4 = len >> 2, total = a.n * q4;
+    for (int q = threadIdx.x; q < total; q += kMtThreads) {
+        const int i = q / q4, o = (q - i * q4) << 2;
+        mt_cp16(stage + i * a.tile + o, a.ent + (size_t)i * a.pitch + c0 + o);
     }
-    *tmax = t;
-    *qsum = q;
 }
 
-// Pass 1: T_min (Eq. 3).  Grid-stride loop, per-thread minima, one warp
-// reduction and one atomic minimum per warp.
-__global__ void __launch_bounds__(kMtThreads) mt_tmin_kernel(MtArgs a) {
-    const MtCall call = *a.call;
-    const TablesOffsets off = tables_offsets(a.C, a.R);
-    if (reinterpret_cast<const int32_t *>(call.tables + off.status)[0] != TRS_OK) return;
-    const uint64_t *RT = reinterpret_cast<const uint64_t *>(call.tables + off.rect_t);
-    uint64_t best = kInf;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < a.count; c += stride) {
-        uint64_t t, q;
-        mt_eval(a, RT, nullptr, c, &t, &q, false);
-        best = t < best ? t : best;
-    }
-    best = warp_min64(best);
-    if ((threadIdx.x & 31) == 0 && best != kInf)
-        atomicMin(reinterpret_cast<unsigned long long *>(a.tmin), (unsigned long long)best);
-}
-
-// Pass 2: among the sets within Eq. 4's bound, the smallest (Q, list
-// index) -- Q* (Eq. 2) and the first set reaching it in one go; each block
-// stores its own minimum, the decode kernel reduces them.
-__global__ void __launch_bounds__(kMtThreads) mt_q_kernel(MtArgs a) {
+// Both passes stream the slice-major list through shared memory, two tiles
+// in flight per block (the next tile's copies run while the current one is
+// evaluated), blocks striding over the tiles.  Per set: the time (max over
+// slices, Eq. 1) and, in the second pass, the quality term (sum, Eq. 2),
+// gathered from the region tables (any rectangle of CTUs is a tile-column
+// slice there; the tables stay in L1/L2).
+//  PASS 1: T_min (Eq. 3): per-thread minima, one atomic minimum per warp.
+//  PASS 2: among the sets within Eq. 4's bound, the smallest (Q, list
+//          index) -- Q* (Eq. 2) and the first set reaching it in one go;
+//          each block stores its own minimum, the decode kernel reduces.
+template <int PASS>
+__global__ void __launch_bounds__(kMtThreads) mt_pass_kernel(MtArgs a) {
+    extern __shared__ __align__(16) uint32_t mts[];
     __shared__ uint64_t wq[kMtThreads / 32], wc[kMtThreads / 32];
     const MtCall call = *a.call;
     const TablesOffsets off = tables_offsets(a.C, a.R);
-    uint64_t bq = kInf, bc = kInf;
-    if (reinterpret_cast<const int32_t *>(call.tables + off.status)[0] == TRS_OK) {
-        const uint64_t *RT = reinterpret_cast<const uint64_t *>(call.tables + off.rect_t);
-        const uint64_t *RQ = reinterpret_cast<const uint64_t *>(call.tables + off.rect_q);
-        const uint64_t thr = eq4_threshold(*a.tmin, call.lambda_q);
-        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-        for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < a.count; c += stride) {
-            uint64_t t, q;
-            mt_eval(a, RT, RQ, c, &t, &q, true);
-            if (t <= thr && q < bq) {  // c grows, so the first set at a thread's minimum is kept
-                bq = q;
-                bc = (uint64_t)c;
+    const bool ok = reinterpret_cast<const int32_t *>(call.tables + off.status)[0] == TRS_OK;
+    const uint64_t *RT = reinterpret_cast<const uint64_t *>(call.tables + off.rect_t);
+    const uint64_t *RQ = reinterpret_cast<const uint64_t *>(call.tables + off.rect_q);
+    const uint32_t *RT32 = reinterpret_cast<const uint32_t *>(RT);  // low word of entry e at 2e
+    const bool t32 = ok && reinterpret_cast<const int32_t *>(call.tables + off.status)[3] != 0;
+    const uint64_t thr = PASS == 2 ? eq4_threshold(*a.tmin, call.lambda_q) : 0ull;
+    const int64_t ntiles = (a.count + a.tile - 1) / a.tile;
+    uint64_t best = kInf, bq = kInf, bc = kInf;
+    if (ok) {
+        const int words = a.n * a.tile;
+        int buf = 0;
+        int64_t t = blockIdx.x;
+        if (t < ntiles) mt_stage(a, mts, t);
+        mt_commit();
+        for (; t < ntiles; t += gridDim.x) {
+            if (t + gridDim.x < ntiles) mt_stage(a, mts + (buf ^ 1) * words, t + gridDim.x);
+            mt_commit();
+            mt_wait_prev();  // this thread's copies of tile t have landed
+            __syncthreads();  // and every other thread's
+            const uint32_t *st = mts + buf * words;
+            const int64_t c0 = t * a.tile;
+            for (int s = threadIdx.x; s < a.tile; s += kMtThreads) {
+                const int64_t c = c0 + s;
+                if (c >= a.count) break;
+                uint64_t tm = 0, q = 0;
+                // eight slices' gathers in flight at a time; a frame whose
+                // total time is below 2^31 (the tables' flag) reads only the
+                // low words of its times
+                for (int i0 = 0; i0 < a.n; i0 += 8) {
+                    uint32_t e[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) e[u] = i0 + u < a.n ? st[(i0 + u) * a.tile + s] : 0u;
+                    uint64_t qv[8];
+                    if (t32) {
+                        uint32_t tv[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            tv[u] = i0 + u < a.n ? __ldg(RT32 + 2 * (size_t)e[u]) : 0u;
+                            qv[u] = PASS == 2 && i0 + u < a.n ? __ldg(RQ + e[u]) : 0ull;
+                        }
+                        uint32_t m32 = (uint32_t)tm;
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            m32 = tv[u] > m32 ? tv[u] : m32;
+                            q += qv[u];
+                        }
+                        tm = m32;
+                    } else {
+                        uint64_t tv[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            tv[u] = i0 + u < a.n ? __ldg(RT + e[u]) : 0ull;
+                            qv[u] = PASS == 2 && i0 + u < a.n ? __ldg(RQ + e[u]) : 0ull;
+                        }
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            tm = tv[u] > tm ? tv[u] : tm;
+                            q += qv[u];
+                        }
+                    }
+                }
+                if (PASS == 1) {
+                    best = tm < best ? tm : best;
+                } else if (tm <= thr && q < bq) {  // c grows, so the first set at a thread's minimum is kept
+                    bq = q;
+                    bc = (uint64_t)c;
+                }
             }
+            __syncthreads();  // tile t's buffer is free for tile t + 2 * gridDim.x
+            buf ^= 1;
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) pair_min_xor(bq, bc, o);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) {
-        wq[w] = bq;
-        wc[w] = bc;
-    }
-    __syncthreads();
-    if (w == 0) {
-        bq = lane < (int)(blockDim.x >> 5) ? wq[lane] : kInf;
-        bc = lane < (int)(blockDim.x >> 5) ? wc[lane] : kInf;
+    if constexpr (PASS == 1) {
+        best = warp_min64(best);
+        if ((threadIdx.x & 31) == 0 && best != kInf)
+            atomicMin(reinterpret_cast<unsigned long long *>(a.tmin), (unsigned long long)best);
+    } else {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) pair_min_xor(bq, bc, o);
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
         if (lane == 0) {
-            a.part[2 * blockIdx.x] = bq;
-            a.part[2 * blockIdx.x + 1] = bc;
+            wq[w] = bq;
+            wc[w] = bc;
+        }
+        __syncthreads();
+        if (w == 0) {
+            bq = lane < (int)(blockDim.x >> 5) ? wq[lane] : kInf;
+            bc = lane < (int)(blockDim.x >> 5) ? wc[lane] : kInf;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) pair_min_xor(bq, bc, o);
+            if (lane == 0) {
+                a.part[2 * blockIdx.x] = bq;
+                a.part[2 * blockIdx.x + 1] = bc;
+            }
         }
     }
 }
@@ -475,7 +523,7 @@ __global__ void __launch_bounds__(32) mt_finish_kernel(MtArgs a) {
     uint64_t t = 0, q = 0;
     double sse = 0.0;
     if (lane < a.n) {
-        const uint32_t e = a.ent[(size_t)lane * a.count + win];
+        const uint32_t e = a.ent[(size_t)lane * a.pitch + win];
         // e = (band * R + (y1 - y0 - 1)) * R + y0, band = band_index(C, x0, x1)
         const int R = a.R, C = a.C;
         const int y0 = (int)(e % (uint32_t)R);
@@ -542,21 +590,48 @@ static int mt_create(trs_ctx *ctx, int W, int H, int n, MtEntry **out) {
     int64_t count = 0;
     TRS_TRY(mt_enumerate(W, H, n, ctx->o.k_area, &keys, &count));
     const int C = (W + kCtu - 1) / kCtu, R = (H + kCtu - 1) / kCtu;
-    std::vector<uint32_t> ent((size_t)count * n);
+    const int64_t pitch = (count + 3) & ~int64_t(3);  // 16-byte rows for the staged copies
+    std::vector<uint32_t> ent((size_t)pitch * n, 0u);
     for (int64_t c = 0; c < count; ++c)
         for (int i = 0; i < n; ++i) {
             const uint8_t *k = &keys[((size_t)c * n + i) * 4];  // y0, x0, y1, x1
-            ent[(size_t)i * count + c] =
+            ent[(size_t)i * pitch + c] =
                 (uint32_t)(((size_t)band_index(C, k[1], k[3]) * R + (k[2] - k[0] - 1)) * R + k[0]);
         }
     std::vector<uint8_t>().swap(keys);
     MtEntry *me = new (std::nothrow) MtEntry;
     if (!me) return TRS_ENOMEM;
     me->count = count;
-    const int nblocks = (int)std::max<int64_t>(1, std::min<int64_t>((count + kMtThreads - 1) / kMtThreads, kMtBlocks));
+    // tiles of up to 8 sets per thread whose n slice rows fit one stage
+    // buffer, smaller when the list would not give every resident block a
+    // tile; as many blocks as stay resident (two stage buffers each)
+    const int tile_max = kMtThreads * std::max(1, std::min(8, kMtStageBytes / (4 * kMtThreads * n)));
+    const int smem_max = 2 * n * tile_max * 4;
+    int dev = 0, sms = 0, per_sm1 = 0, per_sm2 = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(mt_pass_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(mt_pass_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, mt_pass_kernel<1>, kMtThreads, smem_max);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, mt_pass_kernel<2>, kMtThreads, smem_max);
+    if (e != cudaSuccess) {
+        delete me;
+        return cuda_fail(e, "multi-tile launch shape");
+    }
+    const int64_t resident = std::max(1, sms * std::max(1, std::min(per_sm1, per_sm2)));
+    const int64_t per_block = (count + resident - 1) / resident;
+    const int tile = (int)std::min<int64_t>(tile_max, std::max<int64_t>(
+                                                          kMtThreads, (per_block + kMtThreads - 1) / kMtThreads * kMtThreads));
+    const int smem = 2 * n * tile * 4;
+    const int64_t ntiles = (count + tile - 1) / tile;
+    const int nblocks = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, resident));
     // work: MtCall (4 words), T_min (4 words), per-block pairs
     const size_t work_bytes = 8 * sizeof(uint64_t) + (size_t)nblocks * 2 * sizeof(uint64_t);
-    int st = dev_alloc(me->cands, std::max<size_t>(ent.size() * 4, 4), &ctx->total);
+    int st = dev_alloc(me->cands, std::max<size_t>(ent.size() * 4, 16), &ctx->total);
     if (st == TRS_OK) st = dev_alloc(me->work, work_bytes, &ctx->total);
     auto fail = [&](int code) {
         ctx->total -= me->cands.n + me->work.n;
@@ -564,7 +639,6 @@ static int mt_create(trs_ctx *ctx, int W, int H, int n, MtEntry **out) {
         return code;
     };
     if (st != TRS_OK) return fail(st);
-    cudaError_t e = cudaSuccess;
     if (!ent.empty()) e = cudaMemcpy(me->cands.p, ent.data(), ent.size() * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&me->call_host, kMtSlots * sizeof(MtCall));
     for (int k = 0; k < kMtSlots && e == cudaSuccess; ++k)
@@ -576,6 +650,8 @@ static int mt_create(trs_ctx *ctx, int W, int H, int n, MtEntry **out) {
     MtArgs a;
     a.ent = (const uint32_t *)me->cands.p;
     a.count = count;
+    a.pitch = pitch;
+    a.tile = tile;
     a.n = n;
     a.C = C;
     a.R = R;
@@ -593,8 +669,8 @@ static int mt_create(trs_ctx *ctx, int W, int H, int n, MtEntry **out) {
         e = cudaMemcpyAsync(wk, me->call_host + k, sizeof(MtCall), cudaMemcpyHostToDevice, cs);
         if (e == cudaSuccess) e = record_event(me->copied[k], cs);
         if (e == cudaSuccess && count > 0) {
-            mt_tmin_kernel<<<nblocks, kMtThreads, 0, cs>>>(a);
-            mt_q_kernel<<<nblocks, kMtThreads, 0, cs>>>(a);
+            mt_pass_kernel<1><<<nblocks, kMtThreads, smem, cs>>>(a);
+            mt_pass_kernel<2><<<nblocks, kMtThreads, smem, cs>>>(a);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) {
