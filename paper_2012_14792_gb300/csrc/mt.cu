@@ -353,10 +353,11 @@ __device__ __forceinline__ void mt_stage(const MtArgs &a, uint32_t *stage, int64
     const int64_t c0 = t * a.tile;
     const int64_t rest = a.pitch - c0;
     const int len = rest < a.tile ? (int)rest : a.tile;  // a multiple of 4
-    const int q4 = len >> 2, total = a.n * q4;
-    for (int q = threadIdx.x; q < total; q += kMtThreads) {
-        const int i = q / q4, o = (q - i * q4) << 2;
-        mt_cp16(stage + i * a.tile + o, a.ent + (size_t)i * a.pitch + c0 + o);
+    const int q4 = len >> 2;
+    for (int i = 0; i < a.n; ++i) {
+        const uint32_t *src = a.ent + (size_t)i * a.pitch + c0;
+        uint32_t *dst = stage + i * a.tile;
+        for (int o = threadIdx.x; o < q4; o += kMtThreads) mt_cp16(dst + 4 * o, src + 4 * o);
     }
 }
 
@@ -370,7 +371,44 @@ __device__ __forceinline__ void mt_stage(const MtArgs &a, uint32_t *stage, int64
 //  PASS 2: among the sets within Eq. 4's bound, the smallest (Q, list
 //          index) -- Q* (Eq. 2) and the first set reaching it in one go;
 //          each block stores its own minimum, the decode kernel reduces.
-template <int PASS>
+// Time and quality term of one set of N slices (N a compile-time count):
+// col[i * stride] holds slice i's rectangle-table index.  A frame whose
+// total time is below 2^31 (the tables' flag) reads only the low words of
+// its times.
+template <int PASS, int N>
+__device__ __forceinline__ void set_eval(const uint32_t *col, int stride, const uint64_t *RT, const uint64_t *RQ,
+                                         bool t32, uint64_t *tmax, uint64_t *qsum) {
+    uint32_t e[N];
+#pragma unroll
+    for (int u = 0; u < N; ++u) e[u] = col[u * stride];
+    uint64_t q = 0;
+    if (t32) {
+        const uint32_t *RT32 = reinterpret_cast<const uint32_t *>(RT);  // low word of entry e at 2e
+        uint32_t tv[N];
+#pragma unroll
+        for (int u = 0; u < N; ++u) tv[u] = __ldg(RT32 + 2 * (size_t)e[u]);
+        if (PASS == 2) {
+#pragma unroll
+            for (int u = 0; u < N; ++u) q += __ldg(RQ + e[u]);
+        }
+        uint32_t m = 0;
+#pragma unroll
+        for (int u = 0; u < N; ++u) m = tv[u] > m ? tv[u] : m;
+        *tmax = m;
+    } else {
+        uint64_t m = 0;
+#pragma unroll
+        for (int u = 0; u < N; ++u) {
+            const uint64_t tv = __ldg(RT + e[u]);
+            m = tv > m ? tv : m;
+            if (PASS == 2) q += __ldg(RQ + e[u]);
+        }
+        *tmax = m;
+    }
+    *qsum = q;
+}
+
+template <int PASS, int N>
 __global__ void __launch_bounds__(kMtThreads) mt_pass_kernel(MtArgs a) {
     extern __shared__ __align__(16) uint32_t mts[];
     __shared__ uint64_t wq[kMtThreads / 32], wc[kMtThreads / 32];
@@ -379,7 +417,6 @@ __global__ void __launch_bounds__(kMtThreads) mt_pass_kernel(MtArgs a) {
     const bool ok = reinterpret_cast<const int32_t *>(call.tables + off.status)[0] == TRS_OK;
     const uint64_t *RT = reinterpret_cast<const uint64_t *>(call.tables + off.rect_t);
     const uint64_t *RQ = reinterpret_cast<const uint64_t *>(call.tables + off.rect_q);
-    const uint32_t *RT32 = reinterpret_cast<const uint32_t *>(RT);  // low word of entry e at 2e
     const bool t32 = ok && reinterpret_cast<const int32_t *>(call.tables + off.status)[3] != 0;
     const uint64_t thr = PASS == 2 ? eq4_threshold(*a.tmin, call.lambda_q) : 0ull;
     const int64_t ntiles = (a.count + a.tile - 1) / a.tile;
@@ -401,42 +438,22 @@ __global__ void __launch_bounds__(kMtThreads) mt_pass_kernel(MtArgs a) {
                 const int64_t c = c0 + s;
                 if (c >= a.count) break;
                 uint64_t tm = 0, q = 0;
-                // eight slices' gathers in flight at a time; a frame whose
-                // total time is below 2^31 (the tables' flag) reads only the
-                // low words of its times
-                for (int i0 = 0; i0 < a.n; i0 += 8) {
-                    uint32_t e[8];
+                if constexpr (N > 0)
+                    set_eval<PASS, N>(st + s, a.tile, RT, RQ, t32, &tm, &q);
+                else
+                    for (int i0 = 0; i0 < a.n; i0 += 8) {
+                        // eight slices' gathers in flight at a time
+                        uint32_t e[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) e[u] = i0 + u < a.n ? st[(i0 + u) * a.tile + s] : 0u;
-                    uint64_t qv[8];
-                    if (t32) {
-                        uint32_t tv[8];
+                        for (int u = 0; u < 8; ++u) e[u] = i0 + u < a.n ? st[(i0 + u) * a.tile + s] : 0u;
 #pragma unroll
                         for (int u = 0; u < 8; ++u) {
-                            tv[u] = i0 + u < a.n ? __ldg(RT32 + 2 * (size_t)e[u]) : 0u;
-                            qv[u] = PASS == 2 && i0 + u < a.n ? __ldg(RQ + e[u]) : 0ull;
-                        }
-                        uint32_t m32 = (uint32_t)tm;
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            m32 = tv[u] > m32 ? tv[u] : m32;
-                            q += qv[u];
-                        }
-                        tm = m32;
-                    } else {
-                        uint64_t tv[8];
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            tv[u] = i0 + u < a.n ? __ldg(RT + e[u]) : 0ull;
-                            qv[u] = PASS == 2 && i0 + u < a.n ? __ldg(RQ + e[u]) : 0ull;
-                        }
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            tm = tv[u] > tm ? tv[u] : tm;
-                            q += qv[u];
+                            const uint64_t tv = i0 + u < a.n ? __ldg(RT + e[u]) : 0ull;
+                            const uint64_t qv = PASS == 2 && i0 + u < a.n ? __ldg(RQ + e[u]) : 0ull;
+                            tm = tv > tm ? tv : tm;
+                            q += qv;
                         }
                     }
-                }
                 if (PASS == 1) {
                     best = tm < best ? tm : best;
                 } else if (tm <= thr && q < bq) {  // c grows, so the first set at a thread's minimum is kept
@@ -610,14 +627,21 @@ static int mt_create(trs_ctx *ctx, int W, int H, int n, MtEntry **out) {
     int dev = 0, sms = 0, per_sm1 = 0, per_sm2 = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(mt_pass_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(mt_pass_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, mt_pass_kernel<1>, kMtThreads, smem_max);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, mt_pass_kernel<2>, kMtThreads, smem_max);
+    void (*k1)(MtArgs) = mt_pass_kernel<1, 0>, (*k2)(MtArgs) = mt_pass_kernel<2, 0>;
+    switch (n) {  // slice counts up to 8 run a kernel compiled for that count
+#define TRS_MT_N(K)                 \
+    case K:                         \
+        k1 = mt_pass_kernel<1, K>;  \
+        k2 = mt_pass_kernel<2, K>;  \
+        break;
+        TRS_MT_N(1) TRS_MT_N(2) TRS_MT_N(3) TRS_MT_N(4) TRS_MT_N(5) TRS_MT_N(6) TRS_MT_N(7) TRS_MT_N(8)
+#undef TRS_MT_N
+        default: break;
+    }
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, k1, kMtThreads, smem_max);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, k2, kMtThreads, smem_max);
     if (e != cudaSuccess) {
         delete me;
         return cuda_fail(e, "multi-tile launch shape");
@@ -669,8 +693,8 @@ static int mt_create(trs_ctx *ctx, int W, int H, int n, MtEntry **out) {
         e = cudaMemcpyAsync(wk, me->call_host + k, sizeof(MtCall), cudaMemcpyHostToDevice, cs);
         if (e == cudaSuccess) e = record_event(me->copied[k], cs);
         if (e == cudaSuccess && count > 0) {
-            mt_pass_kernel<1><<<nblocks, kMtThreads, smem, cs>>>(a);
-            mt_pass_kernel<2><<<nblocks, kMtThreads, smem, cs>>>(a);
+            k1<<<nblocks, kMtThreads, smem, cs>>>(a);
+            k2<<<nblocks, kMtThreads, smem, cs>>>(a);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) {
