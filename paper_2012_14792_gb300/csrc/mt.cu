@@ -374,37 +374,40 @@ __device__ __forceinline__ void mt_stage(const MtArgs &a, uint32_t *stage, int64
 // Time and quality term of one set of N slices (N a compile-time count):
 // col[i * stride] holds slice i's rectangle-table index.  A frame whose
 // total time is below 2^31 (the tables' flag) reads only the low words of
-// its times.
+// its times.  The quality terms are gathered (second pass) only for a set
+// within Eq. 4's bound thr; *qsum is left 0 otherwise.
 template <int PASS, int N>
 __device__ __forceinline__ void set_eval(const uint32_t *col, int stride, const uint64_t *RT, const uint64_t *RQ,
-                                         bool t32, uint64_t *tmax, uint64_t *qsum) {
+                                         bool t32, uint64_t thr, uint64_t *tmax, uint64_t *qsum) {
     uint32_t e[N];
 #pragma unroll
     for (int u = 0; u < N; ++u) e[u] = col[u * stride];
-    uint64_t q = 0;
+    uint64_t m = 0;
     if (t32) {
         const uint32_t *RT32 = reinterpret_cast<const uint32_t *>(RT);  // low word of entry e at 2e
         uint32_t tv[N];
 #pragma unroll
         for (int u = 0; u < N; ++u) tv[u] = __ldg(RT32 + 2 * (size_t)e[u]);
-        if (PASS == 2) {
+        uint32_t m32 = 0;
 #pragma unroll
-            for (int u = 0; u < N; ++u) q += __ldg(RQ + e[u]);
-        }
-        uint32_t m = 0;
+        for (int u = 0; u < N; ++u) m32 = tv[u] > m32 ? tv[u] : m32;
+        m = m32;
+    } else {
+        uint64_t tv[N];
+#pragma unroll
+        for (int u = 0; u < N; ++u) tv[u] = __ldg(RT + e[u]);
 #pragma unroll
         for (int u = 0; u < N; ++u) m = tv[u] > m ? tv[u] : m;
-        *tmax = m;
-    } else {
-        uint64_t m = 0;
-#pragma unroll
-        for (int u = 0; u < N; ++u) {
-            const uint64_t tv = __ldg(RT + e[u]);
-            m = tv > m ? tv : m;
-            if (PASS == 2) q += __ldg(RQ + e[u]);
-        }
-        *tmax = m;
     }
+    uint64_t q = 0;
+    if (PASS == 2 && m <= thr) {
+        uint64_t qv[N];
+#pragma unroll
+        for (int u = 0; u < N; ++u) qv[u] = __ldg(RQ + e[u]);
+#pragma unroll
+        for (int u = 0; u < N; ++u) q += qv[u];
+    }
+    *tmax = m;
     *qsum = q;
 }
 
@@ -439,7 +442,7 @@ __global__ void __launch_bounds__(kMtThreads) mt_pass_kernel(MtArgs a) {
                 if (c >= a.count) break;
                 uint64_t tm = 0, q = 0;
                 if constexpr (N > 0)
-                    set_eval<PASS, N>(st + s, a.tile, RT, RQ, t32, &tm, &q);
+                    set_eval<PASS, N>(st + s, a.tile, RT, RQ, t32, thr, &tm, &q);
                 else
                     for (int i0 = 0; i0 < a.n; i0 += 8) {
                         // eight slices' gathers in flight at a time
