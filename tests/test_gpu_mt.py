@@ -160,6 +160,26 @@ def test_mt_full_frames_six_and_seven_slices(dec, oracle, spec_name, n):
         _assert_equal(dec.search_mt(tab, W, H, n, lam), ref, ref["count"])
 
 
+@pytest.mark.parametrize("W,H,n,tscale", [(640, 512, 8, 1.0), (896, 512, 8, 4000.0), (768, 640, 9, 1.0),
+                                          (768, 512, 10, 4000.0), (640, 640, 12, 1.0)])
+def test_mt_eight_and_more_slices(dec, oracle, W, H, n, tscale):
+    """Slice counts 8 (the largest with a kernel compiled for its count) and
+    9-12 (the generic kernel) against the oracle's rectangle-partition
+    search; tscale = 4000 makes the frame's total Q16 time exceed 2^31, so
+    the passes read 64-bit times."""
+    rng = np.random.default_rng(n * 31 + W)
+    plane = rng.integers(0, 1024, (H, W)).astype(np.uint16)
+    C, R = -(-W // 128), -(-H // 128)
+    times = (rng.uniform(0.5, 2.0, (R, C)) * tscale).astype(np.float32)
+    tab = _tables(dec, plane, times, 10)
+    st = oracle.texture(plane, 10)
+    Tq, _ = oracle.time_q(times)
+    assert (int(Tq.astype(np.int64).sum()) >= 2 ** 31) == (tscale > 1.0)
+    for lam in (0.0, 0.1):
+        ref = oracle.mt_search_rects(st, Tq, n, lam)
+        _assert_equal(dec.search_mt(tab, W, H, n, lam), ref, ref["count"])
+
+
 def test_mt_no_valid_set_and_out_of_range(dec, oracle):
     plane, times = synth.small_frame(256, 256, 10, 1)
     tab = _tables(dec, plane, times, 10)
