@@ -428,7 +428,7 @@ int trs_set_tune(trs_ctx *ctx, int band_warps, int col_warps, int col_batch);
  * call that runs as one launch chain.  0 before the first batched call. */
 int trs_batch_stage_frames(const trs_ctx *ctx);
 
-/* Kernels launched by the most recent batched call (8 per chunk; 0 before
+/* Kernels launched by the most recent batched call (9 per chunk; 0 before
  * the first call). */
 int trs_batch_kernels(const trs_ctx *ctx);
 

@@ -55,7 +55,7 @@ struct BatchGraph {
     size_t staged_bytes = 0;
 };
 
-constexpr int kKernelsPerBatch = 8;  // texture, tables, 2 x (rows, columns), rebuild, finish
+constexpr int kKernelsPerBatch = 9;  // texture, tables, 2 x (rows, columns), rebuild walk, cut bits, finish
 constexpr int kMaxParts = 4;         // most chunks a captured batch is pipelined in
 constexpr int kChunkMin = 4;         // fewest frames in a chunk
 

@@ -790,6 +790,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32) column_kernel(LaunchArgs args,
 // '0' < '1' read from CTU line 1 downwards: compare bit-reversed words.
 __device__ __forceinline__ bool bits_less(uint32_t a, uint32_t b) { return __brev(a) < __brev(b); }
 
+// A code's cut word before cuts_kernel: bit 31 set, the band's item in
+// bits 6..30 and its slice count in bits 0..5.  Cut bits themselves never
+// set bit 31 (at most 31 CTU lines inside a frame of 32 rows).
+constexpr uint32_t kCutPending = 1u << 31;
+
 // Smallest cut bits of a k-slice split of the item's band that reaches
 // layers[k][0], read greedily top-down: the largest next cut line first.
 // Slice values and admissibility come from the shared-memory staging of
@@ -833,8 +838,11 @@ __device__ bool code_less_g(const WinCode &a, const WinCode &b) {
 // lanes at once) and, with lanes over the slice count k, keeps the first x1
 // for which some k completes an optimal partition:
 //   V2[item][k] + H2[x1][m-k] == H2[x][m].
-// The band's row DP is then redone with every layer kept in shared memory
-// and, among the admissible k, the smallest cut bits win.
+// When one k does (every column of the benchmarked sequence), the column's
+// cut word records the item and k with kCutPending set and cuts_kernel
+// fills in the bits; when several do, the band's row DP is redone here with
+// every layer kept in shared memory and the smallest cut bits among them
+// win.
 __global__ void __launch_bounds__(32) rebuild_kernel(LaunchArgs args, int total, int layer_words,
                                                       int stage_words) {
     extern __shared__ uint64_t rsm[];
@@ -891,19 +899,30 @@ __global__ void __launch_bounds__(32) rebuild_kernel(LaunchArgs args, int total,
             if (lane == 0) code.c = -1;
             return;
         }
-        const PlanItem it = pl.items[slot];
-        item_dp<2>(fr, it, thr, n, nullptr, layers, stage, vm);
-        uint32_t bb = 0;
-        int bk = -1;
-        for (unsigned mm = kmask; mm; mm &= mm - 1) {
-            const int kk = __ffs(mm);  // slice count kk = bit index + 1
-            const uint32_t bits = lexmin_bits(it, R, layers, stage, vm, kk);
-            if (bk < 0 || bits_less(bits, bb)) {
-                bb = bits;
-                bk = kk;
+        uint32_t bb;
+        int bk;
+        if (!(kmask & (kmask - 1)) && slot < (1 << 25)) {
+            // one slice count completes the optimum: the column's cut bits
+            // are left to cuts_kernel, which runs the row DPs of all the
+            // code's tile columns in parallel
+            bk = __ffs(kmask);
+            bb = kCutPending | (uint32_t)slot << 6 | (uint32_t)bk;
+        } else {
+            // several do: the smallest cut bits among them decide here
+            const PlanItem it = pl.items[slot];
+            item_dp<2>(fr, it, thr, n, nullptr, layers, stage, vm);
+            bb = 0;
+            bk = -1;
+            for (unsigned mm = kmask; mm; mm &= mm - 1) {
+                const int kk = __ffs(mm);  // slice count kk = bit index + 1
+                const uint32_t bits = lexmin_bits(it, R, layers, stage, vm, kk);
+                if (bk < 0 || bits_less(bits, bb)) {
+                    bb = bits;
+                    bk = kk;
+                }
             }
+            __syncwarp();
         }
-        __syncwarp();
         if (lane == 0) {
             code.xe[c + 1] = (int16_t)x1;
             code.cut[c] = bb;
@@ -915,6 +934,48 @@ __global__ void __launch_bounds__(32) rebuild_kernel(LaunchArgs args, int total,
     if (lane == 0) {
         code.xe[0] = 0;
         code.c = c;
+    }
+}
+
+// The cut bits of the tile columns the rebuild left pending.  Block (frame
+// f, slot s) takes the windows of f that reached Q* (c > 0) whose rank among
+// them is s modulo kCutSlots; its warps take their tile columns j = warp,
+// warp + kCutWarps, ...: each redoes the column's row DP with every layer
+// kept and reads the smallest cut bits of its slice count (lexmin_bits).
+constexpr int kCutSlots = 8, kCutWarps = 4;
+__global__ void __launch_bounds__(kCutWarps * 32) cuts_kernel(LaunchArgs args, int layer_words, int stage_words) {
+    extern __shared__ uint64_t csm[];
+    __shared__ uint32_t cvm[kCutWarps][32];
+    const int f = blockIdx.x / kCutSlots, slot = blockIdx.x % kCutSlots;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const DevFrame &fr = frame_at(args, f);
+    const DevPlan &pl = *fr.plan;
+    const uint64_t qstar = fr.scal[1];
+    if (frame_status(fr) != TRS_OK || qstar == kInf) return;
+    const uint64_t thr = eq4_threshold(fr.scal[0], fr.lambda_q);
+    uint64_t *layers = csm + (size_t)wib * (layer_words + stage_words);
+    uint64_t *stage = layers + layer_words;
+    uint32_t *vm = cvm[wib];
+    const int R = fr.R, n = pl.n;
+    int rank = 0;
+    for (int w0 = 0; w0 < pl.nwin; w0 += 32) {
+        const int wl = w0 + lane;
+        const unsigned tied = __ballot_sync(kFull, wl < pl.nwin && fr.codes[wl].c > 0);
+        for (unsigned mm = tied; mm; mm &= mm - 1, ++rank) {
+            if (rank % kCutSlots != slot) continue;
+            WinCode &code = fr.codes[w0 + __ffs(mm) - 1];
+            const int c = code.c;
+            for (int j = wib; j < c; j += kCutWarps) {
+                const uint32_t word = code.cut[j];
+                if (!(word & kCutPending)) continue;
+                const int item = (int)((word & ~kCutPending) >> 6), k = (int)(word & 63u);
+                const PlanItem it = pl.items[item];
+                item_dp<2>(fr, it, thr, n, nullptr, layers, stage, vm);
+                const uint32_t bits = lexmin_bits(it, R, layers, stage, vm, k);
+                __syncwarp();
+                if (lane == 0) code.cut[j] = bits;
+            }
+        }
     }
 }
 
@@ -1069,6 +1130,7 @@ int prepare_search_kernels() {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(column_kernel<1>, A, col_smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(column_kernel<2>, A, col_smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(rebuild_kernel, A, rb_smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(cuts_kernel, A, kCutWarps * rb_smem);
     return (int)e;
 }
 
@@ -1124,8 +1186,10 @@ int launch_search(const LaunchArgs &a, int total_bands, int total_windows, int m
     mark(3);
     const int layer_words = (maxN + 1) * 32;
     const size_t rb_smem = (size_t)(layer_words + stage_words) * sizeof(uint64_t);
-    if (total_windows > 0) rebuild_kernel<<<total_windows, 32, rb_smem, s>>>(a, total_windows, layer_words,
-                                                                             stage_words);
+    if (total_windows > 0) {
+        rebuild_kernel<<<total_windows, 32, rb_smem, s>>>(a, total_windows, layer_words, stage_words);
+        cuts_kernel<<<a.nframes * kCutSlots, kCutWarps * 32, kCutWarps * rb_smem, s>>>(a, layer_words, stage_words);
+    }
     mark(4);
     finish_kernel<<<a.nframes, 32, 0, s>>>(a);
     mark(5);

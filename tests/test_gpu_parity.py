@@ -240,7 +240,7 @@ def test_bench_launch_matches_oracle_on_all_64_frames(dec, oracle):
     try:
         dec.batch_decide(ins)  # capture
         ps = dec.partitions(dec.batch_decide(ins), 64)  # replay
-        assert trs.trs_batch_kernels(dec.ctx) == 16
+        assert trs.trs_batch_kernels(dec.ctx) == 18  # 9 kernels per chunk
     finally:
         trs.trs_set_tune(dec.ctx, 4, 4, 8)
     for (plane, times), p in zip(frames, ps):
@@ -342,7 +342,7 @@ def test_batch_chunks_equal_alone(dec, nf):
             for _ in range(2):  # capture, then replay
                 ps = dec.partitions(dec.batch_decide(ins), nf)
                 assert trs.trs_batch_stage_frames(dec.ctx) == nf // P
-                assert trs.trs_batch_kernels(dec.ctx) == 8 * P
+                assert trs.trs_batch_kernels(dec.ctx) == 9 * P
                 assert [bytes(p) for p in ps] == alone, parts
     finally:
         trs.trs_set_batch_parts(dec.ctx, 2)
