@@ -160,6 +160,24 @@ def test_mt_full_frames_six_and_seven_slices(dec, oracle, spec_name, n):
         _assert_equal(dec.search_mt(tab, W, H, n, lam), ref, ref["count"])
 
 
+def test_mt_full_frame_eight_slices_golden(dec):
+    """The benchmarked 1920x1080 search with n = 8 (3,889,333 slice sets) on
+    the same seeded frame, against the oracle's records stored in
+    tests/golden/mt_1080p10_n8.json (its enumeration takes about a minute
+    per lambda, so the records are written once by make_mt_golden.py)."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "mt_1080p10_n8.json")) as f:
+        g = json.load(f)
+    spec = getattr(synth, g["spec"])
+    W, H = spec.width, spec.height
+    plane, times = synth.make_frame(spec, seed=g["seed"])
+    tab = _tables(dec, plane, times, spec.bit_depth)
+    for ref in g["records"]:
+        ref = dict(ref, regions=[tuple(r) for r in ref["regions"]])
+        _assert_equal(dec.search_mt(tab, W, H, g["n"], ref["lambda"]), ref, ref["count"])
+
+
 @pytest.mark.parametrize("W,H,n,tscale", [(640, 512, 8, 1.0), (896, 512, 8, 4000.0), (768, 640, 9, 1.0),
                                           (768, 512, 10, 4000.0), (640, 640, 12, 1.0)])
 def test_mt_eight_and_more_slices(dec, oracle, W, H, n, tscale):
