@@ -312,11 +312,13 @@ constexpr int kMtThreads = 256;
 constexpr int kMtStageBytes = 32 * 1024;  // one tile's slice indices (two tiles in flight per block)
 
 struct MtArgs {
-    const uint32_t *ent;  // slice i of set c at ent[i * pitch + c]: its rectangle-table entry index
+    const void *ent;      // slice i of set c at ent[i * pitch + c]: its rectangle-table entry index,
+                          // 16-bit when every entry index fits (e16), else 32-bit
     int64_t count;        // slice sets
-    int64_t pitch;        // count rounded up to a multiple of 4 (16-byte rows)
+    int64_t pitch;        // count rounded up to 16-byte rows (a multiple of 8 or 4 entries)
     int n, C, R, W, H, nblocks;
-    int tile;             // sets per tile: a multiple of kMtThreads with n * tile * 4 <= kMtStageBytes
+    int e16;              // 1: 16-bit entries
+    int tile;             // sets per tile: a multiple of kMtThreads with n * tile * entry bytes <= kMtStageBytes
     const MtCall *call;   // tables, output, lambda of this call
     uint64_t *tmin;       // T_min: +infinity before the first pass (set at creation, reset by each decode)
     uint64_t *part;       // [nblocks][2]: each block's smallest (Q, set) of the second pass
@@ -347,17 +349,20 @@ __device__ __forceinline__ void mt_cp16(void *smem, const void *gmem) {
 __device__ __forceinline__ void mt_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void mt_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-// Copies tile t's slice indices (n rows of up to `tile` words, 16 bytes
-// at a time) into stage buffer `buf` with asynchronous copies.
-__device__ __forceinline__ void mt_stage(const MtArgs &a, uint32_t *stage, int64_t t) {
+// Copies tile t's slice indices (n rows of up to `tile` entries of type E,
+// 16 bytes at a time) into a stage buffer with asynchronous copies.
+template <typename E>
+__device__ __forceinline__ void mt_stage(const MtArgs &a, E *stage, int64_t t) {
+    constexpr int per = 16 / (int)sizeof(E);  // entries per 16-byte copy
+    const E *ent = static_cast<const E *>(a.ent);
     const int64_t c0 = t * a.tile;
     const int64_t rest = a.pitch - c0;
-    const int len = rest < a.tile ? (int)rest : a.tile;  // a multiple of 4
-    const int q4 = len >> 2;
+    const int len = rest < a.tile ? (int)rest : a.tile;  // a multiple of per
+    const int q = len / per;
     for (int i = 0; i < a.n; ++i) {
-        const uint32_t *src = a.ent + (size_t)i * a.pitch + c0;
-        uint32_t *dst = stage + i * a.tile;
-        for (int o = threadIdx.x; o < q4; o += kMtThreads) mt_cp16(dst + 4 * o, src + 4 * o);
+        const E *src = ent + (size_t)i * a.pitch + c0;
+        E *dst = stage + (size_t)i * a.tile;
+        for (int o = threadIdx.x; o < q; o += kMtThreads) mt_cp16(dst + per * o, src + per * o);
     }
 }
 
@@ -376,8 +381,8 @@ __device__ __forceinline__ void mt_stage(const MtArgs &a, uint32_t *stage, int64
 // total time is below 2^31 (the tables' flag) reads only the low words of
 // its times.  The quality terms are gathered (second pass) only for a set
 // within Eq. 4's bound thr; *qsum is left 0 otherwise.
-template <int PASS, int N>
-__device__ __forceinline__ void set_eval(const uint32_t *col, int stride, const uint64_t *RT, const uint64_t *RQ,
+template <int PASS, int N, typename E>
+__device__ __forceinline__ void set_eval(const E *col, int stride, const uint64_t *RT, const uint64_t *RQ,
                                          bool t32, uint64_t thr, uint64_t *tmax, uint64_t *qsum) {
     uint32_t e[N];
 #pragma unroll
@@ -411,9 +416,11 @@ __device__ __forceinline__ void set_eval(const uint32_t *col, int stride, const 
     *qsum = q;
 }
 
-template <int PASS, int N>
+// E: the list's entry type (16-bit only with a compiled slice count).
+template <int PASS, int N, typename E>
 __global__ void __launch_bounds__(kMtThreads) mt_pass_kernel(MtArgs a) {
-    extern __shared__ __align__(16) uint32_t mts[];
+    extern __shared__ __align__(16) uint32_t mts_raw[];
+    E *mts = reinterpret_cast<E *>(mts_raw);
     __shared__ uint64_t wq[kMtThreads / 32], wc[kMtThreads / 32];
     const MtCall call = *a.call;
     const TablesOffsets off = tables_offsets(a.C, a.R);
@@ -435,14 +442,14 @@ __global__ void __launch_bounds__(kMtThreads) mt_pass_kernel(MtArgs a) {
             mt_commit();
             mt_wait_prev();  // this thread's copies of tile t have landed
             __syncthreads();  // and every other thread's
-            const uint32_t *st = mts + buf * words;
+            const E *st = mts + buf * words;
             const int64_t c0 = t * a.tile;
             for (int s = threadIdx.x; s < a.tile; s += kMtThreads) {
                 const int64_t c = c0 + s;
                 if (c >= a.count) break;
                 uint64_t tm = 0, q = 0;
                 if constexpr (N > 0)
-                    set_eval<PASS, N>(st + s, a.tile, RT, RQ, t32, thr, &tm, &q);
+                    set_eval<PASS, N, E>(st + s, a.tile, RT, RQ, t32, thr, &tm, &q);
                 else
                     for (int i0 = 0; i0 < a.n; i0 += 8) {
                         // eight slices' gathers in flight at a time
@@ -543,7 +550,8 @@ __global__ void __launch_bounds__(32) mt_finish_kernel(MtArgs a) {
     uint64_t t = 0, q = 0;
     double sse = 0.0;
     if (lane < a.n) {
-        const uint32_t e = a.ent[(size_t)lane * a.pitch + win];
+        const size_t at = (size_t)lane * a.pitch + win;
+        const uint32_t e = a.e16 ? static_cast<const uint16_t *>(a.ent)[at] : static_cast<const uint32_t *>(a.ent)[at];
         // e = (band * R + (y1 - y0 - 1)) * R + y0, band = band_index(C, x0, x1)
         const int R = a.R, C = a.C;
         const int y0 = (int)(e % (uint32_t)R);
@@ -610,32 +618,44 @@ static int mt_create(trs_ctx *ctx, int W, int H, int n, MtEntry **out) {
     int64_t count = 0;
     TRS_TRY(mt_enumerate(W, H, n, ctx->o.k_area, &keys, &count));
     const int C = (W + kCtu - 1) / kCtu, R = (H + kCtu - 1) / kCtu;
-    const int64_t pitch = (count + 3) & ~int64_t(3);  // 16-byte rows for the staged copies
-    std::vector<uint32_t> ent((size_t)pitch * n, 0u);
+    // 16-bit entries when every rectangle-table index fits them (1920x1080:
+    // 120 tile columns x 9 x 9 entries) and the slice count has a compiled
+    // kernel: half the bytes for the passes to stream
+    const bool e16 = n <= 8 && (size_t)num_bands(C) * R * R <= 65536;
+    const size_t esz = e16 ? 2 : 4;
+    const int64_t per16 = (int64_t)(16 / esz);
+    const int64_t pitch = (count + per16 - 1) / per16 * per16;  // 16-byte rows for the staged copies
+    std::vector<uint32_t> ent32(e16 ? 0 : (size_t)pitch * n, 0u);
+    std::vector<uint16_t> ent16(e16 ? (size_t)pitch * n : 0, 0u);
     for (int64_t c = 0; c < count; ++c)
         for (int i = 0; i < n; ++i) {
             const uint8_t *k = &keys[((size_t)c * n + i) * 4];  // y0, x0, y1, x1
-            ent[(size_t)i * pitch + c] =
-                (uint32_t)(((size_t)band_index(C, k[1], k[3]) * R + (k[2] - k[0] - 1)) * R + k[0]);
+            const size_t v = ((size_t)band_index(C, k[1], k[3]) * R + (k[2] - k[0] - 1)) * R + k[0];
+            if (e16)
+                ent16[(size_t)i * pitch + c] = (uint16_t)v;
+            else
+                ent32[(size_t)i * pitch + c] = (uint32_t)v;
         }
     std::vector<uint8_t>().swap(keys);
+    const size_t ent_bytes = (size_t)pitch * n * esz;
+    const void *ent_host = e16 ? (const void *)ent16.data() : (const void *)ent32.data();
     MtEntry *me = new (std::nothrow) MtEntry;
     if (!me) return TRS_ENOMEM;
     me->count = count;
     // tiles of up to 8 sets per thread whose n slice rows fit one stage
     // buffer, smaller when the list would not give every resident block a
     // tile; as many blocks as stay resident (two stage buffers each)
-    const int tile_max = kMtThreads * std::max(1, std::min(8, kMtStageBytes / (4 * kMtThreads * n)));
-    const int smem_max = 2 * n * tile_max * 4;
+    const int tile_max = kMtThreads * std::max(1, std::min(8, kMtStageBytes / ((int)esz * kMtThreads * n)));
+    const int smem_max = 2 * n * tile_max * (int)esz;
     int dev = 0, sms = 0, per_sm1 = 0, per_sm2 = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    void (*k1)(MtArgs) = mt_pass_kernel<1, 0>, (*k2)(MtArgs) = mt_pass_kernel<2, 0>;
+    void (*k1)(MtArgs) = mt_pass_kernel<1, 0, uint32_t>, (*k2)(MtArgs) = mt_pass_kernel<2, 0, uint32_t>;
     switch (n) {  // slice counts up to 8 run a kernel compiled for that count
-#define TRS_MT_N(K)                 \
-    case K:                         \
-        k1 = mt_pass_kernel<1, K>;  \
-        k2 = mt_pass_kernel<2, K>;  \
+#define TRS_MT_N(K)                                                        \
+    case K:                                                                \
+        k1 = e16 ? mt_pass_kernel<1, K, uint16_t> : mt_pass_kernel<1, K, uint32_t>; \
+        k2 = e16 ? mt_pass_kernel<2, K, uint16_t> : mt_pass_kernel<2, K, uint32_t>; \
         break;
         TRS_MT_N(1) TRS_MT_N(2) TRS_MT_N(3) TRS_MT_N(4) TRS_MT_N(5) TRS_MT_N(6) TRS_MT_N(7) TRS_MT_N(8)
 #undef TRS_MT_N
@@ -653,12 +673,12 @@ static int mt_create(trs_ctx *ctx, int W, int H, int n, MtEntry **out) {
     const int64_t per_block = (count + resident - 1) / resident;
     const int tile = (int)std::min<int64_t>(tile_max, std::max<int64_t>(
                                                           kMtThreads, (per_block + kMtThreads - 1) / kMtThreads * kMtThreads));
-    const int smem = 2 * n * tile * 4;
+    const int smem = 2 * n * tile * (int)esz;
     const int64_t ntiles = (count + tile - 1) / tile;
     const int nblocks = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, resident));
     // work: MtCall (4 words), T_min (4 words), per-block pairs
     const size_t work_bytes = 8 * sizeof(uint64_t) + (size_t)nblocks * 2 * sizeof(uint64_t);
-    int st = dev_alloc(me->cands, std::max<size_t>(ent.size() * 4, 16), &ctx->total);
+    int st = dev_alloc(me->cands, std::max<size_t>(ent_bytes, 16), &ctx->total);
     if (st == TRS_OK) st = dev_alloc(me->work, work_bytes, &ctx->total);
     auto fail = [&](int code) {
         ctx->total -= me->cands.n + me->work.n;
@@ -666,7 +686,7 @@ static int mt_create(trs_ctx *ctx, int W, int H, int n, MtEntry **out) {
         return code;
     };
     if (st != TRS_OK) return fail(st);
-    if (!ent.empty()) e = cudaMemcpy(me->cands.p, ent.data(), ent.size() * 4, cudaMemcpyHostToDevice);
+    if (ent_bytes) e = cudaMemcpy(me->cands.p, ent_host, ent_bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&me->call_host, kMtSlots * sizeof(MtCall));
     for (int k = 0; k < kMtSlots && e == cudaSuccess; ++k)
         e = cudaEventCreateWithFlags(&me->copied[k], cudaEventDisableTiming);
@@ -675,7 +695,8 @@ static int mt_create(trs_ctx *ctx, int W, int H, int n, MtEntry **out) {
     if (e == cudaSuccess) e = cudaMemset((uint8_t *)me->work.p + 4 * sizeof(uint64_t), 0xff, sizeof(uint64_t));
     if (e != cudaSuccess) return fail(cuda_fail(e, "multi-tile list upload"));
     MtArgs a;
-    a.ent = (const uint32_t *)me->cands.p;
+    a.ent = me->cands.p;
+    a.e16 = e16 ? 1 : 0;
     a.count = count;
     a.pitch = pitch;
     a.tile = tile;
