@@ -31,9 +31,14 @@
 //                       Step 1's window minima reduce into T_min (Eq. 3),
 //                       step 2's into Q*.
 //  rebuild_kernel       one warp per (frame, window): in a window that
-//                       reaches Q*, rebuilds the smallest canonical code
-//                       (smallest next edge first, then the smallest cut
-//                       bits, chosen with warp ballots).
+//                       reaches Q*, walks the smallest canonical code's
+//                       tile columns (smallest next edge first); a column
+//                       whose optimum one slice count completes is left
+//                       pending, otherwise its smallest cut bits are chosen
+//                       here with warp ballots.
+//  cuts_kernel          the pending columns of a frame's tied codes, one
+//                       warp each: the column's row DP with every layer
+//                       kept, then its smallest cut bits.
 //  finish_kernel        one warp per frame: the smallest code over windows,
 //                       decoded into trs_partition.
 #include <cuda_runtime.h>
