@@ -39,8 +39,13 @@ sys.path.insert(0, ROOT)
 METRIC = "TRS partition decisions/sec at 2160p (batched vs plain); p50/p99 latency; % HBM peak"
 UNIT = "decisions/s"
 NFRAMES = 64
-PARTS = 2  # chunks a captured batch is pipelined in (trs_set_batch_parts)
-IN_FLIGHT = 2  # batches in flight in the timed stream of steps
+# Batches in flight in the timed stream of steps, and the chunks each
+# captured batch is pipelined in (trs_set_batch_parts).  Measured at 2160p,
+# n = 16 (decisions/s): 2 in flight 125.6 k (1 chunk), 127.2 k (2), 109.4 k (3);
+# 3 in flight 132.1 k (1 chunk), 126.9 k (2), 123.1 k (3).
+PARTS = 1
+IN_FLIGHT = 3
+E2E_THREADS = 2  # host threads of the end-to-end form (at most IN_FLIGHT)
 N_REGIONS = 16
 LAMBDA = 0.1
 WORKLOAD = "3840x2160p10 moving-blob sequence, 64 frames, n=16, lambda=0.1, k=3"
@@ -589,7 +594,7 @@ def main():
                     help="only the multi-tile search at 1920x1080, n = 6, 7 and 8, 50 timed calls each")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default launch shapes (short profiling runs)")
-    ap.add_argument("--in-flight", type=int, default=IN_FLIGHT, choices=[1, 2, 3],
+    ap.add_argument("--in-flight", type=int, default=IN_FLIGHT, choices=[1, 2, 3, 4],
                     help="batches in flight (contexts on separate streams)")
     ap.add_argument("--parts", type=int, default=PARTS, choices=[1, 2, 3, 4],
                     help="chunks a captured batch is pipelined in")
@@ -793,23 +798,28 @@ def main():
     pinned_t = [torch.from_numpy(t).pin_memory() for _, t in frames]
     import threading
 
+    # host threads of the end-to-end form: the host link bounds it, and a
+    # third thread measured slower on two-byte planes (9.5 k against 12.1 k
+    # decisions/s; 18.2 k either way on packed planes)
+    e2e_threads = min(args.in_flight, E2E_THREADS)
+
     def e2e_run(descs, lumas, form):
-        # the same stream of steps as the timed region: IN_FLIGHT host threads,
+        # a stream of steps like the timed region's: e2e_threads host threads,
         # each calling the synchronous host-buffer entry point on its own
         # context and stream, so one batch's copies overlap another's kernels
-        for i in range(args.in_flight):
+        for i in range(e2e_threads):
             for _ in range(2):
                 trs.trs_batch_decide_host(decs[i].ctx, descs, streams[i])
         sync_all()
         e_steps = max(3, args.steps // 4)
-        e_steps += (-e_steps) % args.in_flight
-        results = [None] * args.in_flight
+        e_steps += (-e_steps) % e2e_threads
+        results = [None] * e2e_threads
 
         def host_worker(i: int):
-            for _ in range(e_steps // args.in_flight):
+            for _ in range(e_steps // e2e_threads):
                 results[i] = trs.trs_batch_decide_host(decs[i].ctx, descs, streams[i])
 
-        workers = [threading.Thread(target=host_worker, args=(i,)) for i in range(args.in_flight)]
+        workers = [threading.Thread(target=host_worker, args=(i,)) for i in range(e2e_threads)]
         t0 = time.perf_counter()
         for t in workers:
             t.start()
@@ -822,7 +832,7 @@ def main():
         return {"value": job_throughput(nfr * e_steps, world, dt), "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(p.numel() for p in lumas) + sum(t.numel() * 4 for t in pinned_t)),
                 "d2h_bytes_per_step": nfr * trs.PARTITION_BYTES,
-                "form": f"trs_batch_decide_host from pinned host buffers ({form}), {args.in_flight} host threads "
+                "form": f"trs_batch_decide_host from pinned host buffers ({form}), {e2e_threads} host threads "
                         "with a context and stream each"}
 
     pk_bytes = (10 * 3840 + 7) // 8

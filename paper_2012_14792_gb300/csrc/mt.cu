@@ -20,14 +20,16 @@
 //    (y0, x0, y1, x1) bytes per slice; the partitions under each choice of
 //    the first two slices are enumerated on a pool of host threads and the
 //    pieces joined in that order.  The device keeps, slice-major, each
-//    slice's 32-bit index into the region tables' rectangle entries (any
-//    rectangle of CTUs is a tile-column slice there).
+//    slice's index into the region tables' rectangle entries (any
+//    rectangle of CTUs is a tile-column slice there): 16-bit when every
+//    index fits, else 32-bit.
 //  * device, one captured graph per call: a pass streams the list through
 //    shared memory (asynchronous copies, the next tile in flight while the
 //    current one is evaluated) and takes T_min (Eq. 3); a second keeps, per
 //    block, the smallest (Q, list index) among the sets within Eq. 4's
 //    bound, so Q* (Eq. 2) and the first set reaching it come out together;
-//    one warp reduces the blocks' pairs and decodes the winner.
+//    the last block of that pass to finish reduces the blocks' pairs in one
+//    warp and decodes the winner.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -322,7 +324,10 @@ struct MtArgs {
     const MtCall *call;   // tables, output, lambda of this call
     uint64_t *tmin;       // T_min: +infinity before the first pass (set at creation, reset by each decode)
     uint64_t *part;       // [nblocks][2]: each block's smallest (Q, set) of the second pass
+    unsigned *done;       // blocks of the second pass that have stored their pair (0 between searches)
 };
+
+__device__ void mt_finish_warp(const MtArgs &a);
 
 __device__ __forceinline__ uint64_t warp_min64(uint64_t v) {
 #pragma unroll
@@ -375,7 +380,8 @@ __device__ __forceinline__ void mt_stage(const MtArgs &a, E *stage, int64_t t) {
 //  PASS 1: T_min (Eq. 3): per-thread minima, one atomic minimum per warp.
 //  PASS 2: among the sets within Eq. 4's bound, the smallest (Q, list
 //          index) -- Q* (Eq. 2) and the first set reaching it in one go;
-//          each block stores its own minimum, the decode kernel reduces.
+//          each block stores its own minimum; the last block to do so
+//          reduces them and decodes the winner.
 // Time and quality term of one set of N slices (N a compile-time count):
 // col[i * stride] holds slice i's rectangle-table index.  A frame whose
 // total time is below 2^31 (the tables' flag) reads only the low words of
@@ -493,18 +499,32 @@ __global__ void __launch_bounds__(kMtThreads) mt_pass_kernel(MtArgs a) {
             bc = lane < (int)(blockDim.x >> 5) ? wc[lane] : kInf;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) pair_min_xor(bq, bc, o);
+            // the last block to store its pair reduces and decodes (no
+            // separate launch): each block's pair is made visible before
+            // it is counted, and the block that takes the last ticket
+            // reads them after it
+            unsigned last = 0;
             if (lane == 0) {
                 a.part[2 * blockIdx.x] = bq;
                 a.part[2 * blockIdx.x + 1] = bc;
+                __threadfence();
+                last = atomicAdd(a.done, 1u) == gridDim.x - 1 ? 1u : 0u;
+            }
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {
+                __threadfence();
+                if (lane == 0) *a.done = 0u;  // for the next search of this shape
+                mt_finish_warp(a);
             }
         }
     }
 }
 
 // One warp: the smallest (Q, set) over the blocks of pass 2, then lane i
-// decodes slice i of the winner from its rectangle-table entry.
-__global__ void __launch_bounds__(32) mt_finish_kernel(MtArgs a) {
-    const int lane = threadIdx.x;
+// decodes slice i of the winner from its rectangle-table entry.  Run by the
+// last block of pass 2, or by mt_finish_kernel when the list is empty.
+__device__ void mt_finish_warp(const MtArgs &a) {
+    const int lane = threadIdx.x & 31;
     const MtCall call = *a.call;
     trs_mt_partition *out = call.out;
     uint64_t *words = reinterpret_cast<uint64_t *>(out);
@@ -516,8 +536,8 @@ __global__ void __launch_bounds__(32) mt_finish_kernel(MtArgs a) {
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int b = b0 + u * 32 + lane;
-            pq[u] = b < a.nblocks ? a.part[2 * b] : kInf;
-            pc[u] = b < a.nblocks ? a.part[2 * b + 1] : kInf;
+            pq[u] = b < a.nblocks ? __ldcg(a.part + 2 * b) : kInf;  // other blocks' stores: read from L2
+            pc[u] = b < a.nblocks ? __ldcg(a.part + 2 * b + 1) : kInf;
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u)
@@ -595,6 +615,9 @@ __global__ void __launch_bounds__(32) mt_finish_kernel(MtArgs a) {
         out->status = (q != qstar || t > out->thr_q) ? TRS_EINFEASIBLE : TRS_OK;
     }
 }
+
+// The decode alone, for a shape whose list is empty (no pass runs).
+__global__ void __launch_bounds__(32) mt_finish_kernel(MtArgs a) { mt_finish_warp(a); }
 
 }  // namespace
 
@@ -676,7 +699,7 @@ static int mt_create(trs_ctx *ctx, int W, int H, int n, MtEntry **out) {
     const int smem = 2 * n * tile * (int)esz;
     const int64_t ntiles = (count + tile - 1) / tile;
     const int nblocks = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, resident));
-    // work: MtCall (4 words), T_min (4 words), per-block pairs
+    // work: MtCall (4 words), T_min and the pass-2 block count (4 words), per-block pairs
     const size_t work_bytes = 8 * sizeof(uint64_t) + (size_t)nblocks * 2 * sizeof(uint64_t);
     int st = dev_alloc(me->cands, std::max<size_t>(ent_bytes, 16), &ctx->total);
     if (st == TRS_OK) st = dev_alloc(me->work, work_bytes, &ctx->total);
@@ -691,8 +714,9 @@ static int mt_create(trs_ctx *ctx, int W, int H, int n, MtEntry **out) {
     for (int k = 0; k < kMtSlots && e == cudaSuccess; ++k)
         e = cudaEventCreateWithFlags(&me->copied[k], cudaEventDisableTiming);
     if (e == cudaSuccess && !ctx->mt_cap) e = cudaStreamCreateWithFlags(&ctx->mt_cap, cudaStreamNonBlocking);
-    // T_min starts at +infinity; each search's decode kernel resets it for the next
+    // T_min starts at +infinity and the block count at 0; each search's decode resets both for the next
     if (e == cudaSuccess) e = cudaMemset((uint8_t *)me->work.p + 4 * sizeof(uint64_t), 0xff, sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMemset((uint8_t *)me->work.p + 5 * sizeof(uint64_t), 0, sizeof(uint64_t));
     if (e != cudaSuccess) return fail(cuda_fail(e, "multi-tile list upload"));
     MtArgs a;
     a.ent = me->cands.p;
@@ -709,6 +733,7 @@ static int mt_create(trs_ctx *ctx, int W, int H, int n, MtEntry **out) {
     uint64_t *wk = (uint64_t *)me->work.p;
     a.call = (const MtCall *)wk;
     a.tmin = wk + 4;
+    a.done = reinterpret_cast<unsigned *>(wk + 5);
     a.part = wk + 8;
     cudaStream_t cs = ctx->mt_cap;
     for (int k = 0; k < kMtSlots && e == cudaSuccess; ++k) {
@@ -718,10 +743,9 @@ static int mt_create(trs_ctx *ctx, int W, int H, int n, MtEntry **out) {
         if (e == cudaSuccess) e = record_event(me->copied[k], cs);
         if (e == cudaSuccess && count > 0) {
             k1<<<nblocks, kMtThreads, smem, cs>>>(a);
-            k2<<<nblocks, kMtThreads, smem, cs>>>(a);
+            k2<<<nblocks, kMtThreads, smem, cs>>>(a);  // its last block decodes
             e = cudaGetLastError();
-        }
-        if (e == cudaSuccess) {
+        } else if (e == cudaSuccess) {
             mt_finish_kernel<<<1, 32, 0, cs>>>(a);
             e = cudaGetLastError();
         }
