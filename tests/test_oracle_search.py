@@ -203,6 +203,27 @@ def test_o2_equals_o1_random_tiny(oracle, seed):
         assert a.x_edges == b.x_edges and a.band_cuts == b.band_cuts
 
 
+def test_o2_equals_o1_ten_thousand_tiny(oracle):
+    """O2 equals O1 on 10,000 more seeded tiny instances (grids up to 6 x 6
+    CTUs with clipped edges, n up to 8, the three value modes, four lambdas):
+    one loop, so a failure names its seed."""
+    for seed in range(10_000):
+        rng = np.random.default_rng(200_000 + seed)
+        C, R = int(rng.integers(1, 7)), int(rng.integers(1, 7))
+        W = (C - 1) * 128 + int(rng.integers(1, 129))
+        H = (R - 1) * 128 + int(rng.integers(1, 129))
+        n = int(rng.integers(1, 9))
+        S1, S2, N, Tq = random_instance(rng, W, H, ["random", "flat", "uniform"][seed % 3])
+        st = stats_from(oracle, W, H, S1, S2, N)
+        lam_q = int(rng.choice([0, 6554, 19661, 65536]))
+        a = oracle.search_enum(st, Tq, n, lam_q=lam_q)
+        b = oracle.search_dp(st, Tq, n, lam_q=lam_q)
+        assert a.status == b.status, seed
+        if a.status == oracle.OK:
+            assert (a.t_min, a.thr, a.t, a.q, a.x_edges, a.band_cuts) == \
+                (b.t_min, b.thr, b.t, b.q, b.x_edges, b.band_cuts), seed
+
+
 @pytest.mark.parametrize("spec_name,n", [("SPEC_480P8", 4), ("SPEC_480P8", 8), ("SPEC_480P8", 16),
                                          ("SPEC_1080P10", 4)])
 def test_o2_equals_o1_paper_sizes(oracle, spec_name, n):
