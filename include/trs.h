@@ -319,8 +319,8 @@ int trs_mt_list(int width, int height, int n_regions, int k_area, uint8_t *list,
  * tables_dev (trs_region_tables): T_min (Eq. 3), then the smallest Q (Eq. 2)
  * among slice sets within Eq. 4's bound.  Writes one trs_mt_partition to
  * out_dev (device memory).  The first call for a shape enumerates it on the
- * host, keeps the list on the device (one 32-bit rectangle-table index per
- * slice, slice-major) and captures the search as a CUDA graph; every call
+ * host, keeps the list on the device (one 16- or 32-bit rectangle-table index
+ * per slice, slice-major) and captures the search as a CUDA graph; every call
  * then copies its arguments into the graph's pinned block (after the
  * previous call's copy has run) and launches the graph on `stream`.  Calls
  * on one context must be ordered on the device.  Errors as trs_mt_count,
