@@ -381,6 +381,7 @@ def run_serving(trs, device: int, duration_s: float = 7.0, saturate_s: float = 1
     saturated rate (every stream keeps both slots busy) and the latency at
     offered loads of 10, 50 and 90 % of it (all stream rates scaled alike)."""
     import collections
+    import gc
 
     import synth
     import torch
@@ -444,7 +445,12 @@ def run_serving(trs, device: int, duration_s: float = 7.0, saturate_s: float = 1
                     lat.append(accepted.pop(d.ticket) * 1e3 + d.latency_us / 1e3)
             return np.array(lat), time.perf_counter() - t0
 
-        # Poisson arrivals at the workload's rates
+        # Poisson arrivals at the workload's rates.  The objects alive now
+        # (torch, numpy, the frames) are moved out of the cyclic collector's
+        # reach first, so that no full collection over them runs inside the
+        # submitting loop, where its time would be counted as latency
+        gc.collect()
+        gc.freeze()
         lat, elapsed = poisson_run(arrivals)
 
         # saturation: every stream keeps both request slots busy
@@ -486,6 +492,7 @@ def run_serving(trs, device: int, duration_s: float = 7.0, saturate_s: float = 1
                 "mean_batch": info.frames / max(1, info.batches), "device_bytes": int(info.mem_used_bytes),
                 "form": "continuous batching, 3 batches in flight on separate CUDA streams"}
     finally:
+        gc.unfreeze()
         trs.trs_server_destroy(srv)
 
 
