@@ -41,6 +41,15 @@ MUTANTS = [
      "if (h > it.hlo && h <= it.hhi) reach[y] |= (reach[yp] << 1) & full;"),
     ("count_min_area_double_counted", "plan.cu",
      "if (i + 1 < a.size() && a[i + 1] <= hi) total -=", "if (i + 1 < a.size() && a[i + 1] < hi) total -="),
+    ("plan_kset_largest_count_dropped", "plan.cu",
+     "kset[i] = reach[R] & ~1ull & ((2ull << kmax) - 1);", "kset[i] = reach[R] & ~1ull & ((1ull << kmax) - 1);"),
+    ("plan_window_single_count_dropped", "plan.cu",
+     "if (kmax_w < kmin_w) continue;", "if (kmax_w <= kmin_w) continue;"),
+    ("plan_lowest_height_excluded", "plan.cu",
+     "it.hlo = hs[ilo];", "it.hlo = hs[ilo] + 1;"),
+    ("plan_band_bounds_single_count_dropped", "plan.cu",
+     "if (std::max(kmin_w, kgeo_lo) > std::min(kmax_w, kgeo_hi))",
+     "if (std::max(kmin_w, kgeo_lo) >= std::min(kmax_w, kgeo_hi))"),
     ("mt_corner_bound_high", "mt.cu",
      "return (corners + 3) / 4;", "return (corners + 4) / 4;"),
     ("mt_area_rule_not_strict", "mt.cu",
