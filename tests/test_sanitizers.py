@@ -16,6 +16,7 @@ checked this way instead:
 Both build into temporary folders; the committed sources are read, never
 changed."""
 
+import concurrent.futures as cf
 import os
 import shutil
 import subprocess
@@ -124,16 +125,17 @@ def test_library_host_logic_passes_under_asan_and_ubsan(tmp_path):
         pytest.skip("no nvcc")
     B.build()
     host = [a for f in SAN_FLAGS for a in ("-Xcompiler", f)]
-    objs = []
-    for s in B.SOURCES:
-        if s not in HOST_UNITS:
-            objs.append(os.path.join(B.BUILD, s[:-3] + ".o"))
-            continue
+
+    def compile_unit(s):
         obj = str(tmp_path / (s[:-3] + ".o"))
         r = subprocess.run([B._nvcc(), *B.ARCH, *B.NVCC_FLAGS, *host, "-I", B.CSRC, "-c",
                             os.path.join(B.CSRC, s), "-o", obj], capture_output=True, text=True)
         assert r.returncode == 0, r.stderr[-2000:]
-        objs.append(obj)
+        return obj
+
+    with cf.ThreadPoolExecutor(max_workers=len(HOST_UNITS)) as ex:
+        built = dict(zip(HOST_UNITS, ex.map(compile_unit, HOST_UNITS)))
+    objs = [built.get(s, os.path.join(B.BUILD, s[:-3] + ".o")) for s in B.SOURCES]
     lib = str(tmp_path / "libtrs.so")
     r = subprocess.run([B._nvcc(), *B.ARCH, "-shared", "-o", lib, *objs], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-2000:]
