@@ -1,4 +1,5 @@
-"""Host code under AddressSanitizer and UndefinedBehaviorSanitizer.
+"""Host code under AddressSanitizer, UndefinedBehaviorSanitizer and
+ThreadSanitizer.
 
 compute-sanitizer is not available for the device side, so the host side is
 checked this way instead:
@@ -11,7 +12,11 @@ checked this way instead:
   * the library's host logic: plan.cu, mt.cu and api.cu rebuilt with the
     same flags (host code only; the device code is unchanged) and linked
     with the other objects of the normal build; the host-logic ABI tests
-    run against that library (no GPU is touched).
+    run against that library (no GPU is touched);
+  * the multi-tile list's enumeration on a pool of host threads: mt.cu
+    rebuilt with ThreadSanitizer runs the full-frame enumeration tests
+    without a race report, and a copy with one planted race must be
+    reported.
 
 Both build into temporary folders; the committed sources are read, never
 changed."""
@@ -139,10 +144,79 @@ def test_library_host_logic_passes_under_asan_and_ubsan(tmp_path):
     lib = str(tmp_path / "libtrs.so")
     r = subprocess.run([B._nvcc(), *B.ARCH, "-shared", "-o", lib, *objs], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-2000:]
-    # left out: linking a plain C program against this library (it would need
-    # the sanitizer runtimes at link time) and the 60-shape coverage sweep,
-    # which runs the same code as the fixed shapes, only longer
-    skip = "not test_header_is_plain_c_and_links and not test_plan_loses_no_partition_random_shapes"
+    # the host-logic tests (plan windows and pruning, partition counts, plan
+    # coverage, the multi-tile list); left out: linking a plain C program
+    # against this library (it would need the sanitizer runtimes at link
+    # time) and the 60-shape coverage sweep, which runs the same code as the
+    # fixed shapes, only longer
+    skip = ("(area_rule or count_partitions or plan_ or mt_) and not test_header_is_plain_c_and_links "
+            "and not test_plan_loses_no_partition_random_shapes")
     code = _ABI_DRIVER.format(root=ROOT, tests=TESTS, lib=lib, skip=skip, abi=os.path.join(TESTS, "test_abi.py"))
     r = _child(code, str(tmp_path), preload)
+    assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-3000:]
+
+
+def _sanitized_library(B, tmp_path, units, flags):
+    """libtrs.so with `units` (name -> source text) compiled with the host
+    flags `flags`, linked with the other objects of the normal build."""
+    host = [a for f in flags for a in ("-Xcompiler", f)]
+
+    def compile_unit(item):
+        name, text = item
+        src = tmp_path / name
+        src.write_text(text)
+        obj = str(tmp_path / (name[:-3] + ".o"))
+        r = subprocess.run([B._nvcc(), *B.ARCH, *B.NVCC_FLAGS, *host, "-I", B.CSRC, "-c", str(src), "-o", obj],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr[-2000:]
+        return name, obj
+
+    with cf.ThreadPoolExecutor(max_workers=len(units)) as ex:
+        built = dict(ex.map(compile_unit, units.items()))
+    objs = [built.get(s, os.path.join(B.BUILD, s[:-3] + ".o")) for s in B.SOURCES]
+    lib = str(tmp_path / "libtrs.so")
+    r = subprocess.run([B._nvcc(), *B.ARCH, "-shared", "-o", lib, *objs], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return lib
+
+
+def test_multitile_enumeration_threads_under_tsan(tmp_path):
+    """The multi-tile list is enumerated on a pool of host threads (mt.cu).
+    Rebuilt with ThreadSanitizer, the host-logic tests that enumerate full
+    frames run without a race report; a copy with one planted race (every
+    thread adding its count into one shared word) must be reported."""
+    tsan = subprocess.run(["gcc", "-print-file-name=libtsan.so"], capture_output=True,
+                          text=True).stdout.strip() if shutil.which("gcc") else ""
+    if not os.path.isabs(tsan) or not os.path.exists(tsan):
+        pytest.skip("no gcc ThreadSanitizer runtime")
+    sys.path.insert(0, ROOT)
+    from paper_2012_14792_gb300 import build as B
+    if shutil.which(B._nvcc()) is None and not os.path.exists(B._nvcc()):
+        pytest.skip("no nvcc")
+    B.build()
+    with open(os.path.join(B.CSRC, "mt.cu")) as f:
+        mt = f.read()
+    flags = ["-fsanitize=thread", "-fno-omit-frame-pointer", "-g"]
+    env = dict(os.environ, LD_PRELOAD=tsan, TSAN_OPTIONS="halt_on_error=1 report_signal_unsafe=0")
+
+    def run(lib, select, d):
+        # -s: a report is written while a test runs, and the process stops
+        # there, so pytest must not be holding the output
+        code = _ABI_DRIVER.format(root=ROOT, tests=TESTS, lib=lib, skip=select,
+                                  abi=os.path.join(TESTS, "test_abi.py")).replace('"-x", "-q"', '"-x", "-q", "-s"')
+        return subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=1200, cwd=d,
+                              env=env)
+
+    old = "wv[t] = e.visits;"
+    assert mt.count(old) == 1
+    d = tmp_path / "planted"
+    d.mkdir()
+    lib = _sanitized_library(B, d, {"mt.cu": mt.replace(old, "wv[0] += e.visits;")}, flags)
+    r = run(lib, "mt_count_full_frames_matches_cut_partitions and 1920-1080-5", str(d))
+    assert r.returncode != 0 and "ThreadSanitizer" in r.stdout + r.stderr, r.stdout[-1000:] + r.stderr[-2000:]
+
+    d = tmp_path / "mt"
+    d.mkdir()
+    lib = _sanitized_library(B, d, {"mt.cu": mt}, flags)
+    r = run(lib, "(mt_count_full_frames or mt_list_full_frames) and 1920", str(d))
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-3000:]
