@@ -18,7 +18,7 @@ checked this way instead:
     without a race report, and a copy with one planted race must be
     reported.
 
-Both build into temporary folders; the committed sources are read, never
+Each builds into a temporary folder; the committed sources are read, never
 changed."""
 
 import concurrent.futures as cf
