@@ -37,17 +37,31 @@ ORACLE_PINS = ("test_oracle_texture.py", "test_oracle_tables.py", "test_oracle_s
                "test_golden_mt.py")
 
 
-def _runtimes():
-    """The gcc sanitizer runtimes to preload, or None."""
+def _starts(preload: str) -> bool:
+    """Whether Python starts with these runtimes preloaded (a sanitizer
+    runtime can refuse the process's memory layout on some kernels)."""
+    r = subprocess.run([sys.executable, "-c", "pass"], capture_output=True, text=True, timeout=120,
+                       env=dict(os.environ, LD_PRELOAD=preload, ASAN_OPTIONS="detect_leaks=0"))
+    return r.returncode == 0
+
+
+def _runtime(*names):
+    """The gcc sanitizer runtimes `names` to preload (':'-joined), or None
+    when gcc lacks them or they cannot start here."""
     if shutil.which("gcc") is None:
         return None
     libs = []
-    for name in ("libasan.so", "libubsan.so"):
+    for name in names:
         p = subprocess.run(["gcc", "-print-file-name=" + name], capture_output=True, text=True).stdout.strip()
         if not os.path.isabs(p) or not os.path.exists(p):
             return None
         libs.append(p)
-    return ":".join(libs)
+    preload = ":".join(libs)
+    return preload if _starts(preload) else None
+
+
+def _runtimes():
+    return _runtime("libasan.so", "libubsan.so")
 
 
 def _child(code: str, cwd: str, preload: str):
@@ -79,7 +93,7 @@ def _sanitized_oracle(d, text):
 def test_oracle_pins_pass_under_asan_and_ubsan(tmp_path):
     preload = _runtimes()
     if preload is None:
-        pytest.skip("no gcc sanitizer runtimes")
+        pytest.skip("no usable gcc sanitizer runtimes")
     with open(os.path.join(ROOT, "oracle", "trs_oracle.c")) as f:
         original = f.read()
 
@@ -123,7 +137,7 @@ HOST_UNITS = ("plan.cu", "mt.cu", "api.cu")
 def test_library_host_logic_passes_under_asan_and_ubsan(tmp_path):
     preload = _runtimes()
     if preload is None:
-        pytest.skip("no gcc sanitizer runtimes")
+        pytest.skip("no usable gcc sanitizer runtimes")
     sys.path.insert(0, ROOT)
     from paper_2012_14792_gb300 import build as B
     if shutil.which(B._nvcc()) is None and not os.path.exists(B._nvcc()):
@@ -185,10 +199,9 @@ def test_multitile_enumeration_threads_under_tsan(tmp_path):
     Rebuilt with ThreadSanitizer, the host-logic tests that enumerate full
     frames run without a race report; a copy with one planted race (every
     thread adding its count into one shared word) must be reported."""
-    tsan = subprocess.run(["gcc", "-print-file-name=libtsan.so"], capture_output=True,
-                          text=True).stdout.strip() if shutil.which("gcc") else ""
-    if not os.path.isabs(tsan) or not os.path.exists(tsan):
-        pytest.skip("no gcc ThreadSanitizer runtime")
+    tsan = _runtime("libtsan.so")
+    if tsan is None:
+        pytest.skip("no usable gcc ThreadSanitizer runtime")
     sys.path.insert(0, ROOT)
     from paper_2012_14792_gb300 import build as B
     if shutil.which(B._nvcc()) is None and not os.path.exists(B._nvcc()):
